@@ -1,0 +1,181 @@
+/*
+ * nqs.h -- C ABI of the B300 (sm_103a) hot path of neural-quantum-state
+ * variational Monte Carlo, after "Neural Quantum States in Mixed Precision"
+ * (arXiv 2601.20782).
+ *
+ * One VMC step (Sec. 2: sample, then gradients; Sec. 4.2: two model copies)
+ * maps onto these calls:
+ *   nqs_set_params    FP64 master parameters -> sampling copy (Sec. 4.2, Table tab:precision)
+ *   nqs_init_chains   random initial spin configurations
+ *   nqs_sweep         Metropolis-Hastings sweeps over pi ~ |psi|^2 (Sec. 3.1)
+ *   nqs_local_energy  eps(x) = sum_{x'} H(x,x') psi(x')/psi(x)       (App. I, Eq. local_energies)
+ *   nqs_logpsi_grad   O_k(x) = d log psi / d theta_k and the force F  (App. I, Eq. forces)
+ *   nqs_stats         FP64 energy mean / variance / error, acceptance (Sec. 2, Eq. loss)
+ *
+ * Conventions shared by every call
+ *  - Spins are s_i in {-1,+1}.  A configuration is stored bit-packed in
+ *    W = ceil(N/32) uint32 words: bit (i mod 32) of word i/32 is 1 iff s_i = +1.
+ *  - Every array argument is a DEVICE pointer owned by the caller unless the
+ *    comment says "host".  The library keeps no reference after the call returns.
+ *  - Every call is asynchronous on the given stream (NULL = legacy default
+ *    stream) unless it says it synchronises.  Calls on one context must not
+ *    run concurrently on different streams.
+ *  - Return value: NQS_OK, or an error code; nqs_last_error() gives the text.
+ *    Arguments are validated on the host before anything is launched; a call
+ *    that returns an error has launched nothing.  CUDA launch failures return
+ *    NQS_ECUDA.  Device-side range violations (see nqs_set_params) and
+ *    exhausted bounded waits set a sticky device status word read by
+ *    nqs_check_status().
+ *  - Parameter vectors are FP64 and flat:
+ *      RBM   : [a (N) | b (M) | W (M x N, row-major, W[j*N + i])]           (App. G)
+ *      dense : [W1 (H1 x N) | b1 | W2 (H2 x H1) | b2 | ... | w_out (H_L) | b_out]
+ *    and rows of O use the same order.
+ */
+#ifndef NQS_H
+#define NQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *nqs_stream; /* identical to cudaStream_t */
+
+typedef enum {
+  NQS_OK = 0,
+  NQS_EINVAL = 1,       /* bad argument (shape, pointer, range) */
+  NQS_ECUDA = 2,        /* a CUDA runtime call failed */
+  NQS_ENOMEM = 3,       /* device allocation at create time failed */
+  NQS_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
+  NQS_EUNSUPPORTED = 5  /* combination not implemented */
+} nqs_status;
+
+/* Arithmetic type of the sampling copy (Table tab:precision; FP8 is an extension). */
+typedef enum { NQS_F32 = 0, NQS_BF16 = 1, NQS_F16 = 2, NQS_FP8E4M3 = 3 } nqs_dtype;
+
+enum { NQS_RBM = 0, NQS_DENSE = 1 };
+enum { NQS_TFIM = 0, NQS_HEISENBERG = 1 };
+
+/* Hamiltonian on a periodic Lx x Ly lattice (Ly == 1: chain of Lx sites; Lx >= 3,
+ * Ly == 1 or Ly >= 3).  Site index i = x + Lx*y.
+ *  TFIM       (Sec. 4.1, Eq. TFIM): J1 sum_<ij> sz sz + h sum_i sx.  Single-flip moves.
+ *  HEISENBERG (App. E): J1 sum_<ij> s.s + J2 sum_<<ij>> s.s (Pauli matrices; J2 on the
+ *             diagonal next-nearest bonds).  Exchange moves over a uniform bond;
+ *             marshall != 0 multiplies psi by (-1)^(#up spins with x+y even). */
+typedef struct {
+  int32_t kind;
+  int32_t Lx, Ly;
+  double J1, J2, h;
+  int32_t marshall;
+} nqs_ham_desc;
+
+/* Ansatz.  RBM (App. G): n_hidden = M.  DENSE: n_layers hidden widths in widths[]
+ * (host array, copied), a_1 = log cosh(W1 s + b1), a_l = tanh(W_l a_{l-1} + b_l),
+ * log psi = w_out . a_L + b_out. */
+typedef struct {
+  int32_t kind;
+  int32_t n_hidden;
+  int32_t n_layers;
+  const int32_t *widths;
+} nqs_model_desc;
+
+typedef struct nqs_ctx nqs_ctx;
+
+/* Creates a context on the current CUDA device and allocates its parameter
+ * copies and tables (the only allocations the library makes).  Synchronous.
+ * NQS_EUNSUPPORTED for model/Hamiltonian/dtype combinations not built. */
+nqs_status nqs_create(nqs_ctx **out, const nqs_model_desc *model, const nqs_ham_desc *ham,
+                      nqs_dtype sample_dtype);
+void nqs_destroy(nqs_ctx *ctx);
+/* Text of the last error on ctx (ctx may be NULL: last error of nqs_create). */
+const char *nqs_last_error(const nqs_ctx *ctx);
+
+int32_t nqs_n_sites(const nqs_ctx *ctx);           /* N */
+int32_t nqs_words_per_config(const nqs_ctx *ctx);  /* W = ceil(N/32) */
+int64_t nqs_n_params(const nqs_ctx *ctx);          /* P */
+int32_t nqs_n_bonds(const nqs_ctx *ctx);           /* bonds of the Hamiltonian */
+
+/* Tuning knobs.  NQS_OPT_REFRESH: the RBM sweep recomputes its per-chain cache
+ * from scratch every this many sweeps (default 20, >= 1).
+ * NQS_OPT_CHAINS_PER_WARP: RBM sweep lanes per chain = 32 / value (1, 2 or 4;
+ * 0 = chosen by the built-in tuner). */
+enum { NQS_OPT_REFRESH = 0, NQS_OPT_CHAINS_PER_WARP = 1 };
+nqs_status nqs_set_option(nqs_ctx *ctx, int32_t option, int64_t value);
+
+/* Sec. 4.2 (two-copy scheme): the FP64 master parameters (device, P doubles) are
+ * rounded to the sampling dtype and the sampler's tables are rebuilt from the
+ * rounded copy.  Range limits of the RBM sampler: |W| <= 20 (F16 tables:
+ * |W| <= 2.5); a violation is reported.  Synchronises with the stream. */
+nqs_status nqs_set_params(nqs_ctx *ctx, const double *params, nqs_stream stream);
+
+/* Writes n_chains random configurations to state [n_chains x W]: i.i.d. uniform
+ * spins for TFIM, a uniformly random zero-magnetisation configuration for
+ * HEISENBERG (N even).  Drawn from Philox4x32-10 keyed by seed. */
+nqs_status nqs_init_chains(nqs_ctx *ctx, uint32_t *state, int64_t n_chains, uint64_t seed,
+                           nqs_stream stream);
+
+/* Optional per-proposal record, for tests and bias studies (any member may be NULL).
+ *  accept_bits [n_chains x n_sweeps x W]: bit p of the sweep's word block = proposal p accepted.
+ *  delta       [n_chains x n_sweeps x N]: the log psi(y) - log psi(x) the sampler used. */
+typedef struct {
+  uint32_t *accept_bits;
+  float *delta;
+} nqs_sweep_trace;
+
+/* Sec. 3.1: n_sweeps sweeps of N Metropolis-Hastings proposals on each chain,
+ * accepting y with probability min{1, |psi(y)/psi(x)|^2}, decided as
+ * u < exp(2 (log psi(y) - log psi(x))) with u uniform in [0,1) (u = 0 always accepts).
+ * Proposal p of sweep t of chain c uses Philox4x32-10 counter
+ * (p/2, sweep_offset + t, c, 0x53574550) under key (seed lo, seed hi): words
+ * (0,1) for even p, (2,3) for odd p; site = (w * N) >> 32 (TFIM) or
+ * bond = (w * n_bonds) >> 32 (HEISENBERG), u = (w' >> 8) * 2^-24.
+ *  state     [n_chains x W]      in/out chain configurations.
+ *  samples   [(n_sweeps-burn_in) x n_chains x W] or NULL: configuration after each
+ *            sweep t >= burn_in, row (t - burn_in) * n_chains + c.
+ *  logpsi    [(n_sweeps-burn_in) x n_chains] or NULL: FP32 log psi of those rows.
+ *  n_accepted [n_chains] or NULL: accepted proposals of this call, per chain.
+ *  trace     host struct or NULL. */
+nqs_status nqs_sweep(nqs_ctx *ctx, uint32_t *state, int64_t n_chains, int32_t n_sweeps,
+                     int32_t burn_in, uint64_t seed, uint32_t sweep_offset, uint32_t *samples,
+                     float *logpsi, int64_t *n_accepted, const nqs_sweep_trace *trace,
+                     nqs_stream stream);
+
+/* log psi of n configurations (FP32 output; the sampling copy's parameters).
+ * With marshall the value is log|psi|. */
+nqs_status nqs_logpsi(nqs_ctx *ctx, const uint32_t *configs, int64_t n, float *out,
+                      nqs_stream stream);
+
+/* App. I, Eq. local_energies: eloc[x] = sum_{x' in C(x)} H(x,x') psi(x')/psi(x), FP32. */
+nqs_status nqs_local_energy(nqs_ctx *ctx, const uint32_t *configs, int64_t n, float *eloc,
+                            nqs_stream stream);
+
+/* App. I, Eq. forces.  O [n x P] (FP32, or NULL) receives O_k(x) = d log psi(x)/d theta_k.
+ * If force != NULL (FP64 [P]) it receives F_k = (1/n) sum_x O_k(x) (eloc[x] - E)
+ * with E = stats[0] (device, as written by nqs_stats); eloc and stats are then
+ * required.  workspace: device scratch of nqs_logpsi_grad_workspace(ctx, n) bytes
+ * (may be NULL when force == NULL).  Gradients use the FP32 rounding of the
+ * master parameters, not the sampling copy. */
+size_t nqs_logpsi_grad_workspace(const nqs_ctx *ctx, int64_t n);
+nqs_status nqs_logpsi_grad(nqs_ctx *ctx, const uint32_t *configs, int64_t n, float *O,
+                           const float *eloc, const double *stats, double *force,
+                           void *workspace, size_t workspace_bytes, nqs_stream stream);
+
+/* Sec. 2 (Eq. loss) statistics in FP64 over n = K * n_chains sweep-major samples:
+ * out[0] = mean of eloc, out[1] = variance (1/n), out[2] = error of the mean from
+ * the per-chain means (std with ddof 1 over sqrt(n_chains)), out[3] = acceptance
+ * rate sum(n_accepted) / (n_chains * proposals_per_chain) (0 if n_accepted is NULL),
+ * out[4] = n.  out: device, 5 doubles. */
+nqs_status nqs_stats(nqs_ctx *ctx, const float *eloc, int64_t n, int64_t n_chains,
+                     const int64_t *n_accepted, int64_t proposals_per_chain, double *out,
+                     nqs_stream stream);
+
+/* Reads and clears the sticky device status word (synchronises the stream).
+ * NQS_OK, NQS_EINVAL (a value left the documented range) or NQS_ETIMEOUT. */
+nqs_status nqs_check_status(nqs_ctx *ctx, nqs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NQS_H */

@@ -63,7 +63,7 @@ def mh_sweeps(logpsi_fn, spins0, chain_ids, seed, n_sweeps, burn_in, proposal="f
             lp_y = logpsi_fn(y)
             delta = lp_y - lp
             with np.errstate(over="ignore"):
-                acc = u[:, p] < np.exp(2.0 * delta)
+                acc = (u[:, p] == 0.0) | (u[:, p] < np.exp(2.0 * delta))
             if record_deltas:
                 deltas[:, t, p] = delta
             if replay_accepts is not None:

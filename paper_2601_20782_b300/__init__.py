@@ -1,0 +1,208 @@
+"""B300 (sm_103a) hot path of neural-quantum-state VMC: thin Python binding of libnqs.so.
+
+Every call marshals torch CUDA tensors (device pointers) and the current CUDA
+stream into the C ABI of include/nqs.h; all arithmetic runs in the library's
+kernels.  There is no CPU fallback: importing this package raises if the
+library has not been built, and every call raises ``NQSError`` on failure.
+
+Packed configurations are int32 (or uint32) tensors of shape [n, W], W = ceil(N/32),
+bit (i mod 32) of word i // 32 set iff s_i = +1.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnqs.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2601_20782_b300.build` "
+                      "(or __graft_entry__.build())")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+NQS_OK, NQS_EINVAL, NQS_ECUDA, NQS_ENOMEM, NQS_ETIMEOUT, NQS_EUNSUPPORTED = range(6)
+DTYPES = {"f32": 0, "bf16": 1, "f16": 2, "fp8": 3}
+MODELS = {"rbm": 0, "dense": 1}
+HAMS = {"tfim": 0, "heisenberg": 1}
+OPT_REFRESH, OPT_CHAINS_PER_WARP = 0, 1
+
+
+class NQSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nqs error {code}: {msg}")
+        self.code = code
+
+
+class HamDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
+                ("J1", ctypes.c_double), ("J2", ctypes.c_double), ("h", ctypes.c_double),
+                ("marshall", ctypes.c_int32)]
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_hidden", ctypes.c_int32), ("n_layers", ctypes.c_int32),
+                ("widths", ctypes.POINTER(ctypes.c_int32))]
+
+
+class SweepTrace(ctypes.Structure):
+    _fields_ = [("accept_bits", ctypes.c_void_p), ("delta", ctypes.c_void_p)]
+
+
+_vp, _i32, _i64, _u32, _u64, _sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                    ctypes.c_uint64, ctypes.c_size_t)
+_SIGS = {
+    "nqs_create": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(ModelDesc), ctypes.POINTER(HamDesc), _i32]),
+    "nqs_destroy": (None, [_vp]),
+    "nqs_last_error": (ctypes.c_char_p, [_vp]),
+    "nqs_n_sites": (_i32, [_vp]),
+    "nqs_words_per_config": (_i32, [_vp]),
+    "nqs_n_params": (_i64, [_vp]),
+    "nqs_n_bonds": (_i32, [_vp]),
+    "nqs_set_option": (_i32, [_vp, _i32, _i64]),
+    "nqs_set_params": (_i32, [_vp, _vp, _vp]),
+    "nqs_init_chains": (_i32, [_vp, _vp, _i64, _u64, _vp]),
+    "nqs_sweep": (_i32, [_vp, _vp, _i64, _i32, _i32, _u64, _u32, _vp, _vp, _vp, ctypes.POINTER(SweepTrace), _vp]),
+    "nqs_logpsi": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "nqs_local_energy": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "nqs_logpsi_grad_workspace": (_sz, [_vp, _i64]),
+    "nqs_logpsi_grad": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "nqs_stats": (_i32, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp]),
+    "nqs_check_status": (_i32, [_vp, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def _ptr(t, dtypes, name, shape=None, allow_none=True):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name} must have dtype in {dtypes}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+_WORD = (torch.int32, torch.uint32)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """One nqs_ctx: a Hamiltonian, an ansatz and the dtype of its sampling copy."""
+
+    def __init__(self, ham="tfim", Lx=4, Ly=1, J1=1.0, J2=0.0, h=0.0, marshall=False,
+                 model="rbm", n_hidden=0, widths=(), dtype="f32"):
+        self._h = None
+        hd = HamDesc(HAMS[ham], Lx, Ly, J1, J2, h, int(bool(marshall)))
+        self._widths = (ctypes.c_int32 * max(len(widths), 1))(*widths)
+        md = ModelDesc(MODELS[model], n_hidden, len(widths), self._widths)
+        out = ctypes.c_void_p()
+        st = _lib.nqs_create(ctypes.byref(out), ctypes.byref(md), ctypes.byref(hd), DTYPES[dtype])
+        if st != NQS_OK:
+            raise NQSError(st, _lib.nqs_last_error(None).decode())
+        self._h = out
+        self.N = _lib.nqs_n_sites(out)
+        self.W = _lib.nqs_words_per_config(out)
+        self.P = _lib.nqs_n_params(out)
+        self.n_bonds = _lib.nqs_n_bonds(out)
+        self.dtype = dtype
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.nqs_destroy(self._h)
+            self._h = None
+
+    def _check(self, st):
+        if st != NQS_OK:
+            raise NQSError(st, _lib.nqs_last_error(self._h).decode())
+
+    def set_option(self, option, value):
+        self._check(_lib.nqs_set_option(self._h, option, int(value)))
+
+    def set_params(self, params):
+        self._check(_lib.nqs_set_params(self._h, _ptr(params, (torch.float64,), "params", (self.P,), False), _stream()))
+
+    def init_chains(self, state, seed):
+        n = state.shape[0]
+        self._check(_lib.nqs_init_chains(self._h, _ptr(state, _WORD, "state", (n, self.W), False), n,
+                                         int(seed) & (2 ** 64 - 1), _stream()))
+
+    def sweep(self, state, n_sweeps, burn_in, seed, sweep_offset=0, samples=None, logpsi=None,
+              n_accepted=None, accept_bits=None, delta=None):
+        C = state.shape[0]
+        K = max(n_sweeps - burn_in, 0)
+        tr = None
+        if accept_bits is not None or delta is not None:
+            tr = SweepTrace(_ptr(accept_bits, _WORD, "accept_bits", (C, n_sweeps, self.W)),
+                            _ptr(delta, (torch.float32,), "delta", (C, n_sweeps, self.N)))
+        self._check(_lib.nqs_sweep(
+            self._h, _ptr(state, _WORD, "state", (C, self.W), False), C, n_sweeps, burn_in,
+            int(seed) & (2 ** 64 - 1), int(sweep_offset),
+            _ptr(samples, _WORD, "samples", (K * C, self.W)),
+            _ptr(logpsi, (torch.float32,), "logpsi", (K * C,)),
+            _ptr(n_accepted, (torch.int64,), "n_accepted", (C,)),
+            ctypes.byref(tr) if tr is not None else None, _stream()))
+
+    def logpsi(self, configs, out):
+        n = configs.shape[0]
+        self._check(_lib.nqs_logpsi(self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
+                                    _ptr(out, (torch.float32,), "out", (n,), False), _stream()))
+
+    def local_energy(self, configs, eloc):
+        n = configs.shape[0]
+        self._check(_lib.nqs_local_energy(self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
+                                          _ptr(eloc, (torch.float32,), "eloc", (n,), False), _stream()))
+
+    def logpsi_grad_workspace(self, n):
+        return int(_lib.nqs_logpsi_grad_workspace(self._h, n))
+
+    def logpsi_grad(self, configs, O=None, eloc=None, stats=None, force=None, workspace=None):
+        n = configs.shape[0]
+        ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+        self._check(_lib.nqs_logpsi_grad(
+            self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
+            _ptr(O, (torch.float32,), "O", (n, self.P)), _ptr(eloc, (torch.float32,), "eloc", (n,)),
+            _ptr(stats, (torch.float64,), "stats"), _ptr(force, (torch.float64,), "force", (self.P,)),
+            _ptr(workspace, (torch.uint8, torch.float64, torch.float32, torch.int32), "workspace"), ws_bytes,
+            _stream()))
+
+    def stats(self, eloc, n_chains, out, n_accepted=None, proposals_per_chain=0):
+        n = eloc.shape[0]
+        self._check(_lib.nqs_stats(self._h, _ptr(eloc, (torch.float32,), "eloc", (n,), False), n, n_chains,
+                                   _ptr(n_accepted, (torch.int64,), "n_accepted", (n_chains,)),
+                                   int(proposals_per_chain), _ptr(out, (torch.float64,), "out", (5,), False),
+                                   _stream()))
+
+    def check_status(self):
+        self._check(_lib.nqs_check_status(self._h, _stream()))
+
+
+def pack_spins(s):
+    """[n, N] +-1 tensor (any device) -> [n, W] int32 packed words (same device)."""
+    n, N = s.shape
+    W = (N + 31) // 32
+    bits = (s > 0).to(torch.int64)
+    pad = torch.zeros((n, W * 32 - N), dtype=torch.int64, device=s.device)
+    bits = torch.cat([bits, pad], dim=1).view(n, W, 32)
+    words = (bits << torch.arange(32, device=s.device, dtype=torch.int64)).sum(dim=2)
+    return torch.where(words >= 2 ** 31, words - 2 ** 32, words).to(torch.int32)
+
+
+def unpack_spins(words, N):
+    """[n, W] packed words -> [n, N] int8 +-1 (same device)."""
+    w = words.to(torch.int64) & 0xFFFFFFFF
+    bits = (w.unsqueeze(2) >> torch.arange(32, device=w.device, dtype=torch.int64)) & 1
+    return (bits.view(words.shape[0], -1)[:, :N] * 2 - 1).to(torch.int8)

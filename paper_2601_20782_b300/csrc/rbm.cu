@@ -1,0 +1,842 @@
+// RBM path of the hot loop: sampling-copy preparation, chain initialisation,
+// Metropolis-Hastings sweeps with an incremental per-chain cache, log psi,
+// TFIM local energies, per-sample log-derivatives O_k and the force.
+//
+// RBM (App. G), with spins s in {-1,+1}:
+//     log psi(s) = sum_i a_i s_i + sum_j log cosh(theta_j),  theta = W s + b.
+//
+// Per-chain cache.  Instead of theta_j the sweep keeps the pair
+//     lam_j = e^{theta_j} / (e^{theta_j} + e^{-theta_j}),  mu_j = 1 - lam_j,
+// each stored as its own FP32 number (so neither loses relative precision).
+// Flipping site i (d_j = 2 W_ji s_i) multiplies cosh(theta_j) by
+//     cosh(theta_j - d_j) / cosh(theta_j) = lam_j e^{-d_j} + mu_j e^{d_j}
+//                                        = e^{2 W_ji} g_j,
+//     g_j = mu_j + lam_j R_ji (s_i = +1),   g_j = lam_j + mu_j R_ji (s_i = -1),
+// with the table R_ji = exp(-4 W_ji).  Hence
+//     log psi(y) - log psi(x) = 2 (K_i - a_i s_i) + sum_j log g_j,  K_i = sum_j W_ji,
+// one FMA and one multiply per hidden unit and no cancellation.  An accepted
+// flip updates the cache multiplicatively (lam/mu = e^{2 theta}):
+//     s_i = +1: lam' = lam R / g, mu' = mu / g;   s_i = -1: lam' = lam / g, mu' = mu R / g,
+// and log cosh(theta_j) = -1/2 log(4 lam_j mu_j).  The cache is rebuilt from
+// theta = W s + b every `refresh` sweeps so rounding cannot accumulate.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace nqs {
+namespace {
+
+constexpr uint32_t BULK_CHUNK = 32768;
+
+// Threads per CTA bound for E cached units per lane: the register budget grows
+// with E (four E-wide arrays live across a proposal), about 4 E + 48 per thread.
+constexpr int max_threads_for(int E) {
+  int w = 65536 / (32 * (4 * E + 56));
+  w = w < 2 ? 2 : (w > 32 ? 32 : w);
+  return 32 * w;
+}
+constexpr uint32_t WAIT_POLLS = 1u << 22;
+
+// ------------------------------------------------------------------------------------
+// sampling-copy preparation (Sec. 4.2: FP64 master -> rounded sampling copy)
+template <typename TT>
+__device__ __forceinline__ TT round_to(double x);
+template <>
+__device__ __forceinline__ float round_to<float>(double x) { return static_cast<float>(x); }
+template <>
+__device__ __forceinline__ __half round_to<__half>(double x) { return __double2half(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 round_to<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <typename TT>
+__global__ void rbm_prepare_kernel(const double *__restrict__ p, int N, int M, int M_pad, float *a, float *b,
+                                   float *Wt, TT *R, float *Wm, float *bm, int *status, double wmax) {
+  const int64_t total = (int64_t)N * M_pad;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / M_pad), j = (int)(idx % M_pad);
+    const double w = j < M ? p[N + M + (int64_t)j * N + i] : 0.0;
+    const float wr = to_f(round_to<TT>(w));
+    Wt[idx] = wr;
+    R[idx] = round_to<TT>(exp(-4.0 * (double)wr));
+    if (j < M) Wm[(int64_t)i * M + j] = (float)w;
+    if (!(fabs(w) <= wmax)) atomicOr(status, STATUS_RANGE);
+    if (idx < N) a[idx] = to_f(round_to<TT>(p[idx]));
+    if (idx < M_pad) {
+      b[idx] = idx < M ? to_f(round_to<TT>(p[N + idx])) : 0.f;
+      if (idx < M) bm[idx] = (float)p[N + idx];
+    }
+  }
+}
+
+// aK[i] = (a_i, K_i = sum_j W_ji) from the rounded copy; one warp per site, FP64 sum.
+__global__ void rbm_colsum_kernel(const float *Wt, const float *a, int N, int M_pad, float2 *aK) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= N) return;
+  double s = 0.0;
+  for (int j = lane; j < M_pad; j += 32) s += Wt[(int64_t)warp * M_pad + j];
+  s = group_allsum<32>(s);
+  if (lane == 0) aK[warp] = make_float2(a[warp], (float)s);
+}
+
+// ------------------------------------------------------------------------------------
+// chain initialisation (same draws as the oracle's init_spins_random / _balanced)
+__global__ void init_random_kernel(uint32_t *state, int64_t C, int N, int W, uint32_t k0, uint32_t k1) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+    for (int b = 0; b < (N + 127) / 128; ++b) {
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)b, 0u, (uint32_t)c, TAG_INIT), k0, k1);
+      const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+      for (int q = 0; q < 4; ++q) {
+        const int wi = 4 * b + q;
+        if (wi >= W) break;
+        const int nb = N - 32 * wi;
+        state[c * W + wi] = nb >= 32 ? ws[q] : (ws[q] & ((1u << nb) - 1u));
+      }
+    }
+  }
+}
+
+// Fisher-Yates shuffle of (+1 x N/2, -1 x N/2), from the top; N <= 1024.
+__global__ void init_balanced_kernel(uint32_t *state, int64_t C, int N, int W, uint32_t k0, uint32_t k1) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t bits[32];
+    for (int q = 0; q < 32; ++q) bits[q] = 0u;
+    for (int i = 0; i < N / 2; ++i) bits[i >> 5] |= 1u << (i & 31);
+    uint4 w = make_uint4(0, 0, 0, 0);
+    int cur_blk = -1;
+    for (int i = N - 1; i >= 1; --i) {
+      if ((i >> 2) != cur_blk) {
+        cur_blk = i >> 2;
+        w = philox4x32_10(make_uint4((uint32_t)cur_blk, 1u, (uint32_t)c, TAG_INIT), k0, k1);
+      }
+      const uint32_t ws = (i & 3) == 0 ? w.x : (i & 3) == 1 ? w.y : (i & 3) == 2 ? w.z : w.w;
+      const int j = (int)index_from_word(ws, (uint32_t)(i + 1));
+      const uint32_t bi = (bits[i >> 5] >> (i & 31)) & 1u, bj = (bits[j >> 5] >> (j & 31)) & 1u;
+      if (bi != bj) {
+        bits[i >> 5] ^= 1u << (i & 31);
+        bits[j >> 5] ^= 1u << (j & 31);
+      }
+    }
+    for (int q = 0; q < W; ++q) state[c * W + q] = bits[q];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// per-chain cache helpers (L lanes per chain, E hidden units per lane: j = e * L + gl)
+__device__ __forceinline__ void sigmoid_pair(float th, float &lam, float &mu) {
+  const float e = expf(-2.f * fabsf(th));
+  const float p = 1.f / (1.f + e);
+  const float q = e * p;
+  lam = th >= 0.f ? p : q;
+  mu = th >= 0.f ? q : p;
+}
+
+template <int L, int E>
+__device__ __forceinline__ void compute_theta(float (&th)[E], uint32_t sw, const float *__restrict__ Wt,
+                                              const float *__restrict__ b, int N, int W, int M_pad, int gl) {
+#pragma unroll
+  for (int e = 0; e < E; ++e) th[e] = b[e * L + gl];
+  for (int wi = 0; wi < W; ++wi) {
+    const uint32_t word = __shfl_sync(FULL_MASK, sw, wi, L);
+    const int nb = min(32, N - 32 * wi);
+    for (int bit = 0; bit < nb; ++bit) {
+      const float s = ((word >> bit) & 1u) ? 1.f : -1.f;
+      const float *row = Wt + (size_t)(32 * wi + bit) * M_pad + gl;
+#pragma unroll
+      for (int e = 0; e < E; ++e) th[e] = fmaf(s, __ldg(row + e * L), th[e]);
+    }
+  }
+}
+
+template <int L, int E>
+__device__ __forceinline__ void build_cache(float (&lam)[E], float (&mu)[E], uint32_t sw, const float *Wt,
+                                            const float *b, int N, int W, int M_pad, int gl) {
+  float th[E];
+  compute_theta<L, E>(th, sw, Wt, b, N, W, M_pad, gl);
+#pragma unroll
+  for (int e = 0; e < E; ++e) sigmoid_pair(th[e], lam[e], mu[e]);
+}
+
+// sum_i a_i s_i over the group (every lane gets the same value)
+template <int L>
+__device__ __forceinline__ float visible_term(uint32_t sw, const float2 *aK, int N, int gl) {
+  float v = 0.f;
+  for (int i0 = 0; i0 < N; i0 += L) {
+    const int i = i0 + gl;
+    const uint32_t word = __shfl_sync(FULL_MASK, sw, (min(i, N - 1)) >> 5, L);
+    if (i < N) v += ((word >> (i & 31)) & 1u) ? aK[i].x : -aK[i].x;
+  }
+  return group_allsum<L>(v);
+}
+
+// log psi from the cache: sum_i a_i s_i - 1/2 sum_j log(4 lam_j mu_j)
+template <int L, int E>
+__device__ __forceinline__ float cache_logpsi(const float (&lam)[E], const float (&mu)[E], uint32_t sw,
+                                              const float2 *aK, int N, int gl) {
+  float part = 0.f;
+#pragma unroll
+  for (int e = 0; e < E; ++e) part += log2f(4.f * lam[e] * mu[e]);
+  return visible_term<L>(sw, aK, N, gl) - 0.5f * LN2F * group_allsum<L>(part);
+}
+
+// sum_j log2 g_j over the group, products of up to 8 factors per MUFU lg2.  A
+// product that leaves the normal FP32 range makes the sum non-finite; the group
+// then recomputes with one accurate log per factor.
+template <int L, int E>
+__device__ __forceinline__ float sum_log2(const float (&g)[E]) {
+  float part = 0.f;
+#pragma unroll
+  for (int e0 = 0; e0 < E; e0 += 8) {
+    float pr = g[e0];
+#pragma unroll
+    for (int e = e0 + 1; e < (e0 + 8 < E ? e0 + 8 : E); ++e) pr *= g[e];
+    part += lg2_approx(pr);
+  }
+  float tot = group_allsum<L>(part);
+  const bool bad = !isfinite(tot);
+  if (__any_sync(FULL_MASK, bad)) {
+    float p2 = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) p2 += log2f(g[e]);
+    p2 = group_allsum<L>(p2);
+    if (bad) tot = p2;
+  }
+  return tot;
+}
+
+// Loads the [N][M_pad] table into shared memory with 1D bulk copies.  Returns false
+// (after recording STATUS_TIMEOUT) if the copies did not land within the poll limit.
+template <typename TT>
+__device__ bool load_table(TT *sR, const TT *R, uint32_t bytes, uint64_t *bar, int *status) {
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, bytes);
+    for (uint32_t off = 0; off < bytes; off += BULK_CHUNK)
+      bulk_g2s(reinterpret_cast<char *>(sR) + off, reinterpret_cast<const char *>(R) + off,
+               min(BULK_CHUNK, bytes - off), bar);
+  }
+  bool ok = mbar_wait_bounded(bar, 0, WAIT_POLLS);
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(status, STATUS_TIMEOUT);
+    mbar_wait_bounded(bar, 0, WAIT_POLLS);  // let copies in flight land before the CTA exits
+  }
+  return __syncthreads_and(ok);
+}
+
+struct SweepParams {
+  const float *R;
+  const float2 *aK;
+  const float *Wt;
+  const float *b;
+  uint32_t *state;
+  uint32_t *samples;
+  float *logpsi;
+  int64_t *n_acc;
+  uint32_t *acc_bits;
+  float *delta;
+  int *status;
+  int64_t C;
+  int N, W, M_pad, n_sweeps, burn_in, refresh;
+  uint32_t sweep_offset, k0, k1;
+};
+
+// One group of L lanes runs one chain for all sweeps; the block shares one copy of
+// the R table in shared memory (or reads it through L2 when it does not fit).
+template <int L, int E, bool SMEM>
+__global__ void __launch_bounds__(max_threads_for(E), 1) rbm_sweep_f32_kernel(const SweepParams p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  const float *R = p.R;
+  const uint32_t table_bytes = SMEM ? (uint32_t)p.N * p.M_pad * 4u : 0u;
+  if constexpr (SMEM) {
+    if (!load_table(reinterpret_cast<float *>(smem_raw), p.R, table_bytes, &bar, p.status)) return;
+    R = reinterpret_cast<const float *>(smem_raw);
+  }
+  float2 *saK = reinterpret_cast<float2 *>(smem_raw + table_bytes);
+  for (int i = threadIdx.x; i < p.N; i += blockDim.x) saK[i] = p.aK[i];
+  __syncthreads();
+
+  constexpr int G = 32 / L;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / L, gl = lane % L;
+  const int64_t wpb = blockDim.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * wpb * G;
+  const int N = p.N, W = p.W, M_pad = p.M_pad;
+
+  for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * G; base < p.C; base += stride) {
+    const int64_t c = base + grp;
+    const bool valid = c < p.C;
+    const int64_t cc = valid ? c : p.C - 1;  // idle groups shadow the last chain and write nothing
+    uint32_t sw = gl < W ? p.state[cc * W + gl] : 0u;
+    float lam[E], mu[E];
+    build_cache<L, E>(lam, mu, sw, p.Wt, p.b, N, W, M_pad, gl);
+    int64_t nacc = 0;
+
+    for (int t = 0; t < p.n_sweeps; ++t) {
+      const uint32_t sweep_id = p.sweep_offset + (uint32_t)t;
+      uint32_t abits = 0u;
+      for (int p0 = 0; p0 < N; p0 += 2 * L) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(p0 / 2 + gl), sweep_id, (uint32_t)cc, TAG_SWEEP),
+                                      p.k0, p.k1);
+        const uint32_t site0 = index_from_word(w.x, (uint32_t)N), u0 = w.y >> 8;
+        const uint32_t site1 = index_from_word(w.z, (uint32_t)N), u1 = w.w >> 8;
+        const int np = min(2 * L, N - p0);
+        for (int q = 0; q < np; ++q) {
+          const int src = q >> 1;
+          const uint32_t site = __shfl_sync(FULL_MASK, (q & 1) ? site1 : site0, src, L);
+          const uint32_t ub = __shfl_sync(FULL_MASK, (q & 1) ? u1 : u0, src, L);
+          const uint32_t word = __shfl_sync(FULL_MASK, sw, site >> 5, L);
+          const bool up = (word >> (site & 31)) & 1u;
+          const float *row = R + (size_t)site * M_pad + gl;
+          float rv[E], g[E];
+#pragma unroll
+          for (int e = 0; e < E; ++e) rv[e] = row[e * L];
+          if (up) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) g[e] = fmaf(lam[e], rv[e], mu[e]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) g[e] = fmaf(mu[e], rv[e], lam[e]);
+          }
+          const float tot = sum_log2<L, E>(g);
+          const float2 ak = saK[site];
+          const float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F;
+          const float x = 2.f * dlt;
+          const bool acc = (x >= 0.f) || (ub == 0u) || ((float)ub * 5.9604644775390625e-8f < expf(x));
+          if (acc) {
+            if (up) {
+#pragma unroll
+              for (int e = 0; e < E; ++e) {
+                const float inv = rcp_approx(g[e]);
+                lam[e] = lam[e] * rv[e] * inv;
+                mu[e] = mu[e] * inv;
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < E; ++e) {
+                const float inv = rcp_approx(g[e]);
+                mu[e] = mu[e] * rv[e] * inv;
+                lam[e] = lam[e] * inv;
+              }
+            }
+            if (gl == (int)(site >> 5)) sw ^= 1u << (site & 31);
+            ++nacc;
+          }
+          const int pq = p0 + q;
+          if (p.acc_bits) {
+            abits |= (acc ? 1u : 0u) << (pq & 31);
+            if ((pq & 31) == 31 || pq == N - 1) {
+              if (valid && gl == 0) p.acc_bits[((int64_t)cc * p.n_sweeps + t) * W + (pq >> 5)] = abits;
+              abits = 0u;
+            }
+          }
+          if (p.delta && valid && gl == 0) p.delta[((int64_t)cc * p.n_sweeps + t) * N + pq] = dlt;
+        }
+      }
+      if (t >= p.burn_in) {
+        const int64_t row = (int64_t)(t - p.burn_in) * p.C + cc;
+        if (p.samples && valid && gl < W) p.samples[row * W + gl] = sw;
+        if (p.logpsi) {
+          const float lp = cache_logpsi<L, E>(lam, mu, sw, saK, N, gl);
+          if (valid && gl == 0) p.logpsi[row] = lp;
+        }
+      }
+      if ((t + 1) % p.refresh == 0 && t + 1 < p.n_sweeps) build_cache<L, E>(lam, mu, sw, p.Wt, p.b, N, W, M_pad, gl);
+    }
+    if (valid && gl < W) p.state[cc * W + gl] = sw;
+    if (valid && gl == 0 && p.n_acc) p.n_acc[cc] = nacc;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// log psi by direct evaluation: log cosh z = |z| + log1p(exp(-2|z|)) - log 2
+template <int L, int E>
+__global__ void rbm_logpsi_kernel(const uint32_t *__restrict__ cfg, int64_t n, const float *Wt, const float *b,
+                                  const float2 *aK, int N, int W, int M_pad, float *out) {
+  constexpr int G = 32 / L;
+  const int lane = threadIdx.x & 31, grp = lane / L, gl = lane % L;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x >> 5) * G;
+  for (int64_t base = gw * G; base < n; base += stride) {
+    const int64_t x = min(base + grp, n - 1);
+    const uint32_t sw = gl < W ? cfg[x * W + gl] : 0u;
+    float th[E];
+    compute_theta<L, E>(th, sw, Wt, b, N, W, M_pad, gl);
+    float part = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const float z = fabsf(th[e]);
+      part += z + log1pf(expf(-2.f * z)) - LN2F;
+    }
+    const float lp = visible_term<L>(sw, aK, N, gl) + group_allsum<L>(part);
+    if (base + grp < n && gl == 0) out[x] = lp;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// TFIM local energy (Eq. TFIM, App. I Eq. local_energies):
+//   eps(x) = J sum_<ij> s_i s_j + h sum_i exp(log psi(flip_i x) - log psi(x)).
+template <int L, int E, bool SMEM>
+__global__ void __launch_bounds__(max_threads_for(E), 1) rbm_tfim_eloc_kernel(const uint32_t *__restrict__ cfg, int64_t n,
+                                                                 const float *Rg, const float2 *aK,
+                                                                 const float *Wt, const float *b,
+                                                                 const int2 *bonds, int n_bonds, float J,
+                                                                 float h, int N, int W, int M_pad, float *eloc,
+                                                                 int *status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  const float *R = Rg;
+  const uint32_t table_bytes = SMEM ? (uint32_t)N * M_pad * 4u : 0u;
+  if constexpr (SMEM) {
+    if (!load_table(reinterpret_cast<float *>(smem_raw), Rg, table_bytes, &bar, status)) return;
+    R = reinterpret_cast<const float *>(smem_raw);
+  }
+  float2 *saK = reinterpret_cast<float2 *>(smem_raw + table_bytes);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) saK[i] = aK[i];
+  __syncthreads();
+
+  constexpr int G = 32 / L;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane / L, gl = lane % L;
+  const int64_t wpb = blockDim.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * wpb * G;
+  for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * G; base < n; base += stride) {
+    const int64_t x = min(base + grp, n - 1);
+    const uint32_t sw = gl < W ? cfg[x * W + gl] : 0u;
+    float lam[E], mu[E];
+    build_cache<L, E>(lam, mu, sw, Wt, b, N, W, M_pad, gl);
+    // diagonal: J sum over bonds of s_a s_b
+    float d = 0.f;
+    for (int b0 = 0; b0 < n_bonds; b0 += L) {
+      const int bi = min(b0 + gl, n_bonds - 1);
+      const int2 bd = bonds[bi];
+      const uint32_t wa = __shfl_sync(FULL_MASK, sw, bd.x >> 5, L);
+      const uint32_t wb = __shfl_sync(FULL_MASK, sw, bd.y >> 5, L);
+      const uint32_t sa = (wa >> (bd.x & 31)) & 1u, sb = (wb >> (bd.y & 31)) & 1u;
+      if (b0 + gl < n_bonds) d += sa == sb ? 1.f : -1.f;
+    }
+    d = J * group_allsum<L>(d);
+    float off = 0.f;
+    for (int i = 0; i < N; ++i) {
+      const uint32_t word = __shfl_sync(FULL_MASK, sw, i >> 5, L);
+      const bool up = (word >> (i & 31)) & 1u;
+      const float *row = R + (size_t)i * M_pad + gl;
+      float g[E];
+      if (up) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) g[e] = fmaf(lam[e], row[e * L], mu[e]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) g[e] = fmaf(mu[e], row[e * L], lam[e]);
+      }
+      const float tot = sum_log2<L, E>(g);
+      const float2 ak = saK[i];
+      off += expf(2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F);
+    }
+    if (base + grp < n && gl == 0) eloc[x] = d + h * off;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// O_k rows (App. I, Eq. forces; closed form for the RBM): O_a = s, O_b = tanh theta,
+// O_W[j, i] = tanh(theta_j) s_i, with the FP32 master parameters.  One block per row.
+__global__ void rbm_grad_rows_kernel(const uint32_t *__restrict__ cfg, int64_t n, const float *__restrict__ Wm,
+                                     const float *__restrict__ bm, int N, int W, int M, int64_t P, float *O) {
+  extern __shared__ float sh[];
+  float *ss = sh;       // [N] spins as +-1
+  float *st = sh + N;   // [M] tanh(theta)
+  for (int64_t x = blockIdx.x; x < n; x += gridDim.x) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) ss[i] = ((cfg[x * W + (i >> 5)] >> (i & 31)) & 1u) ? 1.f : -1.f;
+    __syncthreads();
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+      float th = bm[j];
+      for (int i = 0; i < N; ++i) th = fmaf(ss[i], Wm[(int64_t)i * M + j], th);
+      st[j] = tanhf(th);
+    }
+    __syncthreads();
+    float *row = O + x * P;
+    for (int64_t q = threadIdx.x; q < P; q += blockDim.x) {
+      float v;
+      if (q < N) v = ss[q];
+      else if (q < N + M) v = st[q - N];
+      else {
+        const int64_t r = q - N - M;
+        v = st[r / N] * ss[r % N];
+      }
+      row[q] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Force partials (App. I, Eq. forces).  Block (jt, chunk) owns hidden units
+// [32 jt, 32 jt + 32) and one chunk of rows.  Per batch of 64 rows it recomputes
+// theta = W s + b for its units, forms t_j e(x) = tanh(theta_j) (eloc(x) - E) and
+// accumulates sum_x t_j e(x) s_i (W entries), sum_x t_j e(x) (b entries) and, for
+// jt == 0, sum_x s_i e(x) (a entries): FP32 inside a batch, FP64 across batches.
+// The FP64 partial sums go to ws[chunk][P]; force_reduce_kernel adds the chunks.
+// Thread (warp jg, lane il) owns units 4 jg .. 4 jg + 3 and sites il + 32 k.
+constexpr int FT_J = 32;       // hidden units per block
+constexpr int FT_THREADS = 256;
+constexpr int FT_BATCH = 64;   // rows per FP32 batch
+constexpr int FT_MAXI = 8;     // sites per lane: N <= 256
+
+__global__ void __launch_bounds__(FT_THREADS) rbm_force_partial_kernel(
+    const uint32_t *__restrict__ cfg, int64_t n, const float *__restrict__ eloc, const double *__restrict__ stats,
+    const float *__restrict__ Wm, const float *__restrict__ bm, int N, int W, int M, int64_t P, int n_chunks,
+    double *ws) {
+  extern __shared__ __align__(16) float sh[];
+  float *sW = sh;                     // [N][FT_J] master weights of this tile
+  float *ss = sW + N * FT_J;          // [FT_BATCH][N] spins, row-major
+  float *ssT = ss + FT_BATCH * N;     // [N][FT_BATCH] spins, site-major
+  float *st = ssT + N * FT_BATCH;     // [FT_BATCH][FT_J] tanh(theta) * e(x)
+  float *se = st + FT_BATCH * FT_J;   // [FT_BATCH] e(x)
+  const int jt = blockIdx.x, chunk = blockIdx.y;
+  const int j0 = jt * FT_J;
+  const int nj = min(FT_J, M - j0);
+  const int jg = threadIdx.x >> 5, il = threadIdx.x & 31;
+  for (int q = threadIdx.x; q < N * FT_J; q += FT_THREADS) {
+    const int i = q / FT_J, jj = q % FT_J;
+    sW[q] = jj < nj ? Wm[(int64_t)i * M + j0 + jj] : 0.f;
+  }
+  float bj[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) bj[k] = (4 * jg + k < nj) ? bm[j0 + 4 * jg + k] : 0.f;
+  const double E = stats[0];
+  const int64_t rows_per_chunk = (n + n_chunks - 1) / n_chunks;
+  const int64_t r0 = (int64_t)chunk * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+  double accW[FT_MAXI][4];
+#pragma unroll
+  for (int k = 0; k < FT_MAXI; ++k)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) accW[k][m] = 0.0;
+  double accB = 0.0, accA = 0.0;
+  __syncthreads();
+  for (int64_t xb = r0; xb < r1; xb += FT_BATCH) {
+    const int nb = (int)(r1 - xb < FT_BATCH ? r1 - xb : FT_BATCH);
+    for (int q = threadIdx.x; q < FT_BATCH * N; q += FT_THREADS) {
+      const int r = q / N, i = q % N;
+      float v = 0.f;
+      if (r < nb) v = ((cfg[(xb + r) * W + (i >> 5)] >> (i & 31)) & 1u) ? 1.f : -1.f;
+      ss[q] = v;
+      ssT[i * FT_BATCH + r] = v;
+    }
+    for (int r = threadIdx.x; r < FT_BATCH; r += FT_THREADS)
+      se[r] = r < nb ? (float)((double)eloc[xb + r] - E) : 0.f;
+    __syncthreads();
+    {  // theta for rows il, il + 32 and units 4 jg .. 4 jg + 3
+      float th0[4], th1[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) th0[k] = th1[k] = bj[k];
+      for (int i = 0; i < N; ++i) {
+        const float4 w4 = *reinterpret_cast<const float4 *>(sW + i * FT_J + 4 * jg);
+        const float s0 = ssT[i * FT_BATCH + il], s1 = ssT[i * FT_BATCH + il + 32];
+        th0[0] = fmaf(s0, w4.x, th0[0]); th0[1] = fmaf(s0, w4.y, th0[1]);
+        th0[2] = fmaf(s0, w4.z, th0[2]); th0[3] = fmaf(s0, w4.w, th0[3]);
+        th1[0] = fmaf(s1, w4.x, th1[0]); th1[1] = fmaf(s1, w4.y, th1[1]);
+        th1[2] = fmaf(s1, w4.z, th1[2]); th1[3] = fmaf(s1, w4.w, th1[3]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool ok = 4 * jg + k < nj;
+        st[il * FT_J + 4 * jg + k] = ok ? tanhf(th0[k]) * se[il] : 0.f;
+        st[(il + 32) * FT_J + 4 * jg + k] = ok ? tanhf(th1[k]) * se[il + 32] : 0.f;
+      }
+    }
+    __syncthreads();
+    float acc[FT_MAXI][4];
+#pragma unroll
+    for (int k = 0; k < FT_MAXI; ++k)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[k][m] = 0.f;
+    for (int r = 0; r < nb; ++r) {
+      const float4 t4 = *reinterpret_cast<const float4 *>(st + r * FT_J + 4 * jg);
+#pragma unroll
+      for (int k = 0; k < FT_MAXI; ++k) {
+        const int i = il + 32 * k;
+        if (i < N) {
+          const float sv = ss[r * N + i];
+          acc[k][0] = fmaf(t4.x, sv, acc[k][0]); acc[k][1] = fmaf(t4.y, sv, acc[k][1]);
+          acc[k][2] = fmaf(t4.z, sv, acc[k][2]); acc[k][3] = fmaf(t4.w, sv, acc[k][3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < FT_MAXI; ++k)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) accW[k][m] += acc[k][m];
+    if (il < 4) {
+      float a = 0.f;
+      for (int r = 0; r < nb; ++r) a += st[r * FT_J + 4 * jg + il];
+      accB += a;
+    }
+    if (jt == 0 && threadIdx.x < N) {
+      float a = 0.f;
+      for (int r = 0; r < nb; ++r) a = fmaf(ss[r * N + threadIdx.x], se[r], a);
+      accA += a;
+    }
+    __syncthreads();
+  }
+  double *out = ws + (int64_t)chunk * P;
+#pragma unroll
+  for (int k = 0; k < FT_MAXI; ++k) {
+    const int i = il + 32 * k;
+    if (i < N) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int jj = 4 * jg + m;
+        if (jj < nj) out[N + M + (int64_t)(j0 + jj) * N + i] = accW[k][m];
+      }
+    }
+  }
+  if (il < 4 && 4 * jg + il < nj) out[N + j0 + 4 * jg + il] = accB;
+  if (jt == 0 && threadIdx.x < N) out[threadIdx.x] = accA;
+}
+
+__global__ void force_reduce_kernel(const double *ws, int n_chunks, int64_t P, int64_t n, double *force) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < n_chunks; ++c) s += ws[(int64_t)c * P + k];
+    force[k] = s / (double)n;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// dispatch over (L, E)
+template <template <int, int> class F, typename... A>
+cudaError_t dispatch_le(int L, int E, A... args) {
+#define NQS_CASE(LL, EE) \
+  if (L == LL && E == EE) return F<LL, EE>::run(args...);
+  NQS_CASE(8, 4) NQS_CASE(16, 2) NQS_CASE(16, 4)
+  NQS_CASE(32, 1) NQS_CASE(32, 2) NQS_CASE(32, 3) NQS_CASE(32, 4) NQS_CASE(32, 5) NQS_CASE(32, 6)
+  NQS_CASE(32, 7) NQS_CASE(32, 8) NQS_CASE(32, 9) NQS_CASE(32, 10) NQS_CASE(32, 11) NQS_CASE(32, 12)
+  NQS_CASE(32, 13) NQS_CASE(32, 14) NQS_CASE(32, 16) NQS_CASE(32, 18) NQS_CASE(32, 20) NQS_CASE(32, 24)
+  NQS_CASE(32, 28) NQS_CASE(32, 32)
+#undef NQS_CASE
+  return cudaErrorInvalidConfiguration;
+}
+
+bool e_instantiated(int E32) {
+  switch (E32) {
+    case 1: case 2: case 3: case 4: case 5: case 6: case 7: case 8: case 9: case 10: case 11: case 12:
+    case 13: case 14: case 16: case 18: case 20: case 24: case 28: case 32:
+      return true;
+    default:
+      return false;
+  }
+}
+
+// Lanes per chain: one chain per warp unless the hidden layer is tiny.
+int pick_lanes(const nqs_ctx *c) {
+  const int E32 = c->M_pad / 32;
+  if (c->chains_per_warp == 4 && E32 == 1 && c->W <= 8) return 8;
+  if (c->chains_per_warp == 2 && E32 <= 2 && c->W <= 16) return 16;
+  if (c->chains_per_warp == 0 && E32 == 1 && c->W <= 8) return 8;
+  return 32;
+}
+
+template <int L, int E>
+struct SweepRun {
+  static cudaError_t run(const nqs_ctx *c, SweepParams p, cudaStream_t s) {
+    const size_t table = (size_t)c->N * c->M_pad * 4;
+    const size_t extra = (size_t)c->N * sizeof(float2) + 16;
+    const bool smem = table + extra + 256 <= (size_t)c->smem_optin;  // + static mbarrier
+    auto kern = smem ? rbm_sweep_f32_kernel<L, E, true> : rbm_sweep_f32_kernel<L, E, false>;
+    const size_t shm = (smem ? table : 0) + extra;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    const int regs = std::max(fa.numRegs, 16);
+    const int regs_alloc = (regs + 7) / 8 * 8;
+    int warps = 65536 / (regs_alloc * 32);
+    warps = std::max(1, std::min(fa.maxThreadsPerBlock / 32, warps));
+    constexpr int G = 32 / L;
+    const int64_t warps_needed = (p.C + G - 1) / G;
+    const int blocks_cap = c->num_sms;  // one CTA per SM shares one table copy
+    int64_t blocks = std::min<int64_t>(blocks_cap, (warps_needed + warps - 1) / warps);
+    if (blocks < c->num_sms) {  // spread small jobs over more SMs with fewer warps each
+      blocks = std::min<int64_t>(c->num_sms, warps_needed);
+      warps = (int)std::max<int64_t>(1, (warps_needed + blocks - 1) / blocks);
+    } else {  // equal rounds: the fewest warps per CTA that keep the round count
+      const int64_t rounds = (warps_needed + blocks * warps - 1) / (blocks * warps);
+      warps = (int)((warps_needed + blocks * rounds - 1) / (blocks * rounds));
+    }
+    kern<<<(unsigned)blocks, warps * 32, shm, s>>>(p);
+    return cudaGetLastError();
+  }
+};
+
+template <int L, int E>
+struct LogpsiRun {
+  static cudaError_t run(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *out, cudaStream_t s) {
+    constexpr int G = 32 / L;
+    const int64_t warps = (n + G - 1) / G;
+    const int64_t blocks = std::min<int64_t>((warps + 7) / 8, (int64_t)c->num_sms * 16);
+    rbm_logpsi_kernel<L, E><<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(
+        cfg, n, c->d_Wt, c->d_b, c->d_aK, c->N, c->W, c->M_pad, out);
+    return cudaGetLastError();
+  }
+};
+
+template <int L, int E>
+struct ElocRun {
+  static cudaError_t run(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *eloc, cudaStream_t s) {
+    const size_t table = (size_t)c->N * c->M_pad * 4;
+    const size_t extra = (size_t)c->N * sizeof(float2) + 16;
+    const bool smem = table + extra + 256 <= (size_t)c->smem_optin;  // + static mbarrier
+    auto kern = smem ? rbm_tfim_eloc_kernel<L, E, true> : rbm_tfim_eloc_kernel<L, E, false>;
+    const size_t shm = (smem ? table : 0) + extra;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    const int regs_alloc = (std::max(fa.numRegs, 16) + 7) / 8 * 8;
+    int warps = std::max(1, std::min(fa.maxThreadsPerBlock / 32, 65536 / (regs_alloc * 32)));
+    constexpr int G = 32 / L;
+    const int64_t warps_needed = (n + G - 1) / G;
+    int64_t blocks = std::min<int64_t>(c->num_sms, (warps_needed + warps - 1) / warps);
+    if (blocks < c->num_sms) {
+      blocks = std::min<int64_t>(c->num_sms, warps_needed);
+      warps = (int)std::max<int64_t>(1, (warps_needed + blocks - 1) / blocks);
+    }
+    kern<<<(unsigned)blocks, warps * 32, shm, s>>>(cfg, n, c->d_R ? (const float *)c->d_R : nullptr, c->d_aK,
+                                                   c->d_Wt, c->d_b, c->d_bonds, c->n_bonds, (float)c->J1,
+                                                   (float)c->h, c->N, c->W, c->M_pad, eloc, c->d_status);
+    return cudaGetLastError();
+  }
+};
+
+int force_chunks(const nqs_ctx *c, int64_t n) {
+  const int jt = (c->M + FT_J - 1) / FT_J;
+  int64_t want = (2 * (int64_t)c->num_sms + jt - 1) / jt;
+  want = std::min<int64_t>(want, (n + FT_BATCH - 1) / FT_BATCH);
+  return (int)std::max<int64_t>(1, want);
+}
+
+}  // namespace
+
+// ====================================================================================
+bool rbm_supported(const nqs_ctx *c, std::string *why) {
+  if (c->ham_kind != NQS_TFIM) {
+    *why = "the RBM path implements the TFIM Hamiltonian (single-flip moves)";
+    return false;
+  }
+  if (c->dtype != NQS_F32) {
+    *why = "the RBM sampler is built for F32 sampling copies";
+    return false;
+  }
+  if (c->N > 256) {
+    *why = "RBM path supports N <= 256";
+    return false;
+  }
+  if (!e_instantiated(c->M_pad / 32)) {
+    *why = "hidden-layer width not instantiated";
+    return false;
+  }
+  return true;
+}
+
+cudaError_t rbm_prepare(nqs_ctx *c, const double *params, cudaStream_t s) {
+  const int64_t total = (int64_t)c->N * c->M_pad;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)c->num_sms * 8);
+  rbm_prepare_kernel<float><<<blocks, 256, 0, s>>>(params, c->N, c->M, c->M_pad, c->d_a, c->d_b, c->d_Wt,
+                                                   (float *)c->d_R, c->d_Wm, c->d_bm, c->d_status, 20.0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  rbm_colsum_kernel<<<(c->N * 32 + 255) / 256, 256, 0, s>>>(c->d_Wt, c->d_a, c->N, c->M_pad, c->d_aK);
+  return cudaGetLastError();
+}
+
+cudaError_t init_chains(const nqs_ctx *c, uint32_t *state, int64_t n, uint64_t seed, cudaStream_t s) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)c->num_sms * 16));
+  if (c->ham_kind == NQS_HEISENBERG)
+    init_balanced_kernel<<<blocks, 128, 0, s>>>(state, n, c->N, c->W, k0, k1);
+  else
+    init_random_kernel<<<blocks, 128, 0, s>>>(state, n, c->N, c->W, k0, k1);
+  return cudaGetLastError();
+}
+
+cudaError_t rbm_sweep(const nqs_ctx *c, uint32_t *state, int64_t n_chains, int n_sweeps, int burn_in,
+                      uint64_t seed, uint32_t sweep_offset, uint32_t *samples, float *logpsi, int64_t *n_acc,
+                      uint32_t *acc_bits, float *delta, cudaStream_t s) {
+  SweepParams p;
+  p.R = (const float *)c->d_R;
+  p.aK = c->d_aK;
+  p.Wt = c->d_Wt;
+  p.b = c->d_b;
+  p.state = state;
+  p.samples = samples;
+  p.logpsi = logpsi;
+  p.n_acc = n_acc;
+  p.acc_bits = acc_bits;
+  p.delta = delta;
+  p.status = c->d_status;
+  p.C = n_chains;
+  p.N = c->N;
+  p.W = c->W;
+  p.M_pad = c->M_pad;
+  p.n_sweeps = n_sweeps;
+  p.burn_in = burn_in;
+  p.refresh = c->refresh;
+  p.sweep_offset = sweep_offset;
+  p.k0 = (uint32_t)seed;
+  p.k1 = (uint32_t)(seed >> 32);
+  const int L = pick_lanes(c);
+  return dispatch_le<SweepRun>(L, c->M_pad / L, c, p, s);
+}
+
+cudaError_t rbm_logpsi(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *out, cudaStream_t s) {
+  const int L = pick_lanes(c);
+  return dispatch_le<LogpsiRun>(L, c->M_pad / L, c, cfg, n, out, s);
+}
+
+cudaError_t rbm_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *eloc, cudaStream_t s) {
+  const int L = pick_lanes(c);
+  return dispatch_le<ElocRun>(L, c->M_pad / L, c, cfg, n, eloc, s);
+}
+
+size_t rbm_grad_workspace(const nqs_ctx *c, int64_t n) {
+  return (size_t)force_chunks(c, n) * (size_t)c->P * sizeof(double);
+}
+
+cudaError_t rbm_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
+                            const double *stats, double *force, void *ws, cudaStream_t s) {
+  if (O) {
+    const size_t shm = (size_t)(c->N + c->M) * sizeof(float);
+    const int64_t blocks = std::min<int64_t>(n, (int64_t)c->num_sms * 8);
+    rbm_grad_rows_kernel<<<(unsigned)blocks, 256, shm, s>>>(cfg, n, c->d_Wm, c->d_bm, c->N, c->W, c->M, c->P, O);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (force) {
+    const int chunks = force_chunks(c, n);
+    const int jt = (c->M + FT_J - 1) / FT_J;
+    const size_t shm = (size_t)(c->N * FT_J + 2 * FT_BATCH * c->N + FT_BATCH * FT_J + FT_BATCH) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(rbm_force_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)shm);
+    if (e != cudaSuccess) return e;
+    rbm_force_partial_kernel<<<dim3(jt, chunks), FT_THREADS, shm, s>>>(cfg, n, eloc, stats, c->d_Wm, c->d_bm, c->N,
+                                                                       c->W, c->M, c->P, chunks, (double *)ws);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int rb = (int)std::min<int64_t>((c->P + 255) / 256, (int64_t)c->num_sms * 8);
+    force_reduce_kernel<<<rb, 256, 0, s>>>((const double *)ws, chunks, c->P, n, force);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+}  // namespace nqs

@@ -1,0 +1,209 @@
+"""Parity of the CUDA RBM / TFIM path with the FP64 oracle (run on a B300).
+
+Bit-exact: initial spins, Philox proposal stream (through lockstep replay of the
+recorded accept decisions), sample configurations and accept counts.  FP32:
+|d log psi| <= 1e-5 relative, decisions may differ from FP64 only within
+tau = 1e-4 of the threshold (|2 dlogpsi - log u| <= tau).
+"""
+import numpy as np
+import pytest
+
+from helpers import nqs, pack_np, unpack_np, unpack_accept_bits, to_words_tensor, words_from_tensor
+from oracle import exact
+from oracle.estimators import local_energy as oracle_eloc, energy_stats, force as oracle_force
+from oracle.hamiltonian import TFIM
+from oracle.models import RBM
+from oracle.philox import init_spins_random
+from oracle.sampler import mh_sweeps
+from workloads import rbm_params
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TAU = 1e-4
+LOGPSI_RTOL = 1e-5
+
+
+def make(Lx, Ly, M, sigma, seed, h=1.0, J=1.0):
+    p = nqs()
+    ctx = p.Context("tfim", Lx, Ly, J1=J, h=h, model="rbm", n_hidden=M, dtype="f32")
+    params = rbm_params(Lx * Ly, M, sigma, seed)
+    ctx.set_params(torch.from_numpy(params).cuda())
+    return ctx, RBM(Lx * Ly, M, params), TFIM(Lx, Ly, J, h)
+
+
+@pytest.mark.parametrize("N,C", [(16, 1000), (37, 333), (100, 64), (256, 17)])
+def test_init_chains_bit_exact(N, C):
+    p = nqs()
+    ctx = p.Context("tfim", N, 1, h=1.0, model="rbm", n_hidden=8)
+    state = torch.zeros((C, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, seed=123456789)
+    got = unpack_np(words_from_tensor(state), N)
+    np.testing.assert_array_equal(got, init_spins_random(123456789, np.arange(C), N))
+    # unused high bits of the last word stay clear
+    if N % 32:
+        assert np.all(words_from_tensor(state)[:, -1] >> np.uint32(N % 32) == 0)
+
+
+@pytest.mark.parametrize("Lx,Ly,M,sigma", [(16, 1, 16, 0.3), (37, 1, 50, 0.2), (10, 10, 400, 0.05),
+                                           (16, 16, 100, 0.1)])
+def test_logpsi_fp32_matches_oracle(Lx, Ly, M, sigma):
+    ctx, model, _ = make(Lx, Ly, M, sigma, 7)
+    s = np.random.default_rng(1).choice([-1, 1], size=(517, Lx * Ly)).astype(np.int8)
+    out = torch.empty(517, dtype=torch.float32, device="cuda")
+    ctx.logpsi(to_words_tensor(pack_np(s)), out)
+    ref = model.logpsi(s)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=LOGPSI_RTOL, atol=LOGPSI_RTOL)
+
+
+def _lockstep(Lx, Ly, M, sigma, C, T, burn, seed=99, offset=0, refresh=None, cpw=None):
+    ctx, model, _ = make(Lx, Ly, M, sigma, 5)
+    N = Lx * Ly
+    if refresh:
+        ctx.set_option(nqs().OPT_REFRESH, refresh)
+    if cpw is not None:
+        ctx.set_option(nqs().OPT_CHAINS_PER_WARP, cpw)
+    state = torch.zeros((C, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, seed=seed + 1)
+    s0 = unpack_np(words_from_tensor(state), N)
+    K = T - burn
+    samples = torch.zeros((K * C, ctx.W), dtype=torch.int32, device="cuda")
+    logpsi = torch.zeros(K * C, dtype=torch.float32, device="cuda")
+    nacc = torch.zeros(C, dtype=torch.int64, device="cuda")
+    bits = torch.zeros((C, T, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.sweep(state, T, burn, seed, offset, samples, logpsi, nacc, accept_bits=bits)
+    torch.cuda.synchronize()
+    acc = unpack_accept_bits(words_from_tensor(bits), N)
+    ref = mh_sweeps(model.logpsi, s0, np.arange(C), seed, T, burn, sweep_offset=offset,
+                    replay_accepts=acc, tau=TAU)
+    return ctx, model, ref, state, samples, logpsi, nacc, acc
+
+
+@pytest.mark.parametrize("Lx,Ly,M,sigma,C,T,burn,cpw", [
+    (16, 1, 16, 0.01, 1024, 100, 10, None),    # the 1D N = 16 workload, in full
+    (16, 1, 16, 0.3, 300, 12, 2, 1),           # one chain per warp, ragged chain count
+    (37, 1, 50, 0.25, 301, 7, 3, None),        # ragged N (two words), padded hidden units
+    (10, 10, 400, 0.05, 64, 3, 1, None),       # the 10 x 10, alpha = 4 shape
+])
+def test_sweep_lockstep_with_oracle(Lx, Ly, M, sigma, C, T, burn, cpw):
+    _, model, ref, state, samples, logpsi, nacc, acc = _lockstep(Lx, Ly, M, sigma, C, T, burn, cpw=cpw)
+    N = Lx * Ly
+    # replay succeeded (no decision outside tau disagreed); configurations are then identical
+    np.testing.assert_array_equal(unpack_np(words_from_tensor(state), N), ref["spins"])
+    np.testing.assert_array_equal(unpack_np(words_from_tensor(samples), N), ref["samples"])
+    np.testing.assert_array_equal(nacc.cpu().numpy(), acc.sum(axis=(1, 2)))
+    lp = logpsi.cpu().numpy()
+    np.testing.assert_allclose(lp, ref["logpsi"], rtol=LOGPSI_RTOL, atol=LOGPSI_RTOL)
+    assert ref["near_threshold"] <= max(2, 1e-5 * ref["checked"])
+
+
+def test_sweep_resumes_across_calls():
+    p = nqs()
+    ctx, _, _ = make(12, 1, 24, 0.3, 3)
+    C = 200
+    a = torch.zeros((C, 1), dtype=torch.int32, device="cuda")
+    ctx.init_chains(a, 5)
+    b = a.clone()
+    ctx.sweep(a, 6, 0, 77, 0)
+    ctx.sweep(b, 2, 0, 77, 0)
+    ctx.sweep(b, 4, 0, 77, 2)
+    # the cache is rebuilt at a call boundary; decisions still agree except within FP32 rounding
+    assert (a != b).any(dim=1).float().mean().item() <= 0.01
+
+
+def test_local_energy_matches_oracle():
+    ctx, model, ham = make(10, 10, 400, 0.05, 9, h=3.04)
+    s = np.random.default_rng(2).choice([-1, 1], size=(300, 100)).astype(np.int8)
+    e = torch.empty(300, dtype=torch.float32, device="cuda")
+    ctx.local_energy(to_words_tensor(pack_np(s)), e)
+    ref = oracle_eloc(ham, model.logpsi, s)
+    scale = len(ham.bonds) * abs(ham.J) + abs(ham.h) * 100 * 2
+    np.testing.assert_allclose(e.cpu().numpy(), ref, rtol=0, atol=2e-5 * scale)
+
+
+def test_local_energy_ragged_and_1d():
+    ctx, model, ham = make(37, 1, 50, 0.3, 4, h=0.7, J=1.3)
+    s = np.random.default_rng(3).choice([-1, 1], size=(65, 37)).astype(np.int8)
+    e = torch.empty(65, dtype=torch.float32, device="cuda")
+    ctx.local_energy(to_words_tensor(pack_np(s)), e)
+    ref = oracle_eloc(ham, model.logpsi, s)
+    np.testing.assert_allclose(e.cpu().numpy(), ref, rtol=0, atol=2e-5 * (37 * 1.3 + 0.7 * 37 * 3))
+
+
+@pytest.mark.parametrize("Lx,Ly,M", [(16, 1, 16), (10, 10, 400), (7, 1, 33)])
+def test_logpsi_grad_rows_and_force_match_oracle(Lx, Ly, M):
+    N = Lx * Ly
+    ctx, model, _ = make(Lx, Ly, M, 0.1, 8)
+    n = 203
+    s = np.random.default_rng(4).choice([-1, 1], size=(n, N)).astype(np.int8)
+    cfg = to_words_tensor(pack_np(s))
+    O = torch.empty((n, ctx.P), dtype=torch.float32, device="cuda")
+    eloc = torch.from_numpy(np.random.default_rng(5).normal(-3.0, 1.0, n).astype(np.float32)).cuda()
+    stats = torch.empty(5, dtype=torch.float64, device="cuda")
+    ctx.stats(eloc, n, stats)
+    force = torch.empty(ctx.P, dtype=torch.float64, device="cuda")
+    ws = torch.empty(ctx.logpsi_grad_workspace(n), dtype=torch.uint8, device="cuda")
+    ctx.logpsi_grad(cfg, O=O, eloc=eloc, stats=stats, force=force, workspace=ws)
+    Oref = model.grad(s)
+    np.testing.assert_allclose(O.cpu().numpy(), Oref, rtol=0, atol=1e-5)
+    Fref = oracle_force(Oref, eloc.cpu().numpy().astype(np.float64))
+    np.testing.assert_allclose(force.cpu().numpy(), Fref, rtol=0, atol=1e-5 * max(1.0, np.abs(Fref).max()))
+
+
+def test_stats_match_oracle_and_acceptance():
+    p = nqs()
+    ctx, _, _ = make(16, 1, 16, 0.1, 1)
+    C, K = 96, 7
+    e = np.random.default_rng(6).normal(-20, 2, C * K).astype(np.float32)
+    acc = torch.arange(C, dtype=torch.int64, device="cuda")
+    out = torch.empty(5, dtype=torch.float64, device="cuda")
+    ctx.stats(torch.from_numpy(e).cuda(), C, out, n_accepted=acc, proposals_per_chain=160)
+    E, var, err = energy_stats(e.astype(np.float64), C)
+    got = out.cpu().numpy()
+    np.testing.assert_allclose(got[:3], [E, var, err], rtol=1e-12)
+    assert got[3] == pytest.approx(np.arange(C).sum() / (C * 160))
+    assert got[4] == C * K
+
+
+def test_tfim_1d_n16_energy_against_exact_enumeration_and_ed():
+    """1D TFIM N = 16, J = h = 1, RBM alpha = 1 with N(0, 0.01^2) weights, 1024 chains x
+    100 sweeps (10 burn-in): the sampled energy agrees with the exact expectation by
+    enumeration within 3 standard errors and lies above the ED ground energy."""
+    p = nqs()
+    ctx, model, ham = make(16, 1, 16, 0.01, 20260001)
+    C, T, B = 1024, 100, 10
+    state = torch.zeros((C, 1), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, 11)
+    S = torch.zeros(((T - B) * C, 1), dtype=torch.int32, device="cuda")
+    nacc = torch.zeros(C, dtype=torch.int64, device="cuda")
+    ctx.sweep(state, T, B, 12, 0, S, None, nacc)
+    e = torch.empty((T - B) * C, dtype=torch.float32, device="cuda")
+    ctx.local_energy(S, e)
+    st = torch.empty(5, dtype=torch.float64, device="cuda")
+    ctx.stats(e, C, st, nacc, T * 16)
+    E, var, err, accr, n = st.cpu().numpy()
+    pi = exact.exact_pi(model.logpsi, 16)
+    e_exact = pi @ oracle_eloc(ham, model.logpsi, exact.all_configs(16))
+    assert abs(E - e_exact) < 3 * err, (E, e_exact, err)
+    e0 = exact.ground_energy(exact.sparse_hamiltonian(ham))[0]
+    assert E > e0
+    assert 0.0 < accr <= 1.0
+
+
+def test_histogram_tv_against_exact_distribution_4x4():
+    """4 x 4 TFIM, alpha = 4 RBM: total-variation distance of the GPU sample histogram
+    from the exact pi (enumeration of 2^16 states) is at the level of i.i.d. sampling noise."""
+    ctx, model, _ = make(4, 4, 64, 0.25, 13, h=3.04)
+    C, T, B = 4096, 60, 10
+    state = torch.zeros((C, 1), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, 21)
+    S = torch.zeros(((T - B) * C, 1), dtype=torch.int32, device="cuda")
+    ctx.sweep(state, T, B, 22, 0, S)
+    idx = words_from_tensor(S)[:, 0].astype(np.int64)
+    hist = np.bincount(idx, minlength=2 ** 16) / idx.size
+    pi = exact.exact_pi(model.logpsi, 16)
+    tv = 0.5 * np.abs(hist - pi).sum()
+    rng = np.random.default_rng(0)
+    floor = max(0.5 * np.abs(np.bincount(rng.choice(pi.size, idx.size, p=pi), minlength=pi.size) / idx.size - pi).sum()
+                for _ in range(3))
+    assert tv < 1.3 * floor + 0.005, (tv, floor)
