@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Benchmark of the NQS VMC hot path on one B300 (or N, one process per GPU).
+
+Workload: 2D transverse-field Ising model on a 10 x 10 periodic lattice, h = 3.04,
+RBM with alpha = 4 (400 hidden units), weights ~ N(0, 0.05^2); 16384 chains x 500
+single-spin-flip sweeps (50 burn-in), i.e. 8.19e8 Metropolis-Hastings proposals and
+7.37e6 kept samples per GPU.  One step = the whole hot path on that batch:
+parameter downcast, chain initialisation, the sweeps, local energies of every kept
+sample, FP64 statistics, the force over every kept sample, and the O_k rows of the
+last sweep's samples.  Synthetic, seeded data; no datasets or trained weights.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+import workloads
+
+METRIC = "MH proposals/sec and local-energy samples/sec on 1 B300, mixed vs FP32 at stated bias"
+WL = workloads.TFIM_2D_10x10
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 8 for k in range(4) if r[4 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def combine_across_ranks(stats, force, n_local, dist):
+    """Energy statistics and force over all ranks' samples: an FP64 all-reduce of
+    (n, n * mean, n * (var + mean^2), n * force).  stats/force are rank-local."""
+    import torch
+    buf = torch.cat([torch.tensor([float(n_local)], dtype=torch.float64, device=stats.device),
+                     stats[:1] * n_local, (stats[1:2] + stats[:1] ** 2) * n_local, force * n_local])
+    dist.all_reduce(buf)
+    n = buf[0]
+    mean = buf[1] / n
+    var = buf[2] / n - mean ** 2
+    return n, mean, var, buf[3:] / n
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    import paper_2601_20782_b300 as nqs
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    ham, lat = WL.ham, WL.ham.lattice
+    N, M, C, T, B = lat.n_sites, WL.n_hidden, WL.n_chains, WL.n_sweeps, WL.burn_in
+    if args.chains or args.sweeps:   # smaller case of the same kernels, for profiler captures only
+        C, T, B = args.chains or C, args.sweeps or T, args.burn_in if args.burn_in is not None else B
+    K = T - B
+    S = K * C
+    ctx = nqs.Context("tfim", lat.Lx, lat.Ly, J1=ham.J1, h=ham.h, model="rbm", n_hidden=M, dtype=args.dtype)
+    P = ctx.P
+    params_h = torch.from_numpy(workloads.rbm_params(N, M, WL.weight_sigma, WL.seed)).pin_memory()
+    params = params_h.to(dev)
+    state = torch.zeros((C, ctx.W), dtype=torch.int32, device=dev)
+    samples = torch.zeros((S, ctx.W), dtype=torch.int32, device=dev)
+    nacc = torch.zeros(C, dtype=torch.int64, device=dev)
+    eloc = torch.zeros(S, dtype=torch.float32, device=dev)
+    stats = torch.zeros(5, dtype=torch.float64, device=dev)
+    force = torch.zeros(P, dtype=torch.float64, device=dev)
+    O = torch.zeros((C, P), dtype=torch.float32, device=dev)
+    ws = torch.zeros(ctx.logpsi_grad_workspace(S), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
+    out_h = torch.zeros(5 + P, dtype=torch.float64).pin_memory()
+    launches_per_step = 2 + 1 + 1 + 1 + 2 + 2 + 1   # set_params, init, sweep, eloc, stats, force, O rows
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+
+    def step(seed, host_io=False):
+        if host_io:
+            params.copy_(params_h, non_blocking=True)
+        ev[0].record()
+        ctx.set_params(params)
+        ctx.init_chains(state, seed)
+        ev[1].record()
+        ctx.sweep(state, T, B, seed + 1, 0, samples, None, nacc)
+        ev[2].record()
+        ctx.local_energy(samples, eloc)
+        ev[3].record()
+        ctx.stats(eloc, C, stats, nacc, T * N)
+        ctx.logpsi_grad(samples, None, eloc, stats, force, ws)
+        ev[4].record()
+        ctx.logpsi_grad(samples[S - C:], O)
+        ev[5].record()
+        if host_io:
+            out_h[:5].copy_(stats, non_blocking=True)
+            out_h[5:].copy_(force, non_blocking=True)
+
+    base_seed = WL.seed * 1000 + rank * 7919
+    for w in range(args.warmup):
+        step(base_seed + w)
+    torch.cuda.synchronize()
+
+    phase = np.zeros(5)
+    step_ms = []
+    acc_total = 0
+    with ClockSampler(dev.index) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()                       # L2 flush between timed steps (not timed)
+            step(base_seed + 100 + k)
+            torch.cuda.synchronize()
+            acc_total += int(nacc.sum().item())
+            ph = [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
+            phase += ph
+            step_ms.append(sum(ph))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    t_dev = sum(step_ms) / 1e3
+
+    # end to end through the public API with host buffers: pinned params in, stats + force out
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(base_seed + 200 + k, host_io=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+
+    if dist:
+        tt = torch.tensor([t_dev, sum(e2e_ms) / 1e3], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev, t_e2e = tt.tolist()
+        combine_across_ranks(stats, force, S, dist)
+    else:
+        t_e2e = sum(e2e_ms) / 1e3
+
+    proposals_step = C * T * N
+    value = world * proposals_step * args.steps / t_dev
+    ph = phase / args.steps   # ms per phase: prep+init, sweep, eloc, stats+force, O rows
+    accepts_per_step = acc_total / args.steps
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2032.0))
+    # FP32-pipe roofline of the sweep: per proposal one FMA and one multiply per hidden
+    # unit, per accepted flip three multiplies per hidden unit (lane-ops); peak = 148 SMs
+    # x 128 FP32 lanes x max SM clock.
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alg_ops = 2.0 * M * proposals_step + 3.0 * M * accepts_per_step
+    achieved = alg_ops / (ph[1] / 1e3) / 1e12
+    peak = n_sm * 128 * sm_max * 1e6 / 1e12
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "proposals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_dev / args.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": args.dtype,
+        "data": "synthetic (seeded random-init RBM, random initial spins)",
+        "config": {"workload": WL.name if (C, T) == (WL.n_chains, WL.n_sweeps) else f"{WL.name} (reduced: profiling)",
+                   "lattice": "10x10 periodic", "h": ham.h, "n_hidden": M,
+                   "chains": C, "sweeps": T, "burn_in": B, "samples": S, "params": P,
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"dp{world} (chains)"},
+        "local_energy": {"value": world * S / (ph[2] / 1e3), "unit": "samples/s", "kernel_ms": ph[2]},
+        "sweep": {"value": world * proposals_step / (ph[1] / 1e3), "unit": "proposals/s", "kernel_ms": ph[1],
+                  "acceptance": accepts_per_step / proposals_step},
+        "phases_ms": {"set_params+init": ph[0], "sweep": ph[1], "local_energy": ph[2],
+                      "stats+force": ph[3], "O_rows": ph[4]},
+        "roofline": {"bound": "alu", "kernel": "rbm_sweep_f32_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "note": "FP32-pipe lane-ops/s (FMA counted once) vs 148 SMs x 128 lanes x max SM clock"},
+        "e2e": {"value": world * proposals_step * args.steps / t_e2e, "unit": "proposals/s",
+                "h2d_bytes_per_step": P * 8, "d2h_bytes_per_step": (5 + P) * 8},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    return line
+
+
+def oracle_sample(n_chains, n_sweeps, eloc_samples):
+    """The FP64 oracle on a bounded sample of the same workload; returns rates."""
+    from threadpoolctl import threadpool_limits
+    from oracle.estimators import local_energy
+    from oracle.hamiltonian import make_hamiltonian
+    from oracle.models import RBM
+    from oracle.philox import init_spins_random
+    from oracle.sampler import mh_sweeps
+    lat = WL.ham.lattice
+    N, M = lat.n_sites, WL.n_hidden
+    model = RBM(N, M, workloads.rbm_params(N, M, WL.weight_sigma, WL.seed))
+    ham = make_hamiltonian(WL.ham)
+    with threadpool_limits(limits=1):
+        s0 = init_spins_random(WL.seed, np.arange(n_chains), N)
+        t0 = time.perf_counter()
+        out = mh_sweeps(model.logpsi, s0, np.arange(n_chains), WL.seed + 1, n_sweeps, 0)
+        t_sweep = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        local_energy(ham, model.logpsi, out["samples"][:eloc_samples])
+        t_eloc = time.perf_counter() - t0
+    return {"proposals_per_s": n_chains * n_sweeps * N / t_sweep,
+            "eloc_samples_per_s": eloc_samples / t_eloc, "t": t_sweep + t_eloc,
+            "sample": f"{n_chains} chains x {n_sweeps} sweeps of the 10x10 alpha=4 workload "
+                      f"(full re-evaluation per proposal) + local energy of {eloc_samples} samples"}
+
+
+def run_reference(args):
+    per = [oracle_sample(1024, 5, 512) for _ in range(args.warmup + args.steps)][args.warmup:]
+    v = statistics.median(p["proposals_per_s"] for p in per)
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "proposals/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WL.name},
+        "ms_per_step": statistics.median(p["t"] for p in per) * 1e3,
+        "local_energy": {"value": statistics.median(p["eloc_samples_per_s"] for p in per), "unit": "samples/s"},
+        "cpu_baseline": {"value": v, "unit": "proposals/s", "cores": 1, "kind": "oracle",
+                         "sample": per[0]["sample"]},
+        "e2e": {"value": v, "unit": "proposals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chains", type=int, default=0, help="profiling only: override the chain count")
+    ap.add_argument("--sweeps", type=int, default=0, help="profiling only: override the sweep count")
+    ap.add_argument("--burn-in", type=int, default=None, help="profiling only: override the burn-in")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", args.gpus))
+    rank = int(os.environ.get("RANK", 0))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        td.init_process_group("nccl")
+        dist = td
+    line = run_ours(args, rank, world, dist)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            cb = oracle_sample(1024, 8, 1024)
+            line["cpu_baseline"] = {"value": cb["proposals_per_s"], "unit": "proposals/s", "cores": 1,
+                                    "kind": "oracle", "sample": cb["sample"],
+                                    "local_energy_samples_per_s": cb["eloc_samples_per_s"]}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -117,8 +117,7 @@ def test_local_energy_matches_oracle():
     e = torch.empty(300, dtype=torch.float32, device="cuda")
     ctx.local_energy(to_words_tensor(pack_np(s)), e)
     ref = oracle_eloc(ham, model.logpsi, s)
-    scale = len(ham.bonds) * abs(ham.J) + abs(ham.h) * 100 * 2
-    np.testing.assert_allclose(e.cpu().numpy(), ref, rtol=0, atol=2e-5 * scale)
+    np.testing.assert_allclose(e.cpu().numpy(), ref, rtol=1e-5, atol=1e-5 * len(ham.bonds) * abs(ham.J))
 
 
 def test_local_energy_ragged_and_1d():
@@ -127,7 +126,8 @@ def test_local_energy_ragged_and_1d():
     e = torch.empty(65, dtype=torch.float32, device="cuda")
     ctx.local_energy(to_words_tensor(pack_np(s)), e)
     ref = oracle_eloc(ham, model.logpsi, s)
-    np.testing.assert_allclose(e.cpu().numpy(), ref, rtol=0, atol=2e-5 * (37 * 1.3 + 0.7 * 37 * 3))
+    # FP32 sum of N ratios: error relative to the size of the off-diagonal sum
+    np.testing.assert_allclose(e.cpu().numpy(), ref, rtol=1e-5, atol=1e-5 * 37 * 1.3)
 
 
 @pytest.mark.parametrize("Lx,Ly,M", [(16, 1, 16), (10, 10, 400), (7, 1, 33)])
@@ -191,19 +191,20 @@ def test_tfim_1d_n16_energy_against_exact_enumeration_and_ed():
 
 
 def test_histogram_tv_against_exact_distribution_4x4():
-    """4 x 4 TFIM, alpha = 4 RBM: total-variation distance of the GPU sample histogram
-    from the exact pi (enumeration of 2^16 states) is at the level of i.i.d. sampling noise."""
+    """4 x 4 TFIM, alpha = 4 RBM: the final configurations of 32768 independent chains
+    after 200 sweeps are compared with the exact pi (enumeration of 2^16 states).  Their
+    total-variation distance must be at the level of i.i.d. draws of the same count
+    (successive sweeps of one chain are correlated, so only one sample per chain is used)."""
     ctx, model, _ = make(4, 4, 64, 0.25, 13, h=3.04)
-    C, T, B = 4096, 60, 10
+    C, T = 32768, 200
     state = torch.zeros((C, 1), dtype=torch.int32, device="cuda")
     ctx.init_chains(state, 21)
-    S = torch.zeros(((T - B) * C, 1), dtype=torch.int32, device="cuda")
-    ctx.sweep(state, T, B, 22, 0, S)
-    idx = words_from_tensor(S)[:, 0].astype(np.int64)
+    ctx.sweep(state, T, T, 22, 0)
+    idx = words_from_tensor(state)[:, 0].astype(np.int64)
     hist = np.bincount(idx, minlength=2 ** 16) / idx.size
     pi = exact.exact_pi(model.logpsi, 16)
     tv = 0.5 * np.abs(hist - pi).sum()
     rng = np.random.default_rng(0)
-    floor = max(0.5 * np.abs(np.bincount(rng.choice(pi.size, idx.size, p=pi), minlength=pi.size) / idx.size - pi).sum()
-                for _ in range(3))
-    assert tv < 1.3 * floor + 0.005, (tv, floor)
+    floors = [0.5 * np.abs(np.bincount(rng.choice(pi.size, C, p=pi), minlength=pi.size) / C - pi).sum()
+              for _ in range(8)]
+    assert tv < max(floors) * 1.15, (tv, floors)
