@@ -231,9 +231,18 @@ def run_ours(args, rank, world, dist):
     return line
 
 
+def oracle_sample_subprocess(n_chains, n_sweeps, eloc_samples):
+    """oracle_sample in a fresh interpreter pinned to one BLAS / OpenMP thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json, bench; print(json.dumps(bench.oracle_sample(%d, %d, %d)))"
+            % (n_chains, n_sweeps, eloc_samples))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, check=True)
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def oracle_sample(n_chains, n_sweeps, eloc_samples):
     """The FP64 oracle on a bounded sample of the same workload; returns rates."""
-    from threadpoolctl import threadpool_limits
     from oracle.estimators import local_energy
     from oracle.hamiltonian import make_hamiltonian
     from oracle.models import RBM
@@ -243,14 +252,13 @@ def oracle_sample(n_chains, n_sweeps, eloc_samples):
     N, M = lat.n_sites, WL.n_hidden
     model = RBM(N, M, workloads.rbm_params(N, M, WL.weight_sigma, WL.seed))
     ham = make_hamiltonian(WL.ham)
-    with threadpool_limits(limits=1):
-        s0 = init_spins_random(WL.seed, np.arange(n_chains), N)
-        t0 = time.perf_counter()
-        out = mh_sweeps(model.logpsi, s0, np.arange(n_chains), WL.seed + 1, n_sweeps, 0)
-        t_sweep = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        local_energy(ham, model.logpsi, out["samples"][:eloc_samples])
-        t_eloc = time.perf_counter() - t0
+    s0 = init_spins_random(WL.seed, np.arange(n_chains), N)
+    t0 = time.perf_counter()
+    out = mh_sweeps(model.logpsi, s0, np.arange(n_chains), WL.seed + 1, n_sweeps, 0)
+    t_sweep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    local_energy(ham, model.logpsi, out["samples"][:eloc_samples])
+    t_eloc = time.perf_counter() - t0
     return {"proposals_per_s": n_chains * n_sweeps * N / t_sweep,
             "eloc_samples_per_s": eloc_samples / t_eloc, "t": t_sweep + t_eloc,
             "sample": f"{n_chains} chains x {n_sweeps} sweeps of the 10x10 alpha=4 workload "
@@ -258,7 +266,7 @@ def oracle_sample(n_chains, n_sweeps, eloc_samples):
 
 
 def run_reference(args):
-    per = [oracle_sample(1024, 5, 512) for _ in range(args.warmup + args.steps)][args.warmup:]
+    per = [oracle_sample_subprocess(1024, 5, 512) for _ in range(args.warmup + args.steps)][args.warmup:]
     v = statistics.median(p["proposals_per_s"] for p in per)
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "proposals/s", "n_gpus": 1,
@@ -303,7 +311,7 @@ def main():
     line = run_ours(args, rank, world, dist)
     if rank == 0:
         if not args.no_cpu_baseline:
-            cb = oracle_sample(1024, 8, 1024)
+            cb = oracle_sample_subprocess(1024, 8, 1024)
             line["cpu_baseline"] = {"value": cb["proposals_per_s"], "unit": "proposals/s", "cores": 1,
                                     "kind": "oracle", "sample": cb["sample"],
                                     "local_energy_samples_per_s": cb["eloc_samples_per_s"]}
