@@ -171,6 +171,20 @@ nqs_status nqs_stats(nqs_ctx *ctx, const float *eloc, int64_t n, int64_t n_chain
                      const int64_t *n_accepted, int64_t proposals_per_chain, double *out,
                      nqs_stream stream);
 
+/* No counterpart in the paper.  The force F of nqs_logpsi_grad (same arguments and
+ * result, no O rows) for callers that cannot allocate device memory when they need
+ * it: code running under another framework's memory budget, plugins whose host
+ * forbids allocation after start-up, or loops that must never reach an allocator.
+ * It takes no workspace: its scratch is a built-in 32 MiB device array that every
+ * GPU loading this library keeps until the process exits, so models with more than
+ * 4,194,304 parameters are rejected with NQS_EINVAL.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  The context's device must be current.  All calls share
+ * the one array, so calls whose kernels overlap on the GPU (different streams, or
+ * different contexts on one device) race; serialise them.  Allocates nothing. */
+nqs_status nqs_force_noalloc(nqs_ctx *ctx, const uint32_t *configs, int64_t n, const float *eloc,
+                             const double *stats, double *force, nqs_stream stream);
+
 /* Reads and clears the sticky device status word (synchronises the stream).
  * NQS_OK, NQS_EINVAL (a value left the documented range) or NQS_ETIMEOUT. */
 nqs_status nqs_check_status(nqs_ctx *ctx, nqs_stream stream);

@@ -70,6 +70,7 @@ _SIGS = {
     "nqs_logpsi_grad": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nqs_stats": (_i32, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp]),
     "nqs_check_status": (_i32, [_vp, _vp]),
+    "nqs_force_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -185,6 +186,14 @@ class Context:
                                    _ptr(n_accepted, (torch.int64,), "n_accepted", (n_chains,)),
                                    int(proposals_per_chain), _ptr(out, (torch.float64,), "out", (5,), False),
                                    _stream()))
+
+    def force_noalloc(self, configs, eloc, stats, force):
+        """nqs_force_noalloc: the force without a workspace (built-in device scratch)."""
+        n = configs.shape[0]
+        self._check(_lib.nqs_force_noalloc(
+            self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
+            _ptr(eloc, (torch.float32,), "eloc", (n,), False), _ptr(stats, (torch.float64,), "stats", None, False),
+            _ptr(force, (torch.float64,), "force", (self.P,), False), _stream()))
 
     def check_status(self):
         self._check(_lib.nqs_check_status(self._h, _stream()))

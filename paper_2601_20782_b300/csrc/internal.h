@@ -66,6 +66,9 @@ size_t rbm_grad_workspace(const nqs_ctx *c, int64_t n);
 cudaError_t rbm_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
                             const double *stats, double *force, void *ws, cudaStream_t s);
 bool rbm_supported(const nqs_ctx *c, std::string *why);
+int rbm_force_chunks(const nqs_ctx *c, int64_t n);
+cudaError_t rbm_force_into(const nqs_ctx *c, const uint32_t *cfg, int64_t n, const float *eloc, const double *stats,
+                           double *force, double *scratch, int chunks, cudaStream_t s);
 
 // stats.cu
 cudaError_t energy_stats(const nqs_ctx *c, const float *eloc, int64_t n, int64_t n_chains,

@@ -809,6 +809,23 @@ cudaError_t rbm_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n, f
   return dispatch_le<ElocRun>(L, c->M_pad / L, c, cfg, n, eloc, s);
 }
 
+int rbm_force_chunks(const nqs_ctx *c, int64_t n) { return force_chunks(c, n); }
+
+cudaError_t rbm_force_into(const nqs_ctx *c, const uint32_t *cfg, int64_t n, const float *eloc, const double *stats,
+                           double *force, double *scratch, int chunks, cudaStream_t s) {
+  const int jt = (c->M + FT_J - 1) / FT_J;
+  const size_t shm = (size_t)(c->N * FT_J + 2 * FT_BATCH * c->N + FT_BATCH * FT_J + FT_BATCH) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(rbm_force_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)shm);
+  if (e != cudaSuccess) return e;
+  rbm_force_partial_kernel<<<dim3(jt, chunks), FT_THREADS, shm, s>>>(cfg, n, eloc, stats, c->d_Wm, c->d_bm, c->N,
+                                                                     c->W, c->M, c->P, chunks, scratch);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int rb = (int)std::min<int64_t>((c->P + 255) / 256, (int64_t)c->num_sms * 8);
+  force_reduce_kernel<<<rb, 256, 0, s>>>(scratch, chunks, c->P, n, force);
+  return cudaGetLastError();
+}
+
 size_t rbm_grad_workspace(const nqs_ctx *c, int64_t n) {
   return (size_t)force_chunks(c, n) * (size_t)c->P * sizeof(double);
 }
