@@ -185,6 +185,16 @@ nqs_status nqs_stats(nqs_ctx *ctx, const float *eloc, int64_t n, int64_t n_chain
 nqs_status nqs_force_noalloc(nqs_ctx *ctx, const uint32_t *configs, int64_t n, const float *eloc,
                              const double *stats, double *force, nqs_stream stream);
 
+/* Self-test of the tensor-core building block used by the contraction kernels (no
+ * counterpart in the paper): D [128 x N] FP32 = A [128 x K] * B [N x K]^T in BF16 with FP32
+ * accumulation, one CTA.  flags bit 0: A is passed transposed ([K x 128]) and staged
+ * MN-major; bit 1: B is passed transposed ([K x N]) and staged MN-major; otherwise both
+ * are row-major with K contiguous and staged K-major.  16 <= N <= 256 (multiple of 16),
+ * 64 <= K <= 256 (multiple of 64).  *status (device int) gets the timeout bit if the MMA
+ * never completed. */
+nqs_status nqs_selftest_tc_gemm(const uint16_t *A, const uint16_t *B, float *D, int32_t N, int32_t K,
+                                int32_t flags, int32_t *status, nqs_stream stream);
+
 /* Reads and clears the sticky device status word (synchronises the stream).
  * NQS_OK, NQS_EINVAL (a value left the documented range) or NQS_ETIMEOUT. */
 nqs_status nqs_check_status(nqs_ctx *ctx, nqs_stream stream);

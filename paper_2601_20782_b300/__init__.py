@@ -71,6 +71,7 @@ _SIGS = {
     "nqs_stats": (_i32, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp]),
     "nqs_check_status": (_i32, [_vp, _vp]),
     "nqs_force_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "nqs_selftest_tc_gemm": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -197,6 +198,23 @@ class Context:
 
     def check_status(self):
         self._check(_lib.nqs_check_status(self._h, _stream()))
+
+
+def selftest_tc_gemm(A, B, a_transposed=False, b_transposed=False):
+    """D = A B^T on the tensor cores (tcgen05).  A [128 x K] (or [K x 128] when a_transposed),
+    B [N x K] (or [K x N] when b_transposed), BF16 CUDA tensors."""
+    K = A.shape[0] if a_transposed else A.shape[1]
+    N = B.shape[1] if b_transposed else B.shape[0]
+    D = torch.empty((128, N), dtype=torch.float32, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    st = _lib.nqs_selftest_tc_gemm(_ptr(A, (torch.bfloat16,), "A", (K, 128) if a_transposed else (128, K), False),
+                                   _ptr(B, (torch.bfloat16,), "B", (K, N) if b_transposed else (N, K), False),
+                                   _ptr(D, (torch.float32,), "D"), N, K,
+                                   int(a_transposed) | (int(b_transposed) << 1),
+                                   _ptr(status, (torch.int32,), "status"), _stream())
+    if st != NQS_OK:
+        raise NQSError(st, "nqs_selftest_tc_gemm failed")
+    return D, status
 
 
 def pack_spins(s):
