@@ -67,6 +67,11 @@ cudaError_t rbm_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, fl
                             const double *stats, double *force, void *ws, cudaStream_t s);
 bool rbm_supported(const nqs_ctx *c, std::string *why);
 int rbm_force_chunks(const nqs_ctx *c, int64_t n);
+// force_tc.cu
+bool rbm_force_tc_supported(const nqs_ctx *c);
+int rbm_force_tc_chunks(const nqs_ctx *c, int64_t n);
+cudaError_t rbm_force_tc(const nqs_ctx *c, const uint32_t *cfg, int64_t n, const float *eloc, const double *stats,
+                         double *ws, int chunks, cudaStream_t s);
 cudaError_t rbm_force_into(const nqs_ctx *c, const uint32_t *cfg, int64_t n, const float *eloc, const double *stats,
                            double *force, double *scratch, int chunks, cudaStream_t s);
 

@@ -827,7 +827,8 @@ cudaError_t rbm_force_into(const nqs_ctx *c, const uint32_t *cfg, int64_t n, con
 }
 
 size_t rbm_grad_workspace(const nqs_ctx *c, int64_t n) {
-  return (size_t)force_chunks(c, n) * (size_t)c->P * sizeof(double);
+  const int chunks = rbm_force_tc_supported(c) ? rbm_force_tc_chunks(c, n) : force_chunks(c, n);
+  return (size_t)chunks * (size_t)c->P * sizeof(double);
 }
 
 cudaError_t rbm_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
@@ -838,6 +839,14 @@ cudaError_t rbm_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, fl
     rbm_grad_rows_kernel<<<(unsigned)blocks, 256, shm, s>>>(cfg, n, c->d_Wm, c->d_bm, c->N, c->W, c->M, c->P, O);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  }
+  if (force && rbm_force_tc_supported(c)) {  // tensor-core path (N <= 127)
+    const int chunks = rbm_force_tc_chunks(c, n);
+    cudaError_t e = rbm_force_tc(c, cfg, n, eloc, stats, (double *)ws, chunks, s);
+    if (e != cudaSuccess) return e;
+    const int rb = (int)std::min<int64_t>((c->P + 255) / 256, (int64_t)c->num_sms * 8);
+    force_reduce_kernel<<<rb, 256, 0, s>>>((const double *)ws, chunks, c->P, n, force);
+    return cudaGetLastError();
   }
   if (force) {
     const int chunks = force_chunks(c, n);

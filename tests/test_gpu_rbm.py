@@ -150,6 +150,41 @@ def test_logpsi_grad_rows_and_force_match_oracle(Lx, Ly, M):
     np.testing.assert_allclose(force.cpu().numpy(), Fref, rtol=0, atol=1e-5 * max(1.0, np.abs(Fref).max()))
 
 
+def _oracle_force_blocked(model, s, eps, block=50000):
+    """F = mean(O (eps - E)) of the RBM without materialising O (same definition, blocked)."""
+    e = eps - eps.mean()
+    Fa = np.zeros(model.N); Fb = np.zeros(model.M); FW = np.zeros((model.M, model.N))
+    for b0 in range(0, len(s), block):
+        sb = s[b0:b0 + block].astype(np.float64)
+        eb = e[b0:b0 + block]
+        t = np.tanh(model.theta(sb))
+        Fa += sb.T @ eb
+        Fb += t.T @ eb
+        FW += (t * eb[:, None]).T @ sb
+    n = len(s)
+    return np.concatenate([Fa / n, Fb / n, (FW / n).ravel()])
+
+
+def test_force_many_tiles_matches_oracle():
+    """600k rows of the 10x10 alpha = 4 shape: every block accumulates > 64 tiles, so the
+    periodic FP64 drain of the tensor-core accumulator is exercised."""
+    ctx, model, _ = make(10, 10, 400, 0.05, 17)
+    n = 600_000
+    rng = np.random.default_rng(18)
+    s = rng.choice([-1, 1], size=(n, 100)).astype(np.int8)
+    eps = rng.normal(-310.0, 5.0, n).astype(np.float32)
+    cfg = to_words_tensor(pack_np(s))
+    eloc = torch.from_numpy(eps).cuda()
+    stats = torch.empty(5, dtype=torch.float64, device="cuda")
+    ctx.stats(eloc, n, stats)
+    force = torch.empty(ctx.P, dtype=torch.float64, device="cuda")
+    ws = torch.empty(ctx.logpsi_grad_workspace(n), dtype=torch.uint8, device="cuda")
+    ctx.logpsi_grad(cfg, None, eloc, stats, force, ws)
+    ref = _oracle_force_blocked(model, s, eps.astype(np.float64))
+    got = force.cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+
+
 def test_stats_match_oracle_and_acceptance():
     p = nqs()
     ctx, _, _ = make(16, 1, 16, 0.1, 1)
