@@ -131,7 +131,42 @@ __global__ void init_balanced_kernel(uint32_t *state, int64_t C, int N, int W, u
 }
 
 // ------------------------------------------------------------------------------------
-// per-chain cache helpers (L lanes per chain, E hidden units per lane: j = e * L + gl)
+// per-chain cache helpers.  L lanes per chain, E hidden units per lane.  Lane gl owns
+// units j = 4 (v L + gl) + c for v < E / 4, c < 4 (read as one 16-byte vector), and
+// j = 4 (E / 4) L + t L + gl for the E % 4 tail units.
+template <int L, int E>
+struct Lay {
+  static constexpr int V = E / 4, T = E % 4;
+  __device__ static __forceinline__ int j(int e, int gl) {
+    return e < 4 * V ? 4 * ((e >> 2) * L + gl) + (e & 3) : 4 * V * L + (e - 4 * V) * L + gl;
+  }
+  // row[j] for the lane's units, from shared or global memory
+  __device__ static __forceinline__ void load(const float *row, int gl, float (&r)[E]) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float4 q = *reinterpret_cast<const float4 *>(row + 4 * (v * L + gl));
+      r[4 * v] = q.x;
+      r[4 * v + 1] = q.y;
+      r[4 * v + 2] = q.z;
+      r[4 * v + 3] = q.w;
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) r[4 * V + t] = row[4 * V * L + t * L + gl];
+  }
+  __device__ static __forceinline__ void load_ldg(const float *row, int gl, float (&r)[E]) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float4 q = __ldg(reinterpret_cast<const float4 *>(row + 4 * (v * L + gl)));
+      r[4 * v] = q.x;
+      r[4 * v + 1] = q.y;
+      r[4 * v + 2] = q.z;
+      r[4 * v + 3] = q.w;
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) r[4 * V + t] = __ldg(row + 4 * V * L + t * L + gl);
+  }
+};
+
 __device__ __forceinline__ void sigmoid_pair(float th, float &lam, float &mu) {
   const float e = expf(-2.f * fabsf(th));
   const float p = 1.f / (1.f + e);
@@ -143,16 +178,16 @@ __device__ __forceinline__ void sigmoid_pair(float th, float &lam, float &mu) {
 template <int L, int E>
 __device__ __forceinline__ void compute_theta(float (&th)[E], uint32_t sw, const float *__restrict__ Wt,
                                               const float *__restrict__ b, int N, int W, int M_pad, int gl) {
-#pragma unroll
-  for (int e = 0; e < E; ++e) th[e] = b[e * L + gl];
+  Lay<L, E>::load_ldg(b, gl, th);
   for (int wi = 0; wi < W; ++wi) {
     const uint32_t word = __shfl_sync(FULL_MASK, sw, wi, L);
     const int nb = min(32, N - 32 * wi);
     for (int bit = 0; bit < nb; ++bit) {
       const float s = ((word >> bit) & 1u) ? 1.f : -1.f;
-      const float *row = Wt + (size_t)(32 * wi + bit) * M_pad + gl;
+      float w[E];
+      Lay<L, E>::load_ldg(Wt + (size_t)(32 * wi + bit) * M_pad, gl, w);
 #pragma unroll
-      for (int e = 0; e < E; ++e) th[e] = fmaf(s, __ldg(row + e * L), th[e]);
+      for (int e = 0; e < E; ++e) th[e] = fmaf(s, w[e], th[e]);
     }
   }
 }
@@ -188,9 +223,13 @@ __device__ __forceinline__ float cache_logpsi(const float (&lam)[E], const float
   return visible_term<L>(sw, aK, N, gl) - 0.5f * LN2F * group_allsum<L>(part);
 }
 
-// sum_j log2 g_j over the group, products of up to 8 factors per MUFU lg2.  A
-// product that leaves the normal FP32 range makes the sum non-finite; the group
-// then recomputes with one accurate log per factor.
+// sum_j log2 g_j over the group, products of up to 8 factors per MUFU lg2.
+// With one chain per warp the lane partials are added exactly as 2^-20 fixed-point
+// integers by one redux.sync (a 32-lane sum in one instruction instead of a 5-stage
+// shuffle tree); each partial is rounded to 2^-21, so the sum carries at most
+// 32 * 2^-21 absolute error in log2 units.  A product that leaves the normal FP32
+// range, or a partial beyond +-2^10, sends the group to the exact path: one accurate
+// log per factor and a floating-point butterfly.
 template <int L, int E>
 __device__ __forceinline__ float sum_log2(const float (&g)[E]) {
   float part = 0.f;
@@ -201,16 +240,20 @@ __device__ __forceinline__ float sum_log2(const float (&g)[E]) {
     for (int e = e0 + 1; e < (e0 + 8 < E ? e0 + 8 : E); ++e) pr *= g[e];
     part += lg2_approx(pr);
   }
-  float tot = group_allsum<L>(part);
-  const bool bad = !isfinite(tot);
-  if (__any_sync(FULL_MASK, bad)) {
-    float p2 = 0.f;
-#pragma unroll
-    for (int e = 0; e < E; ++e) p2 += log2f(g[e]);
-    p2 = group_allsum<L>(p2);
-    if (bad) tot = p2;
+  if constexpr (L == 32) {
+    const bool bad = !(fabsf(part) < 1024.f);  // also catches inf / nan
+    if (!__any_sync(FULL_MASK, bad)) {
+      const int q = __float2int_rn(part * 1048576.f);
+      return (float)__reduce_add_sync(FULL_MASK, q) * 9.5367431640625e-7f;
+    }
+  } else {
+    const float tot = group_allsum<L>(part);
+    if (!__any_sync(FULL_MASK, !isfinite(tot))) return tot;
   }
-  return tot;
+  float p2 = 0.f;
+#pragma unroll
+  for (int e = 0; e < E; ++e) p2 += log2f(g[e]);
+  return group_allsum<L>(p2);
 }
 
 // Loads the [N][M_pad] table into shared memory with 1D bulk copies.  Returns false
@@ -253,6 +296,13 @@ struct SweepParams {
   uint32_t sweep_offset, k0, k1;
 };
 
+// log u for u = k 2^-24 (k = 0 gives -inf: always accept).  Accepting iff
+// 2 dlogpsi > log u is the rule u < exp(2 dlogpsi).
+__device__ __forceinline__ float log_uniform(uint32_t w) {
+  const uint32_t k = w >> 8;
+  return k == 0u ? -INFINITY : logf((float)k * 5.9604644775390625e-8f);
+}
+
 // One group of L lanes runs one chain for all sweeps; the block shares one copy of
 // the R table in shared memory (or reads it through L2 when it does not fit).
 template <int L, int E, bool SMEM>
@@ -291,19 +341,17 @@ __global__ void __launch_bounds__(max_threads_for(E), 1) rbm_sweep_f32_kernel(co
       for (int p0 = 0; p0 < N; p0 += 2 * L) {
         const uint4 w = philox4x32_10(make_uint4((uint32_t)(p0 / 2 + gl), sweep_id, (uint32_t)cc, TAG_SWEEP),
                                       p.k0, p.k1);
-        const uint32_t site0 = index_from_word(w.x, (uint32_t)N), u0 = w.y >> 8;
-        const uint32_t site1 = index_from_word(w.z, (uint32_t)N), u1 = w.w >> 8;
+        const uint32_t site0 = index_from_word(w.x, (uint32_t)N), site1 = index_from_word(w.z, (uint32_t)N);
+        const float thr0 = log_uniform(w.y), thr1 = log_uniform(w.w);
         const int np = min(2 * L, N - p0);
         for (int q = 0; q < np; ++q) {
           const int src = q >> 1;
           const uint32_t site = __shfl_sync(FULL_MASK, (q & 1) ? site1 : site0, src, L);
-          const uint32_t ub = __shfl_sync(FULL_MASK, (q & 1) ? u1 : u0, src, L);
+          const float thr = __shfl_sync(FULL_MASK, (q & 1) ? thr1 : thr0, src, L);
           const uint32_t word = __shfl_sync(FULL_MASK, sw, site >> 5, L);
           const bool up = (word >> (site & 31)) & 1u;
-          const float *row = R + (size_t)site * M_pad + gl;
           float rv[E], g[E];
-#pragma unroll
-          for (int e = 0; e < E; ++e) rv[e] = row[e * L];
+          Lay<L, E>::load(R + (size_t)site * M_pad, gl, rv);
           if (up) {
 #pragma unroll
             for (int e = 0; e < E; ++e) g[e] = fmaf(lam[e], rv[e], mu[e]);
@@ -314,8 +362,7 @@ __global__ void __launch_bounds__(max_threads_for(E), 1) rbm_sweep_f32_kernel(co
           const float tot = sum_log2<L, E>(g);
           const float2 ak = saK[site];
           const float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F;
-          const float x = 2.f * dlt;
-          const bool acc = (x >= 0.f) || (ub == 0u) || ((float)ub * 5.9604644775390625e-8f < expf(x));
+          const bool acc = 2.f * dlt > thr;
           if (acc) {
             if (up) {
 #pragma unroll
@@ -432,14 +479,14 @@ __global__ void __launch_bounds__(max_threads_for(E), 1) rbm_tfim_eloc_kernel(co
     for (int i = 0; i < N; ++i) {
       const uint32_t word = __shfl_sync(FULL_MASK, sw, i >> 5, L);
       const bool up = (word >> (i & 31)) & 1u;
-      const float *row = R + (size_t)i * M_pad + gl;
-      float g[E];
+      float rv[E], g[E];
+      Lay<L, E>::load(R + (size_t)i * M_pad, gl, rv);
       if (up) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) g[e] = fmaf(lam[e], row[e * L], mu[e]);
+        for (int e = 0; e < E; ++e) g[e] = fmaf(lam[e], rv[e], mu[e]);
       } else {
 #pragma unroll
-        for (int e = 0; e < E; ++e) g[e] = fmaf(mu[e], row[e * L], lam[e]);
+        for (int e = 0; e < E; ++e) g[e] = fmaf(mu[e], rv[e], lam[e]);
       }
       const float tot = sum_log2<L, E>(g);
       const float2 ak = saK[i];
@@ -614,16 +661,28 @@ __global__ void force_reduce_kernel(const double *ws, int n_chunks, int64_t P, i
 }
 
 // ------------------------------------------------------------------------------------
-// dispatch over (L, E)
+// dispatch over (L, E): L = 32 for every instantiated width; L = 16 and L = 8 variants
+// (two or four chains per warp) for the widths the tuner may pick.
 template <template <int, int> class F, typename... A>
 cudaError_t dispatch_le(int L, int E, A... args) {
 #define NQS_CASE(LL, EE) \
   if (L == LL && E == EE) return F<LL, EE>::run(args...);
-  NQS_CASE(8, 4) NQS_CASE(16, 2) NQS_CASE(16, 4)
+  NQS_CASE(8, 4) NQS_CASE(16, 2) NQS_CASE(16, 4) NQS_CASE(16, 8) NQS_CASE(16, 16) NQS_CASE(16, 26)
+  NQS_CASE(16, 28) NQS_CASE(16, 32)
   NQS_CASE(32, 1) NQS_CASE(32, 2) NQS_CASE(32, 3) NQS_CASE(32, 4) NQS_CASE(32, 5) NQS_CASE(32, 6)
   NQS_CASE(32, 7) NQS_CASE(32, 8) NQS_CASE(32, 9) NQS_CASE(32, 10) NQS_CASE(32, 11) NQS_CASE(32, 12)
   NQS_CASE(32, 13) NQS_CASE(32, 14) NQS_CASE(32, 16) NQS_CASE(32, 18) NQS_CASE(32, 20) NQS_CASE(32, 24)
   NQS_CASE(32, 28) NQS_CASE(32, 32)
+#undef NQS_CASE
+  return cudaErrorInvalidConfiguration;
+}
+template <template <int, int> class F, typename... A>
+cudaError_t dispatch_l32(int E, A... args) {
+#define NQS_CASE(EE) \
+  if (E == EE) return F<32, EE>::run(args...);
+  NQS_CASE(1) NQS_CASE(2) NQS_CASE(3) NQS_CASE(4) NQS_CASE(5) NQS_CASE(6) NQS_CASE(7) NQS_CASE(8) NQS_CASE(9)
+  NQS_CASE(10) NQS_CASE(11) NQS_CASE(12) NQS_CASE(13) NQS_CASE(14) NQS_CASE(16) NQS_CASE(18) NQS_CASE(20)
+  NQS_CASE(24) NQS_CASE(28) NQS_CASE(32)
 #undef NQS_CASE
   return cudaErrorInvalidConfiguration;
 }
@@ -638,11 +697,13 @@ bool e_instantiated(int E32) {
   }
 }
 
-// Lanes per chain: one chain per warp unless the hidden layer is tiny.
+bool l16_instantiated(int E32) { return E32 == 1 || E32 == 2 || E32 == 4 || E32 == 8 || E32 == 13 || E32 == 14 || E32 == 16; }
+
+// Lanes per chain of the sweep and local-energy kernels.
 int pick_lanes(const nqs_ctx *c) {
   const int E32 = c->M_pad / 32;
   if (c->chains_per_warp == 4 && E32 == 1 && c->W <= 8) return 8;
-  if (c->chains_per_warp == 2 && E32 <= 2 && c->W <= 16) return 16;
+  if (c->chains_per_warp == 2 && l16_instantiated(E32) && c->W <= 16) return 16;
   if (c->chains_per_warp == 0 && E32 == 1 && c->W <= 8) return 8;
   return 32;
 }
@@ -800,8 +861,7 @@ cudaError_t rbm_sweep(const nqs_ctx *c, uint32_t *state, int64_t n_chains, int n
 }
 
 cudaError_t rbm_logpsi(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *out, cudaStream_t s) {
-  const int L = pick_lanes(c);
-  return dispatch_le<LogpsiRun>(L, c->M_pad / L, c, cfg, n, out, s);
+  return dispatch_l32<LogpsiRun>(c->M_pad / 32, c, cfg, n, out, s);
 }
 
 cudaError_t rbm_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *eloc, cudaStream_t s) {

@@ -84,6 +84,8 @@ def _lockstep(Lx, Ly, M, sigma, C, T, burn, seed=99, offset=0, refresh=None, cpw
     (16, 1, 16, 0.3, 300, 12, 2, 1),           # one chain per warp, ragged chain count
     (37, 1, 50, 0.25, 301, 7, 3, None),        # ragged N (two words), padded hidden units
     (10, 10, 400, 0.05, 64, 3, 1, None),       # the 10 x 10, alpha = 4 shape
+    (10, 10, 400, 0.05, 70, 3, 1, 2),          # same, two chains per warp (16 lanes each)
+    (12, 1, 40, 0.3, 99, 5, 1, 2),             # two chains per warp, E = 4 per lane, ragged chains
 ])
 def test_sweep_lockstep_with_oracle(Lx, Ly, M, sigma, C, T, burn, cpw):
     _, model, ref, state, samples, logpsi, nacc, acc = _lockstep(Lx, Ly, M, sigma, C, T, burn, cpw=cpw)
