@@ -33,13 +33,16 @@ namespace {
 
 constexpr uint32_t BULK_CHUNK = 32768;
 
-// Threads per CTA bound for E cached units per lane: the register budget grows
-// with E (four E-wide arrays live across a proposal), about 4 E + 48 per thread.
-constexpr int max_threads_for(int E) {
-  int w = 65536 / (32 * (4 * E + 56));
+// Threads per CTA bound for E cached units per lane (register budget per thread).
+constexpr int threads_for_regs(int regs) {
+  int w = 65536 / (32 * regs);
   w = w < 2 ? 2 : (w > 32 ? 32 : w);
   return 32 * w;
 }
+// sweep: the cache pairs stay live, the row and the factors are streamed
+constexpr int sweep_threads(int E) { return threads_for_regs(2 * E + 56); }
+// local energy: the cache plus two sites' rows and factors in flight
+constexpr int eloc_threads(int E) { return threads_for_regs(3 * E + 48); }
 constexpr uint32_t WAIT_POLLS = 1u << 22;
 
 // ------------------------------------------------------------------------------------
@@ -131,39 +134,52 @@ __global__ void init_balanced_kernel(uint32_t *state, int64_t C, int N, int W, u
 }
 
 // ------------------------------------------------------------------------------------
-// per-chain cache helpers.  L lanes per chain, E hidden units per lane.  Lane gl owns
-// units j = 4 (v L + gl) + c for v < E / 4, c < 4 (read as one 16-byte vector), and
-// j = 4 (E / 4) L + t L + gl for the E % 4 tail units.
+// Paired FP32 arithmetic (fma.rn.f32x2 / mul.rn.f32x2, sm_100 family): two FP32
+// operations per issued instruction, each rounded as its scalar counterpart.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+// ------------------------------------------------------------------------------------
+// Per-chain cache layout.  L lanes per chain, E hidden units per lane held as H = ceil(E/2)
+// float2 pairs.  Lane gl owns units j = 4 (v L + gl) + c for v < E / 4, c < 4 (one 16-byte
+// vector), and j = 4 (E / 4) L + t L + gl for the E % 4 tail units.  For odd E the last
+// pair's second slot is a dummy unit with lam = mu = 1/2 and R = 1, which contributes
+// exactly nothing (g = 1) and stays unchanged by updates.
 template <int L, int E>
 struct Lay {
-  static constexpr int V = E / 4, T = E % 4;
-  __device__ static __forceinline__ int j(int e, int gl) {
-    return e < 4 * V ? 4 * ((e >> 2) * L + gl) + (e & 3) : 4 * V * L + (e - 4 * V) * L + gl;
-  }
-  // row[j] for the lane's units, from shared or global memory
-  __device__ static __forceinline__ void load(const float *row, int gl, float (&r)[E]) {
+  static constexpr int V = E / 4, T = E % 4, H = (E + 1) / 2;
+  // row[j] for the lane's units into pairs; `pad` fills the dummy slot
+  template <bool LDG>
+  __device__ static __forceinline__ void load(const float *row, int gl, float2 (&r)[H], float pad) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      const float4 q = *reinterpret_cast<const float4 *>(row + 4 * (v * L + gl));
-      r[4 * v] = q.x;
-      r[4 * v + 1] = q.y;
-      r[4 * v + 2] = q.z;
-      r[4 * v + 3] = q.w;
+      const float4 *p4 = reinterpret_cast<const float4 *>(row + 4 * (v * L + gl));
+      const float4 q = LDG ? __ldg(p4) : *p4;
+      r[2 * v] = make_float2(q.x, q.y);
+      r[2 * v + 1] = make_float2(q.z, q.w);
     }
-#pragma unroll
-    for (int t = 0; t < T; ++t) r[4 * V + t] = row[4 * V * L + t * L + gl];
-  }
-  __device__ static __forceinline__ void load_ldg(const float *row, int gl, float (&r)[E]) {
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const float4 q = __ldg(reinterpret_cast<const float4 *>(row + 4 * (v * L + gl)));
-      r[4 * v] = q.x;
-      r[4 * v + 1] = q.y;
-      r[4 * v + 2] = q.z;
-      r[4 * v + 3] = q.w;
+    const float *tail = row + 4 * V * L + gl;
+    auto ld = [&](int t) { return LDG ? __ldg(tail + t * L) : tail[t * L]; };
+    if constexpr (T == 1) r[2 * V] = make_float2(ld(0), pad);
+    if constexpr (T == 2) r[2 * V] = make_float2(ld(0), ld(1));
+    if constexpr (T == 3) {
+      r[2 * V] = make_float2(ld(0), ld(1));
+      r[2 * V + 1] = make_float2(ld(2), pad);
     }
-#pragma unroll
-    for (int t = 0; t < T; ++t) r[4 * V + t] = __ldg(row + 4 * V * L + t * L + gl);
   }
 };
 
@@ -176,29 +192,34 @@ __device__ __forceinline__ void sigmoid_pair(float th, float &lam, float &mu) {
 }
 
 template <int L, int E>
-__device__ __forceinline__ void compute_theta(float (&th)[E], uint32_t sw, const float *__restrict__ Wt,
+__device__ __forceinline__ void compute_theta(float2 (&th)[Lay<L, E>::H], uint32_t sw, const float *__restrict__ Wt,
                                               const float *__restrict__ b, int N, int W, int M_pad, int gl) {
-  Lay<L, E>::load_ldg(b, gl, th);
+  using LY = Lay<L, E>;
+  LY::template load<true>(b, gl, th, 0.f);
   for (int wi = 0; wi < W; ++wi) {
     const uint32_t word = __shfl_sync(FULL_MASK, sw, wi, L);
     const int nb = min(32, N - 32 * wi);
     for (int bit = 0; bit < nb; ++bit) {
       const float s = ((word >> bit) & 1u) ? 1.f : -1.f;
-      float w[E];
-      Lay<L, E>::load_ldg(Wt + (size_t)(32 * wi + bit) * M_pad, gl, w);
+      float2 w[LY::H];
+      LY::template load<true>(Wt + (size_t)(32 * wi + bit) * M_pad, gl, w, 0.f);
+      const float2 s2 = make_float2(s, s);
 #pragma unroll
-      for (int e = 0; e < E; ++e) th[e] = fmaf(s, w[e], th[e]);
+      for (int k = 0; k < LY::H; ++k) th[k] = fma2(s2, w[k], th[k]);
     }
   }
 }
 
 template <int L, int E>
-__device__ __forceinline__ void build_cache(float (&lam)[E], float (&mu)[E], uint32_t sw, const float *Wt,
-                                            const float *b, int N, int W, int M_pad, int gl) {
-  float th[E];
+__device__ __forceinline__ void build_cache(float2 (&lam)[Lay<L, E>::H], float2 (&mu)[Lay<L, E>::H], uint32_t sw,
+                                            const float *Wt, const float *b, int N, int W, int M_pad, int gl) {
+  float2 th[Lay<L, E>::H];
   compute_theta<L, E>(th, sw, Wt, b, N, W, M_pad, gl);
 #pragma unroll
-  for (int e = 0; e < E; ++e) sigmoid_pair(th[e], lam[e], mu[e]);
+  for (int k = 0; k < Lay<L, E>::H; ++k) {
+    sigmoid_pair(th[k].x, lam[k].x, mu[k].x);
+    sigmoid_pair(th[k].y, lam[k].y, mu[k].y);
+  }
 }
 
 // sum_i a_i s_i over the group (every lane gets the same value)
@@ -215,30 +236,99 @@ __device__ __forceinline__ float visible_term(uint32_t sw, const float2 *aK, int
 
 // log psi from the cache: sum_i a_i s_i - 1/2 sum_j log(4 lam_j mu_j)
 template <int L, int E>
-__device__ __forceinline__ float cache_logpsi(const float (&lam)[E], const float (&mu)[E], uint32_t sw,
-                                              const float2 *aK, int N, int gl) {
+__device__ __forceinline__ float cache_logpsi(const float2 (&lam)[Lay<L, E>::H], const float2 (&mu)[Lay<L, E>::H],
+                                              uint32_t sw, const float2 *aK, int N, int gl) {
   float part = 0.f;
 #pragma unroll
-  for (int e = 0; e < E; ++e) part += log2f(4.f * lam[e] * mu[e]);
+  for (int k = 0; k < Lay<L, E>::H; ++k)
+    part += log2f(4.f * lam[k].x * mu[k].x) + log2f(4.f * lam[k].y * mu[k].y);
   return visible_term<L>(sw, aK, N, gl) - 0.5f * LN2F * group_allsum<L>(part);
 }
 
-// sum_j log2 g_j over the group, products of up to 8 factors per MUFU lg2.
+// g for a flip of a site with spin `up`: mu + lam R (up) or lam + mu R (down)
+template <int H>
+__device__ __forceinline__ void flip_factors(bool up, const float2 (&lam)[H], const float2 (&mu)[H],
+                                             const float2 (&rv)[H], float2 (&g)[H]) {
+  if (up) {
+#pragma unroll
+    for (int k = 0; k < H; ++k) g[k] = fma2(lam[k], rv[k], mu[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < H; ++k) g[k] = fma2(mu[k], rv[k], lam[k]);
+  }
+}
+
+// Streams the lane's row in 4-pair groups: loads a group, forms its factors g and
+// their product, and returns the lane's partial sum of log2 products; *g_out keeps the
+// factors only when requested (exact fallback path).
+template <int L, int E>
+__device__ __forceinline__ float flip_partial(bool up, const float2 (&lam)[Lay<L, E>::H],
+                                             const float2 (&mu)[Lay<L, E>::H], const float *row, int gl) {
+  using LY = Lay<L, E>;
+  float2 rv[LY::H];
+  LY::template load<false>(row, gl, rv, 1.f);
+  float part = 0.f;
+#pragma unroll
+  for (int k0 = 0; k0 < LY::H; k0 += 4) {
+    float2 pr = up ? fma2(lam[k0], rv[k0], mu[k0]) : fma2(mu[k0], rv[k0], lam[k0]);
+#pragma unroll
+    for (int k = k0 + 1; k < (k0 + 4 < LY::H ? k0 + 4 : LY::H); ++k)
+      pr = mul2(pr, up ? fma2(lam[k], rv[k], mu[k]) : fma2(mu[k], rv[k], lam[k]));
+    part += lg2_approx(pr.x * pr.y);
+  }
+  return part;
+}
+
+// Exact sum of log2 g over the lane's units (fallback when a product left the FP32 range).
+template <int L, int E>
+__device__ __forceinline__ float flip_partial_exact(bool up, const float2 (&lam)[Lay<L, E>::H],
+                                                 const float2 (&mu)[Lay<L, E>::H], const float *row, int gl) {
+  using LY = Lay<L, E>;
+  float2 rv[LY::H];
+  LY::template load<false>(row, gl, rv, 1.f);
+  float p = 0.f;
+#pragma unroll
+  for (int k = 0; k < LY::H; ++k) {
+    const float2 g = up ? fma2(lam[k], rv[k], mu[k]) : fma2(mu[k], rv[k], lam[k]);
+    p += log2f(g.x) + log2f(g.y);
+  }
+  return p;
+}
+
+// Group sum of the lane partials; see sum_log2 for the reduction and its exact fallback.
+template <int L, int E>
+__device__ __forceinline__ float flip_logsum(bool up, const float2 (&lam)[Lay<L, E>::H],
+                                            const float2 (&mu)[Lay<L, E>::H], const float *row, int gl) {
+  const float part = flip_partial<L, E>(up, lam, mu, row, gl);
+  if constexpr (L == 32) {
+    const bool bad = !(fabsf(part) < 1024.f);
+    if (!__any_sync(FULL_MASK, bad)) {
+      const int q = __float2int_rn(part * 1048576.f);
+      return (float)__reduce_add_sync(FULL_MASK, q) * 9.5367431640625e-7f;
+    }
+  } else {
+    const float tot = group_allsum<L>(part);
+    if (!__any_sync(FULL_MASK, !isfinite(tot))) return tot;
+  }
+  return group_allsum<L>(flip_partial_exact<L, E>(up, lam, mu, row, gl));
+}
+
+// sum_j log2 g_j over the group: products of up to 8 factors (4 pairs) per MUFU lg2.
 // With one chain per warp the lane partials are added exactly as 2^-20 fixed-point
 // integers by one redux.sync (a 32-lane sum in one instruction instead of a 5-stage
 // shuffle tree); each partial is rounded to 2^-21, so the sum carries at most
 // 32 * 2^-21 absolute error in log2 units.  A product that leaves the normal FP32
 // range, or a partial beyond +-2^10, sends the group to the exact path: one accurate
 // log per factor and a floating-point butterfly.
-template <int L, int E>
-__device__ __forceinline__ float sum_log2(const float (&g)[E]) {
+template <int L, int H>
+__device__ __forceinline__ float sum_log2(const float2 (&g)[H]) {
   float part = 0.f;
 #pragma unroll
-  for (int e0 = 0; e0 < E; e0 += 8) {
-    float pr = g[e0];
+  for (int k0 = 0; k0 < H; k0 += 4) {
+    float2 pr = g[k0];
 #pragma unroll
-    for (int e = e0 + 1; e < (e0 + 8 < E ? e0 + 8 : E); ++e) pr *= g[e];
-    part += lg2_approx(pr);
+    for (int k = k0 + 1; k < (k0 + 4 < H ? k0 + 4 : H); ++k) pr = mul2(pr, g[k]);
+    part += lg2_approx(pr.x * pr.y);
   }
   if constexpr (L == 32) {
     const bool bad = !(fabsf(part) < 1024.f);  // also catches inf / nan
@@ -252,7 +342,7 @@ __device__ __forceinline__ float sum_log2(const float (&g)[E]) {
   }
   float p2 = 0.f;
 #pragma unroll
-  for (int e = 0; e < E; ++e) p2 += log2f(g[e]);
+  for (int k = 0; k < H; ++k) p2 += log2f(g[k].x) + log2f(g[k].y);
   return group_allsum<L>(p2);
 }
 
@@ -277,6 +367,48 @@ __device__ bool load_table(TT *sR, const TT *R, uint32_t bytes, uint64_t *bar, i
     mbar_wait_bounded(bar, 0, WAIT_POLLS);  // let copies in flight land before the CTA exits
   }
   return __syncthreads_and(ok);
+}
+
+// Accepted flip: lam/mu = e^{2 theta} is multiplied by R (spin up) or 1/R (spin down):
+//   up:   lam' = lam R / g, mu' = mu / g,  g = mu + lam R
+//   down: mu' = mu R / g,  lam' = lam / g, g = lam + mu R
+// The row is re-read pair by pair and g recomputed, so neither has to stay live in
+// registers from the proposal to the decision.
+template <int L, int E, bool SMEM>
+__device__ __forceinline__ void accept_update(bool up, float2 (&lam)[Lay<L, E>::H], float2 (&mu)[Lay<L, E>::H],
+                                              const float *row, int gl) {
+  using LY = Lay<L, E>;
+  auto upd = [&](int k, float2 r) {
+    if (up) {
+      const float2 g = fma2(lam[k], r, mu[k]);
+      const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
+      lam[k] = mul2(mul2(lam[k], r), inv);
+      mu[k] = mul2(mu[k], inv);
+    } else {
+      const float2 g = fma2(mu[k], r, lam[k]);
+      const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
+      mu[k] = mul2(mul2(mu[k], r), inv);
+      lam[k] = mul2(lam[k], inv);
+    }
+  };
+#pragma unroll
+  for (int v = 0; v < LY::V; ++v) {
+    float4 q;
+    q = *reinterpret_cast<const float4 *>(row + 4 * (v * L + gl));
+    upd(2 * v, make_float2(q.x, q.y));
+    upd(2 * v + 1, make_float2(q.z, q.w));
+  }
+  float t[3] = {1.f, 1.f, 1.f};
+#pragma unroll
+  for (int k = 0; k < LY::T; ++k) {
+    t[k] = row[4 * LY::V * L + k * L + gl];
+  }
+  if constexpr (LY::T == 1) upd(2 * LY::V, make_float2(t[0], 1.f));
+  if constexpr (LY::T == 2) upd(2 * LY::V, make_float2(t[0], t[1]));
+  if constexpr (LY::T == 3) {
+    upd(2 * LY::V, make_float2(t[0], t[1]));
+    upd(2 * LY::V + 1, make_float2(t[2], 1.f));
+  }
 }
 
 struct SweepParams {
@@ -306,7 +438,7 @@ __device__ __forceinline__ float log_uniform(uint32_t w) {
 // One group of L lanes runs one chain for all sweeps; the block shares one copy of
 // the R table in shared memory (or reads it through L2 when it does not fit).
 template <int L, int E, bool SMEM>
-__global__ void __launch_bounds__(max_threads_for(E), 1) rbm_sweep_f32_kernel(const SweepParams p) {
+__global__ void __launch_bounds__(sweep_threads(E), 1) rbm_sweep_f32_kernel(const SweepParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t bar;
   const float *R = p.R;
@@ -331,7 +463,8 @@ __global__ void __launch_bounds__(max_threads_for(E), 1) rbm_sweep_f32_kernel(co
     const bool valid = c < p.C;
     const int64_t cc = valid ? c : p.C - 1;  // idle groups shadow the last chain and write nothing
     uint32_t sw = gl < W ? p.state[cc * W + gl] : 0u;
-    float lam[E], mu[E];
+    using LY = Lay<L, E>;
+    float2 lam[LY::H], mu[LY::H];
     build_cache<L, E>(lam, mu, sw, p.Wt, p.b, N, W, M_pad, gl);
     int64_t nacc = 0;
 
@@ -350,35 +483,12 @@ __global__ void __launch_bounds__(max_threads_for(E), 1) rbm_sweep_f32_kernel(co
           const float thr = __shfl_sync(FULL_MASK, (q & 1) ? thr1 : thr0, src, L);
           const uint32_t word = __shfl_sync(FULL_MASK, sw, site >> 5, L);
           const bool up = (word >> (site & 31)) & 1u;
-          float rv[E], g[E];
-          Lay<L, E>::load(R + (size_t)site * M_pad, gl, rv);
-          if (up) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) g[e] = fmaf(lam[e], rv[e], mu[e]);
-          } else {
-#pragma unroll
-            for (int e = 0; e < E; ++e) g[e] = fmaf(mu[e], rv[e], lam[e]);
-          }
-          const float tot = sum_log2<L, E>(g);
+          const float tot = flip_logsum<L, E>(up, lam, mu, R + (size_t)site * M_pad, gl);
           const float2 ak = saK[site];
           const float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F;
           const bool acc = 2.f * dlt > thr;
           if (acc) {
-            if (up) {
-#pragma unroll
-              for (int e = 0; e < E; ++e) {
-                const float inv = rcp_approx(g[e]);
-                lam[e] = lam[e] * rv[e] * inv;
-                mu[e] = mu[e] * inv;
-              }
-            } else {
-#pragma unroll
-              for (int e = 0; e < E; ++e) {
-                const float inv = rcp_approx(g[e]);
-                mu[e] = mu[e] * rv[e] * inv;
-                lam[e] = lam[e] * inv;
-              }
-            }
+            accept_update<L, E, SMEM>(up, lam, mu, R + (size_t)site * M_pad, gl);
             if (gl == (int)(site >> 5)) sw ^= 1u << (site & 31);
             ++nacc;
           }
@@ -420,13 +530,13 @@ __global__ void rbm_logpsi_kernel(const uint32_t *__restrict__ cfg, int64_t n, c
   for (int64_t base = gw * G; base < n; base += stride) {
     const int64_t x = min(base + grp, n - 1);
     const uint32_t sw = gl < W ? cfg[x * W + gl] : 0u;
-    float th[E];
+    float2 th[Lay<L, E>::H];
     compute_theta<L, E>(th, sw, Wt, b, N, W, M_pad, gl);
     float part = 0.f;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const float z = fabsf(th[e]);
-      part += z + log1pf(expf(-2.f * z)) - LN2F;
+    for (int k = 0; k < Lay<L, E>::H; ++k) {  // a dummy slot has theta = 0: log cosh 0 = 0
+      const float zx = fabsf(th[k].x), zy = fabsf(th[k].y);
+      part += (zx + log1pf(expf(-2.f * zx)) - LN2F) + (zy + log1pf(expf(-2.f * zy)) - LN2F);
     }
     const float lp = visible_term<L>(sw, aK, N, gl) + group_allsum<L>(part);
     if (base + grp < n && gl == 0) out[x] = lp;
@@ -437,7 +547,7 @@ __global__ void rbm_logpsi_kernel(const uint32_t *__restrict__ cfg, int64_t n, c
 // TFIM local energy (Eq. TFIM, App. I Eq. local_energies):
 //   eps(x) = J sum_<ij> s_i s_j + h sum_i exp(log psi(flip_i x) - log psi(x)).
 template <int L, int E, bool SMEM>
-__global__ void __launch_bounds__(max_threads_for(E), 1) rbm_tfim_eloc_kernel(const uint32_t *__restrict__ cfg, int64_t n,
+__global__ void __launch_bounds__(eloc_threads(E), 1) rbm_tfim_eloc_kernel(const uint32_t *__restrict__ cfg, int64_t n,
                                                                  const float *Rg, const float2 *aK,
                                                                  const float *Wt, const float *b,
                                                                  const int2 *bonds, int n_bonds, float J,
@@ -462,7 +572,8 @@ __global__ void __launch_bounds__(max_threads_for(E), 1) rbm_tfim_eloc_kernel(co
   for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * G; base < n; base += stride) {
     const int64_t x = min(base + grp, n - 1);
     const uint32_t sw = gl < W ? cfg[x * W + gl] : 0u;
-    float lam[E], mu[E];
+    using LY = Lay<L, E>;
+    float2 lam[LY::H], mu[LY::H];
     build_cache<L, E>(lam, mu, sw, Wt, b, N, W, M_pad, gl);
     // diagonal: J sum over bonds of s_a s_b
     float d = 0.f;
@@ -476,21 +587,21 @@ __global__ void __launch_bounds__(max_threads_for(E), 1) rbm_tfim_eloc_kernel(co
     }
     d = J * group_allsum<L>(d);
     float off = 0.f;
-    for (int i = 0; i < N; ++i) {
-      const uint32_t word = __shfl_sync(FULL_MASK, sw, i >> 5, L);
-      const bool up = (word >> (i & 31)) & 1u;
-      float rv[E], g[E];
-      Lay<L, E>::load(R + (size_t)i * M_pad, gl, rv);
-      if (up) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) g[e] = fmaf(lam[e], rv[e], mu[e]);
-      } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) g[e] = fmaf(mu[e], rv[e], lam[e]);
-      }
-      const float tot = sum_log2<L, E>(g);
-      const float2 ak = saK[i];
-      off += expf(2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F);
+    for (int i = 0; i < N; i += 2) {  // two independent sites per iteration
+      const int i1 = min(i + 1, N - 1);
+      const uint32_t word0 = __shfl_sync(FULL_MASK, sw, i >> 5, L);
+      const uint32_t word1 = __shfl_sync(FULL_MASK, sw, i1 >> 5, L);
+      const bool up0 = (word0 >> (i & 31)) & 1u, up1 = (word1 >> (i1 & 31)) & 1u;
+      float2 rv0[LY::H], g0[LY::H], rv1[LY::H], g1[LY::H];
+      LY::template load<false>(R + (size_t)i * M_pad, gl, rv0, 1.f);
+      LY::template load<false>(R + (size_t)i1 * M_pad, gl, rv1, 1.f);
+      flip_factors<LY::H>(up0, lam, mu, rv0, g0);
+      flip_factors<LY::H>(up1, lam, mu, rv1, g1);
+      const float tot0 = sum_log2<L, LY::H>(g0);
+      const float tot1 = sum_log2<L, LY::H>(g1);
+      const float2 ak0 = saK[i], ak1 = saK[i1];
+      off += expf(2.f * (ak0.y - (up0 ? ak0.x : -ak0.x)) + tot0 * LN2F);
+      if (i + 1 < N) off += expf(2.f * (ak1.y - (up1 ? ak1.x : -ak1.x)) + tot1 * LN2F);
     }
     if (base + grp < n && gl == 0) eloc[x] = d + h * off;
   }
