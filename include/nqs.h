@@ -147,7 +147,17 @@ nqs_status nqs_sweep(nqs_ctx *ctx, uint32_t *state, int64_t n_chains, int32_t n_
 nqs_status nqs_logpsi(nqs_ctx *ctx, const uint32_t *configs, int64_t n, float *out,
                       nqs_stream stream);
 
-/* App. I, Eq. local_energies: eloc[x] = sum_{x' in C(x)} H(x,x') psi(x')/psi(x), FP32. */
+/* Sec. 3.1 (increment of a local proposal): out[x] = log psi(y) - log psi(x) for y =
+ * configs[x] with site sites[x] flipped, evaluated exactly as nqs_sweep evaluates it for
+ * that proposal (the sampling copy's arithmetic: FP32, or BF16/F16 factors with FP32
+ * cache).  TFIM (single-flip) contexts.  Comparing two contexts on the same (x, site)
+ * gives the reduced-precision error eps(x, y) of the log-density increment (x2).
+ * sites: device int32 [n], 0 <= site < N (unchecked on the device). */
+nqs_status nqs_flip_delta(nqs_ctx *ctx, const uint32_t *configs, const int32_t *sites, int64_t n, float *out,
+                          nqs_stream stream);
+
+/* App. I, Eq. local_energies: eloc[x] = sum_{x' in C(x)} H(x,x') psi(x')/psi(x), FP32
+ * accumulation; for a BF16/F16 context the ratios use that copy's factor arithmetic. */
 nqs_status nqs_local_energy(nqs_ctx *ctx, const uint32_t *configs, int64_t n, float *eloc,
                             nqs_stream stream);
 

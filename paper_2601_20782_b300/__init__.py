@@ -65,6 +65,7 @@ _SIGS = {
     "nqs_init_chains": (_i32, [_vp, _vp, _i64, _u64, _vp]),
     "nqs_sweep": (_i32, [_vp, _vp, _i64, _i32, _i32, _u64, _u32, _vp, _vp, _vp, ctypes.POINTER(SweepTrace), _vp]),
     "nqs_logpsi": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "nqs_flip_delta": (_i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
     "nqs_local_energy": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "nqs_logpsi_grad_workspace": (_sz, [_vp, _i64]),
     "nqs_logpsi_grad": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
@@ -162,6 +163,13 @@ class Context:
         n = configs.shape[0]
         self._check(_lib.nqs_logpsi(self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
                                     _ptr(out, (torch.float32,), "out", (n,), False), _stream()))
+
+    def flip_delta(self, configs, sites, out):
+        """log psi(flip_{sites[x]} configs[x]) - log psi(configs[x]) as the sampler evaluates it."""
+        n = configs.shape[0]
+        self._check(_lib.nqs_flip_delta(self._h, _ptr(configs, _WORD, "configs", (n, self.W), False),
+                                        _ptr(sites, (torch.int32,), "sites", (n,), False), n,
+                                        _ptr(out, (torch.float32,), "out", (n,), False), _stream()))
 
     def local_energy(self, configs, eloc):
         n = configs.shape[0]

@@ -66,6 +66,17 @@ size_t rbm_grad_workspace(const nqs_ctx *c, int64_t n);
 cudaError_t rbm_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
                             const double *stats, double *force, void *ws, cudaStream_t s);
 bool rbm_supported(const nqs_ctx *c, std::string *why);
+cudaError_t rbm_flip_delta(const nqs_ctx *c, const uint32_t *cfg, const int32_t *sites, int64_t n, float *out,
+                           cudaStream_t s);
+namespace rbmk {
+struct SweepParams;
+struct ElocParams;
+}  // namespace rbmk
+// rbm_f16.cu, rbm_bf16.cu
+cudaError_t rbm_sweep_f16(const nqs_ctx *c, const rbmk::SweepParams &p, cudaStream_t s);
+cudaError_t rbm_eloc_f16(const nqs_ctx *c, const rbmk::ElocParams &p, cudaStream_t s);
+cudaError_t rbm_sweep_bf16(const nqs_ctx *c, const rbmk::SweepParams &p, cudaStream_t s);
+cudaError_t rbm_eloc_bf16(const nqs_ctx *c, const rbmk::ElocParams &p, cudaStream_t s);
 int rbm_force_chunks(const nqs_ctx *c, int64_t n);
 // force_tc.cu
 bool rbm_force_tc_supported(const nqs_ctx *c);

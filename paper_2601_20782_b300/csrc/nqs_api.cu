@@ -202,7 +202,8 @@ nqs_status nqs_set_params(nqs_ctx *c, const double *params, nqs_stream stream) {
     return cuda_fail(c, e, "nqs_set_params");
   if (st & nqs::STATUS_RANGE) {
     cudaMemsetAsync(c->d_status, 0, sizeof(int), s);
-    return fail(c, NQS_EINVAL, "a weight is outside the sampler's range (|W| <= 20)");
+    return fail(c, NQS_EINVAL, c->dtype == NQS_F16 ? "a weight is outside the F16 sampler's range (|W| <= 2.5)"
+                                                   : "a weight is outside the sampler's range (|W| <= 20)");
   }
   c->params_set = true;
   return NQS_OK;
@@ -249,6 +250,18 @@ nqs_status nqs_local_energy(nqs_ctx *c, const uint32_t *cfg, int64_t n, float *e
   if (n == 0) return NQS_OK;
   cudaError_t e = nqs::rbm_local_energy(c, cfg, n, eloc, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_local_energy");
+}
+
+nqs_status nqs_flip_delta(nqs_ctx *c, const uint32_t *cfg, const int32_t *sites, int64_t n, float *out,
+                          nqs_stream stream) {
+  if (!c) return NQS_EINVAL;
+  if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_flip_delta: parameters not set");
+  if (c->ham_kind != NQS_TFIM) return fail(c, NQS_EUNSUPPORTED, "nqs_flip_delta: single-flip (TFIM) contexts only");
+  if (n < 0 || (n > 0 && (bad_ptr(cfg) || bad_ptr(sites) || bad_ptr(out))))
+    return fail(c, NQS_EINVAL, "nqs_flip_delta: bad arguments");
+  if (n == 0) return NQS_OK;
+  cudaError_t e = nqs::rbm_flip_delta(c, cfg, sites, n, out, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_flip_delta");
 }
 
 size_t nqs_logpsi_grad_workspace(const nqs_ctx *c, int64_t n) {

@@ -1,0 +1,774 @@
+// Device-side building blocks of the RBM sampler and local energy, shared by the
+// per-dtype translation units (rbm.cu: FP32 sampling copy; rbm_f16.cu, rbm_bf16.cu).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace nqs {
+namespace rbmk {
+
+
+constexpr uint32_t BULK_CHUNK = 32768;
+
+// Threads per CTA bound for E cached units per lane (register budget per thread).
+constexpr int threads_for_regs(int regs) {
+  int w = 65536 / (32 * regs);
+  w = w < 2 ? 2 : (w > 32 ? 32 : w);
+  return 32 * w;
+}
+// sweep: the cache pairs stay live, the row and the factors are streamed
+constexpr int sweep_threads(int E) { return threads_for_regs(2 * E + 56); }
+// local energy: the cache plus two sites' rows and factors in flight
+constexpr int eloc_threads(int E) { return threads_for_regs(3 * E + 48); }
+constexpr uint32_t WAIT_POLLS = 1u << 22;
+
+
+// ------------------------------------------------------------------------------------
+// Paired FP32 arithmetic (fma.rn.f32x2 / mul.rn.f32x2, sm_100 family): two FP32
+// operations per issued instruction, each rounded as its scalar counterpart.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+// ------------------------------------------------------------------------------------
+// Per-chain cache layout.  L lanes per chain, E hidden units per lane held as H = ceil(E/2)
+// float2 pairs.  Lane gl owns units j = 4 (v L + gl) + c for v < E / 4, c < 4 (one 16-byte
+// vector), and j = 4 (E / 4) L + t L + gl for the E % 4 tail units.  For odd E the last
+// pair's second slot is a dummy unit with lam = mu = 1/2 and R = 1, which contributes
+// exactly nothing (g = 1) and stays unchanged by updates.
+template <int L, int E>
+struct Lay {
+  static constexpr int V = E / 4, T = E % 4, H = (E + 1) / 2;
+  // row[j] for the lane's units into pairs; `pad` fills the dummy slot
+  template <bool LDG>
+  __device__ static __forceinline__ void load(const float *row, int gl, float2 (&r)[H], float pad) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float4 *p4 = reinterpret_cast<const float4 *>(row + 4 * (v * L + gl));
+      const float4 q = LDG ? __ldg(p4) : *p4;
+      r[2 * v] = make_float2(q.x, q.y);
+      r[2 * v + 1] = make_float2(q.z, q.w);
+    }
+    const float *tail = row + 4 * V * L + gl;
+    auto ld = [&](int t) { return LDG ? __ldg(tail + t * L) : tail[t * L]; };
+    if constexpr (T == 1) r[2 * V] = make_float2(ld(0), pad);
+    if constexpr (T == 2) r[2 * V] = make_float2(ld(0), ld(1));
+    if constexpr (T == 3) {
+      r[2 * V] = make_float2(ld(0), ld(1));
+      r[2 * V + 1] = make_float2(ld(2), pad);
+    }
+  }
+};
+
+// Sampling-copy arithmetic of the 16-bit tables: pairs of BF16 / F16 values and their
+// packed FMA / multiply (Table tab:precision; the sampling copy of Sec. 4.2).  PD is how
+// many pair factors are multiplied in 16-bit before the product goes to FP32: F16 stops at
+// two (each factor is at most e^{4|W|}, |W| <= 1.38 keeps two below 65504; a larger
+// product overflows to inf and the group takes the exact path), BF16 has the FP32 range.
+template <typename TT>
+struct Prec;
+template <>
+struct Prec<float> {  // the FP32 sampling copy has no 16-bit shadows
+  using T2 = float2;
+};
+template <>
+struct Prec<__half> {
+  using T2 = __half2;
+  static constexpr int PD = 2;
+  __device__ static __forceinline__ T2 from_f2(float2 v) { return __float22half2_rn(v); }
+  __device__ static __forceinline__ float2 to_f2(T2 v) { return __half22float2(v); }
+  __device__ static __forceinline__ T2 fma(T2 a, T2 b, T2 c) { return __hfma2(a, b, c); }
+  __device__ static __forceinline__ T2 mul(T2 a, T2 b) { return __hmul2(a, b); }
+  __device__ static __forceinline__ T2 make(__half x, __half y) { return __halves2half2(x, y); }
+  __device__ static __forceinline__ __half one() { return __float2half(1.f); }
+};
+template <>
+struct Prec<__nv_bfloat16> {
+  using T2 = __nv_bfloat162;
+  static constexpr int PD = 4;
+  __device__ static __forceinline__ T2 from_f2(float2 v) { return __float22bfloat162_rn(v); }
+  __device__ static __forceinline__ float2 to_f2(T2 v) { return __bfloat1622float2(v); }
+  __device__ static __forceinline__ T2 fma(T2 a, T2 b, T2 c) { return __hfma2(a, b, c); }
+  __device__ static __forceinline__ T2 mul(T2 a, T2 b) { return __hmul2(a, b); }
+  __device__ static __forceinline__ T2 make(__nv_bfloat16 x, __nv_bfloat16 y) { return __halves2bfloat162(x, y); }
+  __device__ static __forceinline__ __nv_bfloat16 one() { return __float2bfloat16(1.f); }
+};
+
+// row[j] of a 16-bit table for the lane's units, as pairs (same unit layout as Lay)
+template <int L, int E, typename TT>
+__device__ __forceinline__ void load_pairs_tt(const TT *row, int gl, typename Prec<TT>::T2 (&r)[Lay<L, E>::H]) {
+  using LY = Lay<L, E>;
+  using P = Prec<TT>;
+#pragma unroll
+  for (int v = 0; v < LY::V; ++v) {
+    const uint2 q = *reinterpret_cast<const uint2 *>(row + 4 * (v * L + gl));
+    r[2 * v] = *reinterpret_cast<const typename P::T2 *>(&q.x);
+    r[2 * v + 1] = *reinterpret_cast<const typename P::T2 *>(&q.y);
+  }
+  const TT *tail = row + 4 * LY::V * L + gl;
+  if constexpr (LY::T == 1) r[2 * LY::V] = P::make(tail[0], P::one());
+  if constexpr (LY::T == 2) r[2 * LY::V] = P::make(tail[0], tail[L]);
+  if constexpr (LY::T == 3) {
+    r[2 * LY::V] = P::make(tail[0], tail[L]);
+    r[2 * LY::V + 1] = P::make(tail[2 * L], P::one());
+  }
+}
+
+// 16-bit shadows of the FP32 cache, used by the low-precision factor arithmetic
+template <int H, typename TT>
+__device__ __forceinline__ void make_shadows(const float2 (&lam)[H], const float2 (&mu)[H],
+                                             typename Prec<TT>::T2 (&lh)[H], typename Prec<TT>::T2 (&mh)[H]) {
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    lh[k] = Prec<TT>::from_f2(lam[k]);
+    mh[k] = Prec<TT>::from_f2(mu[k]);
+  }
+}
+
+__device__ __forceinline__ void sigmoid_pair(float th, float &lam, float &mu) {
+  const float e = expf(-2.f * fabsf(th));
+  const float p = 1.f / (1.f + e);
+  const float q = e * p;
+  lam = th >= 0.f ? p : q;
+  mu = th >= 0.f ? q : p;
+}
+
+template <int L, int E>
+__device__ __forceinline__ void compute_theta(float2 (&th)[Lay<L, E>::H], uint32_t sw, const float *__restrict__ Wt,
+                                              const float *__restrict__ b, int N, int W, int M_pad, int gl) {
+  using LY = Lay<L, E>;
+  LY::template load<true>(b, gl, th, 0.f);
+  for (int wi = 0; wi < W; ++wi) {
+    const uint32_t word = __shfl_sync(FULL_MASK, sw, wi, L);
+    const int nb = min(32, N - 32 * wi);
+    for (int bit = 0; bit < nb; ++bit) {
+      const float s = ((word >> bit) & 1u) ? 1.f : -1.f;
+      float2 w[LY::H];
+      LY::template load<true>(Wt + (size_t)(32 * wi + bit) * M_pad, gl, w, 0.f);
+      const float2 s2 = make_float2(s, s);
+#pragma unroll
+      for (int k = 0; k < LY::H; ++k) th[k] = fma2(s2, w[k], th[k]);
+    }
+  }
+}
+
+template <int L, int E>
+__device__ __forceinline__ void build_cache(float2 (&lam)[Lay<L, E>::H], float2 (&mu)[Lay<L, E>::H], uint32_t sw,
+                                            const float *Wt, const float *b, int N, int W, int M_pad, int gl) {
+  float2 th[Lay<L, E>::H];
+  compute_theta<L, E>(th, sw, Wt, b, N, W, M_pad, gl);
+#pragma unroll
+  for (int k = 0; k < Lay<L, E>::H; ++k) {
+    sigmoid_pair(th[k].x, lam[k].x, mu[k].x);
+    sigmoid_pair(th[k].y, lam[k].y, mu[k].y);
+  }
+}
+
+// sum_i a_i s_i over the group (every lane gets the same value)
+template <int L>
+__device__ __forceinline__ float visible_term(uint32_t sw, const float2 *aK, int N, int gl) {
+  float v = 0.f;
+  for (int i0 = 0; i0 < N; i0 += L) {
+    const int i = i0 + gl;
+    const uint32_t word = __shfl_sync(FULL_MASK, sw, (min(i, N - 1)) >> 5, L);
+    if (i < N) v += ((word >> (i & 31)) & 1u) ? aK[i].x : -aK[i].x;
+  }
+  return group_allsum<L>(v);
+}
+
+// log psi from the cache: sum_i a_i s_i - 1/2 sum_j log(4 lam_j mu_j)
+template <int L, int E>
+__device__ __forceinline__ float cache_logpsi(const float2 (&lam)[Lay<L, E>::H], const float2 (&mu)[Lay<L, E>::H],
+                                              uint32_t sw, const float2 *aK, int N, int gl) {
+  float part = 0.f;
+#pragma unroll
+  for (int k = 0; k < Lay<L, E>::H; ++k)
+    part += log2f(4.f * lam[k].x * mu[k].x) + log2f(4.f * lam[k].y * mu[k].y);
+  return visible_term<L>(sw, aK, N, gl) - 0.5f * LN2F * group_allsum<L>(part);
+}
+
+// g for a flip of a site with spin `up`: mu + lam R (up) or lam + mu R (down)
+template <int H>
+__device__ __forceinline__ void flip_factors(bool up, const float2 (&lam)[H], const float2 (&mu)[H],
+                                             const float2 (&rv)[H], float2 (&g)[H]) {
+  if (up) {
+#pragma unroll
+    for (int k = 0; k < H; ++k) g[k] = fma2(lam[k], rv[k], mu[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < H; ++k) g[k] = fma2(mu[k], rv[k], lam[k]);
+  }
+}
+
+// Streams the lane's row in 4-pair groups: loads a group, forms its factors g and
+// their product, and returns the lane's partial sum of log2 products; *g_out keeps the
+// factors only when requested (exact fallback path).
+template <int L, int E>
+__device__ __forceinline__ float flip_partial(bool up, const float2 (&lam)[Lay<L, E>::H],
+                                             const float2 (&mu)[Lay<L, E>::H], const float *row, int gl) {
+  using LY = Lay<L, E>;
+  float2 rv[LY::H];
+  LY::template load<false>(row, gl, rv, 1.f);
+  float part = 0.f;
+#pragma unroll
+  for (int k0 = 0; k0 < LY::H; k0 += 4) {
+    float2 pr = up ? fma2(lam[k0], rv[k0], mu[k0]) : fma2(mu[k0], rv[k0], lam[k0]);
+#pragma unroll
+    for (int k = k0 + 1; k < (k0 + 4 < LY::H ? k0 + 4 : LY::H); ++k)
+      pr = mul2(pr, up ? fma2(lam[k], rv[k], mu[k]) : fma2(mu[k], rv[k], lam[k]));
+    part += lg2_approx(pr.x * pr.y);
+  }
+  return part;
+}
+
+// Exact sum of log2 g over the lane's units (fallback when a product left the FP32 range).
+template <int L, int E>
+__device__ __forceinline__ float flip_partial_exact(bool up, const float2 (&lam)[Lay<L, E>::H],
+                                                 const float2 (&mu)[Lay<L, E>::H], const float *row, int gl) {
+  using LY = Lay<L, E>;
+  float2 rv[LY::H];
+  LY::template load<false>(row, gl, rv, 1.f);
+  float p = 0.f;
+#pragma unroll
+  for (int k = 0; k < LY::H; ++k) {
+    const float2 g = up ? fma2(lam[k], rv[k], mu[k]) : fma2(mu[k], rv[k], lam[k]);
+    p += log2f(g.x) + log2f(g.y);
+  }
+  return p;
+}
+
+// Group sum of the lane partials; see sum_log2 for the reduction and its exact fallback.
+template <int L, int E>
+__device__ __forceinline__ float flip_logsum(bool up, const float2 (&lam)[Lay<L, E>::H],
+                                            const float2 (&mu)[Lay<L, E>::H], const float *row, int gl) {
+  const float part = flip_partial<L, E>(up, lam, mu, row, gl);
+  if constexpr (L == 32) {
+    const bool bad = !(fabsf(part) < 1024.f);
+    if (!__any_sync(FULL_MASK, bad)) {
+      const int q = __float2int_rn(part * 1048576.f);
+      return (float)__reduce_add_sync(FULL_MASK, q) * 9.5367431640625e-7f;
+    }
+  } else {
+    const float tot = group_allsum<L>(part);
+    if (!__any_sync(FULL_MASK, !isfinite(tot))) return tot;
+  }
+  return group_allsum<L>(flip_partial_exact<L, E>(up, lam, mu, row, gl));
+}
+
+// Low-precision counterpart of flip_partial: factors g and their products in 16-bit
+// pair arithmetic from the 16-bit shadows and table, PD pair factors per 16-bit product,
+// up to 8 units per FP32 product and MUFU lg2.
+template <int L, int E, typename TT>
+__device__ __forceinline__ float flip_partial_lp(bool up, const typename Prec<TT>::T2 (&lh)[Lay<L, E>::H],
+                                                const typename Prec<TT>::T2 (&mh)[Lay<L, E>::H], const TT *row,
+                                                int gl) {
+  using LY = Lay<L, E>;
+  using P = Prec<TT>;
+  typename P::T2 rv[LY::H];
+  load_pairs_tt<L, E, TT>(row, gl, rv);
+  float part = 0.f;
+#pragma unroll
+  for (int k0 = 0; k0 < LY::H; k0 += 4) {
+    float acc = 1.f;
+#pragma unroll
+    for (int k1 = k0; k1 < (k0 + 4 < LY::H ? k0 + 4 : LY::H); k1 += P::PD) {
+      typename P::T2 pr = up ? P::fma(lh[k1], rv[k1], mh[k1]) : P::fma(mh[k1], rv[k1], lh[k1]);
+#pragma unroll
+      for (int k = k1 + 1; k < (k1 + P::PD < (k0 + 4 < LY::H ? k0 + 4 : LY::H) ? k1 + P::PD : (k0 + 4 < LY::H ? k0 + 4 : LY::H)); ++k)
+        pr = P::mul(pr, up ? P::fma(lh[k], rv[k], mh[k]) : P::fma(mh[k], rv[k], lh[k]));
+      const float2 f = P::to_f2(pr);
+      acc *= f.x * f.y;
+    }
+    part += lg2_approx(acc);
+  }
+  return part;
+}
+
+// exact path of the low-precision sum: each 16-bit factor converted and logged separately
+template <int L, int E, typename TT>
+__device__ __forceinline__ float flip_partial_lp_exact(bool up, const typename Prec<TT>::T2 (&lh)[Lay<L, E>::H],
+                                                      const typename Prec<TT>::T2 (&mh)[Lay<L, E>::H], const TT *row,
+                                                      int gl) {
+  using LY = Lay<L, E>;
+  using P = Prec<TT>;
+  typename P::T2 rv[LY::H];
+  load_pairs_tt<L, E, TT>(row, gl, rv);
+  float p = 0.f;
+#pragma unroll
+  for (int k = 0; k < LY::H; ++k) {
+    const float2 g = P::to_f2(up ? P::fma(lh[k], rv[k], mh[k]) : P::fma(mh[k], rv[k], lh[k]));
+    p += log2f(g.x) + log2f(g.y);
+  }
+  return p;
+}
+
+template <int L, int E, typename TT>
+__device__ __forceinline__ float flip_logsum_lp(bool up, const typename Prec<TT>::T2 (&lh)[Lay<L, E>::H],
+                                               const typename Prec<TT>::T2 (&mh)[Lay<L, E>::H], const TT *row, int gl) {
+  const float part = flip_partial_lp<L, E, TT>(up, lh, mh, row, gl);
+  if constexpr (L == 32) {
+    const bool bad = !(fabsf(part) < 1024.f);
+    if (!__any_sync(FULL_MASK, bad)) {
+      const int q = __float2int_rn(part * 1048576.f);
+      return (float)__reduce_add_sync(FULL_MASK, q) * 9.5367431640625e-7f;
+    }
+  } else {
+    const float tot = group_allsum<L>(part);
+    if (!__any_sync(FULL_MASK, !isfinite(tot))) return tot;
+  }
+  return group_allsum<L>(flip_partial_lp_exact<L, E, TT>(up, lh, mh, row, gl));
+}
+
+// Accepted flip with a 16-bit table: the FP32 cache is updated as in accept_update with
+// the table value converted to FP32, then the 16-bit shadows are refreshed.
+template <int L, int E, typename TT>
+__device__ __forceinline__ void accept_update_lp(bool up, float2 (&lam)[Lay<L, E>::H], float2 (&mu)[Lay<L, E>::H],
+                                                 typename Prec<TT>::T2 (&lh)[Lay<L, E>::H],
+                                                 typename Prec<TT>::T2 (&mh)[Lay<L, E>::H], const TT *row, int gl) {
+  using LY = Lay<L, E>;
+  using P = Prec<TT>;
+  typename P::T2 rv[LY::H];
+  load_pairs_tt<L, E, TT>(row, gl, rv);
+#pragma unroll
+  for (int k = 0; k < LY::H; ++k) {
+    const float2 r = P::to_f2(rv[k]);
+    if (up) {
+      const float2 g = fma2(lam[k], r, mu[k]);
+      const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
+      lam[k] = mul2(mul2(lam[k], r), inv);
+      mu[k] = mul2(mu[k], inv);
+    } else {
+      const float2 g = fma2(mu[k], r, lam[k]);
+      const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
+      mu[k] = mul2(mul2(mu[k], r), inv);
+      lam[k] = mul2(lam[k], inv);
+    }
+    lh[k] = P::from_f2(lam[k]);
+    mh[k] = P::from_f2(mu[k]);
+  }
+}
+
+// sum_j log2 g_j over the group: products of up to 8 factors (4 pairs) per MUFU lg2.
+// With one chain per warp the lane partials are added exactly as 2^-20 fixed-point
+// integers by one redux.sync (a 32-lane sum in one instruction instead of a 5-stage
+// shuffle tree); each partial is rounded to 2^-21, so the sum carries at most
+// 32 * 2^-21 absolute error in log2 units.  A product that leaves the normal FP32
+// range, or a partial beyond +-2^10, sends the group to the exact path: one accurate
+// log per factor and a floating-point butterfly.
+template <int L, int H>
+__device__ __forceinline__ float sum_log2(const float2 (&g)[H]) {
+  float part = 0.f;
+#pragma unroll
+  for (int k0 = 0; k0 < H; k0 += 4) {
+    float2 pr = g[k0];
+#pragma unroll
+    for (int k = k0 + 1; k < (k0 + 4 < H ? k0 + 4 : H); ++k) pr = mul2(pr, g[k]);
+    part += lg2_approx(pr.x * pr.y);
+  }
+  if constexpr (L == 32) {
+    const bool bad = !(fabsf(part) < 1024.f);  // also catches inf / nan
+    if (!__any_sync(FULL_MASK, bad)) {
+      const int q = __float2int_rn(part * 1048576.f);
+      return (float)__reduce_add_sync(FULL_MASK, q) * 9.5367431640625e-7f;
+    }
+  } else {
+    const float tot = group_allsum<L>(part);
+    if (!__any_sync(FULL_MASK, !isfinite(tot))) return tot;
+  }
+  float p2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < H; ++k) p2 += log2f(g[k].x) + log2f(g[k].y);
+  return group_allsum<L>(p2);
+}
+
+// Loads the [N][M_pad] table into shared memory with 1D bulk copies.  Returns false
+// (after recording STATUS_TIMEOUT) if the copies did not land within the poll limit.
+template <typename TT>
+__device__ bool load_table(TT *sR, const TT *R, uint32_t bytes, uint64_t *bar, int *status) {
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, bytes);
+    for (uint32_t off = 0; off < bytes; off += BULK_CHUNK)
+      bulk_g2s(reinterpret_cast<char *>(sR) + off, reinterpret_cast<const char *>(R) + off,
+               min(BULK_CHUNK, bytes - off), bar);
+  }
+  bool ok = mbar_wait_bounded(bar, 0, WAIT_POLLS);
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(status, STATUS_TIMEOUT);
+    mbar_wait_bounded(bar, 0, WAIT_POLLS);  // let copies in flight land before the CTA exits
+  }
+  return __syncthreads_and(ok);
+}
+
+// Accepted flip: lam/mu = e^{2 theta} is multiplied by R (spin up) or 1/R (spin down):
+//   up:   lam' = lam R / g, mu' = mu / g,  g = mu + lam R
+//   down: mu' = mu R / g,  lam' = lam / g, g = lam + mu R
+// The row is re-read pair by pair and g recomputed, so neither has to stay live in
+// registers from the proposal to the decision.
+template <int L, int E, bool SMEM>
+__device__ __forceinline__ void accept_update(bool up, float2 (&lam)[Lay<L, E>::H], float2 (&mu)[Lay<L, E>::H],
+                                              const float *row, int gl) {
+  using LY = Lay<L, E>;
+  auto upd = [&](int k, float2 r) {
+    if (up) {
+      const float2 g = fma2(lam[k], r, mu[k]);
+      const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
+      lam[k] = mul2(mul2(lam[k], r), inv);
+      mu[k] = mul2(mu[k], inv);
+    } else {
+      const float2 g = fma2(mu[k], r, lam[k]);
+      const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
+      mu[k] = mul2(mul2(mu[k], r), inv);
+      lam[k] = mul2(lam[k], inv);
+    }
+  };
+#pragma unroll
+  for (int v = 0; v < LY::V; ++v) {
+    float4 q;
+    q = *reinterpret_cast<const float4 *>(row + 4 * (v * L + gl));
+    upd(2 * v, make_float2(q.x, q.y));
+    upd(2 * v + 1, make_float2(q.z, q.w));
+  }
+  float t[3] = {1.f, 1.f, 1.f};
+#pragma unroll
+  for (int k = 0; k < LY::T; ++k) {
+    t[k] = row[4 * LY::V * L + k * L + gl];
+  }
+  if constexpr (LY::T == 1) upd(2 * LY::V, make_float2(t[0], 1.f));
+  if constexpr (LY::T == 2) upd(2 * LY::V, make_float2(t[0], t[1]));
+  if constexpr (LY::T == 3) {
+    upd(2 * LY::V, make_float2(t[0], t[1]));
+    upd(2 * LY::V + 1, make_float2(t[2], 1.f));
+  }
+}
+
+struct SweepParams {
+  const void *R;  // [N][M_pad] table in the sampling dtype
+  const float2 *aK;
+  const float *Wt;
+  const float *b;
+  uint32_t *state;
+  uint32_t *samples;
+  float *logpsi;
+  int64_t *n_acc;
+  uint32_t *acc_bits;
+  float *delta;
+  int *status;
+  int64_t C;
+  int N, W, M_pad, n_sweeps, burn_in, refresh;
+  uint32_t sweep_offset, k0, k1;
+};
+
+// log u for u = k 2^-24 (k = 0 gives -inf: always accept).  Accepting iff
+// 2 dlogpsi > log u is the rule u < exp(2 dlogpsi).
+__device__ __forceinline__ float log_uniform(uint32_t w) {
+  const uint32_t k = w >> 8;
+  return k == 0u ? -INFINITY : logf((float)k * 5.9604644775390625e-8f);
+}
+
+// Per-chain state of the sampler: the FP32 cache (lam, mu) and, for a 16-bit sampling
+// copy, its 16-bit shadows used by the factor arithmetic.
+template <int L, int E, typename TT>
+struct ChainCache {
+  using LY = Lay<L, E>;
+  static constexpr bool LP = !std::is_same<TT, float>::value;
+  using T2 = typename Prec<TT>::T2;
+  float2 lam[LY::H], mu[LY::H];
+  T2 lh[LP ? LY::H : 1], mh[LP ? LY::H : 1];
+
+  __device__ __forceinline__ void build(uint32_t sw, const float *Wt, const float *b, int N, int W, int M_pad,
+                                        int gl) {
+    build_cache<L, E>(lam, mu, sw, Wt, b, N, W, M_pad, gl);
+    if constexpr (LP) make_shadows<LY::H, TT>(lam, mu, lh, mh);
+  }
+  // sum_j log2 g_j of flipping the site whose table row is `row`
+  __device__ __forceinline__ float logsum(bool up, const TT *row, int gl) const {
+    if constexpr (LP) return flip_logsum_lp<L, E, TT>(up, lh, mh, row, gl);
+    else return flip_logsum<L, E>(up, lam, mu, row, gl);
+  }
+  template <bool SMEM>
+  __device__ __forceinline__ void accept(bool up, const TT *row, int gl) {
+    if constexpr (LP) accept_update_lp<L, E, TT>(up, lam, mu, lh, mh, row, gl);
+    else accept_update<L, E, SMEM>(up, lam, mu, row, gl);
+  }
+  __device__ __forceinline__ float logpsi(uint32_t sw, const float2 *aK, int N, int gl) const {
+    return cache_logpsi<L, E>(lam, mu, sw, aK, N, gl);
+  }
+};
+
+// Copies the table (and aK) into shared memory when SMEM; returns the table pointer to
+// use, or nullptr if the bulk copy timed out (STATUS_TIMEOUT recorded).
+template <typename TT, bool SMEM>
+__device__ __forceinline__ const TT *stage_table(unsigned char *smem_raw, const void *Rg, const float2 *aK, int N,
+                                                 int M_pad, uint64_t *bar, int *status, float2 **saK_out) {
+  const uint32_t table_bytes = SMEM ? (uint32_t)N * M_pad * (uint32_t)sizeof(TT) : 0u;
+  const TT *R = static_cast<const TT *>(Rg);
+  if constexpr (SMEM) {
+    if (!load_table(reinterpret_cast<TT *>(smem_raw), R, table_bytes, bar, status)) return nullptr;
+    R = reinterpret_cast<const TT *>(smem_raw);
+  }
+  float2 *saK = reinterpret_cast<float2 *>(smem_raw + ((table_bytes + 15u) & ~15u));
+  for (int i = threadIdx.x; i < N; i += blockDim.x) saK[i] = aK[i];
+  __syncthreads();
+  *saK_out = saK;
+  return R;
+}
+
+// One group of L lanes runs one chain for all sweeps; the block shares one copy of
+// the table in shared memory (or reads it through L2 when it does not fit).
+template <int L, int E, bool SMEM, typename TT>
+__global__ void __launch_bounds__(sweep_threads(E), 1) rbm_sweep_kernel(const SweepParams p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  float2 *saK;
+  const TT *R = stage_table<TT, SMEM>(smem_raw, p.R, p.aK, p.N, p.M_pad, &bar, p.status, &saK);
+  if (!R) return;
+
+  constexpr int G = 32 / L;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / L, gl = lane % L;
+  const int64_t wpb = blockDim.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * wpb * G;
+  const int N = p.N, W = p.W, M_pad = p.M_pad;
+
+  for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * G; base < p.C; base += stride) {
+    const int64_t c = base + grp;
+    const bool valid = c < p.C;
+    const int64_t cc = valid ? c : p.C - 1;  // idle groups shadow the last chain and write nothing
+    uint32_t sw = gl < W ? p.state[cc * W + gl] : 0u;
+    ChainCache<L, E, TT> cache;
+    cache.build(sw, p.Wt, p.b, N, W, M_pad, gl);
+    int64_t nacc = 0;
+
+    for (int t = 0; t < p.n_sweeps; ++t) {
+      const uint32_t sweep_id = p.sweep_offset + (uint32_t)t;
+      uint32_t abits = 0u;
+      for (int p0 = 0; p0 < N; p0 += 2 * L) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(p0 / 2 + gl), sweep_id, (uint32_t)cc, TAG_SWEEP),
+                                      p.k0, p.k1);
+        const uint32_t site0 = index_from_word(w.x, (uint32_t)N), site1 = index_from_word(w.z, (uint32_t)N);
+        const float thr0 = log_uniform(w.y), thr1 = log_uniform(w.w);
+        const int np = min(2 * L, N - p0);
+        for (int q = 0; q < np; ++q) {
+          const int src = q >> 1;
+          const uint32_t site = __shfl_sync(FULL_MASK, (q & 1) ? site1 : site0, src, L);
+          const float thr = __shfl_sync(FULL_MASK, (q & 1) ? thr1 : thr0, src, L);
+          const uint32_t word = __shfl_sync(FULL_MASK, sw, site >> 5, L);
+          const bool up = (word >> (site & 31)) & 1u;
+          const TT *row = R + (size_t)site * M_pad;
+          const float tot = cache.logsum(up, row, gl);
+          const float2 ak = saK[site];
+          const float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F;
+          const bool acc = 2.f * dlt > thr;
+          if (acc) {
+            cache.template accept<SMEM>(up, row, gl);
+            if (gl == (int)(site >> 5)) sw ^= 1u << (site & 31);
+            ++nacc;
+          }
+          const int pq = p0 + q;
+          if (p.acc_bits) {
+            abits |= (acc ? 1u : 0u) << (pq & 31);
+            if ((pq & 31) == 31 || pq == N - 1) {
+              if (valid && gl == 0) p.acc_bits[((int64_t)cc * p.n_sweeps + t) * W + (pq >> 5)] = abits;
+              abits = 0u;
+            }
+          }
+          if (p.delta && valid && gl == 0) p.delta[((int64_t)cc * p.n_sweeps + t) * N + pq] = dlt;
+        }
+      }
+      if (t >= p.burn_in) {
+        const int64_t row = (int64_t)(t - p.burn_in) * p.C + cc;
+        if (p.samples && valid && gl < W) p.samples[row * W + gl] = sw;
+        if (p.logpsi) {
+          const float lp = cache.logpsi(sw, saK, N, gl);
+          if (valid && gl == 0) p.logpsi[row] = lp;
+        }
+      }
+      if ((t + 1) % p.refresh == 0 && t + 1 < p.n_sweeps) cache.build(sw, p.Wt, p.b, N, W, M_pad, gl);
+    }
+    if (valid && gl < W) p.state[cc * W + gl] = sw;
+    if (valid && gl == 0 && p.n_acc) p.n_acc[cc] = nacc;
+  }
+}
+
+struct ElocParams {
+  const uint32_t *cfg;
+  const int32_t *sites;  // flip-delta mode: the site flipped for each row
+  const void *R;
+  const float2 *aK;
+  const float *Wt;
+  const float *b;
+  const int2 *bonds;
+  float *out;
+  int *status;
+  int64_t n;
+  int n_bonds, N, W, M_pad;
+  float J, h;
+};
+
+// TFIM local energy (Eq. TFIM, App. I Eq. local_energies), FLIP = false:
+//   eps(x) = J sum_<ij> s_i s_j + h sum_i exp(log psi(flip_i x) - log psi(x)),
+// two independent sites per iteration.  FLIP = true: out[x] = log psi(flip_{sites[x]} x)
+// - log psi(x), the increment the sampler uses for that proposal (Sec. 3.1).
+template <int L, int E, bool SMEM, typename TT, bool FLIP>
+__global__ void __launch_bounds__(eloc_threads(E), 1) rbm_tfim_eloc_kernel(const ElocParams p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  float2 *saK;
+  const TT *R = stage_table<TT, SMEM>(smem_raw, p.R, p.aK, p.N, p.M_pad, &bar, p.status, &saK);
+  if (!R) return;
+  const int N = p.N, W = p.W, M_pad = p.M_pad;
+
+  constexpr int G = 32 / L;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane / L, gl = lane % L;
+  const int64_t wpb = blockDim.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * wpb * G;
+  for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * G; base < p.n; base += stride) {
+    const int64_t x = min(base + grp, p.n - 1);
+    const uint32_t sw = gl < W ? p.cfg[x * W + gl] : 0u;
+    ChainCache<L, E, TT> cache;
+    cache.build(sw, p.Wt, p.b, N, W, M_pad, gl);
+    if constexpr (FLIP) {
+      const int i = p.sites[x];
+      const uint32_t word = __shfl_sync(FULL_MASK, sw, i >> 5, L);
+      const bool up = (word >> (i & 31)) & 1u;
+      const float tot = cache.logsum(up, R + (size_t)i * M_pad, gl);
+      const float2 ak = saK[i];
+      if (base + grp < p.n && gl == 0) p.out[x] = 2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F;
+    } else {
+      // diagonal: J sum over bonds of s_a s_b
+      float d = 0.f;
+      for (int b0 = 0; b0 < p.n_bonds; b0 += L) {
+        const int bi = min(b0 + gl, p.n_bonds - 1);
+        const int2 bd = p.bonds[bi];
+        const uint32_t wa = __shfl_sync(FULL_MASK, sw, bd.x >> 5, L);
+        const uint32_t wb = __shfl_sync(FULL_MASK, sw, bd.y >> 5, L);
+        const uint32_t sa = (wa >> (bd.x & 31)) & 1u, sb = (wb >> (bd.y & 31)) & 1u;
+        if (b0 + gl < p.n_bonds) d += sa == sb ? 1.f : -1.f;
+      }
+      d = p.J * group_allsum<L>(d);
+      float off = 0.f;
+      for (int i = 0; i < N; i += 2) {
+        const int i1 = min(i + 1, N - 1);
+        const uint32_t word0 = __shfl_sync(FULL_MASK, sw, i >> 5, L);
+        const uint32_t word1 = __shfl_sync(FULL_MASK, sw, i1 >> 5, L);
+        const bool up0 = (word0 >> (i & 31)) & 1u, up1 = (word1 >> (i1 & 31)) & 1u;
+        const float tot0 = cache.logsum(up0, R + (size_t)i * M_pad, gl);
+        const float tot1 = cache.logsum(up1, R + (size_t)i1 * M_pad, gl);
+        const float2 ak0 = saK[i], ak1 = saK[i1];
+        off += expf(2.f * (ak0.y - (up0 ? ak0.x : -ak0.x)) + tot0 * LN2F);
+        if (i + 1 < N) off += expf(2.f * (ak1.y - (up1 ? ak1.x : -ak1.x)) + tot1 * LN2F);
+      }
+      if (base + grp < p.n && gl == 0) p.out[x] = d + p.h * off;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Launch configuration: one CTA per SM shares one table copy; warps per CTA from the
+// kernel's register use, then trimmed so that every CTA runs the same number of rounds.
+template <typename K>
+cudaError_t launch_persistent(K kern, const nqs_ctx *c, int64_t groups, int G, size_t shm, cudaStream_t s,
+                              const void *arg) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+  const int regs_alloc = (std::max(fa.numRegs, 16) + 7) / 8 * 8;
+  int warps = std::max(1, std::min(fa.maxThreadsPerBlock / 32, 65536 / (regs_alloc * 32)));
+  const int64_t warps_needed = (groups + G - 1) / G;
+  int64_t blocks = std::min<int64_t>(c->num_sms, (warps_needed + warps - 1) / warps);
+  if (blocks < c->num_sms) {  // spread small jobs over more SMs with fewer warps each
+    blocks = std::min<int64_t>(c->num_sms, warps_needed);
+    warps = (int)std::max<int64_t>(1, (warps_needed + blocks - 1) / blocks);
+  } else {  // equal rounds: the fewest warps per CTA that keep the round count
+    const int64_t rounds = (warps_needed + blocks * warps - 1) / (blocks * warps);
+    warps = (int)((warps_needed + blocks * rounds - 1) / (blocks * rounds));
+  }
+  void *args[] = {const_cast<void *>(arg)};
+  return cudaLaunchKernel((const void *)kern, dim3((unsigned)blocks), dim3(warps * 32), args, shm, s);
+}
+
+template <typename TT>
+size_t table_smem(const nqs_ctx *c, bool *fits) {
+  const size_t table = ((size_t)c->N * c->M_pad * sizeof(TT) + 15) & ~size_t(15);
+  const size_t extra = (size_t)c->N * sizeof(float2) + 16;
+  *fits = table + extra + 256 <= (size_t)c->smem_optin;  // + static mbarrier
+  return (*fits ? table : 0) + extra;
+}
+
+template <typename TT>
+struct Runners {
+  template <int L, int E>
+  struct Sweep {
+    static cudaError_t run(const nqs_ctx *c, const SweepParams &p, cudaStream_t s) {
+      bool fits;
+      const size_t shm = table_smem<TT>(c, &fits);
+      return fits ? launch_persistent(rbm_sweep_kernel<L, E, true, TT>, c, p.C, 32 / L, shm, s, &p)
+                  : launch_persistent(rbm_sweep_kernel<L, E, false, TT>, c, p.C, 32 / L, shm, s, &p);
+    }
+  };
+  template <int L, int E>
+  struct Eloc {
+    static cudaError_t run(const nqs_ctx *c, const ElocParams &p, cudaStream_t s) {
+      bool fits;
+      const size_t shm = table_smem<TT>(c, &fits);
+      if (p.sites)
+        return fits ? launch_persistent(rbm_tfim_eloc_kernel<L, E, true, TT, true>, c, p.n, 32 / L, shm, s, &p)
+                    : launch_persistent(rbm_tfim_eloc_kernel<L, E, false, TT, true>, c, p.n, 32 / L, shm, s, &p);
+      return fits ? launch_persistent(rbm_tfim_eloc_kernel<L, E, true, TT, false>, c, p.n, 32 / L, shm, s, &p)
+                  : launch_persistent(rbm_tfim_eloc_kernel<L, E, false, TT, false>, c, p.n, 32 / L, shm, s, &p);
+    }
+  };
+};
+
+// dispatch over the instantiated hidden-unit widths per lane (L = 32)
+template <template <int, int> class F, typename... A>
+cudaError_t dispatch_l32(int E, A &&...args) {
+#define NQS_CASE(EE) \
+  if (E == EE) return F<32, EE>::run(args...);
+  NQS_CASE(1) NQS_CASE(2) NQS_CASE(3) NQS_CASE(4) NQS_CASE(5) NQS_CASE(6) NQS_CASE(7) NQS_CASE(8) NQS_CASE(9)
+  NQS_CASE(10) NQS_CASE(11) NQS_CASE(12) NQS_CASE(13) NQS_CASE(14) NQS_CASE(16) NQS_CASE(18) NQS_CASE(20)
+  NQS_CASE(24) NQS_CASE(28) NQS_CASE(32)
+#undef NQS_CASE
+  return cudaErrorInvalidConfiguration;
+}
+
+// dispatch over (L, E): L = 32 for every instantiated width; L = 16 and L = 8 variants
+// (two or four chains per warp) for the widths the tuner may pick.
+template <template <int, int> class F, typename... A>
+cudaError_t dispatch_le(int L, int E, A &&...args) {
+#define NQS_CASE(LL, EE) \
+  if (L == LL && E == EE) return F<LL, EE>::run(args...);
+  NQS_CASE(8, 4) NQS_CASE(16, 2) NQS_CASE(16, 4) NQS_CASE(16, 8) NQS_CASE(16, 16) NQS_CASE(16, 26)
+  NQS_CASE(16, 28) NQS_CASE(16, 32)
+#undef NQS_CASE
+  if (L == 32) return dispatch_l32<F>(E, args...);
+  return cudaErrorInvalidConfiguration;
+}
+
+}  // namespace rbmk
+}  // namespace nqs

@@ -1,0 +1,130 @@
+"""Reduced-precision sampling copies (BF16, F16) against the FP64 oracle and the bounds of
+Sec. 3 (Pinsker, Theorem 2, Theorem 3).
+
+Bit-exact parity does not apply: a 16-bit sampler takes different decisions.  What is
+checked: the increment error eps(x, y) of the 16-bit arithmetic is small and unbiased,
+every decision of the 16-bit sampler agrees with the FP64 rule outside a band of 10
+sigma_eps around the threshold, and the sampled distribution of a 4 x 4 lattice stays
+within sampling noise plus the analytical bias bound.
+"""
+import numpy as np
+import pytest
+
+from helpers import nqs, pack_np, unpack_np, unpack_accept_bits, to_words_tensor, words_from_tensor
+from oracle import exact, bounds
+from oracle.estimators import local_energy as oracle_eloc
+from oracle.hamiltonian import TFIM
+from oracle.models import RBM
+from oracle.sampler import mh_sweeps
+from workloads import rbm_params
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def make(Lx, Ly, M, sigma, seed, dtype, h=3.04):
+    p = nqs()
+    ctx = p.Context("tfim", Lx, Ly, J1=1.0, h=h, model="rbm", n_hidden=M, dtype=dtype)
+    params = rbm_params(Lx * Ly, M, sigma, seed)
+    ctx.set_params(torch.from_numpy(params).cuda())
+    return ctx, RBM(Lx * Ly, M, params), params
+
+
+def oracle_flip_delta(model, s, sites):
+    y = s.copy()
+    y[np.arange(len(s)), sites] *= -1
+    return model.logpsi(y) - model.logpsi(s)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 2e-5), ("bf16", None), ("f16", None)])
+def test_flip_delta_against_oracle(dtype, tol):
+    ctx, model, _ = make(10, 10, 400, 0.05, 3, dtype)
+    n = 4096
+    rng = np.random.default_rng(4)
+    s = rng.choice([-1, 1], size=(n, 100)).astype(np.int8)
+    sites = rng.integers(0, 100, n).astype(np.int32)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx.flip_delta(to_words_tensor(pack_np(s)), torch.from_numpy(sites).cuda(), out)
+    got = out.cpu().numpy().astype(np.float64)
+    ref = oracle_flip_delta(model, s, sites)
+    eps = 2.0 * (got - ref)                      # error of the log-density increment
+    if tol is not None:
+        assert np.abs(got - ref).max() < tol
+    else:
+        u = bounds.UNIT_ROUNDOFF[dtype]
+        # a few hundred rounded factors per increment: error well below 1 and far above FP32's
+        assert 1e-6 < eps.std() < 0.2, eps.std()
+        assert abs(eps.mean()) < 5 * eps.std() / np.sqrt(n) + 50 * u
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_lowp_sweep_decisions_within_noise_band(dtype):
+    ctx, model, _ = make(10, 10, 400, 0.05, 5, dtype)
+    C, T = 64, 2
+    state = torch.zeros((C, 4), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, 6)
+    s0 = unpack_np(words_from_tensor(state), 100)
+    bits = torch.zeros((C, T, 4), dtype=torch.int32, device="cuda")
+    delta = torch.zeros((C, T, 100), dtype=torch.float32, device="cuda")
+    ctx.sweep(state, T, T, 7, 0, accept_bits=bits, delta=delta)
+    acc = unpack_accept_bits(words_from_tensor(bits), 100)
+    ref = mh_sweeps(model.logpsi, s0, np.arange(C), 7, T, T, replay_accepts=acc, tau=1.0, record_deltas=True)
+    eps = 2.0 * (delta.cpu().numpy().astype(np.float64) - ref["deltas"])
+    sig = eps.std()
+    assert sig < 0.2
+    # replay again with the band of 10 sigma_eps: no decision outside it disagrees
+    mh_sweeps(model.logpsi, s0, np.arange(C), 7, T, T, replay_accepts=acc, tau=max(10 * sig, 1e-4))
+    np.testing.assert_array_equal(unpack_np(words_from_tensor(state), 100), ref["spins"])
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_lowp_histogram_within_noise_plus_bound_4x4(dtype):
+    """4 x 4 TFIM, alpha = 4 RBM sampled with a 16-bit copy: TV(hist, pi) <= i.i.d. noise
+    + min(Pinsker, Theorem 3) evaluated at the measured increment errors (r = 0 reading)."""
+    ctx, model, _ = make(4, 4, 64, 0.25, 13, dtype)
+    C, T = 32768, 200
+    state = torch.zeros((C, 1), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, 21)
+    ctx.sweep(state, T, T, 22, 0)
+    idx = words_from_tensor(state)[:, 0].astype(np.int64)
+    hist = np.bincount(idx, minlength=2 ** 16) / C
+    pi = exact.exact_pi(model.logpsi, 16)
+    tv = 0.5 * np.abs(hist - pi).sum()
+    rng = np.random.default_rng(0)
+    floor = max(0.5 * np.abs(np.bincount(rng.choice(pi.size, C, p=pi), minlength=pi.size) / C - pi).sum()
+                for _ in range(8))
+    # increment errors at x ~ pi~ (the sampled states), y a uniform single flip
+    sites = rng.integers(0, 16, C).astype(np.int32)
+    out = torch.empty(C, dtype=torch.float32, device="cuda")
+    ctx.flip_delta(state, torch.from_numpy(sites).cuda(), out)
+    s = unpack_np(words_from_tensor(state), 16)
+    eps = 2.0 * (out.cpu().numpy().astype(np.float64) - oracle_flip_delta(model, s, sites))
+    bound = bounds.reported_bound(eps.mean(), eps.std())
+    assert tv <= 1.15 * floor + bound, (tv, floor, bound)
+
+
+def test_lowp_energy_matches_fp64_within_error_and_bound():
+    """1D N = 16 TFIM: BF16-sampled energy vs the exact expectation by enumeration."""
+    ctx, model, _ = make(16, 1, 16, 0.2, 20260001, "bf16", h=1.0)
+    C, T, B = 4096, 60, 10
+    state = torch.zeros((C, 1), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, 31)
+    S = torch.zeros(((T - B) * C, 1), dtype=torch.int32, device="cuda")
+    ctx.sweep(state, T, B, 32, 0, S)
+    e = torch.empty((T - B) * C, dtype=torch.float32, device="cuda")
+    ctx.local_energy(S, e)
+    st = torch.empty(5, dtype=torch.float64, device="cuda")
+    ctx.stats(e, C, st)
+    E, var, err = st.cpu().numpy()[:3]
+    ham = TFIM(16, 1, 1.0, 1.0)
+    eps_x = oracle_eloc(ham, model.logpsi, exact.all_configs(16))
+    pi = exact.exact_pi(model.logpsi, 16)
+    e_exact = pi @ eps_x
+    sites = np.random.default_rng(1).integers(0, 16, C).astype(np.int32)
+    out = torch.empty(C, dtype=torch.float32, device="cuda")
+    ctx.flip_delta(state, torch.from_numpy(sites).cuda(), out)
+    s = unpack_np(words_from_tensor(state), 16)
+    eps = 2.0 * (out.cpu().numpy().astype(np.float64) - oracle_flip_delta(model, s, sites))
+    A = np.abs(eps_x).max()
+    bias_bound = 2 * A * bounds.reported_bound(eps.mean(), eps.std())
+    assert abs(E - e_exact) <= 3 * err + bias_bound, (E, e_exact, err, bias_bound)
