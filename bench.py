@@ -14,6 +14,7 @@ bounded sample of the same workload instead.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -93,109 +94,166 @@ def combine_across_ranks(stats, force, n_local, dist):
     return n, mean, var, buf[3:] / n
 
 
+def thm3_bound(mu, sigma):
+    """Theorem 3 (Eq. avg_bound) at r = 0 for log-density increments eps ~ N(mu, 2 sigma^2)."""
+    if sigma <= 0:
+        return 1.0 - math.exp(-abs(mu))
+    return 1.0 - 0.5 * math.exp(sigma ** 2) * (math.exp(-mu) * math.erfc(sigma - mu / (2 * sigma))
+                                               + math.exp(mu) * math.erfc(sigma + mu / (2 * sigma)))
+
+
+class Step:
+    """Buffers and one VMC step of the workload for one sampling dtype."""
+
+    def __init__(self, nqs, torch, dev, dtype, C, T, B, params_h):
+        ham, lat = WL.ham, WL.ham.lattice
+        self.torch, self.dev, self.dtype = torch, dev, dtype
+        self.N, self.M, self.C, self.T, self.B = lat.n_sites, WL.n_hidden, C, T, B
+        self.S = (T - B) * C
+        self.ctx = nqs.Context("tfim", lat.Lx, lat.Ly, J1=ham.J1, h=ham.h, model="rbm", n_hidden=self.M, dtype=dtype)
+        P = self.ctx.P
+        self.params_h = params_h
+        self.params = params_h.to(dev)
+        self.state = torch.zeros((C, self.ctx.W), dtype=torch.int32, device=dev)
+        self.samples = torch.zeros((self.S, self.ctx.W), dtype=torch.int32, device=dev)
+        self.nacc = torch.zeros(C, dtype=torch.int64, device=dev)
+        self.eloc = torch.zeros(self.S, dtype=torch.float32, device=dev)
+        self.stats = torch.zeros(5, dtype=torch.float64, device=dev)
+        self.force = torch.zeros(P, dtype=torch.float64, device=dev)
+        self.O = torch.zeros((C, P), dtype=torch.float32, device=dev)
+        self.ws = torch.zeros(self.ctx.logpsi_grad_workspace(self.S), dtype=torch.uint8, device=dev)
+        self.out_h = torch.zeros(5 + P, dtype=torch.float64).pin_memory()
+        self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        self.launches = 2 + 1 + 1 + 1 + 2 + 2 + 1   # set_params, init, sweep, eloc, stats, force, O rows
+
+    def run(self, seed, host_io=False):
+        c, ev = self.ctx, self.ev
+        if host_io:
+            self.params.copy_(self.params_h, non_blocking=True)
+        ev[0].record()
+        c.set_params(self.params)
+        c.init_chains(self.state, seed)
+        ev[1].record()
+        c.sweep(self.state, self.T, self.B, seed + 1, 0, self.samples, None, self.nacc)
+        ev[2].record()
+        c.local_energy(self.samples, self.eloc)
+        ev[3].record()
+        c.stats(self.eloc, self.C, self.stats, self.nacc, self.T * self.N)
+        c.logpsi_grad(self.samples, None, self.eloc, self.stats, self.force, self.ws)
+        ev[4].record()
+        c.logpsi_grad(self.samples[self.S - self.C:], self.O)
+        ev[5].record()
+        if host_io:
+            self.out_h[:5].copy_(self.stats, non_blocking=True)
+            self.out_h[5:].copy_(self.force, non_blocking=True)
+
+    def phases(self):
+        return [self.ev[i].elapsed_time(self.ev[i + 1]) for i in range(5)]
+
+
 def run_ours(args, rank, world, dist):
     import torch
     import paper_2601_20782_b300 as nqs
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    ham, lat = WL.ham, WL.ham.lattice
+    lat = WL.ham.lattice
     N, M, C, T, B = lat.n_sites, WL.n_hidden, WL.n_chains, WL.n_sweeps, WL.burn_in
     if args.chains or args.sweeps:   # smaller case of the same kernels, for profiler captures only
         C, T, B = args.chains or C, args.sweeps or T, args.burn_in if args.burn_in is not None else B
-    K = T - B
-    S = K * C
-    ctx = nqs.Context("tfim", lat.Lx, lat.Ly, J1=ham.J1, h=ham.h, model="rbm", n_hidden=M, dtype=args.dtype)
-    P = ctx.P
     params_h = torch.from_numpy(workloads.rbm_params(N, M, WL.weight_sigma, WL.seed)).pin_memory()
-    params = params_h.to(dev)
-    state = torch.zeros((C, ctx.W), dtype=torch.int32, device=dev)
-    samples = torch.zeros((S, ctx.W), dtype=torch.int32, device=dev)
-    nacc = torch.zeros(C, dtype=torch.int64, device=dev)
-    eloc = torch.zeros(S, dtype=torch.float32, device=dev)
-    stats = torch.zeros(5, dtype=torch.float64, device=dev)
-    force = torch.zeros(P, dtype=torch.float64, device=dev)
-    O = torch.zeros((C, P), dtype=torch.float32, device=dev)
-    ws = torch.zeros(ctx.logpsi_grad_workspace(S), dtype=torch.uint8, device=dev)
+    dtypes = [args.dtype] + ([d for d in ("f32", "bf16", "f16") if d != args.dtype] if args.compare else [])
+    steps = {d: Step(nqs, torch, dev, d, C, T, B, params_h) for d in dtypes}
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
-    out_h = torch.zeros(5 + P, dtype=torch.float64).pin_memory()
-    launches_per_step = 2 + 1 + 1 + 1 + 2 + 2 + 1   # set_params, init, sweep, eloc, stats, force, O rows
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-
-    def step(seed, host_io=False):
-        if host_io:
-            params.copy_(params_h, non_blocking=True)
-        ev[0].record()
-        ctx.set_params(params)
-        ctx.init_chains(state, seed)
-        ev[1].record()
-        ctx.sweep(state, T, B, seed + 1, 0, samples, None, nacc)
-        ev[2].record()
-        ctx.local_energy(samples, eloc)
-        ev[3].record()
-        ctx.stats(eloc, C, stats, nacc, T * N)
-        ctx.logpsi_grad(samples, None, eloc, stats, force, ws)
-        ev[4].record()
-        ctx.logpsi_grad(samples[S - C:], O)
-        ev[5].record()
-        if host_io:
-            out_h[:5].copy_(stats, non_blocking=True)
-            out_h[5:].copy_(force, non_blocking=True)
-
     base_seed = WL.seed * 1000 + rank * 7919
-    for w in range(args.warmup):
-        step(base_seed + w)
-    torch.cuda.synchronize()
+    proposals_step = C * T * N
+    results = {}
 
-    phase = np.zeros(5)
-    step_ms = []
-    acc_total = 0
-    with ClockSampler(dev.index) as clk:
-        if dist:
-            dist.barrier()
+    for d in dtypes:
+        st = steps[d]
+        for w in range(args.warmup):
+            st.run(base_seed + w)
         torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.zero_()                       # L2 flush between timed steps (not timed)
-            step(base_seed + 100 + k)
+        phase = np.zeros(5)
+        step_ms, acc_total, energies = [], 0, []
+        with ClockSampler(dev.index) as clk:
+            if dist:
+                dist.barrier()
             torch.cuda.synchronize()
-            acc_total += int(nacc.sum().item())
-            ph = [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
-            phase += ph
-            step_ms.append(sum(ph))
-        torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.zero_()                       # L2 flush between timed steps (not timed)
+                st.run(base_seed + 100 + k)
+                torch.cuda.synchronize()
+                acc_total += int(st.nacc.sum().item())
+                energies.append(st.stats[:3].cpu().numpy().copy())
+                ph = st.phases()
+                phase += ph
+                step_ms.append(sum(ph))
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+        t_dev = sum(step_ms) / 1e3
         if dist:
-            dist.barrier()
-    t_dev = sum(step_ms) / 1e3
+            tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_dev = tt.item()
+        en = np.array(energies)
+        results[d] = {"t_dev": t_dev, "phase": phase / args.steps, "accepts": acc_total / args.steps,
+                      "clocks": clk.summary(), "E": float(en[:, 0].mean()),
+                      "E_err": float(np.sqrt((en[:, 2] ** 2).sum()) / len(en))}
 
-    # end to end through the public API with host buffers: pinned params in, stats + force out
+    # end to end through the public API with host buffers (primary dtype): pinned FP64
+    # parameters in, statistics and force out
+    st = steps[args.dtype]
     e2e_ms = []
     for k in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        step(base_seed + 200 + k, host_io=True)
+        st.run(base_seed + 200 + k, host_io=True)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-
+    t_e2e = sum(e2e_ms) / 1e3
     if dist:
-        tt = torch.tensor([t_dev, sum(e2e_ms) / 1e3], dtype=torch.float64, device=dev)
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev, t_e2e = tt.tolist()
-        combine_across_ranks(stats, force, S, dist)
-    else:
-        t_e2e = sum(e2e_ms) / 1e3
+        t_e2e = tt.item()
+        combine_across_ranks(st.stats, st.force, st.S, dist)
 
-    proposals_step = C * T * N
-    value = world * proposals_step * args.steps / t_dev
-    ph = phase / args.steps   # ms per phase: prep+init, sweep, eloc, stats+force, O rows
-    accepts_per_step = acc_total / args.steps
+    # stated bias of each 16-bit copy: increment errors against the FP32 copy at that copy's
+    # own sampled states x, y a uniform single flip (the setting of Theorem 3)
+    bias = {}
+    if "f32" in steps:
+        ref = steps["f32"]
+        for d in dtypes:
+            if d == "f32":
+                continue
+            S = steps[d].samples[steps[d].S - C:]
+            g = torch.Generator(device=dev).manual_seed(WL.seed)
+            sites = torch.randint(0, N, (S.shape[0],), generator=g, dtype=torch.int32, device=dev)
+            d_lp = torch.empty(S.shape[0], dtype=torch.float32, device=dev)
+            d_32 = torch.empty(S.shape[0], dtype=torch.float32, device=dev)
+            steps[d].ctx.flip_delta(S, sites, d_lp)
+            ref.ctx.flip_delta(S, sites, d_32)
+            eps = (2.0 * (d_lp.double() - d_32.double())).cpu().numpy()
+            mu, sig = float(eps.mean()), float(eps.std() / math.sqrt(2.0))
+            dE = results[d]["E"] - results["f32"]["E"]
+            bias[d] = {"eps_mean": mu, "eps_std": float(eps.std()), "sigma_delta": sig,
+                       "pinsker_tv_bound": sig / 2, "thm3_tv_bound_r0": thm3_bound(mu, sig),
+                       "tv_bound": min(sig / 2, thm3_bound(mu, sig)),
+                       "energy_vs_f32": dE, "energy_err": math.hypot(results[d]["E_err"], results["f32"]["E_err"]),
+                       "sweep_speed_vs_f32": (results["f32"]["phase"][1] / results[d]["phase"][1])}
+
+    r = results[args.dtype]
+    ph = r["phase"]   # ms per phase: prep+init, sweep, eloc, stats+force, O rows
+    value = world * proposals_step * args.steps / r["t_dev"]
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2032.0))
-    # FP32-pipe roofline of the sweep: per proposal one FMA and one multiply per hidden
-    # unit, per accepted flip three multiplies per hidden unit (lane-ops); peak = 148 SMs
-    # x 128 FP32 lanes x max SM clock.
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    alg_ops = 2.0 * M * proposals_step + 3.0 * M * accepts_per_step
+    # Sweep roofline (arithmetic of the method per proposal): one FMA (factor) and one multiply
+    # (product) per hidden unit, three multiplies per hidden unit per accepted flip, counted as
+    # lane operations; peak = SMs x 128 FP32 lanes x max SM clock.
+    alg_ops = 2.0 * M * proposals_step + 3.0 * M * r["accepts"]
     achieved = alg_ops / (ph[1] / 1e3) / 1e12
     peak = n_sm * 128 * sm_max * 1e6 / 1e12
     line = {
@@ -205,28 +263,36 @@ def run_ours(args, rank, world, dist):
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": t_dev / args.steps * 1e3,
+        "ms_per_step": r["t_dev"] / args.steps * 1e3,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": args.dtype,
+        "dtype": {"f32": "f32", "bf16": "bf16 sampling (f32 caches, accept, statistics)",
+                  "f16": "f16 sampling (f32 caches, accept, statistics)"}[args.dtype],
         "data": "synthetic (seeded random-init RBM, random initial spins)",
         "config": {"workload": WL.name if (C, T) == (WL.n_chains, WL.n_sweeps) else f"{WL.name} (reduced: profiling)",
-                   "lattice": "10x10 periodic", "h": ham.h, "n_hidden": M,
-                   "chains": C, "sweeps": T, "burn_in": B, "samples": S, "params": P,
+                   "lattice": "10x10 periodic", "h": WL.ham.h, "n_hidden": M, "chains": C, "sweeps": T,
+                   "burn_in": B, "samples": (T - B) * C, "params": steps[args.dtype].ctx.P,
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"dp{world} (chains)"},
-        "local_energy": {"value": world * S / (ph[2] / 1e3), "unit": "samples/s", "kernel_ms": ph[2]},
+        "local_energy": {"value": world * (T - B) * C / (ph[2] / 1e3), "unit": "samples/s", "kernel_ms": ph[2]},
         "sweep": {"value": world * proposals_step / (ph[1] / 1e3), "unit": "proposals/s", "kernel_ms": ph[1],
-                  "acceptance": accepts_per_step / proposals_step},
+                  "acceptance": r["accepts"] / proposals_step},
         "phases_ms": {"set_params+init": ph[0], "sweep": ph[1], "local_energy": ph[2],
                       "stats+force": ph[3], "O_rows": ph[4]},
-        "roofline": {"bound": "alu", "kernel": "rbm_sweep_f32_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "note": "FP32-pipe lane-ops/s (FMA counted once) vs 148 SMs x 128 lanes x max SM clock"},
+        "energy": {"E": r["E"], "err": r["E_err"]},
+        "compare": {d: {"value": world * proposals_step * args.steps / results[d]["t_dev"],
+                        "sweep_proposals_per_s": world * proposals_step / (results[d]["phase"][1] / 1e3),
+                        "local_energy_samples_per_s": world * (T - B) * C / (results[d]["phase"][2] / 1e3),
+                        "E": results[d]["E"], "E_err": results[d]["E_err"]}
+                    for d in dtypes if d != args.dtype},
+        "bias": bias,
+        "roofline": {"bound": "alu", "kernel": "rbm_sweep_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "T lane-ops/s", "frac": achieved / peak, "traffic": None,
+                     "note": "method arithmetic per proposal (2M + 3M per accept) vs SMs x 128 FP32 lanes x max clock"},
         "e2e": {"value": world * proposals_step * args.steps / t_e2e, "unit": "proposals/s",
-                "h2d_bytes_per_step": P * 8, "d2h_bytes_per_step": (5 + P) * 8},
-        "gpu_launches": launches_per_step * args.steps,
-        "clocks": clk.summary(),
+                "h2d_bytes_per_step": steps[args.dtype].ctx.P * 8, "d2h_bytes_per_step": (5 + steps[args.dtype].ctx.P) * 8},
+        "gpu_launches": steps[args.dtype].launches * args.steps,
+        "clocks": r["clocks"],
     }
     return line
 
@@ -287,7 +353,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--dtype", default="f16", choices=["f32", "bf16", "f16"],
+                    help="sampling copy of the timed step (the mixed-precision path by default)")
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the FP32 / other-dtype comparison steps and the bias statement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chains", type=int, default=0, help="profiling only: override the chain count")
     ap.add_argument("--sweeps", type=int, default=0, help="profiling only: override the sweep count")

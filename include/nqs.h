@@ -156,8 +156,9 @@ nqs_status nqs_logpsi(nqs_ctx *ctx, const uint32_t *configs, int64_t n, float *o
 nqs_status nqs_flip_delta(nqs_ctx *ctx, const uint32_t *configs, const int32_t *sites, int64_t n, float *out,
                           nqs_stream stream);
 
-/* App. I, Eq. local_energies: eloc[x] = sum_{x' in C(x)} H(x,x') psi(x')/psi(x), FP32
- * accumulation; for a BF16/F16 context the ratios use that copy's factor arithmetic. */
+/* App. I, Eq. local_energies: eloc[x] = sum_{x' in C(x)} H(x,x') psi(x')/psi(x), in FP32
+ * with the FP32 rounding of the master parameters, whatever the context's sampling
+ * dtype (Sec. 4.2: the low-precision copy is used only for sampling). */
 nqs_status nqs_local_energy(nqs_ctx *ctx, const uint32_t *configs, int64_t n, float *eloc,
                             nqs_stream stream);
 

@@ -40,6 +40,10 @@ struct nqs_ctx {
   float *d_Wt = nullptr;    // [N][M_pad] rounded weights, site-major (W^T)
   void *d_R = nullptr;      // [N][M_pad] exp(-4 W) in the sampling dtype
   float2 *d_aK = nullptr;   // [N] (a_i, sum_j W_ji)
+  // FP32 rounding of the master for the local energy (Sec. 4.2: the low-precision copy is
+  // used only for sampling).  For an F32 context these alias the tables above.
+  float *d_a32 = nullptr, *d_b32 = nullptr, *d_Wt32 = nullptr, *d_R32 = nullptr;
+  float2 *d_aK32 = nullptr;
   float *d_Wm = nullptr;    // [N][M] FP32 master weights, site-major (gradients)
   float *d_bm = nullptr;    // [M] FP32 master hidden bias (gradients)
 

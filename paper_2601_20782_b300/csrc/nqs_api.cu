@@ -33,6 +33,11 @@ void free_all(nqs_ctx *c) {
                   c->d_Wt,     c->d_R,       c->d_aK,    c->d_Wm,    c->d_bm};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  if (c->dtype != NQS_F32) {
+    void *p32[] = {c->d_a32, c->d_b32, c->d_Wt32, c->d_R32, c->d_aK32};
+    for (void *p : p32)
+      if (p) cudaFree(p);
+  }
 }
 
 // Bond lists: nearest neighbours (x+1, y) and (x, y+1); J2 bonds (x+1, y+1) and
@@ -152,6 +157,19 @@ nqs_status nqs_create(nqs_ctx **out, const nqs_model_desc *model, const nqs_ham_
       (e = dev_alloc(&c->d_Wt, (size_t)c->N * c->M_pad)) ||
       (e = cudaMalloc(&c->d_R, (size_t)c->N * c->M_pad * tsz)) || (e = dev_alloc(&c->d_aK, c->N + 1)) ||
       (e = dev_alloc(&c->d_Wm, (size_t)c->N * c->M)) || (e = dev_alloc(&c->d_bm, c->M))) {
+    free_all(c);
+    delete c;
+    return fail(nullptr, NQS_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  if (c->dtype == NQS_F32) {
+    c->d_a32 = c->d_a;
+    c->d_b32 = c->d_b;
+    c->d_Wt32 = c->d_Wt;
+    c->d_R32 = (float *)c->d_R;
+    c->d_aK32 = c->d_aK;
+  } else if ((e = dev_alloc(&c->d_a32, c->N)) || (e = dev_alloc(&c->d_b32, c->M_pad)) ||
+             (e = dev_alloc(&c->d_Wt32, (size_t)c->N * c->M_pad)) ||
+             (e = dev_alloc(&c->d_R32, (size_t)c->N * c->M_pad)) || (e = dev_alloc(&c->d_aK32, c->N + 1))) {
     free_all(c);
     delete c;
     return fail(nullptr, NQS_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));

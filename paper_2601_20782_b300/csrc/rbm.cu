@@ -376,6 +376,7 @@ bool rbm_supported(const nqs_ctx *c, std::string *why) {
 cudaError_t rbm_prepare(nqs_ctx *c, const double *params, cudaStream_t s) {
   const int64_t total = (int64_t)c->N * c->M_pad;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)c->num_sms * 8);
+  // sampling copy in its dtype
   if (c->dtype == NQS_F16)
     rbm_prepare_kernel<__half><<<blocks, 256, 0, s>>>(params, c->N, c->M, c->M_pad, c->d_a, c->d_b, c->d_Wt,
                                                       (__half *)c->d_R, c->d_Wm, c->d_bm, c->d_status, 2.5);
@@ -389,6 +390,12 @@ cudaError_t rbm_prepare(nqs_ctx *c, const double *params, cudaStream_t s) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   rbm_colsum_kernel<<<(c->N * 32 + 255) / 256, 256, 0, s>>>(c->d_Wt, c->d_a, c->N, c->M_pad, c->d_aK);
+  if ((e = cudaGetLastError()) != cudaSuccess || c->dtype == NQS_F32) return e;
+  // FP32 copy for the local energy of a 16-bit context
+  rbm_prepare_kernel<float><<<blocks, 256, 0, s>>>(params, c->N, c->M, c->M_pad, c->d_a32, c->d_b32, c->d_Wt32,
+                                                   c->d_R32, c->d_Wm, c->d_bm, c->d_status, 20.0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  rbm_colsum_kernel<<<(c->N * 32 + 255) / 256, 256, 0, s>>>(c->d_Wt32, c->d_a32, c->N, c->M_pad, c->d_aK32);
   return cudaGetLastError();
 }
 
@@ -458,11 +465,16 @@ static ElocParams eloc_params(const nqs_ctx *c, const uint32_t *cfg, const int32
   return p;
 }
 
+// Local energy with the FP32 copy of the master (Sec. 4.2: a 16-bit copy is used only
+// for sampling).
 cudaError_t rbm_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *eloc, cudaStream_t s) {
-  const ElocParams p = eloc_params(c, cfg, nullptr, n, eloc);
-  if (c->dtype == NQS_F16) return rbm_eloc_f16(c, p, s);
-  if (c->dtype == NQS_BF16) return rbm_eloc_bf16(c, p, s);
-  const int L = pick_lanes(c);
+  ElocParams p = eloc_params(c, cfg, nullptr, n, eloc);
+  p.R = c->d_R32;
+  p.aK = c->d_aK32;
+  p.Wt = c->d_Wt32;
+  p.b = c->d_b32;
+  const int E32 = c->M_pad / 32;
+  const int L = (E32 == 1 && c->W <= 8) ? 8 : 32;
   return dispatch_le<Runners<float>::Eloc>(L, c->M_pad / L, c, p, s);
 }
 

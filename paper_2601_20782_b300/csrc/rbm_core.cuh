@@ -80,10 +80,7 @@ struct Lay {
 };
 
 // Sampling-copy arithmetic of the 16-bit tables: pairs of BF16 / F16 values and their
-// packed FMA / multiply (Table tab:precision; the sampling copy of Sec. 4.2).  PD is how
-// many pair factors are multiplied in 16-bit before the product goes to FP32: F16 stops at
-// two (each factor is at most e^{4|W|}, |W| <= 1.38 keeps two below 65504; a larger
-// product overflows to inf and the group takes the exact path), BF16 has the FP32 range.
+// packed FMA (Table tab:precision; the sampling copy of Sec. 4.2).
 template <typename TT>
 struct Prec;
 template <>
@@ -93,7 +90,6 @@ struct Prec<float> {  // the FP32 sampling copy has no 16-bit shadows
 template <>
 struct Prec<__half> {
   using T2 = __half2;
-  static constexpr int PD = 2;
   __device__ static __forceinline__ T2 from_f2(float2 v) { return __float22half2_rn(v); }
   __device__ static __forceinline__ float2 to_f2(T2 v) { return __half22float2(v); }
   __device__ static __forceinline__ T2 fma(T2 a, T2 b, T2 c) { return __hfma2(a, b, c); }
@@ -104,7 +100,6 @@ struct Prec<__half> {
 template <>
 struct Prec<__nv_bfloat16> {
   using T2 = __nv_bfloat162;
-  static constexpr int PD = 4;
   __device__ static __forceinline__ T2 from_f2(float2 v) { return __float22bfloat162_rn(v); }
   __device__ static __forceinline__ float2 to_f2(T2 v) { return __bfloat1622float2(v); }
   __device__ static __forceinline__ T2 fma(T2 a, T2 b, T2 c) { return __hfma2(a, b, c); }
@@ -274,9 +269,10 @@ __device__ __forceinline__ float flip_logsum(bool up, const float2 (&lam)[Lay<L,
   return group_allsum<L>(flip_partial_exact<L, E>(up, lam, mu, row, gl));
 }
 
-// Low-precision counterpart of flip_partial: factors g and their products in 16-bit
-// pair arithmetic from the 16-bit shadows and table, PD pair factors per 16-bit product,
-// up to 8 units per FP32 product and MUFU lg2.
+// Low-precision counterpart of flip_partial: the factors g are formed in 16-bit pair
+// arithmetic from the 16-bit shadows and table (the network's elementwise math in the
+// sampling dtype); their product over hidden units is the reduction of the log-amplitude
+// and is taken in FP32 (App. I: reductions in higher precision), up to 8 units per MUFU lg2.
 template <int L, int E, typename TT>
 __device__ __forceinline__ float flip_partial_lp(bool up, const typename Prec<TT>::T2 (&lh)[Lay<L, E>::H],
                                                 const typename Prec<TT>::T2 (&mh)[Lay<L, E>::H], const TT *row,
@@ -288,17 +284,11 @@ __device__ __forceinline__ float flip_partial_lp(bool up, const typename Prec<TT
   float part = 0.f;
 #pragma unroll
   for (int k0 = 0; k0 < LY::H; k0 += 4) {
-    float acc = 1.f;
+    float2 pr = P::to_f2(up ? P::fma(lh[k0], rv[k0], mh[k0]) : P::fma(mh[k0], rv[k0], lh[k0]));
 #pragma unroll
-    for (int k1 = k0; k1 < (k0 + 4 < LY::H ? k0 + 4 : LY::H); k1 += P::PD) {
-      typename P::T2 pr = up ? P::fma(lh[k1], rv[k1], mh[k1]) : P::fma(mh[k1], rv[k1], lh[k1]);
-#pragma unroll
-      for (int k = k1 + 1; k < (k1 + P::PD < (k0 + 4 < LY::H ? k0 + 4 : LY::H) ? k1 + P::PD : (k0 + 4 < LY::H ? k0 + 4 : LY::H)); ++k)
-        pr = P::mul(pr, up ? P::fma(lh[k], rv[k], mh[k]) : P::fma(mh[k], rv[k], lh[k]));
-      const float2 f = P::to_f2(pr);
-      acc *= f.x * f.y;
-    }
-    part += lg2_approx(acc);
+    for (int k = k0 + 1; k < (k0 + 4 < LY::H ? k0 + 4 : LY::H); ++k)
+      pr = mul2(pr, P::to_f2(up ? P::fma(lh[k], rv[k], mh[k]) : P::fma(mh[k], rv[k], lh[k])));
+    part += lg2_approx(pr.x * pr.y);
   }
   return part;
 }

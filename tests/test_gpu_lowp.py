@@ -128,3 +128,13 @@ def test_lowp_energy_matches_fp64_within_error_and_bound():
     A = np.abs(eps_x).max()
     bias_bound = 2 * A * bounds.reported_bound(eps.mean(), eps.std())
     assert abs(E - e_exact) <= 3 * err + bias_bound, (E, e_exact, err, bias_bound)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_local_energy_of_a_16bit_context_uses_the_fp32_copy(dtype):
+    ctx, model, _ = make(10, 10, 400, 0.05, 9, dtype)
+    s = np.random.default_rng(2).choice([-1, 1], size=(300, 100)).astype(np.int8)
+    e = torch.empty(300, dtype=torch.float32, device="cuda")
+    ctx.local_energy(to_words_tensor(pack_np(s)), e)
+    ref = oracle_eloc(TFIM(10, 10, 1.0, 3.04), model.logpsi, s)
+    np.testing.assert_allclose(e.cpu().numpy(), ref, rtol=1e-5, atol=1e-5 * 200)
