@@ -71,9 +71,12 @@ typedef struct {
   int32_t marshall;
 } nqs_ham_desc;
 
-/* Ansatz.  RBM (App. G): n_hidden = M.  DENSE: n_layers hidden widths in widths[]
- * (host array, copied), a_1 = log cosh(W1 s + b1), a_l = tanh(W_l a_{l-1} + b_l),
- * log psi = w_out . a_L + b_out. */
+/* Ansatz.  RBM (App. G): n_hidden = M; sampling copy F32, BF16 or F16; TFIM only.
+ * DENSE: n_layers (2..8) hidden widths in widths[] (host array, copied; multiples of
+ * 16), a_1 = log cosh(W1 s + b1), a_l = tanh(W_l a_{l-1} + b_l), log psi = w_out . a_L
+ * + b_out; sampling copy BF16 (layers >= 2 on the tensor cores, FP32 accumulation);
+ * TFIM (single flips) or HEISENBERG (exchange moves).  nqs_logpsi_grad of a dense
+ * context is FP32 from the FP32 rounding of the master and needs no workspace. */
 typedef struct {
   int32_t kind;
   int32_t n_hidden;
@@ -97,11 +100,14 @@ int32_t nqs_words_per_config(const nqs_ctx *ctx);  /* W = ceil(N/32) */
 int64_t nqs_n_params(const nqs_ctx *ctx);          /* P */
 int32_t nqs_n_bonds(const nqs_ctx *ctx);           /* bonds of the Hamiltonian */
 
-/* Tuning knobs.  NQS_OPT_REFRESH: the RBM sweep recomputes its per-chain cache
- * from scratch every this many sweeps (default 20, >= 1).
+/* Tuning knobs.  NQS_OPT_REFRESH: the sweep recomputes its per-chain cache from
+ * scratch every this many sweeps (default 20, >= 1).
  * NQS_OPT_CHAINS_PER_WARP: RBM sweep lanes per chain = 32 / value (1, 2 or 4;
- * 0 = chosen by the built-in tuner). */
-enum { NQS_OPT_REFRESH = 0, NQS_OPT_CHAINS_PER_WARP = 1 };
+ * 0 = chosen by the built-in rule).
+ * NQS_OPT_MAX_ROWS: dense contexts only -- rows of one forward pass held in the
+ * context's workspace (default 65536); bounds the chains of nqs_sweep and sets the
+ * chunk of nqs_logpsi / nqs_local_energy.  Reallocates (synchronous). */
+enum { NQS_OPT_REFRESH = 0, NQS_OPT_CHAINS_PER_WARP = 1, NQS_OPT_MAX_ROWS = 2 };
 nqs_status nqs_set_option(nqs_ctx *ctx, int32_t option, int64_t value);
 
 /* Sec. 4.2 (two-copy scheme): the FP64 master parameters (device, P doubles) are

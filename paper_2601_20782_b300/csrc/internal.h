@@ -6,6 +6,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "../../include/nqs.h"
 
 struct nqs_ctx {
@@ -46,6 +49,30 @@ struct nqs_ctx {
   float2 *d_aK32 = nullptr;
   float *d_Wm = nullptr;    // [N][M] FP32 master weights, site-major (gradients)
   float *d_bm = nullptr;    // [M] FP32 master hidden bias (gradients)
+
+  // ---- dense ansatz: widths H[0..L-1]; layer l >= 1 is a tensor-core GEMM --------------
+  int L = 0;
+  std::vector<int> H, Kp;          // Kp[l]: padded input width of layer l (Kp[0] unused)
+  float *d_W1t = nullptr;          // [N][H0] FP32 sampling-copy layer-1 weights, site-major
+  float *d_b1 = nullptr;           // [H0]
+  std::vector<__nv_bfloat16 *> d_Wl;  // layer l >= 1: [H[l]][Kp[l]] BF16 sampling copy
+  std::vector<float *> d_bl;       // layer l >= 1: [H[l]] bias (sampling copy, FP32 values)
+  float *d_wout = nullptr;         // [H[L-1]]
+  float b_out = 0.f;
+  std::vector<CUtensorMap> mB0, mB1;  // per layer l >= 1
+  std::vector<int> NR, p0, p1;        // per layer l >= 1: columns per CTA and the two MMA parts
+  float *d_master = nullptr;       // [P] FP32 master parameters (backward)
+  // workspace for up to max_rows rows per pass
+  int64_t max_rows = 0;
+  __nv_bfloat16 *d_act[2] = {nullptr, nullptr};  // activations [max_rows][max Kp]
+  float *d_part = nullptr;         // [max_rows][max ranges] DOT partials
+  float *d_out = nullptr;          // [max_rows] log psi of the rows
+  float *d_z1 = nullptr;           // [max_rows][H0] FP32 layer-1 pre-activations (per sample / chain)
+  float *d_lp = nullptr;           // [max_rows] log psi per sample / chain
+  int32_t *d_prop = nullptr;       // [max_rows] proposed bond (or -1) per chain
+  float *d_thr = nullptr;          // [max_rows] log u per chain
+  float *d_grad_scratch = nullptr; // O rows for the force when the caller gives none
+  int grad_chunk = 0;
 
   std::string err;
 };
@@ -89,6 +116,25 @@ cudaError_t rbm_force_tc(const nqs_ctx *c, const uint32_t *cfg, int64_t n, const
                          double *ws, int chunks, cudaStream_t s);
 cudaError_t rbm_force_into(const nqs_ctx *c, const uint32_t *cfg, int64_t n, const float *eloc, const double *stats,
                            double *force, double *scratch, int chunks, cudaStream_t s);
+
+// dense.cu
+bool dense_setup(nqs_ctx *c, const nqs_model_desc *m, std::string *why);
+void dense_free(nqs_ctx *c);
+cudaError_t dense_alloc_rows(nqs_ctx *c, int64_t rows);
+cudaError_t dense_alloc_params(nqs_ctx *c);
+cudaError_t dense_prepare(nqs_ctx *c, const double *params, cudaStream_t s);
+cudaError_t dense_logpsi(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *out, cudaStream_t s);
+cudaError_t dense_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *eloc, cudaStream_t s);
+cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t n_chains, int n_sweeps, int burn_in, uint64_t seed,
+                        uint32_t sweep_offset, uint32_t *samples, float *logpsi, int64_t *n_acc, uint32_t *acc_bits,
+                        float *delta, cudaStream_t s);
+cudaError_t dense_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
+                              const double *stats, double *force, cudaStream_t s);
+// dense_gemm.cu
+bool make_tmap_bf16_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);
+cudaError_t dense_gemm(const nqs_ctx *c, const __nv_bfloat16 *A, int R, int Kpad, const CUtensorMap &mB0,
+                       const CUtensorMap &mB1, int N, int NR, int p0, int p1, int mode, const float *bias,
+                       const float *w, __nv_bfloat16 *out_act, int ld_out, float *out_part, cudaStream_t s);
 
 // stats.cu
 cudaError_t energy_stats(const nqs_ctx *c, const float *eloc, int64_t n, int64_t n_chains,

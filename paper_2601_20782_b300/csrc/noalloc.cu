@@ -53,6 +53,7 @@ extern "C" nqs_status nqs_force_noalloc(nqs_ctx *c, const uint32_t *configs, int
     return st;
   };
   if (!c->params_set) return fail(NQS_EINVAL, "nqs_force_noalloc: parameters not set");
+  if (c->model_kind != NQS_RBM) return fail(NQS_EUNSUPPORTED, "nqs_force_noalloc: RBM contexts only");
   if (n <= 0 || !configs || !eloc || !stats || !force)
     return fail(NQS_EINVAL, "nqs_force_noalloc: needs n > 0 and non-null configs, eloc, stats, force");
   const size_t per_chunk = (size_t)c->P * sizeof(double);

@@ -138,8 +138,12 @@ nqs_status nqs_create(nqs_ctx **out, const nqs_model_desc *model, const nqs_ham_
       return fail(nullptr, NQS_EUNSUPPORTED, why);
     }
   } else {
-    delete c;
-    return fail(nullptr, NQS_EUNSUPPORTED, "dense ansatz not built");
+    if (!nqs::dense_setup(c, model, &why)) {
+      delete c;
+      return fail(nullptr, NQS_EUNSUPPORTED, why);
+    }
+    c->M = 32;  // the RBM tables below are not used by a dense context (kept minimal)
+    c->M_pad = 32;
   }
   if (ham->kind == NQS_HEISENBERG && (c->N % 2) != 0) {
     delete c;
@@ -181,12 +185,19 @@ nqs_status nqs_create(nqs_ctx **out, const nqs_model_desc *model, const nqs_ham_
     delete c;
     return cuda_fail(nullptr, e, "nqs_create");
   }
+  if (c->model_kind == NQS_DENSE && (e = nqs::dense_alloc_params(c)) != cudaSuccess) {
+    nqs::dense_free(c);
+    free_all(c);
+    delete c;
+    return fail(nullptr, NQS_ENOMEM, std::string("dense allocation failed: ") + cudaGetErrorString(e));
+  }
   *out = c;
   return NQS_OK;
 }
 
 void nqs_destroy(nqs_ctx *c) {
   if (!c) return;
+  if (c->model_kind == NQS_DENSE) nqs::dense_free(c);
   free_all(c);
   delete c;
 }
@@ -197,6 +208,12 @@ nqs_status nqs_set_option(nqs_ctx *c, int32_t option, int64_t value) {
     if (value < 1 || value > (1 << 30)) return fail(c, NQS_EINVAL, "refresh must be >= 1");
     c->refresh = (int)value;
     return NQS_OK;
+  }
+  if (option == NQS_OPT_MAX_ROWS) {
+    if (c->model_kind != NQS_DENSE) return NQS_OK;
+    if (value < 128 || value > (int64_t)1 << 24) return fail(c, NQS_EINVAL, "max rows: 128 .. 2^24");
+    cudaError_t e = nqs::dense_alloc_rows(c, value);
+    return e == cudaSuccess ? NQS_OK : fail(c, NQS_ENOMEM, "dense workspace allocation failed");
   }
   if (option == NQS_OPT_CHAINS_PER_WARP) {
     if (value != 0 && value != 1 && value != 2 && value != 4) return fail(c, NQS_EINVAL, "chains per warp: 0, 1, 2 or 4");
@@ -213,7 +230,8 @@ nqs_status nqs_set_params(nqs_ctx *c, const double *params, nqs_stream stream) {
   int zero = 0;
   cudaError_t e = cudaMemcpyAsync(c->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "nqs_set_params");
-  if ((e = nqs::rbm_prepare(c, params, s)) != cudaSuccess) return cuda_fail(c, e, "nqs_set_params");
+  e = c->model_kind == NQS_DENSE ? nqs::dense_prepare(c, params, s) : nqs::rbm_prepare(c, params, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "nqs_set_params");
   int st = 0;
   if ((e = cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -246,9 +264,16 @@ nqs_status nqs_sweep(nqs_ctx *c, uint32_t *state, int64_t n_chains, int32_t n_sw
   if ((uint64_t)sweep_offset + (uint64_t)n_sweeps > (1ull << 32)) return fail(c, NQS_EINVAL, "sweep counter overflow");
   if (n_chains == 0 || n_sweeps == 0) return NQS_OK;
   if (bad_ptr(state)) return fail(c, NQS_EINVAL, "nqs_sweep: null state");
-  cudaError_t e = nqs::rbm_sweep(c, state, n_chains, n_sweeps, burn_in, seed, sweep_offset, samples, logpsi,
-                                 n_accepted, trace ? trace->accept_bits : nullptr, trace ? trace->delta : nullptr,
-                                 reinterpret_cast<cudaStream_t>(stream));
+  if (c->model_kind == NQS_DENSE && n_chains > c->max_rows)
+    return fail(c, NQS_EINVAL, "nqs_sweep: more chains than the dense workspace rows (NQS_OPT_MAX_ROWS)");
+  cudaError_t e =
+      c->model_kind == NQS_DENSE
+          ? nqs::dense_sweep(c, state, n_chains, n_sweeps, burn_in, seed, sweep_offset, samples, logpsi, n_accepted,
+                             trace ? trace->accept_bits : nullptr, trace ? trace->delta : nullptr,
+                             reinterpret_cast<cudaStream_t>(stream))
+          : nqs::rbm_sweep(c, state, n_chains, n_sweeps, burn_in, seed, sweep_offset, samples, logpsi, n_accepted,
+                           trace ? trace->accept_bits : nullptr, trace ? trace->delta : nullptr,
+                           reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_sweep");
 }
 
@@ -257,7 +282,8 @@ nqs_status nqs_logpsi(nqs_ctx *c, const uint32_t *cfg, int64_t n, float *out, nq
   if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_logpsi: parameters not set");
   if (n < 0 || (n > 0 && (bad_ptr(cfg) || bad_ptr(out)))) return fail(c, NQS_EINVAL, "nqs_logpsi: bad arguments");
   if (n == 0) return NQS_OK;
-  cudaError_t e = nqs::rbm_logpsi(c, cfg, n, out, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e = c->model_kind == NQS_DENSE ? nqs::dense_logpsi(c, cfg, n, out, reinterpret_cast<cudaStream_t>(stream))
+                                             : nqs::rbm_logpsi(c, cfg, n, out, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_logpsi");
 }
 
@@ -266,7 +292,9 @@ nqs_status nqs_local_energy(nqs_ctx *c, const uint32_t *cfg, int64_t n, float *e
   if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_local_energy: parameters not set");
   if (n < 0 || (n > 0 && (bad_ptr(cfg) || bad_ptr(eloc)))) return fail(c, NQS_EINVAL, "nqs_local_energy: bad arguments");
   if (n == 0) return NQS_OK;
-  cudaError_t e = nqs::rbm_local_energy(c, cfg, n, eloc, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e = c->model_kind == NQS_DENSE
+                      ? nqs::dense_local_energy(c, cfg, n, eloc, reinterpret_cast<cudaStream_t>(stream))
+                      : nqs::rbm_local_energy(c, cfg, n, eloc, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_local_energy");
 }
 
@@ -274,7 +302,8 @@ nqs_status nqs_flip_delta(nqs_ctx *c, const uint32_t *cfg, const int32_t *sites,
                           nqs_stream stream) {
   if (!c) return NQS_EINVAL;
   if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_flip_delta: parameters not set");
-  if (c->ham_kind != NQS_TFIM) return fail(c, NQS_EUNSUPPORTED, "nqs_flip_delta: single-flip (TFIM) contexts only");
+  if (c->ham_kind != NQS_TFIM || c->model_kind != NQS_RBM)
+    return fail(c, NQS_EUNSUPPORTED, "nqs_flip_delta: RBM single-flip (TFIM) contexts only");
   if (n < 0 || (n > 0 && (bad_ptr(cfg) || bad_ptr(sites) || bad_ptr(out))))
     return fail(c, NQS_EINVAL, "nqs_flip_delta: bad arguments");
   if (n == 0) return NQS_OK;
@@ -283,7 +312,7 @@ nqs_status nqs_flip_delta(nqs_ctx *c, const uint32_t *cfg, const int32_t *sites,
 }
 
 size_t nqs_logpsi_grad_workspace(const nqs_ctx *c, int64_t n) {
-  if (!c || n <= 0) return 0;
+  if (!c || n <= 0 || c->model_kind == NQS_DENSE) return 0;
   return nqs::rbm_grad_workspace(c, n);
 }
 
@@ -294,7 +323,7 @@ nqs_status nqs_logpsi_grad(nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O,
   if (n < 0 || (n > 0 && bad_ptr(cfg))) return fail(c, NQS_EINVAL, "nqs_logpsi_grad: bad arguments");
   if (force && (bad_ptr(eloc) || bad_ptr(stats)))
     return fail(c, NQS_EINVAL, "nqs_logpsi_grad: the force needs eloc and stats");
-  if (force && n > 0 && (bad_ptr(ws) || ws_bytes < nqs::rbm_grad_workspace(c, n)))
+  if (force && n > 0 && c->model_kind == NQS_RBM && (bad_ptr(ws) || ws_bytes < nqs::rbm_grad_workspace(c, n)))
     return fail(c, NQS_EINVAL, "nqs_logpsi_grad: workspace too small");
   if (n == 0) {
     if (force) {
@@ -303,7 +332,10 @@ nqs_status nqs_logpsi_grad(nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O,
     }
     return NQS_OK;
   }
-  cudaError_t e = nqs::rbm_logpsi_grad(c, cfg, n, O, eloc, stats, force, ws, reinterpret_cast<cudaStream_t>(stream));
+  cudaError_t e =
+      c->model_kind == NQS_DENSE
+          ? nqs::dense_logpsi_grad(c, cfg, n, O, eloc, stats, force, reinterpret_cast<cudaStream_t>(stream))
+          : nqs::rbm_logpsi_grad(c, cfg, n, O, eloc, stats, force, ws, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_logpsi_grad");
 }
 

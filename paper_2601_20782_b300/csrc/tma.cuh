@@ -1,0 +1,31 @@
+// Tensor Memory Accelerator: host-side tiled tensor maps (through the driver entry point,
+// so the library does not link libcuda) and the device-side 2D tiled load.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace nqs {
+
+// 2D row-major BF16 matrix [rows x cols] (cols contiguous) read in boxes of box_rows x 64
+// with the 128-byte swizzle (64 BF16 = 128 bytes per box row).  cols * 2 must be a
+// multiple of 16 and the base 16-byte aligned.  Out-of-range rows/cols read as zero.
+bool make_tmap_bf16_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);
+
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *map, int32_t x, int32_t y,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+}  // namespace nqs
