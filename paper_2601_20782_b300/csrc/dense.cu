@@ -29,6 +29,11 @@ __device__ __forceinline__ float log_cosh_f(float z) {
   z = fabsf(z);
   return z + log1pf(expf(-2.f * z)) - LN2;
 }
+// MUFU form for activations that are rounded to BF16 right after (error ~1e-6 << 2^-9)
+__device__ __forceinline__ float log_cosh_fast(float z) {
+  z = fabsf(z);
+  return z + __logf(1.f + __expf(-2.f * z)) - LN2;
+}
 
 // ------------------------------------------------------------------------------------
 // sampling copy and FP32 master from the FP64 parameters
@@ -61,28 +66,33 @@ __global__ void dense_prepare_layer_kernel(const double *__restrict__ p, int64_t
 }
 
 // ------------------------------------------------------------------------------------
-// z0 = W_0 s + b_0 for n configurations (one warp per configuration, FP32)
-__global__ void dense_z0_kernel(const uint32_t *__restrict__ cfg, int64_t n, const float *__restrict__ W1t,
-                                const float *__restrict__ b1, int N, int W, int H0, float *z0) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t x = gw; x < n; x += nw) {
-    for (int j0 = 0; j0 < H0; j0 += 32 * 4) {
-      float acc[4];
-      for (int u = 0; u < 4; ++u) acc[u] = (j0 + lane + 32 * u < H0) ? b1[j0 + lane + 32 * u] : 0.f;
-      for (int w = 0; w < W; ++w) {
-        const uint32_t word = cfg[x * W + w];
-        const int nb = min(32, N - 32 * w);
-        for (int bit = 0; bit < nb; ++bit) {
-          const float s = ((word >> bit) & 1u) ? 1.f : -1.f;
-          const float *row = W1t + (int64_t)(32 * w + bit) * H0 + j0 + lane;
-          for (int u = 0; u < 4; ++u)
-            if (j0 + lane + 32 * u < H0) acc[u] = fmaf(s, row[32 * u], acc[u]);
-        }
+// z0 = W_0 s + b_0 for n configurations, FP32.  Block: 32 configurations; thread j owns
+// hidden units j, j + 256, ... and keeps 32 accumulators; each W_0 row is read once per block.
+constexpr int Z0_ROWS = 32;
+__global__ void __launch_bounds__(256) dense_z0_kernel(const uint32_t *__restrict__ cfg, int64_t n,
+                                                       const float *__restrict__ W1t, const float *__restrict__ b1,
+                                                       int N, int W, int H0, float *z0) {
+  __shared__ uint32_t sw[Z0_ROWS * 32];  // packed spins of the block's rows (W <= 32)
+  for (int64_t x0 = (int64_t)blockIdx.x * Z0_ROWS; x0 < n; x0 += (int64_t)gridDim.x * Z0_ROWS) {
+    const int nr = (int)(n - x0 < Z0_ROWS ? n - x0 : Z0_ROWS);
+    __syncthreads();
+    for (int q = threadIdx.x; q < Z0_ROWS * W; q += blockDim.x) {
+      const int r = q / W, w = q % W;
+      sw[r * 32 + w] = r < nr ? cfg[(x0 + r) * W + w] : 0u;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < H0; j += blockDim.x) {
+      float acc[Z0_ROWS];
+      const float bj = b1[j];
+#pragma unroll
+      for (int r = 0; r < Z0_ROWS; ++r) acc[r] = bj;
+      for (int i = 0; i < N; ++i) {
+        const float w = W1t[(int64_t)i * H0 + j];
+        const float wn = -w;
+#pragma unroll
+        for (int r = 0; r < Z0_ROWS; ++r) acc[r] += ((sw[r * 32 + (i >> 5)] >> (i & 31)) & 1u) ? w : wn;
       }
-      for (int u = 0; u < 4; ++u)
-        if (j0 + lane + 32 * u < H0) z0[x * H0 + j0 + lane + 32 * u] = acc[u];
+      for (int r = 0; r < nr; ++r) z0[(x0 + r) * H0 + j] = acc[r];
     }
   }
 }
@@ -106,10 +116,25 @@ struct A1Args {
   const float *z0;
   const float *W1t;
   const int2 *bonds;
-  const int32_t *prop;
+  int32_t *prop;
+  float *thr;
   __nv_bfloat16 *act;
   int64_t R;
   int N, W, H0, Kp1, nconn, mode, exchange;
+  // sampler proposal (mode 2): Philox counter (p/2, sweep_id, chain, TAG_SWEEP)
+  int p, n_moves;
+  uint32_t sweep_id, k0, k1;
+  // sampler bookkeeping (mode 2, and mode 3 = apply only): the previous step's decision
+  // (acc[c], move prop[c]) is applied first (FP32 z0 update, spin move); then, if
+  // emit_row >= 0, the configuration after the previous sweep is written out.
+  uint32_t *state;
+  float *z0w;
+  const int32_t *acc;
+  const float *lp;
+  uint32_t *samples;
+  float *logpsi;
+  int64_t C;
+  int apply_prev, emit_row;
 };
 
 __device__ __forceinline__ bool row_move(const A1Args &a, int64_t r, int64_t *src, Move *mv) {
@@ -121,9 +146,23 @@ __device__ __forceinline__ bool row_move(const A1Args &a, int64_t r, int64_t *sr
   if (a.mode == 1) {
     *src = r / (1 + a.nconn);
     m = (int)(r % (1 + a.nconn)) - 1;
-  } else {
+  } else {  // draw proposal p of this sweep for chain r (Philox words (0,1) / (2,3))
     *src = r;
-    m = a.prop[r];
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)(a.p / 2), a.sweep_id, (uint32_t)r, TAG_SWEEP), a.k0, a.k1);
+    const uint32_t wm = (a.p & 1) ? w.z : w.x, wu = (a.p & 1) ? w.w : w.y;
+    m = (int)index_from_word(wm, (uint32_t)a.n_moves);
+    const uint32_t k = wu >> 8;
+    bool ident = false;
+    if (a.exchange) {
+      const int2 b = a.bonds[m];
+      ident = spin_of(a.cfg, a.W, r, b.x) == spin_of(a.cfg, a.W, r, b.y);  // identity: always accepted
+    }
+    __syncwarp();  // every lane has read prop[r] (apply_pending) before it is replaced
+    if ((threadIdx.x & 31) == 0) {
+      a.thr[r] = k == 0u ? -INFINITY : logf((float)k * 5.9604644775390625e-8f);
+      a.prop[r] = ident ? -1 : m;
+    }
+    if (ident) return false;
   }
   if (m < 0) return false;
   if (a.exchange) {
@@ -137,11 +176,49 @@ __device__ __forceinline__ bool row_move(const A1Args &a, int64_t r, int64_t *sr
   return true;
 }
 
+// Sampler bookkeeping of chain c before its next proposal (see A1Args).
+__device__ __forceinline__ void apply_pending(const A1Args &a, int64_t c, int lane) {
+  if (a.apply_prev && a.acc[c]) {
+    const int m = a.prop[c];
+    if (m >= 0) {
+      int i, j;
+      if (a.exchange) {
+        const int2 b = a.bonds[m];
+        i = b.x;
+        j = b.y;
+      } else {
+        i = m;
+        j = -1;
+      }
+      const float si = (float)spin_of(a.state, a.W, c, i);
+      float *z = a.z0w + c * a.H0;
+      const float *wi = a.W1t + (int64_t)i * a.H0;
+      const float *wj = a.W1t + (int64_t)(j < 0 ? 0 : j) * a.H0;
+      for (int k = lane; k < a.H0; k += 32) z[k] = fmaf(-2.f * si, j < 0 ? wi[k] : wi[k] - wj[k], z[k]);
+      __syncwarp();
+      if (lane == 0) {
+        a.state[c * a.W + (i >> 5)] ^= 1u << (i & 31);
+        if (j >= 0) a.state[c * a.W + (j >> 5)] ^= 1u << (j & 31);
+      }
+      __syncwarp();
+    }
+  }
+  if (a.emit_row >= 0) {
+    const int64_t row = (int64_t)a.emit_row * a.C + c;
+    if (a.samples)
+      for (int w = lane; w < a.W; w += 32) a.samples[row * a.W + w] = a.state[c * a.W + w];
+    if (lane == 0 && a.logpsi) a.logpsi[row] = a.lp[c];
+  }
+  __syncwarp();
+}
+
 __global__ void dense_a1_kernel(const A1Args a) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = gw; r < a.R; r += nw) {
+    if (a.mode >= 2) apply_pending(a, r, lane);
+    if (a.mode == 3) continue;
     int64_t src;
     Move mv{0, -1};
     const bool moved = row_move(a, r, &src, &mv);
@@ -159,7 +236,7 @@ __global__ void dense_a1_kernel(const A1Args a) {
         z0v = fmaf(-2.f * si, d0, z0v);
         z1v = fmaf(-2.f * si, d1, z1v);
       }
-      *reinterpret_cast<__nv_bfloat162 *>(out + k) = __floats2bfloat162_rn(log_cosh_f(z0v), log_cosh_f(z1v));
+      *reinterpret_cast<__nv_bfloat162 *>(out + k) = __floats2bfloat162_rn(log_cosh_fast(z0v), log_cosh_fast(z1v));
     }
   }
 }
@@ -168,7 +245,7 @@ __global__ void dense_a1_kernel(const A1Args a) {
 __global__ void dense_sum_kernel(const float *part, int64_t R, int n_ranges, const float *b_out, float *out) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
     float s = b_out[0];
-    for (int q = 0; q < n_ranges; ++q) s += part[r * n_ranges + q];
+    for (int q = 0; q < 2 * n_ranges; ++q) s += part[r * 2 * n_ranges + q];
     out[r] = s;
   }
 }
@@ -213,98 +290,46 @@ __global__ void dense_eloc_combine_kernel(const uint32_t *__restrict__ cfg, int6
 // ------------------------------------------------------------------------------------
 // Sampler.  Proposal p of sweep t of chain c: Philox counter (p/2, sweep, c, TAG_SWEEP),
 // words (0,1) for even p and (2,3) for odd p: move = (w * n_moves) >> 32 (a bond of the
-// Hamiltonian for Heisenberg, a site for TFIM), u = (w' >> 8) 2^-24.
-__global__ void dense_propose_kernel(const uint32_t *__restrict__ state, int64_t C, int W, int exchange, int n_moves,
-                                     const int2 *bonds, int p, uint32_t sweep_id, uint32_t k0, uint32_t k1,
-                                     int32_t *prop, float *thr) {
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)(p / 2), sweep_id, (uint32_t)c, TAG_SWEEP), k0, k1);
-    const uint32_t wm = (p & 1) ? w.z : w.x, wu = (p & 1) ? w.w : w.y;
-    const int m = (int)index_from_word(wm, (uint32_t)n_moves);
-    const uint32_t k = wu >> 8;
-    thr[c] = k == 0u ? -INFINITY : logf((float)k * 5.9604644775390625e-8f);
-    int mv = m;
-    if (exchange) {
-      const int2 b = bonds[m];
-      if (spin_of(state, W, c, b.x) == spin_of(state, W, c, b.y)) mv = -1;  // identity: always accepted
-    }
-    prop[c] = mv;
-  }
-}
-
-struct AcceptArgs {
-  uint32_t *state;
-  float *z0;
+// Hamiltonian for Heisenberg, a site for TFIM), u = (w' >> 8) 2^-24.  The draw happens
+// in dense_a1_kernel (mode 2), which also writes the proposal's layer-0 row.
+struct DecideArgs {
+  const float *part;
+  int n_ranges;
+  const float *b_out;
   float *lp;
-  const float *lp_new;
   const int32_t *prop;
   const float *thr;
-  const float *W1t;
-  const int2 *bonds;
+  int32_t *acc;
   int64_t *n_acc;
   uint32_t *acc_bits;
   float *delta;
-  uint32_t *samples;
-  float *logpsi;
   int64_t C;
-  int N, W, H0, exchange, p, t, n_sweeps, emit_row;  // emit_row < 0: no sample this step
-  int first;  // reset n_acc
+  int N, W, p, t, n_sweeps, first;
 };
 
-// One warp per chain: decision u < exp(2 (log psi(y) - log psi(x))), then on accept the
-// FP32 z0 update (one or two columns of W_0), the spin move and the cached log psi.
-__global__ void dense_accept_kernel(const AcceptArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = gw; c < a.C; c += nw) {
+// log psi of the proposals (sum of the last layer's partials) and the decision
+// u < exp(2 (log psi(y) - log psi(x))): thread per chain; the accepted move itself is
+// applied by the next dense_a1_kernel (or the closing apply pass).
+__global__ void dense_decide_kernel(const DecideArgs a) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < a.C; c += (int64_t)gridDim.x * blockDim.x) {
     const int m = a.prop[c];
-    bool acc;
+    bool acc = true;
     float dlt = 0.f;
-    if (m < 0) {
-      acc = true;
-    } else {
-      dlt = a.lp_new[c] - a.lp[c];
+    if (m >= 0) {
+      float lpn = a.b_out[0];
+      for (int q = 0; q < 2 * a.n_ranges; ++q) lpn += a.part[c * 2 * a.n_ranges + q];
+      dlt = lpn - a.lp[c];
       acc = 2.f * dlt > a.thr[c];
+      if (acc) a.lp[c] = lpn;
     }
-    if (acc && m >= 0) {
-      int i, j;
-      if (a.exchange) {
-        const int2 b = a.bonds[m];
-        i = b.x;
-        j = b.y;
-      } else {
-        i = m;
-        j = -1;
-      }
-      const float si = (float)spin_of(a.state, a.W, c, i);
-      float *z = a.z0 + c * a.H0;
-      const float *wi = a.W1t + (int64_t)i * a.H0;
-      const float *wj = a.W1t + (int64_t)(j < 0 ? 0 : j) * a.H0;
-      for (int k = lane; k < a.H0; k += 32) z[k] = fmaf(-2.f * si, j < 0 ? wi[k] : wi[k] - wj[k], z[k]);
-      __syncwarp();
-      if (lane == 0) {
-        a.state[c * a.W + (i >> 5)] ^= 1u << (i & 31);
-        if (j >= 0) a.state[c * a.W + (j >> 5)] ^= 1u << (j & 31);
-        a.lp[c] = a.lp_new[c];
-      }
+    a.acc[c] = acc ? 1 : 0;
+    if (a.n_acc) a.n_acc[c] = (a.first ? 0 : a.n_acc[c]) + (acc ? 1 : 0);
+    if (a.acc_bits) {
+      const int64_t wi = ((int64_t)c * a.n_sweeps + a.t) * a.W + (a.p >> 5);
+      const uint32_t bit = 1u << (a.p & 31);
+      a.acc_bits[wi] = ((a.p & 31) == 0 ? 0u : a.acc_bits[wi]) | (acc ? bit : 0u);
     }
-    if (lane == 0) {
-      if (a.n_acc) a.n_acc[c] = (a.first ? 0 : a.n_acc[c]) + (acc ? 1 : 0);
-      if (a.acc_bits) {
-        const int64_t wi = ((int64_t)c * a.n_sweeps + a.t) * a.W + (a.p >> 5);
-        const uint32_t bit = 1u << (a.p & 31);
-        a.acc_bits[wi] = ((a.p & 31) == 0 ? 0u : a.acc_bits[wi]) | (acc ? bit : 0u);
-      }
-      if (a.delta) a.delta[((int64_t)c * a.n_sweeps + a.t) * a.N + a.p] = dlt;
-    }
-    __syncwarp();
-    if (a.emit_row >= 0) {
-      const int64_t row = (int64_t)a.emit_row * a.C + c;
-      if (a.samples)
-        for (int w = lane; w < a.W; w += 32) a.samples[row * a.W + w] = a.state[c * a.W + w];
-      if (lane == 0 && a.logpsi) a.logpsi[row] = a.lp[c];
-    }
+    if (a.delta) a.delta[((int64_t)c * a.n_sweeps + a.t) * a.N + a.p] = dlt;
   }
 }
 
@@ -376,8 +401,12 @@ __global__ void __launch_bounds__(256) dense_grad_kernel(const GradArgs g) {
       const int Hl = g.H[l];
       const int Kl = l == 0 ? g.N : g.H[l - 1];
       const float *ain = l == 0 ? s : zl2 - Kl;  // a_{l-1}
-      // O_{W_l} = delta_l a_{l-1}^T and O_{b_l} = delta_l
-      for (int64_t q = tid; q < (int64_t)Hl * Kl; q += blockDim.x) row[g.offW[l] + q] = dl[q / Kl] * ain[q % Kl];
+      // O_{W_l} = delta_l a_{l-1}^T (row n of the block = delta_l[n] a_{l-1}) and O_{b_l} = delta_l
+      for (int nn = warp; nn < Hl; nn += 8) {
+        const float dn = dl[nn];
+        float *dst = row + g.offW[l] + (int64_t)nn * Kl;
+        for (int k = lane; k < Kl; k += 32) dst[k] = dn * ain[k];
+      }
       for (int nn = tid; nn < Hl; nn += blockDim.x) row[g.offb[l] + nn] = dl[nn];
       if (l > 0) {
         // delta_{l-1} = (W_l^T delta_l) f'(z_{l-1}) into the z slot of layer l-1
@@ -400,13 +429,44 @@ __global__ void __launch_bounds__(256) dense_grad_kernel(const GradArgs g) {
   }
 }
 
-// F_k (+)= sum_x O[x][k] (eloc[x] - E) / n over a chunk of rows (FP64, fixed order)
-__global__ void dense_force_kernel(const float *O, int64_t rows, int64_t P, const float *eloc, const double *stats,
-                                   int64_t n_total, int accumulate, double *force) {
+// F_k (+)= sum_x O[x][k] (eloc[x] - E) / n over a chunk of rows.  Block (column tile of
+// 256, row slice of at most 256 rows): FP32 products and sum within the slice (FP64 arithmetic
+// is a small fraction of the FP32 rate on this GPU), FP64 across slices: part[slice][k],
+// added in a fixed order by dense_force_sum_kernel.
+constexpr int FORCE_SLICES = 64;
+__global__ void __launch_bounds__(256) dense_force_part_kernel(const float *O, int64_t rows, int64_t P,
+                                                               const float *eloc, const double *stats, double *part) {
+  __shared__ float se[256];
   const double E = stats[0];
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int slice = blockIdx.y;
+  const int64_t per = (rows + FORCE_SLICES - 1) / FORCE_SLICES;
+  const int64_t x0 = slice * per, x1 = min(rows, x0 + per);
+  double s = 0.0;
+  for (int64_t xb = x0; xb < x1; xb += 256) {
+    const int nb = (int)(x1 - xb < 256 ? x1 - xb : 256);
+    __syncthreads();
+    if (threadIdx.x < nb) se[threadIdx.x] = (float)((double)eloc[xb + threadIdx.x] - E);
+    __syncthreads();
+    if (k < P) {
+      float f0 = 0.f, f1 = 0.f;
+      const float *col = O + xb * P + k;
+      int x = 0;
+      for (; x + 1 < nb; x += 2) {
+        f0 = fmaf(col[(int64_t)x * P], se[x], f0);
+        f1 = fmaf(col[(int64_t)(x + 1) * P], se[x + 1], f1);
+      }
+      if (x < nb) f0 = fmaf(col[(int64_t)x * P], se[x], f0);
+      s += (double)f0 + (double)f1;
+    }
+  }
+  if (k < P) part[slice * P + k] = s;
+}
+__global__ void dense_force_sum_kernel(const double *part, int64_t P, int64_t n_total, int accumulate,
+                                       double *force) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int64_t x = 0; x < rows; ++x) s += (double)O[x * P + k] * ((double)eloc[x] - E);
+    for (int q = 0; q < FORCE_SLICES; ++q) s += part[q * P + k];
     s /= (double)n_total;
     force[k] = accumulate ? force[k] + s : s;
   }
@@ -416,20 +476,31 @@ int grid_for(int64_t work, int per_block, int num_sms) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((work + per_block - 1) / per_block, (int64_t)num_sms * 16));
 }
 
-// GEMM chain over layers 1..L-1 for R rows whose layer-0 output is in act[0]; writes log psi.
-cudaError_t run_chain(const nqs_ctx *c, int64_t R, float *out, const float *b_out_dev, cudaStream_t s) {
+// GEMM chain over layers 1..L-1 for R rows whose layer-0 output is in act[0]; writes log psi
+// (out == nullptr: leaves the last layer's partials in d_part and returns their range count).
+// With fewer row tiles than half the SMs each layer uses its split configuration (N-ranges
+// of half the width) so that more CTAs share the work.
+cudaError_t run_chain(const nqs_ctx *c, int64_t R, float *out, const float *b_out_dev, cudaStream_t s,
+                      int *n_ranges_out = nullptr) {
   int cur = 0;
   cudaError_t e;
+  const bool split = (R + 127) / 128 < c->num_sms / 2;
+  int n_ranges = 1;
   for (int l = 1; l < c->L; ++l) {
     const bool last = l == c->L - 1;
     const int ld_out = last ? 0 : c->Kp[l + 1];
-    if ((e = dense_gemm(c, c->d_act[cur], (int)R, c->Kp[l], c->mB0[l], c->mB1[l], c->H[l], c->NR[l], c->p0[l],
-                        c->p1[l], last ? 1 : 0, c->d_bl[l], last ? c->d_wout : nullptr,
-                        last ? nullptr : c->d_act[cur ^ 1], ld_out, last ? c->d_part : nullptr, s)) != cudaSuccess)
+    const bool sp = split && c->NRs[l] > 0;
+    const int NR = sp ? c->NRs[l] : c->NR[l];
+    if ((e = dense_gemm(c, c->d_act[cur], (int)R, c->Kp[l], sp ? c->mBs0[l] : c->mB0[l], sp ? c->mBs1[l] : c->mB1[l],
+                        c->H[l], NR, sp ? c->p0s[l] : c->p0[l], sp ? c->p1s[l] : c->p1[l], last ? 1 : 0, c->d_bl[l],
+                        last ? c->d_wout : nullptr, last ? nullptr : c->d_act[cur ^ 1], ld_out,
+                        last ? c->d_part : nullptr, s)) != cudaSuccess)
       return e;
+    if (last) n_ranges = (c->H[l] + NR - 1) / NR;
     cur ^= 1;
   }
-  const int n_ranges = (c->H[c->L - 1] + c->NR[c->L - 1] - 1) / c->NR[c->L - 1];
+  if (n_ranges_out) *n_ranges_out = n_ranges;
+  if (!out) return cudaSuccess;
   dense_sum_kernel<<<grid_for(R, 256, c->num_sms), 256, 0, s>>>(c->d_part, R, n_ranges, b_out_dev, out);
   return cudaGetLastError();
 }
@@ -441,6 +512,7 @@ A1Args a1_args(const nqs_ctx *c, const uint32_t *cfg, int64_t R, int mode) {
   a.W1t = c->d_W1t;
   a.bonds = c->d_bonds;
   a.prop = c->d_prop;
+  a.thr = c->d_thr;
   a.act = c->d_act[0];
   a.R = R;
   a.N = c->N;
@@ -450,6 +522,18 @@ A1Args a1_args(const nqs_ctx *c, const uint32_t *cfg, int64_t R, int mode) {
   a.nconn = c->ham_kind == NQS_HEISENBERG ? c->n_bonds : c->N;
   a.mode = mode;
   a.exchange = c->ham_kind == NQS_HEISENBERG;
+  a.p = 0;
+  a.n_moves = a.exchange ? c->n_bonds : c->N;
+  a.sweep_id = a.k0 = a.k1 = 0;
+  a.state = nullptr;
+  a.z0w = c->d_z1;
+  a.acc = c->d_acc;
+  a.lp = c->d_lp;
+  a.samples = nullptr;
+  a.logpsi = nullptr;
+  a.C = R;
+  a.apply_prev = 0;
+  a.emit_row = -1;
   return a;
 }
 
@@ -483,18 +567,28 @@ bool dense_setup(nqs_ctx *c, const nqs_model_desc *m, std::string *why) {
   c->NR.assign(c->L, 0);
   c->p0.assign(c->L, 0);
   c->p1.assign(c->L, 0);
+  c->NRs.assign(c->L, 0);
+  c->p0s.assign(c->L, 0);
+  c->p1s.assign(c->L, 0);
   for (int l = 1; l < c->L; ++l) {
     const int NR = std::min(c->H[l], 512);
     c->NR[l] = NR;
     c->p0[l] = std::min(256, 16 * ((NR + 31) / 32));
     c->p1[l] = NR - c->p0[l];
+    const int NRs = 16 * ((NR / 2 + 15) / 16);  // split configuration: half the range
+    if (NRs >= 32 && NRs < NR) {
+      c->NRs[l] = NRs;
+      c->p0s[l] = std::min(256, 16 * ((NRs + 31) / 32));
+      c->p1s[l] = NRs - c->p0s[l];
+    }
   }
   return true;
 }
 
 void dense_free(nqs_ctx *c) {
-  void *ptrs[] = {c->d_W1t, c->d_b1, c->d_wout, c->d_master, c->d_act[0], c->d_act[1], c->d_part, c->d_out,
-                  c->d_z1,  c->d_lp, c->d_prop, c->d_thr,    c->d_grad_scratch};
+  void *ptrs[] = {c->d_W1t, c->d_b1,   c->d_wout, c->d_master,     c->d_act[0],     c->d_act[1], c->d_part,
+                  c->d_out, c->d_z1,   c->d_lp,   c->d_prop,       c->d_thr,        c->d_grad_scratch,
+                  c->d_force_part, c->d_acc};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto p : c->d_Wl)
@@ -504,20 +598,22 @@ void dense_free(nqs_ctx *c) {
 }
 
 cudaError_t dense_alloc_rows(nqs_ctx *c, int64_t rows) {
-  void *old[] = {c->d_act[0], c->d_act[1], c->d_part, c->d_out, c->d_z1, c->d_lp, c->d_prop, c->d_thr};
+  void *old[] = {c->d_act[0], c->d_act[1], c->d_part, c->d_out, c->d_z1, c->d_lp, c->d_prop, c->d_thr, c->d_acc};
   for (void *p : old)
     if (p) cudaFree(p);
   int maxKp = 64, max_ranges = 1;
   for (int l = 1; l < c->L; ++l) {
     maxKp = std::max(maxKp, c->Kp[l]);
     max_ranges = std::max(max_ranges, (c->H[l] + c->NR[l] - 1) / c->NR[l]);
+    if (c->NRs[l]) max_ranges = std::max(max_ranges, (c->H[l] + c->NRs[l] - 1) / c->NRs[l]);
   }
   cudaError_t e;
   const size_t act = (size_t)rows * maxKp * sizeof(__nv_bfloat16);
   if ((e = cudaMalloc(&c->d_act[0], act)) || (e = cudaMalloc(&c->d_act[1], act)) ||
-      (e = cudaMalloc(&c->d_part, (size_t)rows * max_ranges * 4)) || (e = cudaMalloc(&c->d_out, (size_t)rows * 4)) ||
+      (e = cudaMalloc(&c->d_part, (size_t)rows * max_ranges * 2 * 4)) || (e = cudaMalloc(&c->d_out, (size_t)rows * 4)) ||
       (e = cudaMalloc(&c->d_z1, (size_t)rows * c->H[0] * 4)) || (e = cudaMalloc(&c->d_lp, (size_t)rows * 4 + 16)) ||
-      (e = cudaMalloc(&c->d_prop, (size_t)rows * 4)) || (e = cudaMalloc(&c->d_thr, (size_t)rows * 4)))
+      (e = cudaMalloc(&c->d_prop, (size_t)rows * 4)) || (e = cudaMalloc(&c->d_thr, (size_t)rows * 4)) ||
+      (e = cudaMalloc(&c->d_acc, (size_t)rows * 4)))
     return e;
   if ((e = cudaMemset(c->d_act[0], 0, act)) || (e = cudaMemset(c->d_act[1], 0, act))) return e;
   c->max_rows = rows;
@@ -534,6 +630,8 @@ cudaError_t dense_alloc_params(nqs_ctx *c) {
   c->d_bl.assign(c->L, nullptr);
   c->mB0.resize(c->L);
   c->mB1.resize(c->L);
+  c->mBs0.resize(c->L);
+  c->mBs1.resize(c->L);
   for (int l = 1; l < c->L; ++l) {
     const size_t wbytes = (size_t)c->H[l] * c->Kp[l] * sizeof(__nv_bfloat16);
     if ((e = cudaMalloc(&c->d_Wl[l], wbytes)) || (e = cudaMemset(c->d_Wl[l], 0, wbytes)) ||
@@ -542,10 +640,15 @@ cudaError_t dense_alloc_params(nqs_ctx *c) {
     if (!make_tmap_bf16_2d(&c->mB0[l], c->d_Wl[l], c->H[l], c->Kp[l], c->p0[l]) ||
         !make_tmap_bf16_2d(&c->mB1[l], c->d_Wl[l], c->H[l], c->Kp[l], c->p1[l] ? c->p1[l] : c->p0[l]))
       return cudaErrorInvalidValue;
+    if (c->NRs[l] &&
+        (!make_tmap_bf16_2d(&c->mBs0[l], c->d_Wl[l], c->H[l], c->Kp[l], c->p0s[l]) ||
+         !make_tmap_bf16_2d(&c->mBs1[l], c->d_Wl[l], c->H[l], c->Kp[l], c->p1s[l] ? c->p1s[l] : c->p0s[l])))
+      return cudaErrorInvalidValue;
   }
   const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(256, (int64_t)(256u << 20) / (c->P * 4)));
   c->grad_chunk = chunk;
   if ((e = cudaMalloc(&c->d_grad_scratch, (size_t)chunk * c->P * 4))) return e;
+  if ((e = cudaMalloc(&c->d_force_part, (size_t)FORCE_SLICES * c->P * 8))) return e;
   return dense_alloc_rows(c, 65536);
 }
 
@@ -574,7 +677,7 @@ cudaError_t dense_logpsi(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float
   const float *b_out = c->d_wout + c->H[c->L - 1];
   for (int64_t x0 = 0; x0 < n; x0 += c->max_rows) {
     const int64_t R = std::min<int64_t>(c->max_rows, n - x0);
-    dense_z0_kernel<<<grid_for(R, 8, c->num_sms), 256, 0, s>>>(cfg + x0 * c->W, R, c->d_W1t, c->d_b1, c->N, c->W,
+    dense_z0_kernel<<<grid_for(R, Z0_ROWS, c->num_sms), 256, 0, s>>>(cfg + x0 * c->W, R, c->d_W1t, c->d_b1, c->N, c->W,
                                                                c->H[0], c->d_z1);
     A1Args a = a1_args(c, cfg + x0 * c->W, R, 0);
     dense_a1_kernel<<<grid_for(R, 8, c->num_sms), 256, 0, s>>>(a);
@@ -594,7 +697,7 @@ cudaError_t dense_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n,
   for (int64_t x0 = 0; x0 < n; x0 += chunk) {
     const int64_t ns = std::min<int64_t>(chunk, n - x0);
     const uint32_t *cx = cfg + x0 * c->W;
-    dense_z0_kernel<<<grid_for(ns, 8, c->num_sms), 256, 0, s>>>(cx, ns, c->d_W1t, c->d_b1, c->N, c->W, c->H[0],
+    dense_z0_kernel<<<grid_for(ns, Z0_ROWS, c->num_sms), 256, 0, s>>>(cx, ns, c->d_W1t, c->d_b1, c->N, c->W, c->H[0],
                                                                 c->d_z1);
     A1Args a = a1_args(c, cx, ns * per, 1);
     dense_a1_kernel<<<grid_for(ns * per, 8, c->num_sms), 256, 0, s>>>(a);
@@ -612,13 +715,11 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swee
                         uint32_t sweep_offset, uint32_t *samples, float *logpsi, int64_t *n_acc, uint32_t *acc_bits,
                         float *delta, cudaStream_t s) {
   if (C > c->max_rows) return cudaErrorInvalidValue;
-  const bool exch = c->ham_kind == NQS_HEISENBERG;
-  const int n_moves = exch ? c->n_bonds : c->N;
   const float *b_out = c->d_wout + c->H[c->L - 1];
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   cudaError_t e;
   auto refresh = [&]() -> cudaError_t {  // z0 and log psi of the chains from scratch
-    dense_z0_kernel<<<grid_for(C, 8, c->num_sms), 256, 0, s>>>(state, C, c->d_W1t, c->d_b1, c->N, c->W, c->H[0],
+    dense_z0_kernel<<<grid_for(C, Z0_ROWS, c->num_sms), 256, 0, s>>>(state, C, c->d_W1t, c->d_b1, c->N, c->W, c->H[0],
                                                                c->d_z1);
     A1Args a = a1_args(c, state, C, 0);
     dense_a1_kernel<<<grid_for(C, 8, c->num_sms), 256, 0, s>>>(a);
@@ -627,45 +728,74 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swee
     return run_chain(c, C, c->d_lp, b_out, s);
   };
   if ((e = refresh()) != cudaSuccess) return e;
+  bool pending = false;  // a decision of the previous step still to be applied
+  int emit = -1;         // sample row to write before the next proposal
+  auto bookkeeping = [&](A1Args &a) {
+    a.state = state;
+    a.samples = samples;
+    a.logpsi = logpsi;
+    a.apply_prev = pending;
+    a.emit_row = emit;
+  };
   for (int t = 0; t < n_sweeps; ++t) {
     const uint32_t sweep_id = sweep_offset + (uint32_t)t;
     for (int p = 0; p < c->N; ++p) {
-      dense_propose_kernel<<<grid_for(C, 256, c->num_sms), 256, 0, s>>>(state, C, c->W, exch, n_moves, c->d_bonds, p,
-                                                                        sweep_id, k0, k1, c->d_prop, c->d_thr);
       A1Args a = a1_args(c, state, C, 2);
+      a.p = p;
+      a.sweep_id = sweep_id;
+      a.k0 = k0;
+      a.k1 = k1;
+      bookkeeping(a);
       dense_a1_kernel<<<grid_for(C, 8, c->num_sms), 256, 0, s>>>(a);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      if ((e = run_chain(c, C, c->d_out, b_out, s)) != cudaSuccess) return e;
-      AcceptArgs ac;
-      ac.state = state;
-      ac.z0 = c->d_z1;
-      ac.lp = c->d_lp;
-      ac.lp_new = c->d_out;
-      ac.prop = c->d_prop;
-      ac.thr = c->d_thr;
-      ac.W1t = c->d_W1t;
-      ac.bonds = c->d_bonds;
-      ac.n_acc = n_acc;
-      ac.acc_bits = acc_bits;
-      ac.delta = delta;
-      ac.samples = samples;
-      ac.logpsi = logpsi;
-      ac.C = C;
-      ac.N = c->N;
-      ac.W = c->W;
-      ac.H0 = c->H[0];
-      ac.exchange = exch;
-      ac.p = p;
-      ac.t = t;
-      ac.n_sweeps = n_sweeps;
-      ac.emit_row = (p == c->N - 1 && t >= burn_in) ? t - burn_in : -1;
-      ac.first = (t == 0 && p == 0);
-      dense_accept_kernel<<<grid_for(C, 8, c->num_sms), 256, 0, s>>>(ac);
+      emit = -1;
+      int n_ranges = 1;
+      if ((e = run_chain(c, C, nullptr, b_out, s, &n_ranges)) != cudaSuccess) return e;
+      DecideArgs d;
+      d.part = c->d_part;
+      d.n_ranges = n_ranges;
+      d.b_out = b_out;
+      d.lp = c->d_lp;
+      d.prop = c->d_prop;
+      d.thr = c->d_thr;
+      d.acc = c->d_acc;
+      d.n_acc = n_acc;
+      d.acc_bits = acc_bits;
+      d.delta = delta;
+      d.C = C;
+      d.N = c->N;
+      d.W = c->W;
+      d.p = p;
+      d.t = t;
+      d.n_sweeps = n_sweeps;
+      d.first = (t == 0 && p == 0);
+      dense_decide_kernel<<<grid_for(C, 256, c->num_sms), 256, 0, s>>>(d);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      pending = true;
     }
-    if ((t + 1) % c->refresh == 0 && t + 1 < n_sweeps && (e = refresh()) != cudaSuccess) return e;
+    if (t >= burn_in) emit = t - burn_in;
+    if ((t + 1) % c->refresh == 0 && t + 1 < n_sweeps) {  // apply, emit, then rebuild the caches
+      A1Args a = a1_args(c, state, C, 3);
+      bookkeeping(a);
+      dense_a1_kernel<<<grid_for(C, 8, c->num_sms), 256, 0, s>>>(a);
+      pending = false;
+      emit = -1;
+      if ((e = refresh()) != cudaSuccess) return e;
+    }
   }
-  return cudaSuccess;
+  A1Args a = a1_args(c, state, C, 3);  // closing pass: last decision and last sample
+  bookkeeping(a);
+  dense_a1_kernel<<<grid_for(C, 8, c->num_sms), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t force_rows(const nqs_ctx *c, const float *O, int64_t rows, const float *eloc, const double *stats,
+                              int64_t n_total, int accumulate, double *force, cudaStream_t s) {
+  double *part = reinterpret_cast<double *>(c->d_force_part);
+  dense_force_part_kernel<<<dim3((unsigned)((c->P + 255) / 256), FORCE_SLICES), 256, 0, s>>>(O, rows, c->P, eloc, stats,
+                                                                                             part);
+  dense_force_sum_kernel<<<grid_for(c->P, 256, c->num_sms), 256, 0, s>>>(part, c->P, n_total, accumulate, force);
+  return cudaGetLastError();
 }
 
 cudaError_t dense_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
@@ -701,16 +831,9 @@ cudaError_t dense_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, 
     g.n = rows;
     dense_grad_kernel<<<(unsigned)std::min<int64_t>(rows, (int64_t)c->num_sms * 8), 256, shm, s>>>(g);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (force && !O) {
-      dense_force_kernel<<<grid_for(c->P, 256, c->num_sms), 256, 0, s>>>(g.O, rows, c->P, eloc + x0, stats, n,
-                                                                         x0 > 0, force);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    if (force && !O && (e = force_rows(c, g.O, rows, eloc + x0, stats, n, x0 > 0, force, s)) != cudaSuccess) return e;
   }
-  if (force && O) {
-    dense_force_kernel<<<grid_for(c->P, 256, c->num_sms), 256, 0, s>>>(O, n, c->P, eloc, stats, n, 0, force);
-    return cudaGetLastError();
-  }
+  if (force && O) return force_rows(c, O, n, eloc, stats, n, 0, force, s);
   return cudaSuccess;
 }
 

@@ -3,14 +3,17 @@
 //   z[r][n] = sum_k A[r][k] B[n][k]     (tcgen05.mma kind::f16, FP32 accumulation in TMEM)
 // followed by one of two epilogues:
 //   STORE: out[r][n] = bf16(tanh(z + bias[n]))                      (the next layer's input)
-//   DOT:   part[r][range] = sum_{n in range} tanh(z + bias[n]) w[n]  (last hidden layer -> log psi)
+//   DOT:   part[r][range][h] = sum over the range's column chunks of parity h of
+//          tanh(z + bias[n]) w[n]                               (last hidden layer -> log psi)
 // (dense ansatz: a_l = tanh(W_l a_{l-1} + b_l), log psi = w_out . a_L + b_out).
 //
 // A CTA owns 128 rows and an N-range of NR <= 512 columns, computed as two MMA parts of
 // p0 and p1 columns into one 512-column TMEM accumulator.  Warp roles: warp 0 issues the
 // TMA loads of A and B K-blocks (64 wide, 128-byte swizzle) into a ring of stages, warp 1
-// allocates TMEM and issues the MMAs (one thread), warps 2-5 run the epilogue (thread =
-// row = TMEM lane).  The CTA loops over row tiles; stage and accumulator hand-offs use
+// allocates TMEM and issues the MMAs (one thread), warps 2-9 run the epilogue: two warps
+// per TMEM lane quarter (thread = row = lane), each taking every other 32-column chunk.
+// tanh is the MUFU tanh.approx (relative error ~2^-11, below the BF16 rounding of the
+// activations).  The CTA loops over row tiles; stage and accumulator hand-offs use
 // mbarriers, every wait bounded.
 #include <cuda_bf16.h>
 
@@ -47,7 +50,13 @@ bool make_tmap_bf16_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64
 
 namespace {
 
-constexpr int GEMM_THREADS = 192;
+constexpr int GEMM_THREADS = 320;
+
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 constexpr uint32_t GEMM_POLLS = 1u << 24;
 
 struct GemmArgs {
@@ -79,7 +88,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(&tfull, 1);
-    mbar_init(&tempty, 4);
+    mbar_init(&tempty, 8);
     fence_mbar_init();
     abort_flag = 0;
     prefetch_tmap(&mA);
@@ -158,8 +167,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         tc::mma_commit(&tfull);  // accumulator ready
       }
     }
-  } else {  // ---- epilogue warps 2..5: row = TMEM lane
-    const int q = warp & 3;
+  } else {  // ---- epilogue warps 2..9: row = TMEM lane, every other 32-column chunk
+    const int q = warp & 3, half = (warp - 2) >> 2;
     const int row_in_tile = 32 * q + lane;
     uint32_t t = 0;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
@@ -167,7 +176,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       tc::fence_after_sync();
       const int r = tile * 128 + row_in_tile;
       float dot = 0.f;
-      for (int c0 = 0; c0 < g.NR; c0 += 32) {
+      for (int c0 = 32 * half; c0 < g.NR; c0 += 64) {
         float v[32];
         tc::tmem_ld32(tc::tmem_lane_addr(tmem, 32 * q, c0), v);
         if (r < g.R) {
@@ -175,26 +184,26 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             uint32_t pk[16];
 #pragma unroll
             for (int e = 0; e < 32; e += 2) {
-              const int n = nbase + c0 + e;
-              const float a0 = n < g.N ? tanhf(v[e] + g.bias[n]) : 0.f;
-              const float a1 = n + 1 < g.N ? tanhf(v[e + 1] + g.bias[n + 1]) : 0.f;
+              const int n = nbase + c0 + e;  // columns of this CTA's range only
+              const float a0 = (n < g.N && c0 + e < g.NR) ? tanh_fast(v[e] + g.bias[n]) : 0.f;
+              const float a1 = (n + 1 < g.N && c0 + e + 1 < g.NR) ? tanh_fast(v[e + 1] + g.bias[n + 1]) : 0.f;
               const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
               pk[e / 2] = *reinterpret_cast<const uint32_t *>(&h);
             }
             const int n0 = nbase + c0;
             uint4 *dst = reinterpret_cast<uint4 *>(g.out_act + (int64_t)r * g.ld_out + n0);
-            const int nv = min(4, (g.N - n0 + 7) / 8);
+            const int nv = min(4, (min(g.N - n0, g.NR - c0) + 7) / 8);
             for (int u = 0; u < nv; ++u) dst[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
           } else {
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
               const int n = nbase + c0 + e;
-              if (n < g.N) dot = fmaf(tanhf(v[e] + g.bias[n]), g.w[n], dot);
+              if (n < g.N && c0 + e < g.NR) dot = fmaf(tanh_fast(v[e] + g.bias[n]), g.w[n], dot);
             }
           }
         }
       }
-      if (g.mode == 1 && r < g.R) g.out_part[(int64_t)r * g.n_ranges + range] = dot;
+      if (g.mode == 1 && r < g.R) g.out_part[((int64_t)r * g.n_ranges + range) * 2 + half] = dot;
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty)) : "memory");

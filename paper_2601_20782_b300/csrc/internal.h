@@ -61,6 +61,8 @@ struct nqs_ctx {
   float b_out = 0.f;
   std::vector<CUtensorMap> mB0, mB1;  // per layer l >= 1
   std::vector<int> NR, p0, p1;        // per layer l >= 1: columns per CTA and the two MMA parts
+  std::vector<CUtensorMap> mBs0, mBs1;  // split configuration (half-width ranges) for small row counts
+  std::vector<int> NRs, p0s, p1s;
   float *d_master = nullptr;       // [P] FP32 master parameters (backward)
   // workspace for up to max_rows rows per pass
   int64_t max_rows = 0;
@@ -71,7 +73,9 @@ struct nqs_ctx {
   float *d_lp = nullptr;           // [max_rows] log psi per sample / chain
   int32_t *d_prop = nullptr;       // [max_rows] proposed bond (or -1) per chain
   float *d_thr = nullptr;          // [max_rows] log u per chain
+  int32_t *d_acc = nullptr;        // [max_rows] decision of the last proposal per chain
   float *d_grad_scratch = nullptr; // O rows for the force when the caller gives none
+  void *d_force_part = nullptr;    // FP64 force partials [slices][P]
   int grad_chunk = 0;
 
   std::string err;
