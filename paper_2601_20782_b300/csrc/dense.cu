@@ -110,31 +110,15 @@ __device__ __forceinline__ int spin_of(const uint32_t *cfg, int W, int64_t x, in
 // Row r of the layer-0 output: log cosh(z0[src] + move delta) in BF16, [R][Kp1].
 // mode 0: plain rows (src = r).  mode 1: local-energy rows r = x * (1 + nconn) + k; k = 0 is
 // the configuration itself, k >= 1 the k-1-th connected move (site flip for TFIM, bond
-// exchange for Heisenberg).  mode 2: sampler rows r = chain, move prop[r] (< 0: identity).
+// exchange for Heisenberg).  The sampler's rows come from dense_propose_kernel.
 struct A1Args {
   const uint32_t *cfg;
   const float *z0;
   const float *W1t;
   const int2 *bonds;
-  int32_t *prop;
-  float *thr;
   __nv_bfloat16 *act;
   int64_t R;
   int N, W, H0, Kp1, nconn, mode, exchange;
-  // sampler proposal (mode 2): Philox counter (p/2, sweep_id, chain, TAG_SWEEP)
-  int p, n_moves;
-  uint32_t sweep_id, k0, k1;
-  // sampler bookkeeping (mode 2, and mode 3 = apply only): the previous step's decision
-  // (acc[c], move prop[c]) is applied first (FP32 z0 update, spin move); then, if
-  // emit_row >= 0, the configuration after the previous sweep is written out.
-  uint32_t *state;
-  float *z0w;
-  const int32_t *acc;
-  const float *lp;
-  uint32_t *samples;
-  float *logpsi;
-  int64_t C;
-  int apply_prev, emit_row;
 };
 
 __device__ __forceinline__ bool row_move(const A1Args &a, int64_t r, int64_t *src, Move *mv) {
@@ -142,28 +126,8 @@ __device__ __forceinline__ bool row_move(const A1Args &a, int64_t r, int64_t *sr
     *src = r;
     return false;
   }
-  int m;
-  if (a.mode == 1) {
-    *src = r / (1 + a.nconn);
-    m = (int)(r % (1 + a.nconn)) - 1;
-  } else {  // draw proposal p of this sweep for chain r (Philox words (0,1) / (2,3))
-    *src = r;
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)(a.p / 2), a.sweep_id, (uint32_t)r, TAG_SWEEP), a.k0, a.k1);
-    const uint32_t wm = (a.p & 1) ? w.z : w.x, wu = (a.p & 1) ? w.w : w.y;
-    m = (int)index_from_word(wm, (uint32_t)a.n_moves);
-    const uint32_t k = wu >> 8;
-    bool ident = false;
-    if (a.exchange) {
-      const int2 b = a.bonds[m];
-      ident = spin_of(a.cfg, a.W, r, b.x) == spin_of(a.cfg, a.W, r, b.y);  // identity: always accepted
-    }
-    __syncwarp();  // every lane has read prop[r] (apply_pending) before it is replaced
-    if ((threadIdx.x & 31) == 0) {
-      a.thr[r] = k == 0u ? -INFINITY : logf((float)k * 5.9604644775390625e-8f);
-      a.prop[r] = ident ? -1 : m;
-    }
-    if (ident) return false;
-  }
+  *src = r / (1 + a.nconn);
+  const int m = (int)(r % (1 + a.nconn)) - 1;
   if (m < 0) return false;
   if (a.exchange) {
     const int2 b = a.bonds[m];
@@ -176,49 +140,11 @@ __device__ __forceinline__ bool row_move(const A1Args &a, int64_t r, int64_t *sr
   return true;
 }
 
-// Sampler bookkeeping of chain c before its next proposal (see A1Args).
-__device__ __forceinline__ void apply_pending(const A1Args &a, int64_t c, int lane) {
-  if (a.apply_prev && a.acc[c]) {
-    const int m = a.prop[c];
-    if (m >= 0) {
-      int i, j;
-      if (a.exchange) {
-        const int2 b = a.bonds[m];
-        i = b.x;
-        j = b.y;
-      } else {
-        i = m;
-        j = -1;
-      }
-      const float si = (float)spin_of(a.state, a.W, c, i);
-      float *z = a.z0w + c * a.H0;
-      const float *wi = a.W1t + (int64_t)i * a.H0;
-      const float *wj = a.W1t + (int64_t)(j < 0 ? 0 : j) * a.H0;
-      for (int k = lane; k < a.H0; k += 32) z[k] = fmaf(-2.f * si, j < 0 ? wi[k] : wi[k] - wj[k], z[k]);
-      __syncwarp();
-      if (lane == 0) {
-        a.state[c * a.W + (i >> 5)] ^= 1u << (i & 31);
-        if (j >= 0) a.state[c * a.W + (j >> 5)] ^= 1u << (j & 31);
-      }
-      __syncwarp();
-    }
-  }
-  if (a.emit_row >= 0) {
-    const int64_t row = (int64_t)a.emit_row * a.C + c;
-    if (a.samples)
-      for (int w = lane; w < a.W; w += 32) a.samples[row * a.W + w] = a.state[c * a.W + w];
-    if (lane == 0 && a.logpsi) a.logpsi[row] = a.lp[c];
-  }
-  __syncwarp();
-}
-
 __global__ void dense_a1_kernel(const A1Args a) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = gw; r < a.R; r += nw) {
-    if (a.mode >= 2) apply_pending(a, r, lane);
-    if (a.mode == 3) continue;
     int64_t src;
     Move mv{0, -1};
     const bool moved = row_move(a, r, &src, &mv);
@@ -292,44 +218,174 @@ __global__ void dense_eloc_combine_kernel(const uint32_t *__restrict__ cfg, int6
 // words (0,1) for even p and (2,3) for odd p: move = (w * n_moves) >> 32 (a bond of the
 // Hamiltonian for Heisenberg, a site for TFIM), u = (w' >> 8) 2^-24.  The draw happens
 // in dense_a1_kernel (mode 2), which also writes the proposal's layer-0 row.
-struct DecideArgs {
-  const float *part;
-  int n_ranges;
-  const float *b_out;
+// ------------------------------------------------------------------------------------
+// One Metropolis step of every chain for the dense ansatz (Sec. 2.2 sampler, App. I
+// incremental layer 0).  Warp per chain c; the chain's layer-0 pre-activations z0[c] live
+// in FP32 and are updated by the accepted move only.  In order:
+//  1. decision of the previous step (decide): log psi(y) = b_out + the last layer's range
+//     partials of row c, accepted iff 2 (log psi(y) - log psi(x)) > log u (u = 0 always);
+//     bookkeeping (accept count, accept bits, increments) for proposal (t_prev, p_prev);
+//  2. the accepted move (pending): z0 += -2 s_i (W_i - W_j) (W_j only for an exchange),
+//     spins moved;
+//  3. the configuration after a completed sweep (emit_row >= 0) written to the samples;
+//  4. proposal p of sweep sweep_id (propose): Philox words (0,1) / (2,3) of counter
+//     (p/2, sweep_id, chain, TAG_SWEEP) give the move and u; the proposal's layer-0 row
+//     log cosh(z0 + its delta) is written in BF16 for the GEMM chain.  An exchange of
+//     equal spins is the identity (prop = -1, accepted without evaluation).
+struct ProposeArgs {
+  uint32_t *state;
+  float *z0;
+  const float *W1t;
+  const int2 *bonds;
+  int32_t *prop;
+  float *thr;
   float *lp;
-  const int32_t *prop;
-  const float *thr;
-  int32_t *acc;
+  __nv_bfloat16 *act;
+  const float *part;
+  const float *b_out;
+  int n_ranges;
   int64_t *n_acc;
   uint32_t *acc_bits;
   float *delta;
+  uint32_t *samples;
+  float *logpsi;
   int64_t C;
-  int N, W, p, t, n_sweeps, first;
+  int N, W, H0, Kp1, exchange, n_moves, n_sweeps;
+  int decide, first, t_prev, p_prev;
+  int emit_row;
+  int propose, p;
+  uint32_t sweep_id, k0, k1;
 };
 
-// log psi of the proposals (sum of the last layer's partials) and the decision
-// u < exp(2 (log psi(y) - log psi(x))): thread per chain; the accepted move itself is
-// applied by the next dense_a1_kernel (or the closing apply pass).
-__global__ void dense_decide_kernel(const DecideArgs a) {
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < a.C; c += (int64_t)gridDim.x * blockDim.x) {
-    const int m = a.prop[c];
-    bool acc = true;
-    float dlt = 0.f;
-    if (m >= 0) {
-      float lpn = a.b_out[0];
-      for (int q = 0; q < 2 * a.n_ranges; ++q) lpn += a.part[c * 2 * a.n_ranges + q];
-      dlt = lpn - a.lp[c];
-      acc = 2.f * dlt > a.thr[c];
-      if (acc) a.lp[c] = lpn;
+template <int NJ>  // column block of 64 * NJ units held in registers, two per lane per j
+__global__ void __launch_bounds__(256) dense_propose_kernel(const ProposeArgs a) {
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = gw; c < a.C; c += nw) {
+    uint32_t word = lane < a.W ? a.state[c * a.W + lane] : 0u;
+    // this step's proposal: independent of memory, drawn first
+    int m = 0;
+    float thr_new = 0.f;
+    int2 nb = make_int2(0, -1);
+    if (a.propose) {
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)(a.p / 2), a.sweep_id, (uint32_t)c, TAG_SWEEP), a.k0, a.k1);
+      const uint32_t wm = (a.p & 1) ? w.z : w.x, wu = (a.p & 1) ? w.w : w.y;
+      m = (int)index_from_word(wm, (uint32_t)a.n_moves);
+      const uint32_t k = wu >> 8;
+      thr_new = k == 0u ? -INFINITY : logf((float)k * 5.9604644775390625e-8f);
+      nb = a.exchange ? a.bonds[m] : make_int2(m, -1);
     }
-    a.acc[c] = acc ? 1 : 0;
-    if (a.n_acc) a.n_acc[c] = (a.first ? 0 : a.n_acc[c]) + (acc ? 1 : 0);
-    if (a.acc_bits) {
-      const int64_t wi = ((int64_t)c * a.n_sweeps + a.t) * a.W + (a.p >> 5);
-      const uint32_t bit = 1u << (a.p & 31);
-      a.acc_bits[wi] = ((a.p & 31) == 0 ? 0u : a.acc_bits[wi]) | (acc ? bit : 0u);
+    // decision of the previous proposal
+    int2 pb = make_int2(0, -1);
+    bool pending = false;
+    float lp_c = a.lp[c];
+    if (a.decide) {
+      const int mp = a.prop[c];
+      bool acc = true;
+      float dlt = 0.f;
+      if (mp >= 0) {
+        float part = 0.f;
+        for (int q = lane; q < 2 * a.n_ranges; q += 32) part += a.part[c * 2 * a.n_ranges + q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(full, part, o);
+        const float lpn = a.b_out[0] + part;
+        dlt = lpn - lp_c;
+        acc = 2.f * dlt > a.thr[c];
+        if (acc) {
+          lp_c = lpn;
+          pending = true;
+          pb = a.exchange ? a.bonds[mp] : make_int2(mp, -1);
+        }
+      }
+      __syncwarp();  // every lane has read prop/thr/lp of chain c
+      if (lane == 0) {
+        if (acc && mp >= 0) a.lp[c] = lp_c;
+        if (a.n_acc) a.n_acc[c] = (a.first ? 0 : a.n_acc[c]) + (acc ? 1 : 0);
+        if (a.acc_bits) {
+          const int64_t wi = ((int64_t)c * a.n_sweeps + a.t_prev) * a.W + (a.p_prev >> 5);
+          const uint32_t bit = 1u << (a.p_prev & 31);
+          a.acc_bits[wi] = ((a.p_prev & 31) == 0 ? 0u : a.acc_bits[wi]) | (acc ? bit : 0u);
+        }
+        if (a.delta) a.delta[((int64_t)c * a.n_sweeps + a.t_prev) * a.N + a.p_prev] = dlt;
+      }
     }
-    if (a.delta) a.delta[((int64_t)c * a.n_sweeps + a.t) * a.N + a.p] = dlt;
+    float gp = 0.f;  // pending move: z0 += gp (W_i - W_j)
+    if (pending) {
+      gp = ((__shfl_sync(full, word, pb.x >> 5) >> (pb.x & 31)) & 1u) ? -2.f : 2.f;
+      if (lane == (pb.x >> 5)) word ^= 1u << (pb.x & 31);
+      if (pb.y >= 0 && lane == (pb.y >> 5)) word ^= 1u << (pb.y & 31);
+      if (lane < a.W) a.state[c * a.W + lane] = word;
+    }
+    if (a.emit_row >= 0) {
+      const int64_t row = (int64_t)a.emit_row * a.C + c;
+      if (a.samples && lane < a.W) a.samples[row * a.W + lane] = word;
+      if (a.logpsi && lane == 0) a.logpsi[row] = lp_c;
+    }
+    bool moved = false;
+    float gn = 0.f;  // proposal: z = z0 + gn (W_i - W_j)
+    if (a.propose) {
+      const int sx = (__shfl_sync(full, word, nb.x >> 5) >> (nb.x & 31)) & 1u;
+      moved = true;
+      if (nb.y >= 0) moved = sx != (int)((__shfl_sync(full, word, nb.y >> 5) >> (nb.y & 31)) & 1u);
+      gn = sx ? -2.f : 2.f;
+      __syncwarp();
+      if (lane == 0) {
+        a.thr[c] = thr_new;
+        a.prop[c] = moved ? m : -1;
+      }
+    }
+    if (!pending && !a.propose) continue;
+    float *zr = a.z0 + c * a.H0;
+    const float *pi = a.W1t + (int64_t)pb.x * a.H0, *pj = a.W1t + (int64_t)(pb.y < 0 ? 0 : pb.y) * a.H0;
+    const float *ni = a.W1t + (int64_t)nb.x * a.H0, *nj = a.W1t + (int64_t)(nb.y < 0 ? 0 : nb.y) * a.H0;
+    __nv_bfloat16 *out = a.act + c * a.Kp1;
+    for (int kb = 0; kb < a.H0; kb += 64 * NJ) {
+      float2 z[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int k = kb + 64 * j + 2 * lane;
+        z[j] = k < a.H0 ? *reinterpret_cast<const float2 *>(zr + k) : make_float2(0.f, 0.f);
+      }
+      if (pending) {
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const int k = kb + 64 * j + 2 * lane;
+          if (k < a.H0) {
+            float2 d = *reinterpret_cast<const float2 *>(pi + k);
+            if (pb.y >= 0) {
+              const float2 dj = *reinterpret_cast<const float2 *>(pj + k);
+              d.x -= dj.x;
+              d.y -= dj.y;
+            }
+            z[j].x = fmaf(gp, d.x, z[j].x);
+            z[j].y = fmaf(gp, d.y, z[j].y);
+            *reinterpret_cast<float2 *>(zr + k) = z[j];
+          }
+        }
+      }
+      if (a.propose) {
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          const int k = kb + 64 * j + 2 * lane;
+          if (k < a.H0) {
+            float2 v = z[j];
+            if (moved) {
+              float2 d = *reinterpret_cast<const float2 *>(ni + k);
+              if (nb.y >= 0) {
+                const float2 dj = *reinterpret_cast<const float2 *>(nj + k);
+                d.x -= dj.x;
+                d.y -= dj.y;
+              }
+              v.x = fmaf(gn, d.x, v.x);
+              v.y = fmaf(gn, d.y, v.y);
+            }
+            *reinterpret_cast<__nv_bfloat162 *>(out + k) = __floats2bfloat162_rn(log_cosh_fast(v.x), log_cosh_fast(v.y));
+          }
+        }
+      }
+    }
   }
 }
 
@@ -511,8 +567,6 @@ A1Args a1_args(const nqs_ctx *c, const uint32_t *cfg, int64_t R, int mode) {
   a.z0 = c->d_z1;
   a.W1t = c->d_W1t;
   a.bonds = c->d_bonds;
-  a.prop = c->d_prop;
-  a.thr = c->d_thr;
   a.act = c->d_act[0];
   a.R = R;
   a.N = c->N;
@@ -522,19 +576,18 @@ A1Args a1_args(const nqs_ctx *c, const uint32_t *cfg, int64_t R, int mode) {
   a.nconn = c->ham_kind == NQS_HEISENBERG ? c->n_bonds : c->N;
   a.mode = mode;
   a.exchange = c->ham_kind == NQS_HEISENBERG;
-  a.p = 0;
-  a.n_moves = a.exchange ? c->n_bonds : c->N;
-  a.sweep_id = a.k0 = a.k1 = 0;
-  a.state = nullptr;
-  a.z0w = c->d_z1;
-  a.acc = c->d_acc;
-  a.lp = c->d_lp;
-  a.samples = nullptr;
-  a.logpsi = nullptr;
-  a.C = R;
-  a.apply_prev = 0;
-  a.emit_row = -1;
   return a;
+}
+
+cudaError_t launch_propose(const nqs_ctx *c, const ProposeArgs &a, cudaStream_t s) {
+  const dim3 grid = grid_for(a.C, 8, c->num_sms);
+  if (a.H0 <= 128)
+    dense_propose_kernel<2><<<grid, 256, 0, s>>>(a);
+  else if (a.H0 <= 256)
+    dense_propose_kernel<4><<<grid, 256, 0, s>>>(a);
+  else
+    dense_propose_kernel<8><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -588,7 +641,7 @@ bool dense_setup(nqs_ctx *c, const nqs_model_desc *m, std::string *why) {
 void dense_free(nqs_ctx *c) {
   void *ptrs[] = {c->d_W1t, c->d_b1,   c->d_wout, c->d_master,     c->d_act[0],     c->d_act[1], c->d_part,
                   c->d_out, c->d_z1,   c->d_lp,   c->d_prop,       c->d_thr,        c->d_grad_scratch,
-                  c->d_force_part, c->d_acc};
+                  c->d_force_part};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto p : c->d_Wl)
@@ -598,7 +651,7 @@ void dense_free(nqs_ctx *c) {
 }
 
 cudaError_t dense_alloc_rows(nqs_ctx *c, int64_t rows) {
-  void *old[] = {c->d_act[0], c->d_act[1], c->d_part, c->d_out, c->d_z1, c->d_lp, c->d_prop, c->d_thr, c->d_acc};
+  void *old[] = {c->d_act[0], c->d_act[1], c->d_part, c->d_out, c->d_z1, c->d_lp, c->d_prop, c->d_thr};
   for (void *p : old)
     if (p) cudaFree(p);
   int maxKp = 64, max_ranges = 1;
@@ -612,8 +665,7 @@ cudaError_t dense_alloc_rows(nqs_ctx *c, int64_t rows) {
   if ((e = cudaMalloc(&c->d_act[0], act)) || (e = cudaMalloc(&c->d_act[1], act)) ||
       (e = cudaMalloc(&c->d_part, (size_t)rows * max_ranges * 2 * 4)) || (e = cudaMalloc(&c->d_out, (size_t)rows * 4)) ||
       (e = cudaMalloc(&c->d_z1, (size_t)rows * c->H[0] * 4)) || (e = cudaMalloc(&c->d_lp, (size_t)rows * 4 + 16)) ||
-      (e = cudaMalloc(&c->d_prop, (size_t)rows * 4)) || (e = cudaMalloc(&c->d_thr, (size_t)rows * 4)) ||
-      (e = cudaMalloc(&c->d_acc, (size_t)rows * 4)))
+      (e = cudaMalloc(&c->d_prop, (size_t)rows * 4)) || (e = cudaMalloc(&c->d_thr, (size_t)rows * 4)))
     return e;
   if ((e = cudaMemset(c->d_act[0], 0, act)) || (e = cudaMemset(c->d_act[1], 0, act))) return e;
   c->max_rows = rows;
@@ -728,65 +780,62 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swee
     return run_chain(c, C, c->d_lp, b_out, s);
   };
   if ((e = refresh()) != cudaSuccess) return e;
-  bool pending = false;  // a decision of the previous step still to be applied
-  int emit = -1;         // sample row to write before the next proposal
-  auto bookkeeping = [&](A1Args &a) {
-    a.state = state;
-    a.samples = samples;
-    a.logpsi = logpsi;
-    a.apply_prev = pending;
-    a.emit_row = emit;
-  };
+  ProposeArgs a;
+  a.state = state;
+  a.z0 = c->d_z1;
+  a.W1t = c->d_W1t;
+  a.bonds = c->d_bonds;
+  a.prop = c->d_prop;
+  a.thr = c->d_thr;
+  a.lp = c->d_lp;
+  a.act = c->d_act[0];
+  a.part = c->d_part;
+  a.b_out = b_out;
+  a.n_ranges = 1;
+  a.n_acc = n_acc;
+  a.acc_bits = acc_bits;
+  a.delta = delta;
+  a.samples = samples;
+  a.logpsi = logpsi;
+  a.C = C;
+  a.N = c->N;
+  a.W = c->W;
+  a.H0 = c->H[0];
+  a.Kp1 = c->Kp[1];
+  a.exchange = c->ham_kind == NQS_HEISENBERG;
+  a.n_moves = a.exchange ? c->n_bonds : c->N;
+  a.n_sweeps = n_sweeps;
+  a.decide = 0;
+  a.first = 1;
+  a.t_prev = a.p_prev = 0;
+  a.emit_row = -1;
+  a.k0 = k0;
+  a.k1 = k1;
   for (int t = 0; t < n_sweeps; ++t) {
-    const uint32_t sweep_id = sweep_offset + (uint32_t)t;
+    a.sweep_id = sweep_offset + (uint32_t)t;
     for (int p = 0; p < c->N; ++p) {
-      A1Args a = a1_args(c, state, C, 2);
+      a.propose = 1;
       a.p = p;
-      a.sweep_id = sweep_id;
-      a.k0 = k0;
-      a.k1 = k1;
-      bookkeeping(a);
-      dense_a1_kernel<<<grid_for(C, 8, c->num_sms), 256, 0, s>>>(a);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      emit = -1;
-      int n_ranges = 1;
-      if ((e = run_chain(c, C, nullptr, b_out, s, &n_ranges)) != cudaSuccess) return e;
-      DecideArgs d;
-      d.part = c->d_part;
-      d.n_ranges = n_ranges;
-      d.b_out = b_out;
-      d.lp = c->d_lp;
-      d.prop = c->d_prop;
-      d.thr = c->d_thr;
-      d.acc = c->d_acc;
-      d.n_acc = n_acc;
-      d.acc_bits = acc_bits;
-      d.delta = delta;
-      d.C = C;
-      d.N = c->N;
-      d.W = c->W;
-      d.p = p;
-      d.t = t;
-      d.n_sweeps = n_sweeps;
-      d.first = (t == 0 && p == 0);
-      dense_decide_kernel<<<grid_for(C, 256, c->num_sms), 256, 0, s>>>(d);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      pending = true;
+      if ((e = launch_propose(c, a, s)) != cudaSuccess) return e;
+      if (a.decide) a.first = 0;
+      a.emit_row = -1;
+      if ((e = run_chain(c, C, nullptr, b_out, s, &a.n_ranges)) != cudaSuccess) return e;
+      a.decide = 1;
+      a.t_prev = t;
+      a.p_prev = p;
     }
-    if (t >= burn_in) emit = t - burn_in;
-    if ((t + 1) % c->refresh == 0 && t + 1 < n_sweeps) {  // apply, emit, then rebuild the caches
-      A1Args a = a1_args(c, state, C, 3);
-      bookkeeping(a);
-      dense_a1_kernel<<<grid_for(C, 8, c->num_sms), 256, 0, s>>>(a);
-      pending = false;
-      emit = -1;
+    if (t >= burn_in) a.emit_row = t - burn_in;
+    if ((t + 1) % c->refresh == 0 && t + 1 < n_sweeps) {  // decide, apply, emit, then rebuild the caches
+      a.propose = 0;
+      if ((e = launch_propose(c, a, s)) != cudaSuccess) return e;
+      a.decide = 0;
+      a.first = 0;
+      a.emit_row = -1;
       if ((e = refresh()) != cudaSuccess) return e;
     }
   }
-  A1Args a = a1_args(c, state, C, 3);  // closing pass: last decision and last sample
-  bookkeeping(a);
-  dense_a1_kernel<<<grid_for(C, 8, c->num_sms), 256, 0, s>>>(a);
-  return cudaGetLastError();
+  a.propose = 0;  // closing pass: last decision and last sample
+  return launch_propose(c, a, s);
 }
 
 static cudaError_t force_rows(const nqs_ctx *c, const float *O, int64_t rows, const float *eloc, const double *stats,

@@ -73,7 +73,6 @@ struct nqs_ctx {
   float *d_lp = nullptr;           // [max_rows] log psi per sample / chain
   int32_t *d_prop = nullptr;       // [max_rows] proposed bond (or -1) per chain
   float *d_thr = nullptr;          // [max_rows] log u per chain
-  int32_t *d_acc = nullptr;        // [max_rows] decision of the last proposal per chain
   float *d_grad_scratch = nullptr; // O rows for the force when the caller gives none
   void *d_force_part = nullptr;    // FP64 force partials [slices][P]
   int grad_chunk = 0;
