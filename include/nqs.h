@@ -105,7 +105,7 @@ int32_t nqs_n_bonds(const nqs_ctx *ctx);           /* bonds of the Hamiltonian *
  * NQS_OPT_CHAINS_PER_WARP: RBM sweep lanes per chain = 32 / value (1, 2 or 4;
  * 0 = chosen by the built-in rule).
  * NQS_OPT_MAX_ROWS: dense contexts only -- rows of one forward pass held in the
- * context's workspace (default 65536); bounds the chains of nqs_sweep and sets the
+ * context's workspace (default 262144); bounds the chains of nqs_sweep and sets the
  * chunk of nqs_logpsi / nqs_local_energy.  Reallocates (synchronous). */
 enum { NQS_OPT_REFRESH = 0, NQS_OPT_CHAINS_PER_WARP = 1, NQS_OPT_MAX_ROWS = 2 };
 nqs_status nqs_set_option(nqs_ctx *ctx, int32_t option, int64_t value);

@@ -66,35 +66,49 @@ __global__ void dense_prepare_layer_kernel(const double *__restrict__ p, int64_t
 }
 
 // ------------------------------------------------------------------------------------
-// z0 = W_0 s + b_0 for n configurations, FP32.  Block: 32 configurations; thread j owns
-// hidden units j, j + 256, ... and keeps 32 accumulators; each W_0 row is read once per block.
-constexpr int Z0_ROWS = 32;
-__global__ void __launch_bounds__(256) dense_z0_kernel(const uint32_t *__restrict__ cfg, int64_t n,
-                                                       const float *__restrict__ W1t, const float *__restrict__ b1,
-                                                       int N, int W, int H0, float *z0) {
-  __shared__ uint32_t sw[Z0_ROWS * 32];  // packed spins of the block's rows (W <= 32)
-  for (int64_t x0 = (int64_t)blockIdx.x * Z0_ROWS; x0 < n; x0 += (int64_t)gridDim.x * Z0_ROWS) {
+// z0 = W_0 s + b_0 for n configurations, FP32.  Block (row block, column block): Z0_ROWS
+// configurations x 128 hidden units, thread per unit with Z0_ROWS accumulators; the spin
+// words of the block's rows are read once per 32 sites into registers.
+constexpr int Z0_ROWS = 8;
+constexpr int Z0_COLS = 128;
+__global__ void __launch_bounds__(Z0_COLS) dense_z0_kernel(const uint32_t *__restrict__ cfg, int64_t n,
+                                                           const float *__restrict__ W1t,
+                                                           const float *__restrict__ b1, int N, int W, int H0,
+                                                           float *z0) {
+  const int n_cb = (H0 + Z0_COLS - 1) / Z0_COLS;
+  const int64_t n_blocks = (n + Z0_ROWS - 1) / Z0_ROWS * n_cb;
+  for (int64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
+    const int64_t x0 = blk / n_cb * Z0_ROWS;
+    const int j = (int)(blk % n_cb) * Z0_COLS + threadIdx.x;
     const int nr = (int)(n - x0 < Z0_ROWS ? n - x0 : Z0_ROWS);
-    __syncthreads();
-    for (int q = threadIdx.x; q < Z0_ROWS * W; q += blockDim.x) {
-      const int r = q / W, w = q % W;
-      sw[r * 32 + w] = r < nr ? cfg[(x0 + r) * W + w] : 0u;
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < H0; j += blockDim.x) {
-      float acc[Z0_ROWS];
-      const float bj = b1[j];
+    if (j >= H0) continue;
+    float acc[Z0_ROWS];
+    const float bj = b1[j];
 #pragma unroll
-      for (int r = 0; r < Z0_ROWS; ++r) acc[r] = bj;
-      for (int i = 0; i < N; ++i) {
-        const float w = W1t[(int64_t)i * H0 + j];
-        const float wn = -w;
+    for (int r = 0; r < Z0_ROWS; ++r) acc[r] = bj;
+    for (int w = 0; w < W; ++w) {
+      uint32_t word[Z0_ROWS];
 #pragma unroll
-        for (int r = 0; r < Z0_ROWS; ++r) acc[r] += ((sw[r * 32 + (i >> 5)] >> (i & 31)) & 1u) ? w : wn;
+      for (int r = 0; r < Z0_ROWS; ++r) word[r] = r < nr ? __ldg(cfg + (x0 + r) * W + w) : 0u;
+      const int i1 = N - 32 * w < 32 ? N - 32 * w : 32;
+      const float *wp = W1t + (int64_t)(32 * w) * H0 + j;
+#pragma unroll 4
+      for (int b = 0; b < i1; ++b) {
+        const float wv = __ldg(wp + (int64_t)b * H0);
+#pragma unroll
+        for (int r = 0; r < Z0_ROWS; ++r) acc[r] += ((word[r] >> b) & 1u) ? wv : -wv;
       }
-      for (int r = 0; r < nr; ++r) z0[(x0 + r) * H0 + j] = acc[r];
     }
+#pragma unroll
+    for (int r = 0; r < Z0_ROWS; ++r)
+      if (r < nr) z0[(x0 + r) * H0 + j] = acc[r];
   }
+}
+
+static unsigned z0_grid(int64_t n, int H0, int num_sms) {
+  const int64_t blocks = (n + Z0_ROWS - 1) / Z0_ROWS * ((H0 + Z0_COLS - 1) / Z0_COLS);
+  const int64_t cap = (int64_t)num_sms * 16;
+  return (unsigned)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
 }
 
 // A move: flip site i (j < 0) or exchange sites i and j; valid only if the spins differ
@@ -701,7 +715,7 @@ cudaError_t dense_alloc_params(nqs_ctx *c) {
   c->grad_chunk = chunk;
   if ((e = cudaMalloc(&c->d_grad_scratch, (size_t)chunk * c->P * 4))) return e;
   if ((e = cudaMalloc(&c->d_force_part, (size_t)FORCE_SLICES * c->P * 8))) return e;
-  return dense_alloc_rows(c, 65536);
+  return dense_alloc_rows(c, 262144);
 }
 
 cudaError_t dense_prepare(nqs_ctx *c, const double *params, cudaStream_t s) {
@@ -729,7 +743,7 @@ cudaError_t dense_logpsi(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float
   const float *b_out = c->d_wout + c->H[c->L - 1];
   for (int64_t x0 = 0; x0 < n; x0 += c->max_rows) {
     const int64_t R = std::min<int64_t>(c->max_rows, n - x0);
-    dense_z0_kernel<<<grid_for(R, Z0_ROWS, c->num_sms), 256, 0, s>>>(cfg + x0 * c->W, R, c->d_W1t, c->d_b1, c->N, c->W,
+    dense_z0_kernel<<<z0_grid(R, c->H[0], c->num_sms), Z0_COLS, 0, s>>>(cfg + x0 * c->W, R, c->d_W1t, c->d_b1, c->N, c->W,
                                                                c->H[0], c->d_z1);
     A1Args a = a1_args(c, cfg + x0 * c->W, R, 0);
     dense_a1_kernel<<<grid_for(R, 8, c->num_sms), 256, 0, s>>>(a);
@@ -749,7 +763,7 @@ cudaError_t dense_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n,
   for (int64_t x0 = 0; x0 < n; x0 += chunk) {
     const int64_t ns = std::min<int64_t>(chunk, n - x0);
     const uint32_t *cx = cfg + x0 * c->W;
-    dense_z0_kernel<<<grid_for(ns, Z0_ROWS, c->num_sms), 256, 0, s>>>(cx, ns, c->d_W1t, c->d_b1, c->N, c->W, c->H[0],
+    dense_z0_kernel<<<z0_grid(ns, c->H[0], c->num_sms), Z0_COLS, 0, s>>>(cx, ns, c->d_W1t, c->d_b1, c->N, c->W, c->H[0],
                                                                 c->d_z1);
     A1Args a = a1_args(c, cx, ns * per, 1);
     dense_a1_kernel<<<grid_for(ns * per, 8, c->num_sms), 256, 0, s>>>(a);
@@ -771,7 +785,7 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swee
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   cudaError_t e;
   auto refresh = [&]() -> cudaError_t {  // z0 and log psi of the chains from scratch
-    dense_z0_kernel<<<grid_for(C, Z0_ROWS, c->num_sms), 256, 0, s>>>(state, C, c->d_W1t, c->d_b1, c->N, c->W, c->H[0],
+    dense_z0_kernel<<<z0_grid(C, c->H[0], c->num_sms), Z0_COLS, 0, s>>>(state, C, c->d_W1t, c->d_b1, c->N, c->W, c->H[0],
                                                                c->d_z1);
     A1Args a = a1_args(c, state, C, 0);
     dense_a1_kernel<<<grid_for(C, 8, c->num_sms), 256, 0, s>>>(a);
