@@ -81,17 +81,29 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def combine_across_ranks(stats, force, n_local, dist):
-    """Energy statistics and force over all ranks' samples: an FP64 all-reduce of
-    (n, n * mean, n * (var + mean^2), n * force).  stats/force are rank-local."""
+def reduce_stats_across_ranks(stats, n_local, dist):
+    """Energy statistics over all ranks' samples, in place: an FP64 all-reduce of
+    (n, n * mean, n * (var + mean^2), (n * err)^2).  Afterwards stats[0] is the global E,
+    so every rank's force (1/n_r) sum_x O(x) (eps(x) - E) uses the same E."""
     import torch
-    buf = torch.cat([torch.tensor([float(n_local)], dtype=torch.float64, device=stats.device),
-                     stats[:1] * n_local, (stats[1:2] + stats[:1] ** 2) * n_local, force * n_local])
+    n_r = float(n_local)
+    buf = torch.cat([torch.tensor([n_r], dtype=torch.float64, device=stats.device),
+                     stats[:1] * n_r, (stats[1:2] + stats[:1] ** 2) * n_r, (stats[2:3] * n_r) ** 2])
     dist.all_reduce(buf)
     n = buf[0]
     mean = buf[1] / n
-    var = buf[2] / n - mean ** 2
-    return n, mean, var, buf[3:] / n
+    stats[0] = mean
+    stats[1] = buf[2] / n - mean ** 2
+    stats[2] = torch.sqrt(buf[3]) / n
+    return n
+
+
+def reduce_force_across_ranks(force, n_local, n_total, dist):
+    """F = (1/n) sum over all ranks of n_r F_r, exact when every F_r was centred on the
+    global E (reduce_stats_across_ranks first); in place."""
+    force.mul_(float(n_local))
+    dist.all_reduce(force)
+    force.div_(float(n_total))
 
 
 def thm3_bound(mu, sigma):
@@ -105,8 +117,9 @@ def thm3_bound(mu, sigma):
 class Step:
     """Buffers and one VMC step of the workload for one sampling dtype."""
 
-    def __init__(self, nqs, torch, dev, dtype, C, T, B, params_h):
+    def __init__(self, nqs, torch, dev, dtype, C, T, B, params_h, dist=None):
         ham, lat = WL.ham, WL.ham.lattice
+        self.dist = dist
         self.torch, self.dev, self.dtype = torch, dev, dtype
         self.N, self.M, self.C, self.T, self.B = lat.n_sites, WL.n_hidden, C, T, B
         self.S = (T - B) * C
@@ -139,7 +152,11 @@ class Step:
         c.local_energy(self.samples, self.eloc)
         ev[3].record()
         c.stats(self.eloc, self.C, self.stats, self.nacc, self.T * self.N)
+        if self.dist:   # the one exchange of the step: global E first, then the force
+            n_total = reduce_stats_across_ranks(self.stats, self.S, self.dist)
         c.logpsi_grad(self.samples, None, self.eloc, self.stats, self.force, self.ws)
+        if self.dist:
+            reduce_force_across_ranks(self.force, self.S, n_total, self.dist)
         ev[4].record()
         c.logpsi_grad(self.samples[self.S - self.C:], self.O)
         ev[5].record()
@@ -163,7 +180,7 @@ def run_ours(args, rank, world, dist):
         C, T, B = args.chains or C, args.sweeps or T, args.burn_in if args.burn_in is not None else B
     params_h = torch.from_numpy(workloads.rbm_params(N, M, WL.weight_sigma, WL.seed)).pin_memory()
     dtypes = [args.dtype] + ([d for d in ("f32", "bf16", "f16") if d != args.dtype] if args.compare else [])
-    steps = {d: Step(nqs, torch, dev, d, C, T, B, params_h) for d in dtypes}
+    steps = {d: Step(nqs, torch, dev, d, C, T, B, params_h, dist) for d in dtypes}
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
     base_seed = WL.seed * 1000 + rank * 7919
     proposals_step = C * T * N
@@ -218,7 +235,6 @@ def run_ours(args, rank, world, dist):
         tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_e2e = tt.item()
-        combine_across_ranks(st.stats, st.force, st.S, dist)
 
     # stated bias of each 16-bit copy: increment errors against the FP32 copy at that copy's
     # own sampled states x, y a uniform single flip (the setting of Theorem 3)
