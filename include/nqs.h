@@ -216,6 +216,75 @@ nqs_status nqs_selftest_tc_gemm(const uint16_t *A, const uint16_t *B, float *D, 
  * NQS_OK, NQS_EINVAL (a value left the documented range) or NQS_ETIMEOUT. */
 nqs_status nqs_check_status(nqs_ctx *ctx, nqs_stream stream);
 
+/* ---- Batched uneven instances ------------------------------------------------------
+ * Many independent TFIM problems (each its own context: lattice, N, M, h, sampling copy)
+ * sampled by ONE persistent launch over a work list of (instance, block of chains),
+ * largest work first.  The paper runs one problem at a time (Sec. 4.1 workloads); each
+ * batched chain is the Markov chain nqs_sweep produces for that context with 32 lanes per
+ * chain (F16 always; F32 with NQS_OPT_CHAINS_PER_WARP = 1), bit for bit: same proposals
+ * (Philox key = the item's seed, sweep counter = sweep_offset + t), same arithmetic, same
+ * outputs and layouts.
+ *
+ * Every item's context must be a TFIM RBM context with its parameters set, on one device,
+ * and all items share one sampling dtype, F32 or F16 (else NQS_EINVAL / NQS_EUNSUPPORTED).
+ * The batch keeps the item list (pointers included); contexts and buffers must outlive it.
+ * A bounded wait that runs out sets the timeout bit of the item's context
+ * (nqs_check_status). */
+typedef struct nqs_batch nqs_batch;
+typedef struct {
+  nqs_ctx *ctx;
+  uint32_t *state;         /* device [n_chains x W] chain state (nqs_init_chains), updated in place */
+  int64_t n_chains;        /* 1 .. 2^32 - 1 */
+  uint64_t seed;           /* Philox key of this instance's proposals */
+  uint32_t *samples;       /* device [(n_sweeps - burn_in) * n_chains x W] sweep-major, or NULL */
+  float *logpsi;           /* device, same rows, or NULL */
+  int64_t *n_accepted;     /* device [n_chains], or NULL */
+  uint32_t *accept_bits;   /* device [n_chains x n_sweeps x W] decisions as nqs_sweep_trace, or NULL */
+  float *eloc;             /* nqs_batch_step: device [(n_sweeps - burn_in) * n_chains] local energies, or NULL */
+  double *stats;           /* nqs_batch_step: device [5] as nqs_stats over eloc (needs eloc, n_accepted) */
+  float *O;                /* nqs_batch_step: device [n_chains x P] O rows of the last sweep's samples, or NULL */
+} nqs_batch_item;
+
+/* Builds the work list for n_sweeps sweeps (burn_in of them not kept) per call.  One CTA
+ * per SM; each warp runs one chain of the CTA's current item.  warps_per_cta > 0 fixes the
+ * CTA width (F16: the register-capped kernel variant); 0 runs the autotuner: for every
+ * kernel variant (F16: registers capped at 128 with up to 16 warps, capped at 80 with up
+ * to 24 warps, or the widest case's registers with up to 8 warps; F32: one) and candidate
+ * width (4 .. 24 warps, within the
+ * variant's register limit) it times one sweep of every instance on scratch copies of the
+ * chains with CUDA events on `stream`, and keeps the fastest (synchronises the stream; the
+ * chains are not changed).  Allocates the work list and descriptors; the states must be
+ * initialised. */
+nqs_status nqs_batch_create(nqs_batch **out, const nqs_batch_item *items, int32_t n_items, int32_t n_sweeps,
+                            int32_t burn_in, int32_t warps_per_cta, nqs_stream stream);
+
+/* One persistent launch: n_sweeps sweeps of every instance (sweep counters sweep_offset ..
+ * sweep_offset + n_sweeps - 1), writing each item's state, samples, logpsi, n_accepted
+ * and accept_bits as nqs_sweep does.  Asynchronous. */
+nqs_status nqs_batch_sweep(nqs_batch *b, uint32_t sweep_offset, nqs_stream stream);
+
+/* The VMC step of every instance as one CUDA graph (captured on the first call, then
+ * replayed): the batched sweep, then per instance the local energies of its samples
+ * (nqs_local_energy), their statistics (nqs_stats, acceptance over n_sweeps * N proposals
+ * per chain) and the O rows of the last sweep's samples (nqs_logpsi_grad).  Outputs that
+ * are NULL in the item are skipped.  Asynchronous. */
+nqs_status nqs_batch_step(nqs_batch *b, uint32_t sweep_offset, nqs_stream stream);
+
+typedef struct {
+  int32_t warps_per_cta, max_warps_per_cta, ctas;
+  int32_t variant;         /* 0: F32; F16 with registers capped at 128 (1), at 80 (3), or the widest case's (2) */
+  int32_t n_work_items;
+  int32_t n_staged;        /* instances whose table is staged in shared memory */
+  int64_t stage_bytes;     /* dynamic shared memory per CTA */
+  int32_t n_tuned;         /* autotuner candidates timed (<= 16) */
+  int32_t tuned_variant[16];
+  int32_t tuned_warps[16];
+  float tuned_ms[16];      /* one sweep of every instance with that candidate */
+} nqs_batch_info_t;
+nqs_status nqs_batch_info(const nqs_batch *b, nqs_batch_info_t *info);
+const char *nqs_batch_last_error(const nqs_batch *b);
+void nqs_batch_destroy(nqs_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,6 +50,21 @@ class SweepTrace(ctypes.Structure):
     _fields_ = [("accept_bits", ctypes.c_void_p), ("delta", ctypes.c_void_p)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("state", ctypes.c_void_p), ("n_chains", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("samples", ctypes.c_void_p), ("logpsi", ctypes.c_void_p),
+                ("n_accepted", ctypes.c_void_p), ("accept_bits", ctypes.c_void_p), ("eloc", ctypes.c_void_p),
+                ("stats", ctypes.c_void_p), ("O", ctypes.c_void_p)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_int32), ("max_warps_per_cta", ctypes.c_int32), ("ctas", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("n_work_items", ctypes.c_int32), ("n_staged", ctypes.c_int32),
+                ("stage_bytes", ctypes.c_int64), ("n_tuned", ctypes.c_int32),
+                ("tuned_variant", ctypes.c_int32 * 16), ("tuned_warps", ctypes.c_int32 * 16),
+                ("tuned_ms", ctypes.c_float * 16)]
+
+
 _vp, _i32, _i64, _u32, _u64, _sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
                                     ctypes.c_uint64, ctypes.c_size_t)
 _SIGS = {
@@ -73,6 +88,12 @@ _SIGS = {
     "nqs_check_status": (_i32, [_vp, _vp]),
     "nqs_force_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "nqs_selftest_tc_gemm": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "nqs_batch_create": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(BatchItem), _i32, _i32, _i32, _i32, _vp]),
+    "nqs_batch_sweep": (_i32, [_vp, _u32, _vp]),
+    "nqs_batch_step": (_i32, [_vp, _u32, _vp]),
+    "nqs_batch_info": (_i32, [_vp, ctypes.POINTER(BatchInfo)]),
+    "nqs_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "nqs_batch_destroy": (None, [_vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -206,6 +227,61 @@ class Context:
 
     def check_status(self):
         self._check(_lib.nqs_check_status(self._h, _stream()))
+
+
+class Batch:
+    """nqs_batch: many TFIM RBM instances sampled by one persistent launch.
+
+    items: list of dicts with keys ctx (Context), state (required), seed (required) and the
+    optional device tensors samples, logpsi, n_accepted, accept_bits, eloc, stats, O (shapes as
+    for Context.sweep / local_energy / stats / logpsi_grad).  warps_per_cta = 0 autotunes."""
+
+    def __init__(self, items, n_sweeps, burn_in, warps_per_cta=0):
+        self._h = None
+        K = max(n_sweeps - burn_in, 0)
+        arr = (BatchItem * len(items))()
+        self._keep = items                      # the library keeps the pointers
+        for k, it in enumerate(items):
+            c = it["ctx"]
+            C = it["state"].shape[0]
+            arr[k] = BatchItem(
+                c._h, _ptr(it["state"], _WORD, "state", (C, c.W), False), C, int(it["seed"]) & (2 ** 64 - 1),
+                _ptr(it.get("samples"), _WORD, "samples", (K * C, c.W)),
+                _ptr(it.get("logpsi"), (torch.float32,), "logpsi", (K * C,)),
+                _ptr(it.get("n_accepted"), (torch.int64,), "n_accepted", (C,)),
+                _ptr(it.get("accept_bits"), _WORD, "accept_bits", (C, n_sweeps, c.W)),
+                _ptr(it.get("eloc"), (torch.float32,), "eloc", (K * C,)),
+                _ptr(it.get("stats"), (torch.float64,), "stats", (5,)),
+                _ptr(it.get("O"), (torch.float32,), "O", (C, c.P)))
+        out = ctypes.c_void_p()
+        st = _lib.nqs_batch_create(ctypes.byref(out), arr, len(items), n_sweeps, burn_in, warps_per_cta, _stream())
+        if st != NQS_OK:
+            raise NQSError(st, "nqs_batch_create failed")
+        self._h = out
+        self.n_sweeps, self.burn_in = n_sweeps, burn_in
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.nqs_batch_destroy(self._h)
+            self._h = None
+
+    def _check(self, st):
+        if st != NQS_OK:
+            raise NQSError(st, _lib.nqs_batch_last_error(self._h).decode())
+
+    def sweep(self, sweep_offset=0):
+        self._check(_lib.nqs_batch_sweep(self._h, int(sweep_offset), _stream()))
+
+    def step(self, sweep_offset=0):
+        self._check(_lib.nqs_batch_step(self._h, int(sweep_offset), _stream()))
+
+    def info(self):
+        i = BatchInfo()
+        self._check(_lib.nqs_batch_info(self._h, ctypes.byref(i)))
+        return {"warps_per_cta": i.warps_per_cta, "max_warps_per_cta": i.max_warps_per_cta, "ctas": i.ctas,
+                "variant": i.variant, "n_work_items": i.n_work_items, "n_staged": i.n_staged,
+                "stage_bytes": i.stage_bytes,
+                "tuned": [(i.tuned_variant[q], i.tuned_warps[q], i.tuned_ms[q]) for q in range(i.n_tuned)]}
 
 
 def selftest_tc_gemm(A, B, a_transposed=False, b_transposed=False):

@@ -527,6 +527,73 @@ __device__ __forceinline__ const TT *stage_table(unsigned char *smem_raw, const 
   return R;
 }
 
+// All sweeps of the chain base + (lane / L) for a group of L lanes; chains at or beyond
+// `limit` are idle (they shadow chain limit - 1 and write nothing).  R is the table (shared
+// or global memory), saK the (a_i, K_i) pairs in shared memory.
+template <int L, int E, bool SMEM, typename TT>
+__device__ __forceinline__ void sweep_chain(const SweepParams &p, const TT *R, const float2 *saK, int64_t base,
+                                            int64_t limit) {
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / L, gl = lane % L;
+  const int N = p.N, W = p.W, M_pad = p.M_pad;
+  const int64_t c = base + grp;
+  const bool valid = c < limit;
+  const int64_t cc = valid ? c : limit - 1;
+  uint32_t sw = gl < W ? p.state[cc * W + gl] : 0u;
+  ChainCache<L, E, TT> cache;
+  cache.build(sw, p.Wt, p.b, N, W, M_pad, gl);
+  int64_t nacc = 0;
+
+  for (int t = 0; t < p.n_sweeps; ++t) {
+    const uint32_t sweep_id = p.sweep_offset + (uint32_t)t;
+    uint32_t abits = 0u;
+    for (int p0 = 0; p0 < N; p0 += 2 * L) {
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)(p0 / 2 + gl), sweep_id, (uint32_t)cc, TAG_SWEEP),
+                                    p.k0, p.k1);
+      const uint32_t site0 = index_from_word(w.x, (uint32_t)N), site1 = index_from_word(w.z, (uint32_t)N);
+      const float thr0 = log_uniform(w.y), thr1 = log_uniform(w.w);
+      const int np = min(2 * L, N - p0);
+      for (int q = 0; q < np; ++q) {
+        const int src = q >> 1;
+        const uint32_t site = __shfl_sync(FULL_MASK, (q & 1) ? site1 : site0, src, L);
+        const float thr = __shfl_sync(FULL_MASK, (q & 1) ? thr1 : thr0, src, L);
+        const uint32_t word = __shfl_sync(FULL_MASK, sw, site >> 5, L);
+        const bool up = (word >> (site & 31)) & 1u;
+        const TT *row = R + (size_t)site * M_pad;
+        const float tot = cache.logsum(up, row, gl);
+        const float2 ak = saK[site];
+        const float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F;
+        const bool acc = 2.f * dlt > thr;
+        if (acc) {
+          cache.template accept<SMEM>(up, row, gl);
+          if (gl == (int)(site >> 5)) sw ^= 1u << (site & 31);
+          ++nacc;
+        }
+        const int pq = p0 + q;
+        if (p.acc_bits) {
+          abits |= (acc ? 1u : 0u) << (pq & 31);
+          if ((pq & 31) == 31 || pq == N - 1) {
+            if (valid && gl == 0) p.acc_bits[((int64_t)cc * p.n_sweeps + t) * W + (pq >> 5)] = abits;
+            abits = 0u;
+          }
+        }
+        if (p.delta && valid && gl == 0) p.delta[((int64_t)cc * p.n_sweeps + t) * N + pq] = dlt;
+      }
+    }
+    if (t >= p.burn_in) {
+      const int64_t row = (int64_t)(t - p.burn_in) * p.C + cc;
+      if (p.samples && valid && gl < W) p.samples[row * W + gl] = sw;
+      if (p.logpsi) {
+        const float lp = cache.logpsi(sw, saK, N, gl);
+        if (valid && gl == 0) p.logpsi[row] = lp;
+      }
+    }
+    if ((t + 1) % p.refresh == 0 && t + 1 < p.n_sweeps) cache.build(sw, p.Wt, p.b, N, W, M_pad, gl);
+  }
+  if (valid && gl < W) p.state[cc * W + gl] = sw;
+  if (valid && gl == 0 && p.n_acc) p.n_acc[cc] = nacc;
+}
+
 // One group of L lanes runs one chain for all sweeps; the block shares one copy of
 // the table in shared memory (or reads it through L2 when it does not fit).
 template <int L, int E, bool SMEM, typename TT>
@@ -536,72 +603,12 @@ __global__ void __launch_bounds__(sweep_threads(E), 1) rbm_sweep_kernel(const Sw
   float2 *saK;
   const TT *R = stage_table<TT, SMEM>(smem_raw, p.R, p.aK, p.N, p.M_pad, &bar, p.status, &saK);
   if (!R) return;
-
   constexpr int G = 32 / L;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int grp = lane / L, gl = lane % L;
+  const int warp = threadIdx.x >> 5;
   const int64_t wpb = blockDim.x >> 5;
   const int64_t stride = (int64_t)gridDim.x * wpb * G;
-  const int N = p.N, W = p.W, M_pad = p.M_pad;
-
-  for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * G; base < p.C; base += stride) {
-    const int64_t c = base + grp;
-    const bool valid = c < p.C;
-    const int64_t cc = valid ? c : p.C - 1;  // idle groups shadow the last chain and write nothing
-    uint32_t sw = gl < W ? p.state[cc * W + gl] : 0u;
-    ChainCache<L, E, TT> cache;
-    cache.build(sw, p.Wt, p.b, N, W, M_pad, gl);
-    int64_t nacc = 0;
-
-    for (int t = 0; t < p.n_sweeps; ++t) {
-      const uint32_t sweep_id = p.sweep_offset + (uint32_t)t;
-      uint32_t abits = 0u;
-      for (int p0 = 0; p0 < N; p0 += 2 * L) {
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)(p0 / 2 + gl), sweep_id, (uint32_t)cc, TAG_SWEEP),
-                                      p.k0, p.k1);
-        const uint32_t site0 = index_from_word(w.x, (uint32_t)N), site1 = index_from_word(w.z, (uint32_t)N);
-        const float thr0 = log_uniform(w.y), thr1 = log_uniform(w.w);
-        const int np = min(2 * L, N - p0);
-        for (int q = 0; q < np; ++q) {
-          const int src = q >> 1;
-          const uint32_t site = __shfl_sync(FULL_MASK, (q & 1) ? site1 : site0, src, L);
-          const float thr = __shfl_sync(FULL_MASK, (q & 1) ? thr1 : thr0, src, L);
-          const uint32_t word = __shfl_sync(FULL_MASK, sw, site >> 5, L);
-          const bool up = (word >> (site & 31)) & 1u;
-          const TT *row = R + (size_t)site * M_pad;
-          const float tot = cache.logsum(up, row, gl);
-          const float2 ak = saK[site];
-          const float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F;
-          const bool acc = 2.f * dlt > thr;
-          if (acc) {
-            cache.template accept<SMEM>(up, row, gl);
-            if (gl == (int)(site >> 5)) sw ^= 1u << (site & 31);
-            ++nacc;
-          }
-          const int pq = p0 + q;
-          if (p.acc_bits) {
-            abits |= (acc ? 1u : 0u) << (pq & 31);
-            if ((pq & 31) == 31 || pq == N - 1) {
-              if (valid && gl == 0) p.acc_bits[((int64_t)cc * p.n_sweeps + t) * W + (pq >> 5)] = abits;
-              abits = 0u;
-            }
-          }
-          if (p.delta && valid && gl == 0) p.delta[((int64_t)cc * p.n_sweeps + t) * N + pq] = dlt;
-        }
-      }
-      if (t >= p.burn_in) {
-        const int64_t row = (int64_t)(t - p.burn_in) * p.C + cc;
-        if (p.samples && valid && gl < W) p.samples[row * W + gl] = sw;
-        if (p.logpsi) {
-          const float lp = cache.logpsi(sw, saK, N, gl);
-          if (valid && gl == 0) p.logpsi[row] = lp;
-        }
-      }
-      if ((t + 1) % p.refresh == 0 && t + 1 < p.n_sweeps) cache.build(sw, p.Wt, p.b, N, W, M_pad, gl);
-    }
-    if (valid && gl < W) p.state[cc * W + gl] = sw;
-    if (valid && gl == 0 && p.n_acc) p.n_acc[cc] = nacc;
-  }
+  for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * G; base < p.C; base += stride)
+    sweep_chain<L, E, SMEM, TT>(p, R, saK, base, p.C);
 }
 
 struct ElocParams {

@@ -17,7 +17,8 @@ def declared_functions():
 def test_header_declares_the_hot_path_calls():
     names = declared_functions()
     for n in ["nqs_create", "nqs_set_params", "nqs_init_chains", "nqs_sweep", "nqs_local_energy",
-              "nqs_logpsi_grad", "nqs_stats", "nqs_destroy"]:
+              "nqs_logpsi_grad", "nqs_stats", "nqs_destroy", "nqs_batch_create", "nqs_batch_sweep",
+              "nqs_batch_step", "nqs_batch_destroy"]:
         assert n in names
 
 
@@ -50,3 +51,15 @@ def test_packing_helpers_round_trip():
     from helpers import pack_np, unpack_np
     s = np.random.default_rng(0).choice([-1, 1], size=(7, 45)).astype(np.int8)
     np.testing.assert_array_equal(unpack_np(pack_np(s), 45), s)
+
+
+def test_batch_create_validates_before_touching_the_gpu():
+    lib = ctypes.CDLL(ensure_built())
+    import paper_2601_20782_b300 as p
+    out = ctypes.c_void_p()
+    items = (p.BatchItem * 1)()
+    assert lib.nqs_batch_create(ctypes.byref(out), items, 0, 4, 1, 0, None) == p.NQS_EINVAL    # no items
+    assert lib.nqs_batch_create(ctypes.byref(out), items, 1, 4, 1, 0, None) == p.NQS_EINVAL    # null context
+    assert lib.nqs_batch_create(ctypes.byref(out), items, 1, 0, 0, 0, None) == p.NQS_EINVAL    # no sweeps
+    assert lib.nqs_batch_create(ctypes.byref(out), items, 1, 4, 5, 0, None) == p.NQS_EINVAL    # burn-in > sweeps
+    assert out.value is None
