@@ -313,6 +313,313 @@ def run_ours(args, rank, world, dist):
     return line
 
 
+# ------------------------------------------------------------------------------------------
+# The other workloads (--workload): the 1D N = 16 RBM, the dense 10 x 10 Heisenberg, the 48
+# batched TFIM instances and the dense 16 x 16 J1-J2 ansatz.  Each step is the whole hot path
+# of that workload; the line has the same keys as the default workload's.
+
+class _Phased:
+    """CUDA events around the phases of one step, on the current stream."""
+
+    def __init__(self, torch, names):
+        self.names = names
+        self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+
+    def mark(self, k):
+        self.ev[k].record()
+
+    def ms(self):
+        return {n: self.ev[k].elapsed_time(self.ev[k + 1]) for k, n in enumerate(self.names)}
+
+
+class RbmStep:
+    """Downcast, init, sweeps, local energies, statistics, force and last-sweep O rows of one
+    RBM workload (the default workload's step for another lattice / dtype)."""
+
+    def __init__(self, nqs, torch, dev, wl, dtype, C=None, T=None, B=None):
+        lat = wl.ham.lattice
+        self.wl, self.torch = wl, torch
+        self.N, self.M = lat.n_sites, wl.n_hidden
+        self.C, self.T, self.B = C or wl.n_chains, T or wl.n_sweeps, wl.burn_in if B is None else B
+        self.S = (self.T - self.B) * self.C
+        self.ctx = nqs.Context("tfim", lat.Lx, lat.Ly, J1=wl.ham.J1, h=wl.ham.h, model="rbm", n_hidden=self.M,
+                               dtype=dtype)
+        P = self.ctx.P
+        self.params_h = torch.from_numpy(workloads.rbm_params(self.N, self.M, wl.weight_sigma, wl.seed)).pin_memory()
+        self.params = self.params_h.to(dev)
+        z = lambda *sh, dt=torch.int32: torch.zeros(sh, dtype=dt, device=dev)
+        self.state, self.samples = z(self.C, self.ctx.W), z(self.S, self.ctx.W)
+        self.nacc, self.eloc = z(self.C, dt=torch.int64), z(self.S, dt=torch.float32)
+        self.stats, self.force = z(5, dt=torch.float64), z(P, dt=torch.float64)
+        self.O = z(self.C, P, dt=torch.float32)
+        self.ws = z(self.ctx.logpsi_grad_workspace(self.S), dt=torch.uint8)
+        self.out_h = torch.zeros(5 + P, dtype=torch.float64).pin_memory()
+        self.ph = _Phased(torch, ["set_params+init", "sweep", "local_energy", "stats+force", "O_rows"])
+        self.launches = 10
+        self.h2d, self.d2h = P * 8, (5 + P) * 8
+
+    def run(self, seed, host_io=False):
+        c, ph = self.ctx, self.ph
+        if host_io:
+            self.params.copy_(self.params_h, non_blocking=True)
+        ph.mark(0)
+        c.set_params(self.params)
+        c.init_chains(self.state, seed)
+        ph.mark(1)
+        c.sweep(self.state, self.T, self.B, seed + 1, 0, self.samples, None, self.nacc)
+        ph.mark(2)
+        c.local_energy(self.samples, self.eloc)
+        ph.mark(3)
+        c.stats(self.eloc, self.C, self.stats, self.nacc, self.T * self.N)
+        c.logpsi_grad(self.samples, None, self.eloc, self.stats, self.force, self.ws)
+        ph.mark(4)
+        c.logpsi_grad(self.samples[self.S - self.C:], self.O)
+        ph.mark(5)
+        if host_io:
+            self.out_h[:5].copy_(self.stats, non_blocking=True)
+            self.out_h[5:].copy_(self.force, non_blocking=True)
+
+    def units(self):
+        return self.C * self.T * self.N
+
+    def describe(self, ms, accepts, peaks_, n_sm):
+        alg = 2.0 * self.M * self.units() + 3.0 * self.M * accepts
+        ach = alg / (ms["sweep"] / 1e3) / 1e12
+        peak = n_sm * 128 * float(peaks_.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+        lat = self.wl.ham.lattice
+        return {
+            "config": {"workload": self.wl.name, "lattice": f"{lat.Lx}x{lat.Ly} periodic", "h": self.wl.ham.h,
+                       "n_hidden": self.M, "chains": self.C, "sweeps": self.T, "burn_in": self.B,
+                       "samples": self.S, "params": self.ctx.P},
+            "local_energy": {"value": self.S / (ms["local_energy"] / 1e3), "unit": "samples/s"},
+            "sweep": {"value": self.units() / (ms["sweep"] / 1e3), "unit": "proposals/s",
+                      "acceptance": accepts / self.units()},
+            "roofline": {"bound": "alu", "kernel": "rbm_sweep_kernel", "achieved": ach, "peak": peak,
+                         "unit": "T lane-ops/s", "frac": ach / peak, "traffic": None,
+                         "note": "method arithmetic per proposal (2M + 3M per accept) vs SMs x 128 FP32 lanes "
+                                 "x max clock"},
+        }
+
+
+class DenseStep:
+    """Downcast, init, sweeps (burn-in + kept), local energies of the kept samples, statistics,
+    O rows and force of a dense-ansatz workload.  `T` overrides the sweep count (the 16 x 16
+    workload times a bounded number of its sweeps)."""
+
+    def __init__(self, nqs, torch, dev, wl, C=None, T=None, B=None, n_grad=None):
+        lat = wl.ham.lattice
+        self.wl, self.torch = wl, torch
+        self.N = lat.n_sites
+        self.C, self.T = C or wl.n_chains, T or wl.n_sweeps
+        self.B = min(wl.burn_in, self.T - 1) if B is None else B
+        self.S = (self.T - self.B) * self.C
+        self.ctx = nqs.Context("heisenberg", lat.Lx, lat.Ly, J1=wl.ham.J1, J2=wl.ham.J2, marshall=wl.ham.marshall,
+                               model="dense", widths=wl.widths, dtype="bf16")
+        if self.C > 262144:
+            self.ctx.set_option(nqs.OPT_MAX_ROWS, self.C)
+        P = self.ctx.P
+        self.n_grad = min(n_grad or self.S, self.S)
+        self.params_h = torch.from_numpy(workloads.dense_params(self.N, wl.widths, wl.seed)).pin_memory()
+        self.params = self.params_h.to(dev)
+        z = lambda *sh, dt=torch.int32: torch.zeros(sh, dtype=dt, device=dev)
+        self.state, self.samples = z(self.C, self.ctx.W), z(self.S, self.ctx.W)
+        self.nacc, self.eloc = z(self.C, dt=torch.int64), z(self.S, dt=torch.float32)
+        self.stats, self.force = z(5, dt=torch.float64), z(P, dt=torch.float64)
+        self.O = z(self.n_grad, P, dt=torch.float32)
+        self.out_h = torch.zeros(5 + P, dtype=torch.float64).pin_memory()
+        self.ph = _Phased(torch, ["set_params+init", "sweep", "local_energy", "stats", "O_rows+force"])
+        self.launches = None
+        self.h2d, self.d2h = P * 8, (5 + P) * 8
+
+    def run(self, seed, host_io=False):
+        c, ph = self.ctx, self.ph
+        if host_io:
+            self.params.copy_(self.params_h, non_blocking=True)
+        ph.mark(0)
+        c.set_params(self.params)
+        c.init_chains(self.state, seed)
+        ph.mark(1)
+        c.sweep(self.state, self.T, self.B, seed + 1, 0, self.samples, None, self.nacc)
+        ph.mark(2)
+        c.local_energy(self.samples, self.eloc)
+        ph.mark(3)
+        c.stats(self.eloc, self.C, self.stats, self.nacc, self.T * self.N)
+        ph.mark(4)
+        g = self.S - self.n_grad
+        c.logpsi_grad(self.samples[g:], self.O, self.eloc[g:], self.stats, self.force)
+        ph.mark(5)
+        if host_io:
+            self.out_h[:5].copy_(self.stats, non_blocking=True)
+            self.out_h[5:].copy_(self.force, non_blocking=True)
+
+    def units(self):
+        return self.C * self.T * self.N
+
+    def describe(self, ms, accepts, peaks_, n_sm):
+        w, N = list(self.wl.widths), self.N
+        kp = [((h + 63) // 64) * 64 for h in w]
+        gemm_row = sum(2.0 * kp[l - 1] * w[l] for l in range(1, len(w)))     # tensor-core FLOP per row
+        n_conn = self.ctx.n_bonds
+        sweep_flop = gemm_row * self.units()
+        ach = sweep_flop / (ms["sweep"] / 1e3) / 1e12
+        peak = float(peaks_.get("bf16_tflops_sustained", 1400.0))
+        eloc_flop = gemm_row * self.S * (1 + n_conn)
+        lat = self.wl.ham.lattice
+        return {
+            "config": {"workload": self.wl.name, "lattice": f"{lat.Lx}x{lat.Ly} periodic", "J2": self.wl.ham.J2,
+                       "widths": w, "chains": self.C, "sweeps": self.T, "burn_in": self.B, "samples": self.S,
+                       "grad_rows": self.n_grad, "params": self.ctx.P},
+            "local_energy": {"value": self.S / (ms["local_energy"] / 1e3), "unit": "samples/s",
+                             "tensor_tflops": eloc_flop / (ms["local_energy"] / 1e3) / 1e12},
+            "sweep": {"value": self.units() / (ms["sweep"] / 1e3), "unit": "proposals/s",
+                      "acceptance": accepts / self.units()},
+            "O_rows": {"GB_per_s": self.n_grad * self.ctx.P * 4 / (ms["O_rows+force"] / 1e3) / 1e9,
+                       "note": "O rows written plus the force pass over them"},
+            "roofline": {"bound": "tensor", "kernel": "dense_gemm_kernel (sampler steps)", "achieved": ach,
+                         "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                         "note": "BF16 GEMM FLOP of layers >= 2 over all proposals / sweep time, vs measured "
+                                 "sustained cuBLAS BF16"},
+        }
+
+
+class BatchStep:
+    """The 48 batched TFIM instances (FP16 sampling copies): one persistent sweep launch, then
+    per instance local energies, statistics and last-sweep O rows, replayed as one CUDA graph."""
+
+    def __init__(self, nqs, torch, dev):
+        self.insts = workloads.batched_tfim_instances()
+        self.T, self.B = self.insts[0].n_sweeps, self.insts[0].burn_in
+        self.items, self.params = [], []
+        K = self.T - self.B
+        z = lambda *sh, dt=torch.int32: torch.zeros(sh, dtype=dt, device=dev)
+        self.work = 0.0
+        for w in self.insts:
+            lat = w.ham.lattice
+            N, M = lat.n_sites, w.n_hidden
+            ctx = nqs.Context("tfim", lat.Lx, lat.Ly, J1=w.ham.J1, h=w.ham.h, model="rbm", n_hidden=M, dtype="f16")
+            ph = torch.from_numpy(workloads.rbm_params(N, M, w.weight_sigma, w.seed)).pin_memory()
+            C = w.n_chains
+            self.params.append((ctx, ph, ph.to(dev)))
+            self.items.append(dict(ctx=ctx, state=z(C, ctx.W), seed=w.seed + 1, samples=z(K * C, ctx.W),
+                                   n_accepted=z(C, dt=torch.int64), eloc=z(K * C, dt=torch.float32),
+                                   stats=z(5, dt=torch.float64), O=z(C, ctx.P, dt=torch.float32), N=N, M=M, C=C))
+            self.work += C * self.T * N * M
+        for (ctx, _, pd), it in zip(self.params, self.items):
+            ctx.set_params(pd)
+            ctx.init_chains(it["state"], it["seed"])
+        keys = ("ctx", "state", "seed", "samples", "n_accepted", "eloc", "stats", "O")
+        self.batch = nqs.Batch([{k: it[k] for k in keys} for it in self.items], self.T, self.B, warps_per_cta=0)
+        self.stats_h = torch.zeros(5 * len(self.items), dtype=torch.float64).pin_memory()
+        self.ph = _Phased(torch, ["set_params+init", "step_graph"])
+        self.launches = None
+        self.S = sum(K * it["C"] for it in self.items)
+        self.h2d = sum(ph.numel() * 8 for _, ph, _ in self.params)
+        self.d2h = 5 * 8 * len(self.items)
+        self.k = 0
+
+    def run(self, seed, host_io=False):
+        ph = self.ph
+        ph.mark(0)
+        for (ctx, p_h, p_d), it in zip(self.params, self.items):
+            if host_io:
+                p_d.copy_(p_h, non_blocking=True)
+            ctx.set_params(p_d)
+            ctx.init_chains(it["state"], seed + it["seed"])
+        ph.mark(1)
+        self.batch.step(self.k * self.T)
+        self.k += 1
+        ph.mark(2)
+        if host_io:
+            for q, it in enumerate(self.items):
+                self.stats_h[5 * q:5 * q + 5].copy_(it["stats"], non_blocking=True)
+
+    def units(self):
+        return sum(it["C"] * self.T * it["N"] for it in self.items)
+
+    def describe(self, ms, accepts, peaks_, n_sm):
+        info = self.batch.info()
+        return {
+            "config": {"workload": "tfim_batched_48_instances", "instances": len(self.items),
+                       "N": sorted({it["N"] for it in self.items}), "sweeps": self.T, "burn_in": self.B,
+                       "chains_total": sum(it["C"] for it in self.items), "samples": self.S,
+                       "batch": {k: info[k] for k in ("variant", "warps_per_cta", "n_work_items", "n_staged")}},
+            "note": "value: proposals/s of the whole graphed step (sweep + local energies + statistics + O rows)",
+            "roofline": None,
+        }
+
+
+def run_workload(args, rank, world, dist):
+    import torch
+    import paper_2601_20782_b300 as nqs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    if args.workload == "tfim1d":
+        st = RbmStep(nqs, torch, dev, workloads.TFIM_1D_N16, "f32")
+    elif args.workload == "heis2d-dense":
+        st = DenseStep(nqs, torch, dev, workloads.HEIS_2D_10x10)
+    elif args.workload == "j1j2-dense":
+        st = DenseStep(nqs, torch, dev, workloads.J1J2_2D_16x16, T=args.sweeps or 2, B=1, n_grad=4096)
+    else:
+        st = BatchStep(nqs, torch, dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    base = 1000 + rank * 7919
+    for w in range(args.warmup):
+        st.run(base + w)
+    torch.cuda.synchronize()
+    tot, acc = {}, 0
+    with ClockSampler(dev.index) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            st.run(base + 100 + k)
+            torch.cuda.synchronize()
+            for n, v in st.ph.ms().items():
+                tot[n] = tot.get(n, 0.0) + v
+            if isinstance(st, BatchStep):
+                acc += sum(int(it["n_accepted"].sum().item()) for it in st.items)
+            else:
+                acc += int(st.nacc.sum().item())
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    t_dev = sum(tot.values()) / 1e3
+    e2e = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st.run(base + 200 + k, host_io=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    t_e2e = sum(e2e)
+    if dist:
+        tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev, t_e2e = tt.tolist()
+    ms = {n: v / args.steps for n, v in tot.items()}
+    d = st.describe(ms, acc / args.steps, peaks(), torch.cuda.get_device_properties(dev).multi_processor_count)
+    units = st.units()
+    line = {"metric": METRIC, "value": world * units * args.steps / t_dev, "unit": "proposals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"tfim1d": "f32", "heis2d-dense": "bf16 (fp32 accumulate, fp32 layer-0 cache)",
+                      "j1j2-dense": "bf16 (fp32 accumulate, fp32 layer-0 cache)",
+                      "batched": "f16 sampling (f32 caches, accept, statistics)"}[args.workload],
+            "data": "synthetic (seeded random-init networks, random initial spins)"}
+    line.update(d)
+    line["config"]["l2"] = "flushed between timed steps (256 MiB write)"
+    line["config"]["parallelism"] = f"dp{world} (chains)"
+    line["phases_ms"] = ms
+    line["e2e"] = {"value": world * units * args.steps / t_e2e, "unit": "proposals/s",
+                   "h2d_bytes_per_step": st.h2d, "d2h_bytes_per_step": st.d2h}
+    if st.launches:
+        line["gpu_launches"] = st.launches * args.steps
+    line["clocks"] = clk.summary()
+    return line
+
+
 def oracle_sample_subprocess(n_chains, n_sweeps, eloc_samples):
     """oracle_sample in a fresh interpreter pinned to one BLAS / OpenMP thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
@@ -377,6 +684,10 @@ def main():
     ap.add_argument("--chains", type=int, default=0, help="profiling only: override the chain count")
     ap.add_argument("--sweeps", type=int, default=0, help="profiling only: override the sweep count")
     ap.add_argument("--burn-in", type=int, default=None, help="profiling only: override the burn-in")
+    ap.add_argument("--workload", default="tfim2d", choices=["tfim2d", "tfim1d", "heis2d-dense", "batched",
+                                                             "j1j2-dense"],
+                    help="tfim2d: the 10x10 alpha=4 RBM workload (default); the others measure the other "
+                         "workloads' steps with the same line")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", args.gpus))
     rank = int(os.environ.get("RANK", 0))
@@ -393,6 +704,13 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         td.init_process_group("nccl")
         dist = td
+    if args.workload != "tfim2d":
+        line = run_workload(args, rank, world, dist)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
     line = run_ours(args, rank, world, dist)
     if rank == 0:
         if not args.no_cpu_baseline:
