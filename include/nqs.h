@@ -212,6 +212,24 @@ nqs_status nqs_force_noalloc(nqs_ctx *ctx, const uint32_t *configs, int64_t n, c
 nqs_status nqs_selftest_tc_gemm(const uint16_t *A, const uint16_t *B, float *D, int32_t N, int32_t K,
                                 int32_t flags, int32_t *status, nqs_stream stream);
 
+/* Preconditioned force by the SR solve of App. I in its n x n ("minSR") form, with diagonal
+ * shift lambda (App. I uses shifts of 1e-3 and 1e-1):
+ *   Obar = (O - mean_x O) / sqrt(n), ebar = (eloc - E) / sqrt(n), E = stats[0],
+ *   T = Obar Obar^T,  y = (T + lambda I)^-1 ebar,  dtheta = Obar^T y
+ *     = (Obar^T Obar + lambda I)^-1 F  (push-through identity; F the force of nqs_logpsi_grad).
+ *  O       [n x P] FP32 rows of nqs_logpsi_grad (P = nqs_n_params), row-major.
+ *  eloc    [n] FP32; stats: device, stats[0] = E (nqs_stats over the same n rows).
+ *  dtheta  [P] FP64 out.  T_out: [n x n] FP64 out (T without the shift), or NULL.
+ *  workspace of nqs_minsr_workspace(ctx, n) bytes (holds the centred rows as three BF16
+ *  terms, 6 n P bytes, and the FP64 n x n system).  2 <= n <= 8192, lambda > 0.
+ * The Gram matrix runs on the tensor cores with every FP32 value split into three BF16
+ * terms (six products, FP32 accumulation over 1024-wide K blocks, FP64 beyond); the
+ * Cholesky factorisation and both triangular solves are FP64.  If T + lambda I is not
+ * positive definite in FP64 the range bit of the status word is set (nqs_check_status). */
+size_t nqs_minsr_workspace(const nqs_ctx *ctx, int64_t n);
+nqs_status nqs_minsr(nqs_ctx *ctx, const float *O, int64_t n, const float *eloc, const double *stats, double lambda,
+                     double *dtheta, double *T_out, void *workspace, size_t workspace_bytes, nqs_stream stream);
+
 /* Reads and clears the sticky device status word (synchronises the stream).
  * NQS_OK, NQS_EINVAL (a value left the documented range) or NQS_ETIMEOUT. */
 nqs_status nqs_check_status(nqs_ctx *ctx, nqs_stream stream);

@@ -88,6 +88,8 @@ _SIGS = {
     "nqs_check_status": (_i32, [_vp, _vp]),
     "nqs_force_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "nqs_selftest_tc_gemm": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "nqs_minsr_workspace": (_sz, [_vp, _i64]),
+    "nqs_minsr": (_i32, [_vp, _vp, _i64, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _sz, _vp]),
     "nqs_batch_create": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(BatchItem), _i32, _i32, _i32, _i32, _vp]),
     "nqs_batch_sweep": (_i32, [_vp, _u32, _vp]),
     "nqs_batch_step": (_i32, [_vp, _u32, _vp]),
@@ -224,6 +226,21 @@ class Context:
             self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
             _ptr(eloc, (torch.float32,), "eloc", (n,), False), _ptr(stats, (torch.float64,), "stats", None, False),
             _ptr(force, (torch.float64,), "force", (self.P,), False), _stream()))
+
+    def minsr_workspace(self, n):
+        return int(_lib.nqs_minsr_workspace(self._h, n))
+
+    def minsr(self, O, eloc, stats, lam, dtheta, T_out=None, workspace=None):
+        """dtheta = Obar^T (Obar Obar^T + lam I)^-1 ebar (nqs_minsr); allocates the workspace if none."""
+        n = O.shape[0]
+        if workspace is None:
+            workspace = torch.empty(self.minsr_workspace(n), dtype=torch.uint8, device=O.device)
+        self._check(_lib.nqs_minsr(
+            self._h, _ptr(O, (torch.float32,), "O", (n, self.P), False), n,
+            _ptr(eloc, (torch.float32,), "eloc", (n,), False), _ptr(stats, (torch.float64,), "stats", None, False),
+            float(lam), _ptr(dtheta, (torch.float64,), "dtheta", (self.P,), False),
+            _ptr(T_out, (torch.float64,), "T_out", (n, n)),
+            _ptr(workspace, (torch.uint8,), "workspace", None, False), workspace.numel(), _stream()))
 
     def check_status(self):
         self._check(_lib.nqs_check_status(self._h, _stream()))

@@ -139,6 +139,11 @@ cudaError_t dense_gemm(const nqs_ctx *c, const __nv_bfloat16 *A, int R, int Kpad
                        const CUtensorMap &mB1, int N, int NR, int p0, int p1, int mode, const float *bias,
                        const float *w, __nv_bfloat16 *out_act, int ld_out, float *out_part, cudaStream_t s);
 
+// minsr.cu
+size_t minsr_workspace(const nqs_ctx *c, int64_t n);
+cudaError_t minsr(const nqs_ctx *c, const float *O, int64_t n, const float *eloc, const double *stats, double lam,
+                  double *dtheta, double *T_out, void *ws, cudaStream_t s);
+
 // stats.cu
 cudaError_t energy_stats(const nqs_ctx *c, const float *eloc, int64_t n, int64_t n_chains,
                          const int64_t *n_acc, int64_t proposals_per_chain, double *out, cudaStream_t s);

@@ -350,6 +350,24 @@ nqs_status nqs_stats(nqs_ctx *c, const float *eloc, int64_t n, int64_t n_chains,
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_stats");
 }
 
+size_t nqs_minsr_workspace(const nqs_ctx *c, int64_t n) {
+  if (!c || n < 2 || n > 8192) return 0;
+  return nqs::minsr_workspace(c, n);
+}
+
+nqs_status nqs_minsr(nqs_ctx *c, const float *O, int64_t n, const float *eloc, const double *stats, double lambda,
+                     double *dtheta, double *T_out, void *workspace, size_t workspace_bytes, nqs_stream stream) {
+  if (!c) return NQS_EINVAL;
+  if (n < 2 || n > 8192) return fail(c, NQS_EINVAL, "nqs_minsr: need 2 <= n <= 8192 samples");
+  if (!(lambda > 0.0)) return fail(c, NQS_EINVAL, "nqs_minsr: lambda must be positive");
+  if (bad_ptr(O) || bad_ptr(eloc) || bad_ptr(stats) || bad_ptr(dtheta) || bad_ptr(workspace))
+    return fail(c, NQS_EINVAL, "nqs_minsr: null argument");
+  if (workspace_bytes < nqs::minsr_workspace(c, n)) return fail(c, NQS_EINVAL, "nqs_minsr: workspace too small");
+  cudaError_t e = nqs::minsr(c, O, n, eloc, stats, lambda, dtheta, T_out, workspace,
+                             reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_minsr");
+}
+
 nqs_status nqs_check_status(nqs_ctx *c, nqs_stream stream) {
   if (!c) return NQS_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
