@@ -406,7 +406,7 @@ class DenseStep:
     O rows and force of a dense-ansatz workload.  `T` overrides the sweep count (the 16 x 16
     workload times a bounded number of its sweeps)."""
 
-    def __init__(self, nqs, torch, dev, wl, C=None, T=None, B=None, n_grad=None):
+    def __init__(self, nqs, torch, dev, wl, C=None, T=None, B=None, n_grad=None, minsr_lambda=None):
         lat = wl.ham.lattice
         self.wl, self.torch = wl, torch
         self.N = lat.n_sites
@@ -427,7 +427,14 @@ class DenseStep:
         self.stats, self.force = z(5, dt=torch.float64), z(P, dt=torch.float64)
         self.O = z(self.n_grad, P, dt=torch.float32)
         self.out_h = torch.zeros(5 + P, dtype=torch.float64).pin_memory()
-        self.ph = _Phased(torch, ["set_params+init", "sweep", "local_energy", "stats", "O_rows+force"])
+        names = ["set_params+init", "sweep", "local_energy", "stats", "O_rows+force"]
+        self.lam = minsr_lambda
+        if self.lam:     # minSR on the O rows: statistics of those rows, then the solve
+            names.append("minsr")
+            self.stats_g = z(5, dt=torch.float64)
+            self.dtheta = z(P, dt=torch.float64)
+            self.ws_minsr = z(self.ctx.minsr_workspace(self.n_grad), dt=torch.uint8)
+        self.ph = _Phased(torch, names)
         self.launches = None
         self.h2d, self.d2h = P * 8, (5 + P) * 8
 
@@ -448,9 +455,15 @@ class DenseStep:
         g = self.S - self.n_grad
         c.logpsi_grad(self.samples[g:], self.O, self.eloc[g:], self.stats, self.force)
         ph.mark(5)
+        out = self.force
+        if self.lam:
+            c.stats(self.eloc[g:], self.n_grad, self.stats_g)
+            c.minsr(self.O, self.eloc[g:], self.stats_g, self.lam, self.dtheta, workspace=self.ws_minsr)
+            ph.mark(6)
+            out = self.dtheta
         if host_io:
             self.out_h[:5].copy_(self.stats, non_blocking=True)
-            self.out_h[5:].copy_(self.force, non_blocking=True)
+            self.out_h[5:].copy_(out, non_blocking=True)
 
     def units(self):
         return self.C * self.T * self.N
@@ -475,6 +488,11 @@ class DenseStep:
                       "acceptance": accepts / self.units()},
             "O_rows": {"GB_per_s": self.n_grad * self.ctx.P * 4 / (ms["O_rows+force"] / 1e3) / 1e9,
                        "note": "O rows written plus the force pass over them"},
+            **({"minsr": {"samples": self.n_grad, "lambda": self.lam, "ms": ms["minsr"],
+                          "gram_tflops_bf16x6": 6 * 2.0 * (self.n_grad ** 2 / 2 + self.n_grad * 64) * self.ctx.P
+                          / (ms["minsr"] / 1e3) / 1e12,
+                          "note": "whole solve (means, split, Gram, Cholesky, solves, dtheta); Gram FLOP counted "
+                                  "as 6 BF16 products over the upper triangle"}} if self.lam else {}),
             "roofline": {"bound": "tensor", "kernel": "dense_gemm_kernel (sampler steps)", "achieved": ach,
                          "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                          "note": "BF16 GEMM FLOP of layers >= 2 over all proposals / sweep time, vs measured "
@@ -558,7 +576,9 @@ def run_workload(args, rank, world, dist):
     elif args.workload == "heis2d-dense":
         st = DenseStep(nqs, torch, dev, workloads.HEIS_2D_10x10)
     elif args.workload == "j1j2-dense":
-        st = DenseStep(nqs, torch, dev, workloads.J1J2_2D_16x16, T=args.sweeps or 2, B=1, n_grad=4096)
+        wl = workloads.J1J2_2D_16x16
+        st = DenseStep(nqs, torch, dev, wl, T=args.sweeps or 2, B=1, n_grad=wl.extra["minsr_samples"],
+                       minsr_lambda=1e-3)
     else:
         st = BatchStep(nqs, torch, dev)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
