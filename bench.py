@@ -30,6 +30,10 @@ import numpy as np
 import workloads
 
 METRIC = "MH proposals/sec and local-energy samples/sec on 1 B300, mixed vs FP32 at stated bias"
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of the FP16 sweep kernel
+# (16384 chains x 500 sweeps of this workload): 13.1 MB read + 84.0 MB written.  Valid for that
+# kernel as built; None for the other copies, whose traffic was not captured.
+SWEEP_TRAFFIC_BYTES = {"f16": 97.1e6}
 WL = workloads.TFIM_2D_10x10
 
 
@@ -303,7 +307,8 @@ def run_ours(args, rank, world, dist):
                     for d in dtypes if d != args.dtype},
         "bias": bias,
         "roofline": {"bound": "alu", "kernel": "rbm_sweep_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "T lane-ops/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "T lane-ops/s", "frac": achieved / peak,
+                     "traffic": SWEEP_TRAFFIC_BYTES.get(args.dtype) if (C, T) == (WL.n_chains, WL.n_sweeps) else None,
                      "note": "method arithmetic per proposal (2M + 3M per accept) vs SMs x 128 FP32 lanes x max clock"},
         "e2e": {"value": world * proposals_step * args.steps / t_e2e, "unit": "proposals/s",
                 "h2d_bytes_per_step": steps[args.dtype].ctx.P * 8, "d2h_bytes_per_step": (5 + steps[args.dtype].ctx.P) * 8},
@@ -571,14 +576,15 @@ def run_workload(args, rank, world, dist):
     import paper_2601_20782_b300 as nqs
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
+    C, T, B = args.chains or None, args.sweeps or None, args.burn_in   # profiling overrides (smaller cases)
     if args.workload == "tfim1d":
-        st = RbmStep(nqs, torch, dev, workloads.TFIM_1D_N16, "f32")
+        st = RbmStep(nqs, torch, dev, workloads.TFIM_1D_N16, "f32", C, T, B)
     elif args.workload == "heis2d-dense":
-        st = DenseStep(nqs, torch, dev, workloads.HEIS_2D_10x10)
+        st = DenseStep(nqs, torch, dev, workloads.HEIS_2D_10x10, C, T, B)
     elif args.workload == "j1j2-dense":
         wl = workloads.J1J2_2D_16x16
-        st = DenseStep(nqs, torch, dev, wl, T=args.sweeps or 2, B=1, n_grad=wl.extra["minsr_samples"],
-                       minsr_lambda=1e-3)
+        st = DenseStep(nqs, torch, dev, wl, C, T or 2, 1 if B is None else B,
+                       n_grad=args.grad_rows or wl.extra["minsr_samples"], minsr_lambda=1e-3)
     else:
         st = BatchStep(nqs, torch, dev)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
@@ -629,6 +635,8 @@ def run_workload(args, rank, world, dist):
                       "batched": "f16 sampling (f32 caches, accept, statistics)"}[args.workload],
             "data": "synthetic (seeded random-init networks, random initial spins)"}
     line.update(d)
+    if args.chains or args.sweeps or args.burn_in is not None or args.grad_rows:
+        line["config"]["workload"] += " (reduced: profiling)"
     line["config"]["l2"] = "flushed between timed steps (256 MiB write)"
     line["config"]["parallelism"] = f"dp{world} (chains)"
     line["phases_ms"] = ms
@@ -704,6 +712,7 @@ def main():
     ap.add_argument("--chains", type=int, default=0, help="profiling only: override the chain count")
     ap.add_argument("--sweeps", type=int, default=0, help="profiling only: override the sweep count")
     ap.add_argument("--burn-in", type=int, default=None, help="profiling only: override the burn-in")
+    ap.add_argument("--grad-rows", type=int, default=0, help="profiling only (j1j2-dense): O rows / minSR samples")
     ap.add_argument("--workload", default="tfim2d", choices=["tfim2d", "tfim1d", "heis2d-dense", "batched",
                                                              "j1j2-dense"],
                     help="tfim2d: the 10x10 alpha=4 RBM workload (default); the others measure the other "
