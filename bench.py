@@ -571,6 +571,68 @@ class BatchStep:
         }
 
 
+def run_noisy_study(args, rank, world):
+    """Noisy RBM (Sec. 4.1, Fig. 1(b, c)) on the 10 x 10, alpha = 4 model (FP32 sampling): for each
+    sigma, the acceptance rate, the energy (local energies of the unperturbed psi over samples of
+    |psi~|^2) and its shift from sigma = 0 with the Monte Carlo error, against the Pinsker bound
+    sigma / 2 and the Theorem 3 bound (mu = 0, r = 0) on the sampled distribution."""
+    import torch
+    import paper_2601_20782_b300 as nqs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    lat = WL.ham.lattice
+    N, M = lat.n_sites, WL.n_hidden
+    C, T, B = args.chains or 16384, args.sweeps or 100, 10 if args.burn_in is None else args.burn_in
+    ctx = nqs.Context("tfim", lat.Lx, lat.Ly, J1=WL.ham.J1, h=WL.ham.h, model="rbm", n_hidden=M, dtype="f32")
+    ctx.set_params(torch.from_numpy(workloads.rbm_params(N, M, WL.weight_sigma, WL.seed)).to(dev))
+    S = (T - B) * C
+    state = torch.zeros((C, ctx.W), dtype=torch.int32, device=dev)
+    samples = torch.zeros((S, ctx.W), dtype=torch.int32, device=dev)
+    nacc = torch.zeros(C, dtype=torch.int64, device=dev)
+    eloc = torch.zeros(S, dtype=torch.float32, device=dev)
+    stats = torch.zeros(5, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sigmas = [0.0, 0.01, 0.03, 0.1, 0.3, 1.0, 3.0]
+    rows, rate = [], {}
+    with ClockSampler(dev.index) as clk:
+        for sig in sigmas:
+            ctx.set_noise(sig, WL.seed + 6)
+            times = []
+            for k in range(args.warmup + args.steps):
+                flush.zero_()
+                ctx.init_chains(state, WL.seed + 7)
+                torch.cuda.synchronize()
+                ev[0].record()
+                ctx.sweep(state, T, B, WL.seed + 8, 0, samples, None, nacc)
+                ev[1].record()
+                torch.cuda.synchronize()
+                if k >= args.warmup:
+                    times.append(ev[0].elapsed_time(ev[1]))
+            ctx.local_energy(samples, eloc)
+            ctx.stats(eloc, C, stats, nacc, T * N)
+            st = stats.cpu().numpy()
+            rate[sig] = C * T * N / (statistics.median(times) / 1e3)
+            rows.append({"sigma": sig, "acceptance": float(st[3]), "E": float(st[0]), "E_err": float(st[2]),
+                         "pinsker_tv_bound": sig / 2, "thm3_tv_bound_r0": thm3_bound(0.0, sig),
+                         "sweep_proposals_per_s": rate[sig]})
+    e0 = rows[0]
+    for r in rows:
+        r["E_shift"] = r["E"] - e0["E"]
+        r["E_shift_err"] = math.hypot(r["E_err"], e0["E_err"])
+        r["rel_shift"] = abs(r["E_shift"]) / abs(e0["E"])
+    return {
+        "metric": METRIC, "value": rate[0.1], "unit": "proposals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": C * T * N / rate[0.1] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (noisy RBM: configuration-keyed Gaussian zeta)",
+        "data": "synthetic (seeded random-init RBM, random initial spins)",
+        "config": {"workload": "tfim2d_10x10_rbm_a4_noisy", "chains": C, "sweeps": T, "burn_in": B,
+                   "sigmas": sigmas, "l2": "flushed between timed sweeps (256 MiB write)", "parallelism": "dp1"},
+        "note": "value: noisy-sampler proposals/s at sigma = 0.1; the study is in `noisy`",
+        "noisy": rows, "roofline": None, "clocks": clk.summary(),
+    }
+
+
 def run_workload(args, rank, world, dist):
     import torch
     import paper_2601_20782_b300 as nqs
@@ -714,7 +776,7 @@ def main():
     ap.add_argument("--burn-in", type=int, default=None, help="profiling only: override the burn-in")
     ap.add_argument("--grad-rows", type=int, default=0, help="profiling only (j1j2-dense): O rows / minSR samples")
     ap.add_argument("--workload", default="tfim2d", choices=["tfim2d", "tfim1d", "heis2d-dense", "batched",
-                                                             "j1j2-dense"],
+                                                             "j1j2-dense", "noisy-rbm"],
                     help="tfim2d: the 10x10 alpha=4 RBM workload (default); the others measure the other "
                          "workloads' steps with the same line")
     args = ap.parse_args()
@@ -733,6 +795,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         td.init_process_group("nccl")
         dist = td
+    if args.workload == "noisy-rbm":
+        if rank == 0:
+            print(json.dumps(run_noisy_study(args, rank, world)), flush=True)
+        return
     if args.workload != "tfim2d":
         line = run_workload(args, rank, world, dist)
         if rank == 0:

@@ -212,6 +212,18 @@ nqs_status nqs_force_noalloc(nqs_ctx *ctx, const uint32_t *configs, int64_t n, c
 nqs_status nqs_selftest_tc_gemm(const uint16_t *A, const uint16_t *B, float *D, int32_t N, int32_t K,
                                 int32_t flags, int32_t *status, nqs_stream stream);
 
+/* Noisy RBM (Sec. 4.1): from the next nqs_sweep on, the sampler targets |psi~|^2 with
+ *   log psi~(x) = log psi(x) + zeta(x) / 2,  zeta(x) ~ N(0, sigma) held fixed per x,
+ * so the sampled log-density is perturbed by exactly zeta(x) (standard deviation sigma).
+ * zeta(x) = sigma z(x) with z from the configuration itself: Philox4x32-10 chained over the
+ * packed words w_0 .. w_{W-1} (zero-padded to a multiple of 4), h = (0x4E4F4953, W, 0, 0),
+ * per block of four words h = Philox(h XOR words; key lo, key hi); then Box-Muller on
+ * u1 = ((h0 >> 8) + 1) 2^-24, u2 = (h1 >> 8) 2^-24: z = sqrt(-2 ln u1) cos(2 pi u2).
+ * Only sampling is perturbed: logpsi outputs, local energies and gradients use psi.
+ * sigma = 0 turns the noise off.  FP32 TFIM RBM contexts only (else NQS_EUNSUPPORTED);
+ * 0 <= sigma <= 100.  The sampler then runs 32 lanes per chain. */
+nqs_status nqs_set_noise(nqs_ctx *ctx, double sigma, uint64_t key);
+
 /* Preconditioned force by the SR solve of App. I in its n x n ("minSR") form, with diagonal
  * shift lambda (App. I uses shifts of 1e-3 and 1e-1):
  *   Obar = (O - mean_x O) / sqrt(n), ebar = (eloc - E) / sqrt(n), E = stats[0],

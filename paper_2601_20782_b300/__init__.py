@@ -88,6 +88,7 @@ _SIGS = {
     "nqs_check_status": (_i32, [_vp, _vp]),
     "nqs_force_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "nqs_selftest_tc_gemm": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "nqs_set_noise": (_i32, [_vp, ctypes.c_double, _u64]),
     "nqs_minsr_workspace": (_sz, [_vp, _i64]),
     "nqs_minsr": (_i32, [_vp, _vp, _i64, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _sz, _vp]),
     "nqs_batch_create": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(BatchItem), _i32, _i32, _i32, _i32, _vp]),
@@ -226,6 +227,10 @@ class Context:
             self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
             _ptr(eloc, (torch.float32,), "eloc", (n,), False), _ptr(stats, (torch.float64,), "stats", None, False),
             _ptr(force, (torch.float64,), "force", (self.P,), False), _stream()))
+
+    def set_noise(self, sigma, key=0):
+        """Noisy RBM (nqs_set_noise): sample |psi~|^2, log psi~ = log psi + zeta(x)/2."""
+        self._check(_lib.nqs_set_noise(self._h, float(sigma), int(key) & (2 ** 64 - 1)))
 
     def minsr_workspace(self, n):
         return int(_lib.nqs_minsr_workspace(self._h, n))

@@ -23,6 +23,8 @@ struct nqs_ctx {
   int64_t P = 0;  // parameters
   int refresh = 20;
   int chains_per_warp = 0;  // 0: tuner
+  double noise_sigma = 0.0;  // noisy RBM (nqs_set_noise): 0 = off
+  uint64_t noise_key = 0;
   int device = 0;
   int num_sms = 0;
   int smem_optin = 0;

@@ -35,11 +35,22 @@ constexpr int GRAM_DRAIN = 16;     // K blocks (of 64) accumulated in FP32 betwe
 constexpr uint32_t GRAM_POLLS = 1u << 24;
 constexpr int CHOL_NB = 64;
 
+// FP32 sums over chunks of MINSR_CHUNK rows, FP64 across chunks: FP64 arithmetic is a small
+// fraction of FP32 throughput on this part, and a 16-term FP32 sum carries at most 16 x 2^-24
+// relative error before it reaches the FP64 total.
+constexpr int MINSR_CHUNK = 16;
+
 __global__ void minsr_colmean_kernel(const float *__restrict__ O, int64_t n, int64_t P, double *mean_d,
                                      float *mean_f) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int64_t x = 0; x < n; ++x) s += (double)O[x * P + k];
+    for (int64_t x0 = 0; x0 < n; x0 += MINSR_CHUNK) {
+      float c = 0.f;
+      const int m = (int)(n - x0 < MINSR_CHUNK ? n - x0 : MINSR_CHUNK);
+#pragma unroll 4
+      for (int q = 0; q < m; ++q) c += O[(x0 + q) * P + k];
+      s += (double)c;
+    }
     const double m = s / (double)n;
     mean_d[k] = m;
     mean_f[k] = (float)m;
@@ -402,12 +413,23 @@ __global__ void __launch_bounds__(1024) minsr_solve_kernel(const double *__restr
   }
 }
 
+// dtheta_k = (sum_x O_xk y_x - mean_k sum_x y_x) / sqrt(n); the row sums as in
+// minsr_colmean_kernel (FP32 within chunks, y rounded to FP32, FP64 across chunks).
 __global__ void minsr_dtheta_kernel(const float *__restrict__ O, int64_t n, int64_t P, const double *__restrict__ mean_d,
                                     const double *__restrict__ y, const double *__restrict__ ysum, double *dtheta) {
+  extern __shared__ float yf[];  // [n] y in FP32
+  for (int64_t x = threadIdx.x; x < n; x += blockDim.x) yf[x] = (float)y[x];
+  __syncthreads();
   const double rs = 1.0 / sqrt((double)n), ys = *ysum;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int64_t x = 0; x < n; ++x) s += (double)O[x * P + k] * y[x];
+    for (int64_t x0 = 0; x0 < n; x0 += MINSR_CHUNK) {
+      float c = 0.f;
+      const int m = (int)(n - x0 < MINSR_CHUNK ? n - x0 : MINSR_CHUNK);
+#pragma unroll 4
+      for (int q = 0; q < m; ++q) c = fmaf(O[(x0 + q) * P + k], yf[x0 + q], c);
+      s += (double)c;
+    }
     dtheta[k] = (s - mean_d[k] * ys) * rs;
   }
 }
@@ -522,7 +544,8 @@ cudaError_t minsr(const nqs_ctx *c, const float *O, int64_t n, const float *eloc
   }
   minsr_solve_kernel<<<1, 1024, 0, s>>>(T, n, eloc, stats, z, y, ys);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  minsr_dtheta_kernel<<<grid_n(c->P, 256, c->num_sms), 256, 0, s>>>(O, n, c->P, mean_d, y, ys, dtheta);
+  minsr_dtheta_kernel<<<grid_n(c->P, 256, c->num_sms), 256, (size_t)n * sizeof(float), s>>>(O, n, c->P, mean_d, y,
+                                                                                            ys, dtheta);
   return cudaGetLastError();
 }
 

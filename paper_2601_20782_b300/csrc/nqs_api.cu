@@ -350,6 +350,16 @@ nqs_status nqs_stats(nqs_ctx *c, const float *eloc, int64_t n, int64_t n_chains,
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_stats");
 }
 
+nqs_status nqs_set_noise(nqs_ctx *c, double sigma, uint64_t key) {
+  if (!c) return NQS_EINVAL;
+  if (!(sigma >= 0.0) || sigma > 100.0) return fail(c, NQS_EINVAL, "nqs_set_noise: need 0 <= sigma <= 100");
+  if (sigma > 0.0 && (c->model_kind != NQS_RBM || c->ham_kind != NQS_TFIM || c->dtype != NQS_F32))
+    return fail(c, NQS_EUNSUPPORTED, "nqs_set_noise: the noisy RBM is built for FP32 TFIM RBM contexts");
+  c->noise_sigma = sigma;
+  c->noise_key = key;
+  return NQS_OK;
+}
+
 size_t nqs_minsr_workspace(const nqs_ctx *c, int64_t n) {
   if (!c || n < 2 || n > 8192) return 0;
   return nqs::minsr_workspace(c, n);

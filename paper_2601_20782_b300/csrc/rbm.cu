@@ -434,6 +434,10 @@ cudaError_t rbm_sweep(const nqs_ctx *c, uint32_t *state, int64_t n_chains, int n
   p.sweep_offset = sweep_offset;
   p.k0 = (uint32_t)seed;
   p.k1 = (uint32_t)(seed >> 32);
+  p.noise_sigma = (float)c->noise_sigma;
+  p.noise_k0 = (uint32_t)c->noise_key;
+  p.noise_k1 = (uint32_t)(c->noise_key >> 32);
+  if (c->noise_sigma > 0.0) return dispatch_l32<Runners<float>::NoisySweep>(c->M_pad / 32, c, p, s);  // F32 only
   if (c->dtype == NQS_F16) return rbm_sweep_f16(c, p, s);
   if (c->dtype == NQS_BF16) return rbm_sweep_bf16(c, p, s);
   const int L = pick_lanes(c);

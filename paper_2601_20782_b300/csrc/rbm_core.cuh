@@ -470,7 +470,28 @@ struct SweepParams {
   int64_t C;
   int N, W, M_pad, n_sweeps, burn_in, refresh;
   uint32_t sweep_offset, k0, k1;
+  float noise_sigma;  // noisy-RBM kernels only: standard deviation of zeta
+  uint32_t noise_k0, noise_k1;
 };
+
+// Noisy RBM (Sec. 4.1): log psi~(x) = log psi(x) + zeta(x)/2, zeta(x) ~ N(0, sigma) fixed per
+// configuration.  zeta is computed from the configuration: Philox4x32-10 chained over its
+// words (h = (TAG_NOISE, W, 0, 0); per block of four words h = Philox(h ^ words; key)), then
+// Box-Muller on u1 = ((h.x >> 8) + 1) 2^-24, u2 = (h.y >> 8) 2^-24.  Word j is held by lane j
+// of the group (lanes >= W hold 0).  Returns zeta(x) / 2.
+constexpr uint32_t TAG_NOISE = 0x4E4F4953u;  // "NOIS"
+template <int L>
+__device__ __forceinline__ float noise_half(uint32_t sw, int W, float sigma, uint32_t k0, uint32_t k1) {
+  uint4 h = make_uint4(TAG_NOISE, (uint32_t)W, 0u, 0u);
+  for (int b = 0; b < W; b += 4) {
+    const uint32_t w0 = __shfl_sync(FULL_MASK, sw, b, L), w1 = __shfl_sync(FULL_MASK, sw, b + 1, L);
+    const uint32_t w2 = __shfl_sync(FULL_MASK, sw, b + 2, L), w3 = __shfl_sync(FULL_MASK, sw, b + 3, L);
+    h = philox4x32_10(make_uint4(h.x ^ w0, h.y ^ w1, h.z ^ w2, h.w ^ w3), k0, k1);
+  }
+  const float u1 = (float)((h.x >> 8) + 1u) * 5.9604644775390625e-8f;
+  const float u2 = (float)(h.y >> 8) * 5.9604644775390625e-8f;
+  return 0.5f * sigma * sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+}
 
 // log u for u = k 2^-24 (k = 0 gives -inf: always accept).  Accepting iff
 // 2 dlogpsi > log u is the rule u < exp(2 dlogpsi).
@@ -530,7 +551,7 @@ __device__ __forceinline__ const TT *stage_table(unsigned char *smem_raw, const 
 // All sweeps of the chain base + (lane / L) for a group of L lanes; chains at or beyond
 // `limit` are idle (they shadow chain limit - 1 and write nothing).  R is the table (shared
 // or global memory), saK the (a_i, K_i) pairs in shared memory.
-template <int L, int E, bool SMEM, typename TT>
+template <int L, int E, bool SMEM, typename TT, bool NOISE = false>
 __device__ __forceinline__ void sweep_chain(const SweepParams &p, const TT *R, const float2 *saK, int64_t base,
                                             int64_t limit) {
   const int lane = threadIdx.x & 31;
@@ -543,6 +564,8 @@ __device__ __forceinline__ void sweep_chain(const SweepParams &p, const TT *R, c
   ChainCache<L, E, TT> cache;
   cache.build(sw, p.Wt, p.b, N, W, M_pad, gl);
   int64_t nacc = 0;
+  float zx = 0.f;  // noisy RBM: zeta(x) / 2 of the chain's configuration
+  if constexpr (NOISE) zx = noise_half<L>(sw, W, p.noise_sigma, p.noise_k0, p.noise_k1);
 
   for (int t = 0; t < p.n_sweeps; ++t) {
     const uint32_t sweep_id = p.sweep_offset + (uint32_t)t;
@@ -562,12 +585,19 @@ __device__ __forceinline__ void sweep_chain(const SweepParams &p, const TT *R, c
         const TT *row = R + (size_t)site * M_pad;
         const float tot = cache.logsum(up, row, gl);
         const float2 ak = saK[site];
-        const float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F;
+        float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F;
+        float zy = 0.f;
+        if constexpr (NOISE) {  // log psi~(y) - log psi~(x) = dlt + zeta(y)/2 - zeta(x)/2
+          zy = noise_half<L>(sw ^ (gl == (int)(site >> 5) ? 1u << (site & 31) : 0u), W, p.noise_sigma, p.noise_k0,
+                             p.noise_k1);
+          dlt += zy - zx;
+        }
         const bool acc = 2.f * dlt > thr;
         if (acc) {
           cache.template accept<SMEM>(up, row, gl);
           if (gl == (int)(site >> 5)) sw ^= 1u << (site & 31);
           ++nacc;
+          if constexpr (NOISE) zx = zy;
         }
         const int pq = p0 + q;
         if (p.acc_bits) {
@@ -596,7 +626,7 @@ __device__ __forceinline__ void sweep_chain(const SweepParams &p, const TT *R, c
 
 // One group of L lanes runs one chain for all sweeps; the block shares one copy of
 // the table in shared memory (or reads it through L2 when it does not fit).
-template <int L, int E, bool SMEM, typename TT>
+template <int L, int E, bool SMEM, typename TT, bool NOISE = false>
 __global__ void __launch_bounds__(sweep_threads(E), 1) rbm_sweep_kernel(const SweepParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t bar;
@@ -608,7 +638,7 @@ __global__ void __launch_bounds__(sweep_threads(E), 1) rbm_sweep_kernel(const Sw
   const int64_t wpb = blockDim.x >> 5;
   const int64_t stride = (int64_t)gridDim.x * wpb * G;
   for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * G; base < p.C; base += stride)
-    sweep_chain<L, E, SMEM, TT>(p, R, saK, base, p.C);
+    sweep_chain<L, E, SMEM, TT, NOISE>(p, R, saK, base, p.C);
 }
 
 struct ElocParams {
@@ -726,6 +756,15 @@ struct Runners {
       const size_t shm = table_smem<TT>(c, &fits);
       return fits ? launch_persistent(rbm_sweep_kernel<L, E, true, TT>, c, p.C, 32 / L, shm, s, &p)
                   : launch_persistent(rbm_sweep_kernel<L, E, false, TT>, c, p.C, 32 / L, shm, s, &p);
+    }
+  };
+  template <int L, int E>
+  struct NoisySweep {  // noisy RBM (Sec. 4.1)
+    static cudaError_t run(const nqs_ctx *c, const SweepParams &p, cudaStream_t s) {
+      bool fits;
+      const size_t shm = table_smem<TT>(c, &fits);
+      return fits ? launch_persistent(rbm_sweep_kernel<L, E, true, TT, true>, c, p.C, 32 / L, shm, s, &p)
+                  : launch_persistent(rbm_sweep_kernel<L, E, false, TT, true>, c, p.C, 32 / L, shm, s, &p);
     }
   };
   template <int L, int E>
