@@ -153,7 +153,7 @@ class Step:
         ev[1].record()
         c.sweep(self.state, self.T, self.B, seed + 1, 0, self.samples, None, self.nacc)
         ev[2].record()
-        c.local_energy(self.samples, self.eloc)
+        c.local_energy_chains(self.samples, self.C, self.eloc)
         ev[3].record()
         c.stats(self.eloc, self.C, self.stats, self.nacc, self.T * self.N)
         if self.dist:   # the one exchange of the step: global E first, then the force
@@ -373,7 +373,7 @@ class RbmStep:
         ph.mark(1)
         c.sweep(self.state, self.T, self.B, seed + 1, 0, self.samples, None, self.nacc)
         ph.mark(2)
-        c.local_energy(self.samples, self.eloc)
+        c.local_energy_chains(self.samples, self.C, self.eloc)
         ph.mark(3)
         c.stats(self.eloc, self.C, self.stats, self.nacc, self.T * self.N)
         c.logpsi_grad(self.samples, None, self.eloc, self.stats, self.force, self.ws)

@@ -212,6 +212,15 @@ nqs_status nqs_force_noalloc(nqs_ctx *ctx, const uint32_t *configs, int64_t n, c
 nqs_status nqs_selftest_tc_gemm(const uint16_t *A, const uint16_t *B, float *D, int32_t N, int32_t K,
                                 int32_t flags, int32_t *status, nqs_stream stream);
 
+/* nqs_local_energy of the samples nqs_sweep writes: samples [per_chain * n_chains x W],
+ * sweep-major (row k * n_chains + c), eloc the same rows.  The values are those of
+ * nqs_local_energy up to FP32 rounding: the RBM kernel walks each chain's samples in order
+ * and updates its theta = W s + b only for the spins that changed since the chain's previous
+ * sample (rebuilt from scratch every NQS_OPT_REFRESH samples), instead of rebuilding it for
+ * every sample.  Dense contexts evaluate it as nqs_local_energy. */
+nqs_status nqs_local_energy_chains(nqs_ctx *ctx, const uint32_t *samples, int64_t n_chains, int64_t per_chain,
+                                   float *eloc, nqs_stream stream);
+
 /* Noisy RBM (Sec. 4.1): from the next nqs_sweep on, the sampler targets |psi~|^2 with
  *   log psi~(x) = log psi(x) + zeta(x) / 2,  zeta(x) ~ N(0, sigma) held fixed per x,
  * so the sampled log-density is perturbed by exactly zeta(x) (standard deviation sigma).

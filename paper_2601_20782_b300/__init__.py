@@ -89,6 +89,7 @@ _SIGS = {
     "nqs_force_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "nqs_selftest_tc_gemm": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "nqs_set_noise": (_i32, [_vp, ctypes.c_double, _u64]),
+    "nqs_local_energy_chains": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp]),
     "nqs_minsr_workspace": (_sz, [_vp, _i64]),
     "nqs_minsr": (_i32, [_vp, _vp, _i64, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _sz, _vp]),
     "nqs_batch_create": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(BatchItem), _i32, _i32, _i32, _i32, _vp]),
@@ -227,6 +228,15 @@ class Context:
             self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
             _ptr(eloc, (torch.float32,), "eloc", (n,), False), _ptr(stats, (torch.float64,), "stats", None, False),
             _ptr(force, (torch.float64,), "force", (self.P,), False), _stream()))
+
+    def local_energy_chains(self, samples, n_chains, eloc):
+        """nqs_local_energy_chains: eloc of sweep-major samples of n_chains chains."""
+        n = samples.shape[0]
+        if n % n_chains:
+            raise ValueError("samples rows must be a multiple of n_chains")
+        self._check(_lib.nqs_local_energy_chains(
+            self._h, _ptr(samples, _WORD, "samples", (n, self.W), False), n_chains, n // n_chains,
+            _ptr(eloc, (torch.float32,), "eloc", (n,), False), _stream()))
 
     def set_noise(self, sigma, key=0):
         """Noisy RBM (nqs_set_noise): sample |psi~|^2, log psi~ = log psi + zeta(x)/2."""

@@ -98,6 +98,8 @@ cudaError_t rbm_sweep(const nqs_ctx *c, uint32_t *state, int64_t n_chains, int n
                       int64_t *n_acc, uint32_t *acc_bits, float *delta, cudaStream_t s);
 cudaError_t rbm_logpsi(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *out, cudaStream_t s);
 cudaError_t rbm_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *eloc, cudaStream_t s);
+cudaError_t rbm_local_energy_chains(const nqs_ctx *c, const uint32_t *cfg, int64_t n_chains, int64_t per_chain,
+                                    float *eloc, cudaStream_t s);
 size_t rbm_grad_workspace(const nqs_ctx *c, int64_t n);
 cudaError_t rbm_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
                             const double *stats, double *force, void *ws, cudaStream_t s);

@@ -350,6 +350,19 @@ nqs_status nqs_stats(nqs_ctx *c, const float *eloc, int64_t n, int64_t n_chains,
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_stats");
 }
 
+nqs_status nqs_local_energy_chains(nqs_ctx *c, const uint32_t *samples, int64_t n_chains, int64_t per_chain,
+                                   float *eloc, nqs_stream stream) {
+  if (!c) return NQS_EINVAL;
+  if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_local_energy_chains: parameters not set");
+  if (n_chains < 0 || per_chain < 0) return fail(c, NQS_EINVAL, "nqs_local_energy_chains: negative size");
+  if (n_chains == 0 || per_chain == 0) return NQS_OK;
+  if (bad_ptr(samples) || bad_ptr(eloc)) return fail(c, NQS_EINVAL, "nqs_local_energy_chains: null argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = c->model_kind == NQS_DENSE ? nqs::dense_local_energy(c, samples, n_chains * per_chain, eloc, s)
+                                             : nqs::rbm_local_energy_chains(c, samples, n_chains, per_chain, eloc, s);
+  return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_local_energy_chains");
+}
+
 nqs_status nqs_set_noise(nqs_ctx *c, double sigma, uint64_t key) {
   if (!c) return NQS_EINVAL;
   if (!(sigma >= 0.0) || sigma > 100.0) return fail(c, NQS_EINVAL, "nqs_set_noise: need 0 <= sigma <= 100");

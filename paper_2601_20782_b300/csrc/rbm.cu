@@ -466,6 +466,8 @@ static ElocParams eloc_params(const nqs_ctx *c, const uint32_t *cfg, const int32
   p.M_pad = c->M_pad;
   p.J = (float)c->J1;
   p.h = (float)c->h;
+  p.n_chains = 0;
+  p.refresh = c->refresh;
   return p;
 }
 
@@ -480,6 +482,20 @@ cudaError_t rbm_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n, f
   const int E32 = c->M_pad / 32;
   const int L = (E32 == 1 && c->W <= 8) ? 8 : 32;
   return dispatch_le<Runners<float>::Eloc>(L, c->M_pad / L, c, p, s);
+}
+
+// Chain-ordered local energy of sweep-major samples (row k * n_chains + c), FP32 copy.
+cudaError_t rbm_local_energy_chains(const nqs_ctx *c, const uint32_t *cfg, int64_t n_chains, int64_t per_chain,
+                                    float *eloc, cudaStream_t s) {
+  ElocParams p = eloc_params(c, cfg, nullptr, n_chains * per_chain, eloc);
+  p.R = c->d_R32;
+  p.aK = c->d_aK32;
+  p.Wt = c->d_Wt32;
+  p.b = c->d_b32;
+  p.n_chains = n_chains;
+  const int E32 = c->M_pad / 32;
+  const int L = (E32 == 1 && c->W <= 8) ? 8 : 32;
+  return dispatch_le<Runners<float>::ElocChains>(L, c->M_pad / L, c, p, s);
 }
 
 cudaError_t rbm_flip_delta(const nqs_ctx *c, const uint32_t *cfg, const int32_t *sites, int64_t n, float *out,

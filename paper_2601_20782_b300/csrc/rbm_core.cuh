@@ -515,6 +515,15 @@ struct ChainCache {
     build_cache<L, E>(lam, mu, sw, Wt, b, N, W, M_pad, gl);
     if constexpr (LP) make_shadows<LY::H, TT>(lam, mu, lh, mh);
   }
+  // the cache of pre-activations th (sigmoid pairs), e.g. after an incremental update of th
+  __device__ __forceinline__ void from_theta(const float2 (&th)[LY::H]) {
+#pragma unroll
+    for (int k = 0; k < LY::H; ++k) {
+      sigmoid_pair(th[k].x, lam[k].x, mu[k].x);
+      sigmoid_pair(th[k].y, lam[k].y, mu[k].y);
+    }
+    if constexpr (LP) make_shadows<LY::H, TT>(lam, mu, lh, mh);
+  }
   // sum_j log2 g_j of flipping the site whose table row is `row`
   __device__ __forceinline__ float logsum(bool up, const TT *row, int gl) const {
     if constexpr (LP) return flip_logsum_lp<L, E, TT>(up, lh, mh, row, gl);
@@ -654,7 +663,40 @@ struct ElocParams {
   int64_t n;
   int n_bonds, N, W, M_pad;
   float J, h;
+  int64_t n_chains;  // chain-ordered kernel: rows are k * n_chains + c
+  int refresh;       // chain-ordered kernel: theta rebuilt from scratch every this many samples
 };
+
+// eps(x) of the TFIM from the configuration's cache (Eq. TFIM, App. I Eq. local_energies):
+// J sum_<ij> s_i s_j + h sum_i exp(log psi(flip_i x) - log psi(x)), two sites per iteration.
+template <int L, int E, typename TT>
+__device__ __forceinline__ float tfim_eloc_value(const ChainCache<L, E, TT> &cache, uint32_t sw, const ElocParams &p,
+                                                 const TT *R, const float2 *saK, int gl) {
+  const int N = p.N, M_pad = p.M_pad;
+  float d = 0.f;
+  for (int b0 = 0; b0 < p.n_bonds; b0 += L) {
+    const int bi = min(b0 + gl, p.n_bonds - 1);
+    const int2 bd = p.bonds[bi];
+    const uint32_t wa = __shfl_sync(FULL_MASK, sw, bd.x >> 5, L);
+    const uint32_t wb = __shfl_sync(FULL_MASK, sw, bd.y >> 5, L);
+    const uint32_t sa = (wa >> (bd.x & 31)) & 1u, sb = (wb >> (bd.y & 31)) & 1u;
+    if (b0 + gl < p.n_bonds) d += sa == sb ? 1.f : -1.f;
+  }
+  d = p.J * group_allsum<L>(d);
+  float off = 0.f;
+  for (int i = 0; i < N; i += 2) {
+    const int i1 = min(i + 1, N - 1);
+    const uint32_t word0 = __shfl_sync(FULL_MASK, sw, i >> 5, L);
+    const uint32_t word1 = __shfl_sync(FULL_MASK, sw, i1 >> 5, L);
+    const bool up0 = (word0 >> (i & 31)) & 1u, up1 = (word1 >> (i1 & 31)) & 1u;
+    const float tot0 = cache.logsum(up0, R + (size_t)i * M_pad, gl);
+    const float tot1 = cache.logsum(up1, R + (size_t)i1 * M_pad, gl);
+    const float2 ak0 = saK[i], ak1 = saK[i1];
+    off += expf(2.f * (ak0.y - (up0 ? ak0.x : -ak0.x)) + tot0 * LN2F);
+    if (i + 1 < N) off += expf(2.f * (ak1.y - (up1 ? ak1.x : -ak1.x)) + tot1 * LN2F);
+  }
+  return d + p.h * off;
+}
 
 // TFIM local energy (Eq. TFIM, App. I Eq. local_energies), FLIP = false:
 //   eps(x) = J sum_<ij> s_i s_j + h sum_i exp(log psi(flip_i x) - log psi(x)),
@@ -686,30 +728,62 @@ __global__ void __launch_bounds__(eloc_threads(E), 1) rbm_tfim_eloc_kernel(const
       const float2 ak = saK[i];
       if (base + grp < p.n && gl == 0) p.out[x] = 2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F;
     } else {
-      // diagonal: J sum over bonds of s_a s_b
-      float d = 0.f;
-      for (int b0 = 0; b0 < p.n_bonds; b0 += L) {
-        const int bi = min(b0 + gl, p.n_bonds - 1);
-        const int2 bd = p.bonds[bi];
-        const uint32_t wa = __shfl_sync(FULL_MASK, sw, bd.x >> 5, L);
-        const uint32_t wb = __shfl_sync(FULL_MASK, sw, bd.y >> 5, L);
-        const uint32_t sa = (wa >> (bd.x & 31)) & 1u, sb = (wb >> (bd.y & 31)) & 1u;
-        if (b0 + gl < p.n_bonds) d += sa == sb ? 1.f : -1.f;
+      const float e = tfim_eloc_value<L, E, TT>(cache, sw, p, R, saK, gl);
+      if (base + grp < p.n && gl == 0) p.out[x] = e;
+    }
+  }
+}
+
+// Local energies of sweep-major samples of n_chains chains (row k * n_chains + c), one group
+// per chain walking its samples in order: theta = W s + b is updated only for the spins that
+// changed since the chain's previous sample (theta += 2 s'_i W_i), rebuilt from scratch every
+// `refresh` samples, and each sample's eps is evaluated as in rbm_tfim_eloc_kernel.
+template <int L, int E, bool SMEM>
+__global__ void __launch_bounds__(eloc_threads(E), 1) rbm_tfim_eloc_chains_kernel(const ElocParams p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bar;
+  float2 *saK;
+  const float *R = stage_table<float, SMEM>(smem_raw, p.R, p.aK, p.N, p.M_pad, &bar, p.status, &saK);
+  if (!R) return;
+  using LY = Lay<L, E>;
+  const int N = p.N, W = p.W, M_pad = p.M_pad;
+  constexpr int G = 32 / L;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane / L, gl = lane % L;
+  const int64_t wpb = blockDim.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * wpb * G;
+  const int64_t C = p.n_chains, K = p.n / p.n_chains;
+  for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * G; base < C; base += stride) {
+    const int64_t c = base + grp;
+    const bool valid = c < C;
+    const int64_t cc = valid ? c : C - 1;
+    float2 th[LY::H];
+    ChainCache<L, E, float> cache;
+    uint32_t prev = 0u;
+    for (int64_t k = 0; k < K; ++k) {
+      const int64_t x = k * C + cc;
+      const uint32_t sw = gl < W ? p.cfg[x * W + gl] : 0u;
+      if (k % p.refresh == 0) {
+        compute_theta<L, E>(th, sw, p.Wt, p.b, N, W, M_pad, gl);
+      } else {
+        for (int wi = 0; wi < W; ++wi) {
+          uint32_t m = __shfl_sync(FULL_MASK, sw ^ prev, wi, L);
+          const uint32_t now = __shfl_sync(FULL_MASK, sw, wi, L);
+          while (m) {  // uniform within the group
+            const int bit = __ffs(m) - 1;
+            m &= m - 1u;
+            const float s2 = ((now >> bit) & 1u) ? 2.f : -2.f;
+            float2 w[LY::H];
+            LY::template load<true>(p.Wt + (size_t)(32 * wi + bit) * M_pad, gl, w, 0.f);
+            const float2 s22 = make_float2(s2, s2);
+#pragma unroll
+            for (int q = 0; q < LY::H; ++q) th[q] = fma2(s22, w[q], th[q]);
+          }
+        }
       }
-      d = p.J * group_allsum<L>(d);
-      float off = 0.f;
-      for (int i = 0; i < N; i += 2) {
-        const int i1 = min(i + 1, N - 1);
-        const uint32_t word0 = __shfl_sync(FULL_MASK, sw, i >> 5, L);
-        const uint32_t word1 = __shfl_sync(FULL_MASK, sw, i1 >> 5, L);
-        const bool up0 = (word0 >> (i & 31)) & 1u, up1 = (word1 >> (i1 & 31)) & 1u;
-        const float tot0 = cache.logsum(up0, R + (size_t)i * M_pad, gl);
-        const float tot1 = cache.logsum(up1, R + (size_t)i1 * M_pad, gl);
-        const float2 ak0 = saK[i], ak1 = saK[i1];
-        off += expf(2.f * (ak0.y - (up0 ? ak0.x : -ak0.x)) + tot0 * LN2F);
-        if (i + 1 < N) off += expf(2.f * (ak1.y - (up1 ? ak1.x : -ak1.x)) + tot1 * LN2F);
-      }
-      if (base + grp < p.n && gl == 0) p.out[x] = d + p.h * off;
+      cache.from_theta(th);
+      const float e = tfim_eloc_value<L, E, float>(cache, sw, p, R, saK, gl);
+      if (valid && gl == 0) p.out[x] = e;
+      prev = sw;
     }
   }
 }
@@ -765,6 +839,15 @@ struct Runners {
       const size_t shm = table_smem<TT>(c, &fits);
       return fits ? launch_persistent(rbm_sweep_kernel<L, E, true, TT, true>, c, p.C, 32 / L, shm, s, &p)
                   : launch_persistent(rbm_sweep_kernel<L, E, false, TT, true>, c, p.C, 32 / L, shm, s, &p);
+    }
+  };
+  template <int L, int E>
+  struct ElocChains {  // chain-ordered local energy (FP32 tables)
+    static cudaError_t run(const nqs_ctx *c, const ElocParams &p, cudaStream_t s) {
+      bool fits;
+      const size_t shm = table_smem<float>(c, &fits);
+      return fits ? launch_persistent(rbm_tfim_eloc_chains_kernel<L, E, true>, c, p.n_chains, 32 / L, shm, s, &p)
+                  : launch_persistent(rbm_tfim_eloc_chains_kernel<L, E, false>, c, p.n_chains, 32 / L, shm, s, &p);
     }
   };
   template <int L, int E>

@@ -245,3 +245,25 @@ def test_histogram_tv_against_exact_distribution_4x4():
     floors = [0.5 * np.abs(np.bincount(rng.choice(pi.size, C, p=pi), minlength=pi.size) / C - pi).sum()
               for _ in range(8)]
     assert tv < max(floors) * 1.15, (tv, floors)
+
+
+@pytest.mark.parametrize("Lx,Ly,M,dtype", [(10, 10, 400, "f16"), (16, 1, 16, "f32"), (37, 1, 50, "f32")])
+def test_local_energy_chains_matches_per_sample(Lx, Ly, M, dtype):
+    """Chain-ordered local energies (incremental theta over each chain's sweep-major samples,
+    rebuilt every 20 samples) equal the per-sample evaluation up to FP32 rounding."""
+    p = nqs()
+    N = Lx * Ly
+    ctx = p.Context("tfim", Lx, Ly, J1=1.0, h=2.0, model="rbm", n_hidden=M, dtype=dtype)
+    ctx.set_params(torch.from_numpy(rbm_params(N, M, 0.1, 3)).cuda())
+    C, K = 300, 45
+    state = torch.zeros((C, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, 4)
+    samples = torch.zeros((K * C, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.sweep(state, K, 0, 5, 0, samples)
+    e1 = torch.empty(K * C, dtype=torch.float32, device="cuda")
+    e2 = torch.empty(K * C, dtype=torch.float32, device="cuda")
+    ctx.local_energy(samples, e1)
+    ctx.local_energy_chains(samples, C, e2)
+    a, b = e1.cpu().numpy().astype(np.float64), e2.cpu().numpy().astype(np.float64)
+    rel = np.abs(b - a) / (np.abs(a) + 2.0 * N)
+    assert rel.max() <= 2e-5, (rel.max(), np.argmax(rel), a[np.argmax(rel)], b[np.argmax(rel)])
