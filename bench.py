@@ -30,10 +30,10 @@ import numpy as np
 import workloads
 
 METRIC = "MH proposals/sec and local-energy samples/sec on 1 B300, mixed vs FP32 at stated bias"
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of the FP16 sweep kernel
-# (16384 chains x 500 sweeps of this workload): 13.1 MB read + 84.0 MB written.  Valid for that
-# kernel as built; None for the other copies, whose traffic was not captured.
-SWEEP_TRAFFIC_BYTES = {"f16": 97.1e6}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of the sweep kernel
+# (16384 chains x 500 sweeps of this workload), per sampling copy, for the kernel as built;
+# a copy without an entry reports None.
+SWEEP_TRAFFIC_BYTES = {}
 WL = workloads.TFIM_2D_10x10
 
 

@@ -214,6 +214,20 @@ __device__ __forceinline__ void flip_factors(bool up, const float2 (&lam)[H], co
   }
 }
 
+// sum over 4-pair groups of log2 of the product of the factors g_k = a_k r_k + b_k
+template <int H>
+__device__ __forceinline__ float product_log2(const float2 (&a)[H], const float2 (&b)[H], const float2 (&r)[H]) {
+  float part = 0.f;
+#pragma unroll
+  for (int k0 = 0; k0 < H; k0 += 4) {
+    float2 pr = fma2(a[k0], r[k0], b[k0]);
+#pragma unroll
+    for (int k = k0 + 1; k < (k0 + 4 < H ? k0 + 4 : H); ++k) pr = mul2(pr, fma2(a[k], r[k], b[k]));
+    part += lg2_approx(pr.x * pr.y);
+  }
+  return part;
+}
+
 // Streams the lane's row in 4-pair groups: loads a group, forms its factors g and
 // their product, and returns the lane's partial sum of log2 products; *g_out keeps the
 // factors only when requested (exact fallback path).
@@ -223,16 +237,8 @@ __device__ __forceinline__ float flip_partial(bool up, const float2 (&lam)[Lay<L
   using LY = Lay<L, E>;
   float2 rv[LY::H];
   LY::template load<false>(row, gl, rv, 1.f);
-  float part = 0.f;
-#pragma unroll
-  for (int k0 = 0; k0 < LY::H; k0 += 4) {
-    float2 pr = up ? fma2(lam[k0], rv[k0], mu[k0]) : fma2(mu[k0], rv[k0], lam[k0]);
-#pragma unroll
-    for (int k = k0 + 1; k < (k0 + 4 < LY::H ? k0 + 4 : LY::H); ++k)
-      pr = mul2(pr, up ? fma2(lam[k], rv[k], mu[k]) : fma2(mu[k], rv[k], lam[k]));
-    part += lg2_approx(pr.x * pr.y);
-  }
-  return part;
+  // g = mu + lam R (up) or lam + mu R (down): one uniform branch, no per-unit selects
+  return up ? product_log2<LY::H>(lam, mu, rv) : product_log2<LY::H>(mu, lam, rv);
 }
 
 // Exact sum of log2 g over the lane's units (fallback when a product left the FP32 range).
@@ -281,16 +287,19 @@ __device__ __forceinline__ float flip_partial_lp(bool up, const typename Prec<TT
   using P = Prec<TT>;
   typename P::T2 rv[LY::H];
   load_pairs_tt<L, E, TT>(row, gl, rv);
-  float part = 0.f;
+  auto prod = [&](const typename P::T2(&a)[LY::H], const typename P::T2(&b)[LY::H]) {
+    float part = 0.f;
 #pragma unroll
-  for (int k0 = 0; k0 < LY::H; k0 += 4) {
-    float2 pr = P::to_f2(up ? P::fma(lh[k0], rv[k0], mh[k0]) : P::fma(mh[k0], rv[k0], lh[k0]));
+    for (int k0 = 0; k0 < LY::H; k0 += 4) {
+      float2 pr = P::to_f2(P::fma(a[k0], rv[k0], b[k0]));
 #pragma unroll
-    for (int k = k0 + 1; k < (k0 + 4 < LY::H ? k0 + 4 : LY::H); ++k)
-      pr = mul2(pr, P::to_f2(up ? P::fma(lh[k], rv[k], mh[k]) : P::fma(mh[k], rv[k], lh[k])));
-    part += lg2_approx(pr.x * pr.y);
-  }
-  return part;
+      for (int k = k0 + 1; k < (k0 + 4 < LY::H ? k0 + 4 : LY::H); ++k)
+        pr = mul2(pr, P::to_f2(P::fma(a[k], rv[k], b[k])));
+      part += lg2_approx(pr.x * pr.y);
+    }
+    return part;
+  };
+  return up ? prod(lh, mh) : prod(mh, lh);  // one uniform branch, no per-unit selects
 }
 
 // exact path of the low-precision sum: each 16-bit factor converted and logged separately
@@ -328,6 +337,15 @@ __device__ __forceinline__ float flip_logsum_lp(bool up, const typename Prec<TT>
   return group_allsum<L>(flip_partial_lp_exact<L, E, TT>(up, lh, mh, row, gl));
 }
 
+// One factor pair of an accepted flip, with x the cache entry multiplied by R (lam for an up
+// spin, mu for a down spin) and y the other: g = x R + y, x' = x R / g, y' = y / g.
+__device__ __forceinline__ void accept_pair(float2 &x, float2 &y, float2 r) {
+  const float2 g = fma2(x, r, y);
+  const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
+  x = mul2(mul2(x, r), inv);
+  y = mul2(y, inv);
+}
+
 // Accepted flip with a 16-bit table: the FP32 cache is updated as in accept_update with
 // the table value converted to FP32, then the 16-bit shadows are refreshed.
 template <int L, int E, typename TT>
@@ -338,20 +356,16 @@ __device__ __forceinline__ void accept_update_lp(bool up, float2 (&lam)[Lay<L, E
   using P = Prec<TT>;
   typename P::T2 rv[LY::H];
   load_pairs_tt<L, E, TT>(row, gl, rv);
+  auto upd = [&](float2(&x)[LY::H], float2(&y)[LY::H]) {
+#pragma unroll
+    for (int k = 0; k < LY::H; ++k) accept_pair(x[k], y[k], P::to_f2(rv[k]));
+  };
+  if (up)  // one uniform branch on the spin, no per-unit selects
+    upd(lam, mu);
+  else
+    upd(mu, lam);
 #pragma unroll
   for (int k = 0; k < LY::H; ++k) {
-    const float2 r = P::to_f2(rv[k]);
-    if (up) {
-      const float2 g = fma2(lam[k], r, mu[k]);
-      const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
-      lam[k] = mul2(mul2(lam[k], r), inv);
-      mu[k] = mul2(mu[k], inv);
-    } else {
-      const float2 g = fma2(mu[k], r, lam[k]);
-      const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
-      mu[k] = mul2(mul2(mu[k], r), inv);
-      lam[k] = mul2(lam[k], inv);
-    }
     lh[k] = P::from_f2(lam[k]);
     mh[k] = P::from_f2(mu[k]);
   }
@@ -418,41 +432,39 @@ __device__ bool load_table(TT *sR, const TT *R, uint32_t bytes, uint64_t *bar, i
 //   down: mu' = mu R / g,  lam' = lam / g, g = lam + mu R
 // The row is re-read pair by pair and g recomputed, so neither has to stay live in
 // registers from the proposal to the decision.
-template <int L, int E, bool SMEM>
-__device__ __forceinline__ void accept_update(bool up, float2 (&lam)[Lay<L, E>::H], float2 (&mu)[Lay<L, E>::H],
-                                              const float *row, int gl) {
+template <int L, int E>
+__device__ __forceinline__ void accept_rows(float2 (&x)[Lay<L, E>::H], float2 (&y)[Lay<L, E>::H], const float *row,
+                                            int gl) {
   using LY = Lay<L, E>;
-  auto upd = [&](int k, float2 r) {
-    if (up) {
-      const float2 g = fma2(lam[k], r, mu[k]);
-      const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
-      lam[k] = mul2(mul2(lam[k], r), inv);
-      mu[k] = mul2(mu[k], inv);
-    } else {
-      const float2 g = fma2(mu[k], r, lam[k]);
-      const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
-      mu[k] = mul2(mul2(mu[k], r), inv);
-      lam[k] = mul2(lam[k], inv);
-    }
-  };
 #pragma unroll
   for (int v = 0; v < LY::V; ++v) {
-    float4 q;
-    q = *reinterpret_cast<const float4 *>(row + 4 * (v * L + gl));
-    upd(2 * v, make_float2(q.x, q.y));
-    upd(2 * v + 1, make_float2(q.z, q.w));
+    const float4 q = *reinterpret_cast<const float4 *>(row + 4 * (v * L + gl));
+    accept_pair(x[2 * v], y[2 * v], make_float2(q.x, q.y));
+    accept_pair(x[2 * v + 1], y[2 * v + 1], make_float2(q.z, q.w));
   }
   float t[3] = {1.f, 1.f, 1.f};
 #pragma unroll
-  for (int k = 0; k < LY::T; ++k) {
-    t[k] = row[4 * LY::V * L + k * L + gl];
-  }
-  if constexpr (LY::T == 1) upd(2 * LY::V, make_float2(t[0], 1.f));
-  if constexpr (LY::T == 2) upd(2 * LY::V, make_float2(t[0], t[1]));
+  for (int k = 0; k < LY::T; ++k) t[k] = row[4 * LY::V * L + k * L + gl];
+  if constexpr (LY::T == 1) accept_pair(x[2 * LY::V], y[2 * LY::V], make_float2(t[0], 1.f));
+  if constexpr (LY::T == 2) accept_pair(x[2 * LY::V], y[2 * LY::V], make_float2(t[0], t[1]));
   if constexpr (LY::T == 3) {
-    upd(2 * LY::V, make_float2(t[0], t[1]));
-    upd(2 * LY::V + 1, make_float2(t[2], 1.f));
+    accept_pair(x[2 * LY::V], y[2 * LY::V], make_float2(t[0], t[1]));
+    accept_pair(x[2 * LY::V + 1], y[2 * LY::V + 1], make_float2(t[2], 1.f));
   }
+}
+
+// Accepted flip: lam/mu = e^{2 theta} is multiplied by R (spin up) or 1/R (spin down):
+//   up:   lam' = lam R / g, mu' = mu / g,  g = mu + lam R
+//   down: mu' = mu R / g,  lam' = lam / g, g = lam + mu R
+// The row is re-read and g recomputed, so neither has to stay live in registers from the
+// proposal to the decision; one uniform branch on the spin, no per-unit selects.
+template <int L, int E, bool SMEM>
+__device__ __forceinline__ void accept_update(bool up, float2 (&lam)[Lay<L, E>::H], float2 (&mu)[Lay<L, E>::H],
+                                              const float *row, int gl) {
+  if (up)
+    accept_rows<L, E>(lam, mu, row, gl);
+  else
+    accept_rows<L, E>(mu, lam, row, gl);
 }
 
 struct SweepParams {
