@@ -206,6 +206,7 @@ nqs_status nqs_batch_create(nqs_batch **out, const nqs_batch_item *items, int32_
     in.p.W = c->W;
     in.p.M_pad = c->M_pad;
     in.p.refresh = c->refresh;
+    in.p.renorm = c->renorm;
     in.p.k0 = (uint32_t)items[k].seed;
     in.p.k1 = (uint32_t)(items[k].seed >> 32);
   }

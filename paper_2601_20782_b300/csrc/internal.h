@@ -24,6 +24,8 @@ struct nqs_ctx {
   int refresh = 20;
   int chains_per_warp = 0;  // 0: tuner
   double noise_sigma = 0.0;  // noisy RBM (nqs_set_noise): 0 = off
+  int renorm = 1;            // RBM sweep: accepted flips between cache normalisations (set_params)
+  float *d_bounds = nullptr; // RBM: [max |W|, max_j (sum_i |W_ji| + |b_j|)] of the sampling copy
   uint64_t noise_key = 0;
   int device = 0;
   int num_sms = 0;
@@ -92,6 +94,7 @@ constexpr int STATUS_TIMEOUT = 2;  // a bounded wait gave up
 
 // rbm.cu
 cudaError_t rbm_prepare(nqs_ctx *c, const double *params, cudaStream_t s);
+int rbm_renorm_interval(const nqs_ctx *c, float max_w, float max_theta);
 cudaError_t init_chains(const nqs_ctx *c, uint32_t *state, int64_t n, uint64_t seed, cudaStream_t s);
 cudaError_t rbm_sweep(const nqs_ctx *c, uint32_t *state, int64_t n_chains, int n_sweeps, int burn_in,
                       uint64_t seed, uint32_t sweep_offset, uint32_t *samples, float *logpsi,

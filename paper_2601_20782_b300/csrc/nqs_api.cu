@@ -29,7 +29,7 @@ cudaError_t dev_alloc(T **p, size_t count) {
 }
 
 void free_all(nqs_ctx *c) {
-  void *ptrs[] = {c->d_status, c->d_scratch, c->d_bonds, c->d_bondJ, c->d_a, c->d_b,
+  void *ptrs[] = {c->d_bounds, c->d_status, c->d_scratch, c->d_bonds, c->d_bondJ, c->d_a, c->d_b,
                   c->d_Wt,     c->d_R,       c->d_aK,    c->d_Wm,    c->d_bm};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -155,7 +155,7 @@ nqs_status nqs_create(nqs_ctx **out, const nqs_model_desc *model, const nqs_ham_
   build_bonds(c, bonds, bJ);
   c->n_bonds = (int)bonds.size();
   const size_t tsz = c->dtype == NQS_F32 ? 4 : 2;
-  if ((e = dev_alloc(&c->d_status, 1)) != cudaSuccess || (e = dev_alloc(&c->d_scratch, 5 * nqs::STATS_MAX_BLOCKS)) ||
+  if ((e = cudaMalloc(&c->d_bounds, 2 * sizeof(float))) != cudaSuccess || (e = dev_alloc(&c->d_status, 1)) != cudaSuccess || (e = dev_alloc(&c->d_scratch, 5 * nqs::STATS_MAX_BLOCKS)) ||
       (e = dev_alloc(&c->d_bonds, bonds.size())) || (e = dev_alloc(&c->d_bondJ, bJ.size())) ||
       (e = dev_alloc(&c->d_a, c->N)) || (e = dev_alloc(&c->d_b, c->M_pad)) ||
       (e = dev_alloc(&c->d_Wt, (size_t)c->N * c->M_pad)) ||
@@ -233,9 +233,13 @@ nqs_status nqs_set_params(nqs_ctx *c, const double *params, nqs_stream stream) {
   e = c->model_kind == NQS_DENSE ? nqs::dense_prepare(c, params, s) : nqs::rbm_prepare(c, params, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "nqs_set_params");
   int st = 0;
+  float bounds[2] = {0.f, 0.f};
   if ((e = cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (c->model_kind == NQS_RBM &&
+       (e = cudaMemcpyAsync(bounds, c->d_bounds, sizeof(bounds), cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return cuda_fail(c, e, "nqs_set_params");
+  if (c->model_kind == NQS_RBM) c->renorm = nqs::rbm_renorm_interval(c, bounds[0], bounds[1]);
   if (st & nqs::STATUS_RANGE) {
     cudaMemsetAsync(c->d_status, 0, sizeof(int), s);
     return fail(c, NQS_EINVAL, c->dtype == NQS_F16 ? "a weight is outside the F16 sampler's range (|W| <= 2.5)"

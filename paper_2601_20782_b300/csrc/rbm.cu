@@ -78,6 +78,22 @@ __global__ void rbm_colsum_kernel(const float *Wt, const float *a, int N, int M_
   if (lane == 0) aK[warp] = make_float2(a[warp], (float)s);
 }
 
+// Bounds of the sampling copy for the sweep's cache normalisation interval:
+// out[0] = max |W_ji|, out[1] = max_j (sum_i |W_ji| + |b_j|) >= max |theta_j|.  Thread per
+// hidden unit; non-negative floats are ordered like their bit patterns (atomicMax on ints).
+__global__ void rbm_bounds_kernel(const float *Wt, const float *b, int N, int M_pad, float *out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M_pad; j += gridDim.x * blockDim.x) {
+    float s = fabsf(b[j]), m = 0.f;
+    for (int i = 0; i < N; ++i) {
+      const float w = fabsf(Wt[(int64_t)i * M_pad + j]);
+      s += w;
+      m = fmaxf(m, w);
+    }
+    atomicMax(reinterpret_cast<int *>(out), __float_as_int(m));
+    atomicMax(reinterpret_cast<int *>(out) + 1, __float_as_int(s));
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // chain initialisation (same draws as the oracle's init_spins_random / _balanced)
 __global__ void init_random_kernel(uint32_t *state, int64_t C, int N, int W, uint32_t k0, uint32_t k1) {
@@ -390,6 +406,9 @@ cudaError_t rbm_prepare(nqs_ctx *c, const double *params, cudaStream_t s) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   rbm_colsum_kernel<<<(c->N * 32 + 255) / 256, 256, 0, s>>>(c->d_Wt, c->d_a, c->N, c->M_pad, c->d_aK);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c->d_bounds, 0, 2 * sizeof(float), s)) != cudaSuccess) return e;
+  rbm_bounds_kernel<<<(c->M_pad + 127) / 128, 128, 0, s>>>(c->d_Wt, c->d_b, c->N, c->M_pad, c->d_bounds);
   if ((e = cudaGetLastError()) != cudaSuccess || c->dtype == NQS_F32) return e;
   // FP32 copy for the local energy of a 16-bit context
   rbm_prepare_kernel<float><<<blocks, 256, 0, s>>>(params, c->N, c->M, c->M_pad, c->d_a32, c->d_b32, c->d_Wt32,
@@ -434,6 +453,7 @@ cudaError_t rbm_sweep(const nqs_ctx *c, uint32_t *state, int64_t n_chains, int n
   p.sweep_offset = sweep_offset;
   p.k0 = (uint32_t)seed;
   p.k1 = (uint32_t)(seed >> 32);
+  p.renorm = c->renorm;
   p.noise_sigma = (float)c->noise_sigma;
   p.noise_k0 = (uint32_t)c->noise_key;
   p.noise_k1 = (uint32_t)(c->noise_key >> 32);
@@ -504,6 +524,21 @@ cudaError_t rbm_flip_delta(const nqs_ctx *c, const uint32_t *cfg, const int32_t 
   if (c->dtype == NQS_F16) return rbm_eloc_f16(c, p, s);
   if (c->dtype == NQS_BF16) return rbm_eloc_bf16(c, p, s);
   return dispatch_l32<Runners<float>::Eloc>(c->M_pad / 32, c, p, s);
+}
+
+// Accepted flips between normalisations of the sweep's cache.  Between normalisations a pair
+// (lam, mu) drifts by at most e^{4 max|W|} per accepted flip and its smaller entry starts at
+// no less than e^{-2 max|theta|} / 2; K is the largest of 8, 4, 2 with a drift
+// D = 4 max|W| K that keeps both in range: D <= 8 for an F16 copy (its larger entry, >= 1/2,
+// stays above the F16 normal range's bottom), D <= 40 and 2 max|theta| + D <= 80 otherwise
+// (FP32 normal range).  K = 1 normalises after every accepted flip.
+int rbm_renorm_interval(const nqs_ctx *c, float max_w, float max_theta) {
+  for (int K = 8; K > 1; K /= 2) {
+    const double D = 4.0 * max_w * K;
+    const bool ok = c->dtype == NQS_F16 ? D <= 8.0 && 2.0 * max_theta + D <= 80.0 : D <= 40.0 && 2.0 * max_theta + D <= 80.0;
+    if (ok) return K;
+  }
+  return 1;
 }
 
 int rbm_force_chunks(const nqs_ctx *c, int64_t n) { return force_chunks(c, n); }

@@ -197,7 +197,7 @@ __device__ __forceinline__ float cache_logpsi(const float2 (&lam)[Lay<L, E>::H],
   float part = 0.f;
 #pragma unroll
   for (int k = 0; k < Lay<L, E>::H; ++k)
-    part += log2f(4.f * lam[k].x * mu[k].x) + log2f(4.f * lam[k].y * mu[k].y);
+    part += (2.f + log2f(lam[k].x) + log2f(mu[k].x)) + (2.f + log2f(lam[k].y) + log2f(mu[k].y));
   return visible_term<L>(sw, aK, N, gl) - 0.5f * LN2F * group_allsum<L>(part);
 }
 
@@ -337,40 +337,6 @@ __device__ __forceinline__ float flip_logsum_lp(bool up, const typename Prec<TT>
   return group_allsum<L>(flip_partial_lp_exact<L, E, TT>(up, lh, mh, row, gl));
 }
 
-// One factor pair of an accepted flip, with x the cache entry multiplied by R (lam for an up
-// spin, mu for a down spin) and y the other: g = x R + y, x' = x R / g, y' = y / g.
-__device__ __forceinline__ void accept_pair(float2 &x, float2 &y, float2 r) {
-  const float2 g = fma2(x, r, y);
-  const float2 inv = make_float2(rcp_approx(g.x), rcp_approx(g.y));
-  x = mul2(mul2(x, r), inv);
-  y = mul2(y, inv);
-}
-
-// Accepted flip with a 16-bit table: the FP32 cache is updated as in accept_update with
-// the table value converted to FP32, then the 16-bit shadows are refreshed.
-template <int L, int E, typename TT>
-__device__ __forceinline__ void accept_update_lp(bool up, float2 (&lam)[Lay<L, E>::H], float2 (&mu)[Lay<L, E>::H],
-                                                 typename Prec<TT>::T2 (&lh)[Lay<L, E>::H],
-                                                 typename Prec<TT>::T2 (&mh)[Lay<L, E>::H], const TT *row, int gl) {
-  using LY = Lay<L, E>;
-  using P = Prec<TT>;
-  typename P::T2 rv[LY::H];
-  load_pairs_tt<L, E, TT>(row, gl, rv);
-  auto upd = [&](float2(&x)[LY::H], float2(&y)[LY::H]) {
-#pragma unroll
-    for (int k = 0; k < LY::H; ++k) accept_pair(x[k], y[k], P::to_f2(rv[k]));
-  };
-  if (up)  // one uniform branch on the spin, no per-unit selects
-    upd(lam, mu);
-  else
-    upd(mu, lam);
-#pragma unroll
-  for (int k = 0; k < LY::H; ++k) {
-    lh[k] = P::from_f2(lam[k]);
-    mh[k] = P::from_f2(mu[k]);
-  }
-}
-
 // sum_j log2 g_j over the group: products of up to 8 factors (4 pairs) per MUFU lg2.
 // With one chain per warp the lane partials are added exactly as 2^-20 fixed-point
 // integers by one redux.sync (a 32-lane sum in one instruction instead of a 5-stage
@@ -432,41 +398,6 @@ __device__ bool load_table(TT *sR, const TT *R, uint32_t bytes, uint64_t *bar, i
 //   down: mu' = mu R / g,  lam' = lam / g, g = lam + mu R
 // The row is re-read pair by pair and g recomputed, so neither has to stay live in
 // registers from the proposal to the decision.
-template <int L, int E>
-__device__ __forceinline__ void accept_rows(float2 (&x)[Lay<L, E>::H], float2 (&y)[Lay<L, E>::H], const float *row,
-                                            int gl) {
-  using LY = Lay<L, E>;
-#pragma unroll
-  for (int v = 0; v < LY::V; ++v) {
-    const float4 q = *reinterpret_cast<const float4 *>(row + 4 * (v * L + gl));
-    accept_pair(x[2 * v], y[2 * v], make_float2(q.x, q.y));
-    accept_pair(x[2 * v + 1], y[2 * v + 1], make_float2(q.z, q.w));
-  }
-  float t[3] = {1.f, 1.f, 1.f};
-#pragma unroll
-  for (int k = 0; k < LY::T; ++k) t[k] = row[4 * LY::V * L + k * L + gl];
-  if constexpr (LY::T == 1) accept_pair(x[2 * LY::V], y[2 * LY::V], make_float2(t[0], 1.f));
-  if constexpr (LY::T == 2) accept_pair(x[2 * LY::V], y[2 * LY::V], make_float2(t[0], t[1]));
-  if constexpr (LY::T == 3) {
-    accept_pair(x[2 * LY::V], y[2 * LY::V], make_float2(t[0], t[1]));
-    accept_pair(x[2 * LY::V + 1], y[2 * LY::V + 1], make_float2(t[2], 1.f));
-  }
-}
-
-// Accepted flip: lam/mu = e^{2 theta} is multiplied by R (spin up) or 1/R (spin down):
-//   up:   lam' = lam R / g, mu' = mu / g,  g = mu + lam R
-//   down: mu' = mu R / g,  lam' = lam / g, g = lam + mu R
-// The row is re-read and g recomputed, so neither has to stay live in registers from the
-// proposal to the decision; one uniform branch on the spin, no per-unit selects.
-template <int L, int E, bool SMEM>
-__device__ __forceinline__ void accept_update(bool up, float2 (&lam)[Lay<L, E>::H], float2 (&mu)[Lay<L, E>::H],
-                                              const float *row, int gl) {
-  if (up)
-    accept_rows<L, E>(lam, mu, row, gl);
-  else
-    accept_rows<L, E>(mu, lam, row, gl);
-}
-
 struct SweepParams {
   const void *R;  // [N][M_pad] table in the sampling dtype
   const float2 *aK;
@@ -481,6 +412,7 @@ struct SweepParams {
   int *status;
   int64_t C;
   int N, W, M_pad, n_sweeps, burn_in, refresh;
+  int renorm;  // accepted flips between normalisations of the cache (ChainCache)
   uint32_t sweep_offset, k0, k1;
   float noise_sigma;  // noisy-RBM kernels only: standard deviation of zeta
   uint32_t noise_k0, noise_k1;
@@ -514,6 +446,14 @@ __device__ __forceinline__ float log_uniform(uint32_t w) {
 
 // Per-chain state of the sampler: the FP32 cache (lam, mu) and, for a 16-bit sampling
 // copy, its 16-bit shadows used by the factor arithmetic.
+//
+// Between normalisations the pairs are kept unnormalised: (lam~_j, mu~_j) = s_j (lam_j, mu_j)
+// with lam~/mu~ = e^{2 theta_j} exact and the chain's running log-scale ls = sum_j log2 s_j.
+// A proposal's factors become g~_j = s_j g_j, so sum_j log2 g_j = sum_j log2 g~_j - ls.  An
+// accepted flip multiplies lam~ (spin up) or mu~ (spin down) by R and nothing else: then
+// s_j' = s_j g_j, so the new ls is the sum of log2 g~ the accepted proposal just computed.
+// Every `renorm` accepted flips (a bound on the drift chosen from the weights at
+// nqs_set_params) the pairs are normalised again and ls returns to 0.
 template <int L, int E, typename TT>
 struct ChainCache {
   using LY = Lay<L, E>;
@@ -521,11 +461,15 @@ struct ChainCache {
   using T2 = typename Prec<TT>::T2;
   float2 lam[LY::H], mu[LY::H];
   T2 lh[LP ? LY::H : 1], mh[LP ? LY::H : 1];
+  float ls = 0.f;  // sum_j log2 (lam~_j + mu~_j)
+  int since = 0;   // accepted flips since the last normalisation
 
   __device__ __forceinline__ void build(uint32_t sw, const float *Wt, const float *b, int N, int W, int M_pad,
                                         int gl) {
     build_cache<L, E>(lam, mu, sw, Wt, b, N, W, M_pad, gl);
     if constexpr (LP) make_shadows<LY::H, TT>(lam, mu, lh, mh);
+    ls = 0.f;
+    since = 0;
   }
   // the cache of pre-activations th (sigmoid pairs), e.g. after an incremental update of th
   __device__ __forceinline__ void from_theta(const float2 (&th)[LY::H]) {
@@ -535,19 +479,61 @@ struct ChainCache {
       sigmoid_pair(th[k].y, lam[k].y, mu[k].y);
     }
     if constexpr (LP) make_shadows<LY::H, TT>(lam, mu, lh, mh);
+    ls = 0.f;
+    since = 0;
   }
-  // sum_j log2 g_j of flipping the site whose table row is `row`
+  // sum_j log2 g~_j of flipping the site whose table row is `row` (subtract ls for sum log2 g)
   __device__ __forceinline__ float logsum(bool up, const TT *row, int gl) const {
     if constexpr (LP) return flip_logsum_lp<L, E, TT>(up, lh, mh, row, gl);
     else return flip_logsum<L, E>(up, lam, mu, row, gl);
   }
+  __device__ __forceinline__ void normalize() {
+#pragma unroll
+    for (int k = 0; k < LY::H; ++k) {
+      const float2 s = make_float2(lam[k].x + mu[k].x, lam[k].y + mu[k].y);
+      const float2 inv = make_float2(rcp_approx(s.x), rcp_approx(s.y));
+      lam[k] = mul2(lam[k], inv);
+      mu[k] = mul2(mu[k], inv);
+    }
+    if constexpr (LP) make_shadows<LY::H, TT>(lam, mu, lh, mh);
+    ls = 0.f;
+    since = 0;
+  }
+  // accepted flip of the site whose table row is `row`; tot = its logsum(up, row, gl)
   template <bool SMEM>
-  __device__ __forceinline__ void accept(bool up, const TT *row, int gl) {
-    if constexpr (LP) accept_update_lp<L, E, TT>(up, lam, mu, lh, mh, row, gl);
-    else accept_update<L, E, SMEM>(up, lam, mu, row, gl);
+  __device__ __forceinline__ void accept(bool up, const TT *row, int gl, float tot, int renorm) {
+    if constexpr (LP) {
+      typename Prec<TT>::T2 rv[LY::H];
+      load_pairs_tt<L, E, TT>(row, gl, rv);
+      if (up) {
+#pragma unroll
+        for (int k = 0; k < LY::H; ++k) {
+          lam[k] = mul2(lam[k], Prec<TT>::to_f2(rv[k]));
+          lh[k] = Prec<TT>::from_f2(lam[k]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < LY::H; ++k) {
+          mu[k] = mul2(mu[k], Prec<TT>::to_f2(rv[k]));
+          mh[k] = Prec<TT>::from_f2(mu[k]);
+        }
+      }
+    } else {
+      float2 rv[LY::H];
+      LY::template load<false>(row, gl, rv, 1.f);
+      if (up) {
+#pragma unroll
+        for (int k = 0; k < LY::H; ++k) lam[k] = mul2(lam[k], rv[k]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < LY::H; ++k) mu[k] = mul2(mu[k], rv[k]);
+      }
+    }
+    ls = tot;
+    if (++since >= renorm) normalize();
   }
   __device__ __forceinline__ float logpsi(uint32_t sw, const float2 *aK, int N, int gl) const {
-    return cache_logpsi<L, E>(lam, mu, sw, aK, N, gl);
+    return cache_logpsi<L, E>(lam, mu, sw, aK, N, gl) + ls * LN2F;  // log cosh theta_j gains log s_j
   }
 };
 
@@ -606,7 +592,7 @@ __device__ __forceinline__ void sweep_chain(const SweepParams &p, const TT *R, c
         const TT *row = R + (size_t)site * M_pad;
         const float tot = cache.logsum(up, row, gl);
         const float2 ak = saK[site];
-        float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + tot * LN2F;
+        float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + (tot - cache.ls) * LN2F;
         float zy = 0.f;
         if constexpr (NOISE) {  // log psi~(y) - log psi~(x) = dlt + zeta(y)/2 - zeta(x)/2
           zy = noise_half<L>(sw ^ (gl == (int)(site >> 5) ? 1u << (site & 31) : 0u), W, p.noise_sigma, p.noise_k0,
@@ -615,7 +601,7 @@ __device__ __forceinline__ void sweep_chain(const SweepParams &p, const TT *R, c
         }
         const bool acc = 2.f * dlt > thr;
         if (acc) {
-          cache.template accept<SMEM>(up, row, gl);
+          cache.template accept<SMEM>(up, row, gl, tot, p.renorm);
           if (gl == (int)(site >> 5)) sw ^= 1u << (site & 31);
           ++nacc;
           if constexpr (NOISE) zx = zy;
