@@ -555,6 +555,59 @@ __device__ __forceinline__ const TT *stage_table(unsigned char *smem_raw, const 
   return R;
 }
 
+// The N proposals of sweep t of one chain (state sw, cache, accept count nacc, noise zx).
+// TRACE: record accept bits and increments (p.acc_bits / p.delta); the untraced loop
+// carries no bookkeeping.
+template <int L, int E, bool SMEM, typename TT, bool NOISE, bool TRACE>
+__device__ __forceinline__ void sweep_once(const SweepParams &p, const TT *R, const float2 *saK, int t, int64_t cc,
+                                           bool valid, int gl, uint32_t &sw, ChainCache<L, E, TT> &cache,
+                                           int64_t &nacc, float &zx) {
+  const int N = p.N, W = p.W, M_pad = p.M_pad;
+  const uint32_t sweep_id = p.sweep_offset + (uint32_t)t;
+  uint32_t abits = 0u;
+  for (int p0 = 0; p0 < N; p0 += 2 * L) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)(p0 / 2 + gl), sweep_id, (uint32_t)cc, TAG_SWEEP), p.k0, p.k1);
+    const uint32_t site0 = index_from_word(w.x, (uint32_t)N), site1 = index_from_word(w.z, (uint32_t)N);
+    const float thr0 = log_uniform(w.y), thr1 = log_uniform(w.w);
+    const int np = min(2 * L, N - p0);
+    for (int q = 0; q < np; ++q) {
+      const int src = q >> 1;
+      const uint32_t site = __shfl_sync(FULL_MASK, (q & 1) ? site1 : site0, src, L);
+      const float thr = __shfl_sync(FULL_MASK, (q & 1) ? thr1 : thr0, src, L);
+      const uint32_t word = __shfl_sync(FULL_MASK, sw, site >> 5, L);
+      const bool up = (word >> (site & 31)) & 1u;
+      const TT *row = R + (size_t)site * M_pad;
+      const float tot = cache.logsum(up, row, gl);
+      const float2 ak = saK[site];
+      float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + (tot - cache.ls) * LN2F;
+      float zy = 0.f;
+      if constexpr (NOISE) {  // log psi~(y) - log psi~(x) = dlt + zeta(y)/2 - zeta(x)/2
+        zy = noise_half<L>(sw ^ (gl == (int)(site >> 5) ? 1u << (site & 31) : 0u), W, p.noise_sigma, p.noise_k0,
+                           p.noise_k1);
+        dlt += zy - zx;
+      }
+      const bool acc = 2.f * dlt > thr;
+      if (acc) {
+        cache.template accept<SMEM>(up, row, gl, tot, p.renorm);
+        if (gl == (int)(site >> 5)) sw ^= 1u << (site & 31);
+        ++nacc;
+        if constexpr (NOISE) zx = zy;
+      }
+      if constexpr (TRACE) {
+        const int pq = p0 + q;
+        if (p.acc_bits) {
+          abits |= (acc ? 1u : 0u) << (pq & 31);
+          if ((pq & 31) == 31 || pq == N - 1) {
+            if (valid && gl == 0) p.acc_bits[((int64_t)cc * p.n_sweeps + t) * W + (pq >> 5)] = abits;
+            abits = 0u;
+          }
+        }
+        if (p.delta && valid && gl == 0) p.delta[((int64_t)cc * p.n_sweeps + t) * N + pq] = dlt;
+      }
+    }
+  }
+}
+
 // All sweeps of the chain base + (lane / L) for a group of L lanes; chains at or beyond
 // `limit` are idle (they shadow chain limit - 1 and write nothing).  R is the table (shared
 // or global memory), saK the (a_i, K_i) pairs in shared memory.
@@ -573,50 +626,13 @@ __device__ __forceinline__ void sweep_chain(const SweepParams &p, const TT *R, c
   int64_t nacc = 0;
   float zx = 0.f;  // noisy RBM: zeta(x) / 2 of the chain's configuration
   if constexpr (NOISE) zx = noise_half<L>(sw, W, p.noise_sigma, p.noise_k0, p.noise_k1);
+  const bool trace = p.acc_bits != nullptr || p.delta != nullptr;
 
   for (int t = 0; t < p.n_sweeps; ++t) {
-    const uint32_t sweep_id = p.sweep_offset + (uint32_t)t;
-    uint32_t abits = 0u;
-    for (int p0 = 0; p0 < N; p0 += 2 * L) {
-      const uint4 w = philox4x32_10(make_uint4((uint32_t)(p0 / 2 + gl), sweep_id, (uint32_t)cc, TAG_SWEEP),
-                                    p.k0, p.k1);
-      const uint32_t site0 = index_from_word(w.x, (uint32_t)N), site1 = index_from_word(w.z, (uint32_t)N);
-      const float thr0 = log_uniform(w.y), thr1 = log_uniform(w.w);
-      const int np = min(2 * L, N - p0);
-      for (int q = 0; q < np; ++q) {
-        const int src = q >> 1;
-        const uint32_t site = __shfl_sync(FULL_MASK, (q & 1) ? site1 : site0, src, L);
-        const float thr = __shfl_sync(FULL_MASK, (q & 1) ? thr1 : thr0, src, L);
-        const uint32_t word = __shfl_sync(FULL_MASK, sw, site >> 5, L);
-        const bool up = (word >> (site & 31)) & 1u;
-        const TT *row = R + (size_t)site * M_pad;
-        const float tot = cache.logsum(up, row, gl);
-        const float2 ak = saK[site];
-        float dlt = 2.f * (ak.y - (up ? ak.x : -ak.x)) + (tot - cache.ls) * LN2F;
-        float zy = 0.f;
-        if constexpr (NOISE) {  // log psi~(y) - log psi~(x) = dlt + zeta(y)/2 - zeta(x)/2
-          zy = noise_half<L>(sw ^ (gl == (int)(site >> 5) ? 1u << (site & 31) : 0u), W, p.noise_sigma, p.noise_k0,
-                             p.noise_k1);
-          dlt += zy - zx;
-        }
-        const bool acc = 2.f * dlt > thr;
-        if (acc) {
-          cache.template accept<SMEM>(up, row, gl, tot, p.renorm);
-          if (gl == (int)(site >> 5)) sw ^= 1u << (site & 31);
-          ++nacc;
-          if constexpr (NOISE) zx = zy;
-        }
-        const int pq = p0 + q;
-        if (p.acc_bits) {
-          abits |= (acc ? 1u : 0u) << (pq & 31);
-          if ((pq & 31) == 31 || pq == N - 1) {
-            if (valid && gl == 0) p.acc_bits[((int64_t)cc * p.n_sweeps + t) * W + (pq >> 5)] = abits;
-            abits = 0u;
-          }
-        }
-        if (p.delta && valid && gl == 0) p.delta[((int64_t)cc * p.n_sweeps + t) * N + pq] = dlt;
-      }
-    }
+    if (trace)
+      sweep_once<L, E, SMEM, TT, NOISE, true>(p, R, saK, t, cc, valid, gl, sw, cache, nacc, zx);
+    else
+      sweep_once<L, E, SMEM, TT, NOISE, false>(p, R, saK, t, cc, valid, gl, sw, cache, nacc, zx);
     if (t >= p.burn_in) {
       const int64_t row = (int64_t)(t - p.burn_in) * p.C + cc;
       if (p.samples && valid && gl < W) p.samples[row * W + gl] = sw;
