@@ -214,15 +214,21 @@ __device__ __forceinline__ void flip_factors(bool up, const float2 (&lam)[H], co
   }
 }
 
-// sum over 4-pair groups of log2 of the product of the factors g_k = a_k r_k + b_k
+// Factor pairs multiplied together before one MUFU lg2: 16 factors of size e^{+-4|W|} (times
+// the cache's scale drift) stay well inside the FP32 range for the weights the sampler is
+// used with; a product that leaves it sends the group to the exact path (flip_logsum).
+constexpr int PAIRS_PER_LG2 = 8;
+
+// sum over groups of PAIRS_PER_LG2 pairs of log2 of the product of the factors g_k = a_k r_k + b_k
 template <int H>
 __device__ __forceinline__ float product_log2(const float2 (&a)[H], const float2 (&b)[H], const float2 (&r)[H]) {
   float part = 0.f;
 #pragma unroll
-  for (int k0 = 0; k0 < H; k0 += 4) {
+  for (int k0 = 0; k0 < H; k0 += PAIRS_PER_LG2) {
     float2 pr = fma2(a[k0], r[k0], b[k0]);
 #pragma unroll
-    for (int k = k0 + 1; k < (k0 + 4 < H ? k0 + 4 : H); ++k) pr = mul2(pr, fma2(a[k], r[k], b[k]));
+    for (int k = k0 + 1; k < (k0 + PAIRS_PER_LG2 < H ? k0 + PAIRS_PER_LG2 : H); ++k)
+      pr = mul2(pr, fma2(a[k], r[k], b[k]));
     part += lg2_approx(pr.x * pr.y);
   }
   return part;
@@ -278,7 +284,7 @@ __device__ __forceinline__ float flip_logsum(bool up, const float2 (&lam)[Lay<L,
 // Low-precision counterpart of flip_partial: the factors g are formed in 16-bit pair
 // arithmetic from the 16-bit shadows and table (the network's elementwise math in the
 // sampling dtype); their product over hidden units is the reduction of the log-amplitude
-// and is taken in FP32 (App. I: reductions in higher precision), up to 8 units per MUFU lg2.
+// and is taken in FP32 (App. I: reductions in higher precision), PAIRS_PER_LG2 pairs of units per MUFU lg2.
 template <int L, int E, typename TT>
 __device__ __forceinline__ float flip_partial_lp(bool up, const typename Prec<TT>::T2 (&lh)[Lay<L, E>::H],
                                                 const typename Prec<TT>::T2 (&mh)[Lay<L, E>::H], const TT *row,
@@ -290,10 +296,10 @@ __device__ __forceinline__ float flip_partial_lp(bool up, const typename Prec<TT
   auto prod = [&](const typename P::T2(&a)[LY::H], const typename P::T2(&b)[LY::H]) {
     float part = 0.f;
 #pragma unroll
-    for (int k0 = 0; k0 < LY::H; k0 += 4) {
+    for (int k0 = 0; k0 < LY::H; k0 += PAIRS_PER_LG2) {
       float2 pr = P::to_f2(P::fma(a[k0], rv[k0], b[k0]));
 #pragma unroll
-      for (int k = k0 + 1; k < (k0 + 4 < LY::H ? k0 + 4 : LY::H); ++k)
+      for (int k = k0 + 1; k < (k0 + PAIRS_PER_LG2 < LY::H ? k0 + PAIRS_PER_LG2 : LY::H); ++k)
         pr = mul2(pr, P::to_f2(P::fma(a[k], rv[k], b[k])));
       part += lg2_approx(pr.x * pr.y);
     }
