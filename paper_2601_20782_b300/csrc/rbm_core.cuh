@@ -576,10 +576,10 @@ __device__ __forceinline__ void sweep_once(const SweepParams &p, const TT *R, co
     const uint32_t site0 = index_from_word(w.x, (uint32_t)N), site1 = index_from_word(w.z, (uint32_t)N);
     const float thr0 = log_uniform(w.y), thr1 = log_uniform(w.w);
     const int np = min(2 * L, N - p0);
-    for (int q = 0; q < np; ++q) {
-      const int src = q >> 1;
-      const uint32_t site = __shfl_sync(FULL_MASK, (q & 1) ? site1 : site0, src, L);
-      const float thr = __shfl_sync(FULL_MASK, (q & 1) ? thr1 : thr0, src, L);
+    // proposal q = 2k + h of this block: site and log u from lane k's pair h
+    auto step = [&](int q, uint32_t site_src, float thr_src) {
+      const uint32_t site = __shfl_sync(FULL_MASK, site_src, q >> 1, L);
+      const float thr = __shfl_sync(FULL_MASK, thr_src, q >> 1, L);
       const uint32_t word = __shfl_sync(FULL_MASK, sw, site >> 5, L);
       const bool up = (word >> (site & 31)) & 1u;
       const TT *row = R + (size_t)site * M_pad;
@@ -610,6 +610,10 @@ __device__ __forceinline__ void sweep_once(const SweepParams &p, const TT *R, co
         }
         if (p.delta && valid && gl == 0) p.delta[((int64_t)cc * p.n_sweeps + t) * N + pq] = dlt;
       }
+    };
+    for (int q = 0; q < np; q += 2) {
+      step(q, site0, thr0);
+      if (q + 1 < np) step(q + 1, site1, thr1);
     }
   }
 }
