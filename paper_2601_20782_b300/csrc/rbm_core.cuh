@@ -23,9 +23,9 @@ constexpr int threads_for_regs(int regs) {
   return 32 * w;
 }
 // sweep: the cache pairs stay live, the row and the factors are streamed
-constexpr int sweep_threads(int E) { return threads_for_regs(2 * E + 56); }
+constexpr int sweep_threads(int E) { return threads_for_regs(2 * E + 46); }
 // local energy: the cache plus two sites' rows and factors in flight
-constexpr int eloc_threads(int E) { return threads_for_regs(3 * E + 48); }
+constexpr int eloc_threads(int E) { return threads_for_regs(2 * E + 46); }
 constexpr uint32_t WAIT_POLLS = 1u << 22;
 
 
