@@ -457,7 +457,8 @@ __device__ __forceinline__ float log_uniform(uint32_t w) {
 // with lam~/mu~ = e^{2 theta_j} exact and the chain's running log-scale ls = sum_j log2 s_j.
 // A proposal's factors become g~_j = s_j g_j, so sum_j log2 g_j = sum_j log2 g~_j - ls.  An
 // accepted flip multiplies lam~ (spin up) or mu~ (spin down) by R and nothing else: then
-// s_j' = s_j g_j, so the new ls is the sum of log2 g~ the accepted proposal just computed.
+// s_j' = s_j g_j, so for the FP32 copy the new ls is the sum of log2 g~ the accepted proposal
+// just computed; a 16-bit copy recomputes it from the FP32 pairs (see accept).
 // Every `renorm` accepted flips (a bound on the drift chosen from the weights at
 // nqs_set_params) the pairs are normalised again and ls returns to 0.
 template <int L, int E, typename TT>
@@ -492,6 +493,31 @@ struct ChainCache {
   __device__ __forceinline__ float logsum(bool up, const TT *row, int gl) const {
     if constexpr (LP) return flip_logsum_lp<L, E, TT>(up, lh, mh, row, gl);
     else return flip_logsum<L, E>(up, lam, mu, row, gl);
+  }
+  // ls recomputed from the FP32 pairs: sum_j log2 (lam~_j + mu~_j) over the group, with the
+  // grouped products and fixed-point reduction of the proposals (exact logs as fallback)
+  __device__ __forceinline__ float scale_log2() const {
+    const float2 one = make_float2(1.f, 1.f);
+    float part = 0.f;
+#pragma unroll
+    for (int k0 = 0; k0 < LY::H; k0 += PAIRS_PER_LG2) {
+      float2 pr = fma2(lam[k0], one, mu[k0]);
+#pragma unroll
+      for (int k = k0 + 1; k < (k0 + PAIRS_PER_LG2 < LY::H ? k0 + PAIRS_PER_LG2 : LY::H); ++k)
+        pr = mul2(pr, fma2(lam[k], one, mu[k]));
+      part += lg2_approx(pr.x * pr.y);
+    }
+    if constexpr (L == 32) {
+      if (!__any_sync(FULL_MASK, !(fabsf(part) < 1024.f)))
+        return (float)__reduce_add_sync(FULL_MASK, __float2int_rn(part * 1048576.f)) * 9.5367431640625e-7f;
+    } else {
+      const float tot = group_allsum<L>(part);
+      if (!__any_sync(FULL_MASK, !isfinite(tot))) return tot;
+    }
+    float p2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < LY::H; ++k) p2 += log2f(lam[k].x + mu[k].x) + log2f(lam[k].y + mu[k].y);
+    return group_allsum<L>(p2);
   }
   __device__ __forceinline__ void normalize() {
 #pragma unroll
@@ -535,8 +561,15 @@ struct ChainCache {
         for (int k = 0; k < LY::H; ++k) mu[k] = mul2(mu[k], rv[k]);
       }
     }
-    ls = tot;
-    if (++since >= renorm) normalize();
+    if (++since >= renorm) {
+      normalize();
+    } else if constexpr (LP) {
+      // a 16-bit copy's tot carries its factor rounding; taking it as the scale would carry that
+      // error into every later proposal until the next normalisation, so the scale is recomputed
+      ls = scale_log2();
+    } else {
+      ls = tot;  // FP32: the accepted proposal's sum is the new scale (to ~1e-7)
+    }
   }
   __device__ __forceinline__ float logpsi(uint32_t sw, const float2 *aK, int N, int gl) const {
     return cache_logpsi<L, E>(lam, mu, sw, aK, N, gl) + ls * LN2F;  // log cosh theta_j gains log s_j
