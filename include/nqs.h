@@ -71,7 +71,8 @@ typedef struct {
   int32_t marshall;
 } nqs_ham_desc;
 
-/* Ansatz.  RBM (App. G): n_hidden = M; sampling copy F32, BF16 or F16; TFIM only.
+/* Ansatz.  RBM (App. G): n_hidden = M (1 .. 1024); N <= 256 sites; sampling copy F32,
+ * BF16 or F16; TFIM only.
  * DENSE: n_layers (2..8) hidden widths in widths[] (host array, copied; multiples of
  * 16), a_1 = log cosh(W1 s + b1), a_l = tanh(W_l a_{l-1} + b_l), log psi = w_out . a_L
  * + b_out; sampling copy BF16 (layers >= 2 on the tensor cores, FP32 accumulation);
@@ -171,7 +172,7 @@ nqs_status nqs_local_energy(nqs_ctx *ctx, const uint32_t *configs, int64_t n, fl
 /* App. I, Eq. forces.  O [n x P] (FP32, or NULL) receives O_k(x) = d log psi(x)/d theta_k.
  * If force != NULL (FP64 [P]) it receives F_k = (1/n) sum_x O_k(x) (eloc[x] - E)
  * with E = stats[0] (device, as written by nqs_stats); eloc and stats are then
- * required.  workspace: device scratch of nqs_logpsi_grad_workspace(ctx, n) bytes
+ * required when n > 0 (for n = 0 the force is set to zero).  workspace: device scratch of nqs_logpsi_grad_workspace(ctx, n) bytes
  * (may be NULL when force == NULL).  Gradients use the FP32 rounding of the
  * master parameters, not the sampling copy. */
 size_t nqs_logpsi_grad_workspace(const nqs_ctx *ctx, int64_t n);

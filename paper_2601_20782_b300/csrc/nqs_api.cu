@@ -325,7 +325,7 @@ nqs_status nqs_logpsi_grad(nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O,
   if (!c) return NQS_EINVAL;
   if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_logpsi_grad: parameters not set");
   if (n < 0 || (n > 0 && bad_ptr(cfg))) return fail(c, NQS_EINVAL, "nqs_logpsi_grad: bad arguments");
-  if (force && (bad_ptr(eloc) || bad_ptr(stats)))
+  if (force && n > 0 && (bad_ptr(eloc) || bad_ptr(stats)))
     return fail(c, NQS_EINVAL, "nqs_logpsi_grad: the force needs eloc and stats");
   if (force && n > 0 && c->model_kind == NQS_RBM && (bad_ptr(ws) || ws_bytes < nqs::rbm_grad_workspace(c, n)))
     return fail(c, NQS_EINVAL, "nqs_logpsi_grad: workspace too small");
