@@ -218,7 +218,9 @@ nqs_status nqs_selftest_tc_gemm(const uint16_t *A, const uint16_t *B, float *D, 
  * nqs_local_energy up to FP32 rounding: the RBM kernel walks each chain's samples in order
  * and updates its theta = W s + b only for the spins that changed since the chain's previous
  * sample (rebuilt from scratch every NQS_OPT_REFRESH samples), instead of rebuilding it for
- * every sample.  Dense contexts evaluate it as nqs_local_energy. */
+ * every sample.  With fewer than 16 chains per SM it evaluates the samples as
+ * nqs_local_energy does (one group per chain would leave the GPU idle).  Dense contexts
+ * evaluate it as nqs_local_energy. */
 nqs_status nqs_local_energy_chains(nqs_ctx *ctx, const uint32_t *samples, int64_t n_chains, int64_t per_chain,
                                    float *eloc, nqs_stream stream);
 

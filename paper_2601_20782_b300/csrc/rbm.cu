@@ -507,6 +507,9 @@ cudaError_t rbm_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n, f
 // Chain-ordered local energy of sweep-major samples (row k * n_chains + c), FP32 copy.
 cudaError_t rbm_local_energy_chains(const nqs_ctx *c, const uint32_t *cfg, int64_t n_chains, int64_t per_chain,
                                     float *eloc, cudaStream_t s) {
+  // one group per chain walks its samples in order: with fewer than 16 chains per SM that
+  // leaves the GPU mostly idle, and the per-sample kernel (same values to FP32 rounding) is used
+  if (n_chains < (int64_t)c->num_sms * 16) return rbm_local_energy(c, cfg, n_chains * per_chain, eloc, s);
   ElocParams p = eloc_params(c, cfg, nullptr, n_chains * per_chain, eloc);
   p.R = c->d_R32;
   p.aK = c->d_aK32;

@@ -255,7 +255,7 @@ def test_local_energy_chains_matches_per_sample(Lx, Ly, M, dtype):
     N = Lx * Ly
     ctx = p.Context("tfim", Lx, Ly, J1=1.0, h=2.0, model="rbm", n_hidden=M, dtype=dtype)
     ctx.set_params(torch.from_numpy(rbm_params(N, M, 0.1, 3)).cuda())
-    C, K = 300, 45
+    C, K = 2500, 45                      # >= 16 chains per SM: the chain-ordered kernel runs
     state = torch.zeros((C, ctx.W), dtype=torch.int32, device="cuda")
     ctx.init_chains(state, 4)
     samples = torch.zeros((K * C, ctx.W), dtype=torch.int32, device="cuda")
