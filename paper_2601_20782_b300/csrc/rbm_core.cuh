@@ -489,6 +489,16 @@ struct ChainCache {
     ls = 0.f;
     since = 0;
   }
+  // this lane's share of sum_j log2 g~_j (grouped products; may be non-finite for a product
+  // that leaves the FP32 range) and its exact counterpart
+  __device__ __forceinline__ float partial(bool up, const TT *row, int gl) const {
+    if constexpr (LP) return flip_partial_lp<L, E, TT>(up, lh, mh, row, gl);
+    else return flip_partial<L, E>(up, lam, mu, row, gl);
+  }
+  __device__ __forceinline__ float partial_exact(bool up, const TT *row, int gl) const {
+    if constexpr (LP) return flip_partial_lp_exact<L, E, TT>(up, lh, mh, row, gl);
+    else return flip_partial_exact<L, E>(up, lam, mu, row, gl);
+  }
   // sum_j log2 g~_j of flipping the site whose table row is `row` (subtract ls for sum log2 g)
   __device__ __forceinline__ float logsum(bool up, const TT *row, int gl) const {
     if constexpr (LP) return flip_logsum_lp<L, E, TT>(up, lh, mh, row, gl);
@@ -725,7 +735,13 @@ struct ElocParams {
 };
 
 // eps(x) of the TFIM from the configuration's cache (Eq. TFIM, App. I Eq. local_energies):
-// J sum_<ij> s_i s_j + h sum_i exp(log psi(flip_i x) - log psi(x)), two sites per iteration.
+// J sum_<ij> s_i s_j + h sum_i exp(log psi(flip_i x) - log psi(x)).
+//
+// With 32 lanes per configuration the N flips go in blocks of 8: each lane forms its partial
+// sum of log2 g for the 8 flips, a recursive-halving exchange (lane bits 4, 3, 2, then 1 and
+// 0) leaves lane l with the full sum of flip 4 b4 + 2 b3 + b2 of the block, and lanes with
+// b1 = b0 = 0 add that flip's exp.  A block whose sums are not all finite is recomputed flip by
+// flip on the exact path.  Narrower groups evaluate two flips per iteration with a group sum.
 template <int L, int E, typename TT>
 __device__ __forceinline__ float tfim_eloc_value(const ChainCache<L, E, TT> &cache, uint32_t sw, const ElocParams &p,
                                                  const TT *R, const float2 *saK, int gl) {
@@ -741,16 +757,61 @@ __device__ __forceinline__ float tfim_eloc_value(const ChainCache<L, E, TT> &cac
   }
   d = p.J * group_allsum<L>(d);
   float off = 0.f;
-  for (int i = 0; i < N; i += 2) {
-    const int i1 = min(i + 1, N - 1);
-    const uint32_t word0 = __shfl_sync(FULL_MASK, sw, i >> 5, L);
-    const uint32_t word1 = __shfl_sync(FULL_MASK, sw, i1 >> 5, L);
-    const bool up0 = (word0 >> (i & 31)) & 1u, up1 = (word1 >> (i1 & 31)) & 1u;
-    const float tot0 = cache.logsum(up0, R + (size_t)i * M_pad, gl);
-    const float tot1 = cache.logsum(up1, R + (size_t)i1 * M_pad, gl);
-    const float2 ak0 = saK[i], ak1 = saK[i1];
-    off += expf(2.f * (ak0.y - (up0 ? ak0.x : -ak0.x)) + tot0 * LN2F);
-    if (i + 1 < N) off += expf(2.f * (ak1.y - (up1 ? ak1.x : -ak1.x)) + tot1 * LN2F);
+  if constexpr (L == 32) {
+    constexpr int FB = 8;  // flips per block (8 sites of one word: blocks start at multiples of 8)
+    for (int i0 = 0; i0 < N; i0 += FB) {
+      const uint32_t word = __shfl_sync(FULL_MASK, sw, i0 >> 5, L);
+      float v[FB];
+#pragma unroll
+      for (int u = 0; u < FB; ++u) {
+        const int i = min(i0 + u, N - 1);  // a clamped tail site stays in this word; its term is dropped
+        v[u] = cache.partial((word >> (i & 31)) & 1u, R + (size_t)i * M_pad, gl);
+      }
+      // recursive halving: after the steps on lane bits 4, 3, 2 lane l holds the sum over the 8
+      // lanes sharing its low two bits for flip u = 4 b4 + 2 b3 + b2; bits 1 and 0 finish it
+#pragma unroll
+      for (int h = 0; h < 3; ++h) {
+        const int half = FB >> (h + 1);            // 4, 2, 1 values kept
+        const bool hi = (gl >> (4 - h)) & 1;       // lane bits 4, 3, 2
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+          const float keep = hi ? v[q + half] : v[q];
+          const float send = hi ? v[q] : v[q + half];
+          v[q] = keep + __shfl_xor_sync(FULL_MASK, send, 16 >> h);
+        }
+      }
+      float t = v[0];
+      t += __shfl_xor_sync(FULL_MASK, t, 2);
+      t += __shfl_xor_sync(FULL_MASK, t, 1);
+      const int u = ((gl >> 4) & 1) * 4 + ((gl >> 3) & 1) * 2 + ((gl >> 2) & 1);
+      const int i = i0 + u;
+      if (__any_sync(FULL_MASK, !isfinite(t))) {  // exact path for the block
+        for (int w = 0; w < FB && i0 + w < N; ++w) {
+          const int ii = i0 + w;
+          const bool up = (word >> (ii & 31)) & 1u;
+          const float tot = group_allsum<L>(cache.partial_exact(up, R + (size_t)ii * M_pad, gl));
+          const float2 ak = saK[ii];
+          if (gl == 0) off += expf(2.f * (ak.y - (up ? ak.x : -ak.x)) + (tot - cache.ls) * LN2F);
+        }
+      } else if ((gl & 3) == 0 && i < N) {
+        const bool up = (word >> (i & 31)) & 1u;
+        const float2 ak = saK[i];
+        off += expf(2.f * (ak.y - (up ? ak.x : -ak.x)) + (t - cache.ls) * LN2F);
+      }
+    }
+    off = group_allsum<L>(off);
+  } else {
+    for (int i = 0; i < N; i += 2) {
+      const int i1 = min(i + 1, N - 1);
+      const uint32_t word0 = __shfl_sync(FULL_MASK, sw, i >> 5, L);
+      const uint32_t word1 = __shfl_sync(FULL_MASK, sw, i1 >> 5, L);
+      const bool up0 = (word0 >> (i & 31)) & 1u, up1 = (word1 >> (i1 & 31)) & 1u;
+      const float tot0 = cache.logsum(up0, R + (size_t)i * M_pad, gl);
+      const float tot1 = cache.logsum(up1, R + (size_t)i1 * M_pad, gl);
+      const float2 ak0 = saK[i], ak1 = saK[i1];
+      off += expf(2.f * (ak0.y - (up0 ? ak0.x : -ak0.x)) + tot0 * LN2F);
+      if (i + 1 < N) off += expf(2.f * (ak1.y - (up1 ? ak1.x : -ak1.x)) + tot1 * LN2F);
+    }
   }
   return d + p.h * off;
 }
