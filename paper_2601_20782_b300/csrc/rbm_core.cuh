@@ -201,19 +201,6 @@ __device__ __forceinline__ float cache_logpsi(const float2 (&lam)[Lay<L, E>::H],
   return visible_term<L>(sw, aK, N, gl) - 0.5f * LN2F * group_allsum<L>(part);
 }
 
-// g for a flip of a site with spin `up`: mu + lam R (up) or lam + mu R (down)
-template <int H>
-__device__ __forceinline__ void flip_factors(bool up, const float2 (&lam)[H], const float2 (&mu)[H],
-                                             const float2 (&rv)[H], float2 (&g)[H]) {
-  if (up) {
-#pragma unroll
-    for (int k = 0; k < H; ++k) g[k] = fma2(lam[k], rv[k], mu[k]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < H; ++k) g[k] = fma2(mu[k], rv[k], lam[k]);
-  }
-}
-
 // Factor pairs multiplied together before one MUFU lg2: 16 factors of size e^{+-4|W|} (times
 // the cache's scale drift) stay well inside the FP32 range for the weights the sampler is
 // used with; a product that leaves it sends the group to the exact path (flip_logsum).
@@ -263,7 +250,12 @@ __device__ __forceinline__ float flip_partial_exact(bool up, const float2 (&lam)
   return p;
 }
 
-// Group sum of the lane partials; see sum_log2 for the reduction and its exact fallback.
+// Group sum of the lane partials.  With one chain per warp the partials are added exactly
+// as 2^-20 fixed-point integers by one redux.sync (a 32-lane sum in one instruction, and the
+// same bits in every lane, so the accept decision is warp-uniform); each partial is rounded
+// to 2^-21, so the sum carries at most 32 * 2^-21 absolute error in log2 units.  A product
+// that left the normal FP32 range, or a partial beyond +-2^10, sends the group to the exact
+// path: one accurate log per factor and a floating-point butterfly.
 template <int L, int E>
 __device__ __forceinline__ float flip_logsum(bool up, const float2 (&lam)[Lay<L, E>::H],
                                             const float2 (&mu)[Lay<L, E>::H], const float *row, int gl) {
@@ -341,39 +333,6 @@ __device__ __forceinline__ float flip_logsum_lp(bool up, const typename Prec<TT>
     if (!__any_sync(FULL_MASK, !isfinite(tot))) return tot;
   }
   return group_allsum<L>(flip_partial_lp_exact<L, E, TT>(up, lh, mh, row, gl));
-}
-
-// sum_j log2 g_j over the group: products of up to 8 factors (4 pairs) per MUFU lg2.
-// With one chain per warp the lane partials are added exactly as 2^-20 fixed-point
-// integers by one redux.sync (a 32-lane sum in one instruction instead of a 5-stage
-// shuffle tree); each partial is rounded to 2^-21, so the sum carries at most
-// 32 * 2^-21 absolute error in log2 units.  A product that leaves the normal FP32
-// range, or a partial beyond +-2^10, sends the group to the exact path: one accurate
-// log per factor and a floating-point butterfly.
-template <int L, int H>
-__device__ __forceinline__ float sum_log2(const float2 (&g)[H]) {
-  float part = 0.f;
-#pragma unroll
-  for (int k0 = 0; k0 < H; k0 += 4) {
-    float2 pr = g[k0];
-#pragma unroll
-    for (int k = k0 + 1; k < (k0 + 4 < H ? k0 + 4 : H); ++k) pr = mul2(pr, g[k]);
-    part += lg2_approx(pr.x * pr.y);
-  }
-  if constexpr (L == 32) {
-    const bool bad = !(fabsf(part) < 1024.f);  // also catches inf / nan
-    if (!__any_sync(FULL_MASK, bad)) {
-      const int q = __float2int_rn(part * 1048576.f);
-      return (float)__reduce_add_sync(FULL_MASK, q) * 9.5367431640625e-7f;
-    }
-  } else {
-    const float tot = group_allsum<L>(part);
-    if (!__any_sync(FULL_MASK, !isfinite(tot))) return tot;
-  }
-  float p2 = 0.f;
-#pragma unroll
-  for (int k = 0; k < H; ++k) p2 += log2f(g[k].x) + log2f(g[k].y);
-  return group_allsum<L>(p2);
 }
 
 // Loads the [N][M_pad] table into shared memory with 1D bulk copies.  Returns false
