@@ -272,18 +272,21 @@ struct ProposeArgs {
 };
 
 template <int NJ>  // column block of 64 * NJ units held in registers, two per lane per j
-__global__ void __launch_bounds__(256) dense_propose_kernel(const ProposeArgs a) {
+__global__ void __launch_bounds__(256, 4) dense_propose_kernel(const ProposeArgs a) {
   const int lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = gw; c < a.C; c += nw) {
+    // ---- every load that does not depend on the decision is issued first
     uint32_t word = lane < a.W ? a.state[c * a.W + lane] : 0u;
-    // this step's proposal: independent of memory, drawn first
+    const float lp0 = a.lp[c];
+    const int mp = a.decide ? a.prop[c] : -1;
+    const float thr_old = a.decide ? a.thr[c] : 0.f;
     int m = 0;
     float thr_new = 0.f;
     int2 nb = make_int2(0, -1);
-    if (a.propose) {
+    if (a.propose) {  // this step's proposal: Philox, then its bond
       const uint4 w = philox4x32_10(make_uint4((uint32_t)(a.p / 2), a.sweep_id, (uint32_t)c, TAG_SWEEP), a.k0, a.k1);
       const uint32_t wm = (a.p & 1) ? w.z : w.x, wu = (a.p & 1) ? w.w : w.y;
       m = (int)index_from_word(wm, (uint32_t)a.n_moves);
@@ -291,31 +294,31 @@ __global__ void __launch_bounds__(256) dense_propose_kernel(const ProposeArgs a)
       thr_new = k == 0u ? -INFINITY : logf((float)k * 5.9604644775390625e-8f);
       nb = a.exchange ? a.bonds[m] : make_int2(m, -1);
     }
-    // decision of the previous proposal
-    int2 pb = make_int2(0, -1);
+    // the previous proposal's bond, fetched before knowing whether it was accepted
+    const int2 pbc = mp >= 0 ? (a.exchange ? a.bonds[mp] : make_int2(mp, -1)) : make_int2(0, -1);
+    float part = 0.f;
+    if (mp >= 0)
+      for (int q = lane; q < 2 * a.n_ranges; q += 32) part += a.part[c * 2 * a.n_ranges + q];
+    // ---- decision of the previous proposal
     bool pending = false;
-    float lp_c = a.lp[c];
+    float lp_c = lp0;
     if (a.decide) {
-      const int mp = a.prop[c];
       bool acc = true;
       float dlt = 0.f;
       if (mp >= 0) {
-        float part = 0.f;
-        for (int q = lane; q < 2 * a.n_ranges; q += 32) part += a.part[c * 2 * a.n_ranges + q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(full, part, o);
         const float lpn = a.b_out[0] + part;
-        dlt = lpn - lp_c;
-        acc = 2.f * dlt > a.thr[c];
+        dlt = lpn - lp0;
+        acc = 2.f * dlt > thr_old;
         if (acc) {
           lp_c = lpn;
           pending = true;
-          pb = a.exchange ? a.bonds[mp] : make_int2(mp, -1);
         }
       }
       __syncwarp();  // every lane has read prop/thr/lp of chain c
       if (lane == 0) {
-        if (acc && mp >= 0) a.lp[c] = lp_c;
+        if (pending) a.lp[c] = lp_c;
         if (a.n_acc) a.n_acc[c] = (a.first ? 0 : a.n_acc[c]) + (acc ? 1 : 0);
         if (a.acc_bits) {
           const int64_t wi = ((int64_t)c * a.n_sweeps + a.t_prev) * a.W + (a.p_prev >> 5);
@@ -325,6 +328,7 @@ __global__ void __launch_bounds__(256) dense_propose_kernel(const ProposeArgs a)
         if (a.delta) a.delta[((int64_t)c * a.n_sweeps + a.t_prev) * a.N + a.p_prev] = dlt;
       }
     }
+    const int2 pb = pending ? pbc : make_int2(0, -1);
     float gp = 0.f;  // pending move: z0 += gp (W_i - W_j)
     if (pending) {
       gp = ((__shfl_sync(full, word, pb.x >> 5) >> (pb.x & 31)) & 1u) ? -2.f : 2.f;
@@ -355,47 +359,46 @@ __global__ void __launch_bounds__(256) dense_propose_kernel(const ProposeArgs a)
     const float *pi = a.W1t + (int64_t)pb.x * a.H0, *pj = a.W1t + (int64_t)(pb.y < 0 ? 0 : pb.y) * a.H0;
     const float *ni = a.W1t + (int64_t)nb.x * a.H0, *nj = a.W1t + (int64_t)(nb.y < 0 ? 0 : nb.y) * a.H0;
     __nv_bfloat16 *out = a.act + c * a.Kp1;
+    const bool use_new = a.propose && moved;
     for (int kb = 0; kb < a.H0; kb += 64 * NJ) {
-      float2 z[NJ];
+      // all loads of the block (z row, the two moves' weight differences) before any store
+      float2 z[NJ], dp[NJ], dn[NJ];
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
         const int k = kb + 64 * j + 2 * lane;
-        z[j] = k < a.H0 ? *reinterpret_cast<const float2 *>(zr + k) : make_float2(0.f, 0.f);
-      }
-      if (pending) {
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-          const int k = kb + 64 * j + 2 * lane;
-          if (k < a.H0) {
-            float2 d = *reinterpret_cast<const float2 *>(pi + k);
-            if (pb.y >= 0) {
-              const float2 dj = *reinterpret_cast<const float2 *>(pj + k);
-              d.x -= dj.x;
-              d.y -= dj.y;
-            }
-            z[j].x = fmaf(gp, d.x, z[j].x);
-            z[j].y = fmaf(gp, d.y, z[j].y);
-            *reinterpret_cast<float2 *>(zr + k) = z[j];
+        const bool in = k < a.H0;
+        z[j] = in ? *reinterpret_cast<const float2 *>(zr + k) : make_float2(0.f, 0.f);
+        dp[j] = make_float2(0.f, 0.f);
+        dn[j] = make_float2(0.f, 0.f);
+        if (pending && in) {
+          dp[j] = *reinterpret_cast<const float2 *>(pi + k);
+          if (pb.y >= 0) {
+            const float2 t = *reinterpret_cast<const float2 *>(pj + k);
+            dp[j].x -= t.x;
+            dp[j].y -= t.y;
+          }
+        }
+        if (use_new && in) {
+          dn[j] = *reinterpret_cast<const float2 *>(ni + k);
+          if (nb.y >= 0) {
+            const float2 t = *reinterpret_cast<const float2 *>(nj + k);
+            dn[j].x -= t.x;
+            dn[j].y -= t.y;
           }
         }
       }
-      if (a.propose) {
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-          const int k = kb + 64 * j + 2 * lane;
-          if (k < a.H0) {
-            float2 v = z[j];
-            if (moved) {
-              float2 d = *reinterpret_cast<const float2 *>(ni + k);
-              if (nb.y >= 0) {
-                const float2 dj = *reinterpret_cast<const float2 *>(nj + k);
-                d.x -= dj.x;
-                d.y -= dj.y;
-              }
-              v.x = fmaf(gn, d.x, v.x);
-              v.y = fmaf(gn, d.y, v.y);
-            }
-            *reinterpret_cast<__nv_bfloat162 *>(out + k) = __floats2bfloat162_rn(log_cosh_fast(v.x), log_cosh_fast(v.y));
+      for (int j = 0; j < NJ; ++j) {
+        const int k = kb + 64 * j + 2 * lane;
+        if (k < a.H0) {
+          if (pending) {
+            z[j].x = fmaf(gp, dp[j].x, z[j].x);
+            z[j].y = fmaf(gp, dp[j].y, z[j].y);
+            *reinterpret_cast<float2 *>(zr + k) = z[j];
+          }
+          if (a.propose) {
+            const float vx = fmaf(gn, dn[j].x, z[j].x), vy = fmaf(gn, dn[j].y, z[j].y);
+            *reinterpret_cast<__nv_bfloat162 *>(out + k) = __floats2bfloat162_rn(log_cosh_fast(vx), log_cosh_fast(vy));
           }
         }
       }
