@@ -141,7 +141,9 @@ class Step:
         self.ws = torch.zeros(self.ctx.logpsi_grad_workspace(self.S), dtype=torch.uint8, device=dev)
         self.out_h = torch.zeros(5 + P, dtype=torch.float64).pin_memory()
         self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-        self.launches = 2 + 1 + 1 + 1 + 2 + 2 + 1   # set_params, init, sweep, eloc, stats, force, O rows
+        # set_params (prepare, colsum, bounds; a 16-bit copy adds the FP32 copy's prepare and colsum),
+        # init, sweep, local energy, stats (2), force (tensor-core kernel + reduction), O rows
+        self.launches = (3 if dtype == "f32" else 5) + 1 + 1 + 1 + 2 + 2 + 1
 
     def run(self, seed, host_io=False):
         c, ev = self.ctx, self.ev
@@ -360,7 +362,7 @@ class RbmStep:
         self.ws = z(self.ctx.logpsi_grad_workspace(self.S), dt=torch.uint8)
         self.out_h = torch.zeros(5 + P, dtype=torch.float64).pin_memory()
         self.ph = _Phased(torch, ["set_params+init", "sweep", "local_energy", "stats+force", "O_rows"])
-        self.launches = 10
+        self.launches = (3 if dtype == "f32" else 5) + 1 + 1 + 1 + 2 + 2 + 1   # as Step
         self.h2d, self.d2h = P * 8, (5 + P) * 8
 
     def run(self, seed, host_io=False):
