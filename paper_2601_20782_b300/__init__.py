@@ -316,6 +316,42 @@ class Batch:
                 "tuned": [(i.tuned_variant[q], i.tuned_warps[q], i.tuned_ms[q]) for q in range(i.n_tuned)]}
 
 
+class LogPsi(torch.autograd.Function):
+    """log psi(configs; params) as a differentiable function of the FP64 parameter vector.
+
+    forward: nqs_set_params(params), then nqs_logpsi(configs) -> FP32 [n].
+    backward: d/dparams of sum_x g_x log psi(x) = sum_x g_x O(x), the hand-written backward
+    (App. I, Eq. forces) in the library's force kernel: with eloc = g and E = 0 the force is
+    (1/n) sum_x O(x) g_x, scaled here by n.  No O rows are materialised.  The derivative is
+    that of the FP32 rounding of the master parameters; the forward of a 16-bit context is its
+    sampling copy's log psi.
+
+    Use: LogPsi.apply(ctx, params, configs) with params a CUDA float64 tensor [P] that
+    requires grad, configs packed [n, W]."""
+
+    @staticmethod
+    def forward(fctx, nctx, params, configs):
+        n = configs.shape[0]
+        nctx.set_params(params.detach().contiguous())
+        out = torch.empty(n, dtype=torch.float32, device=configs.device)
+        nctx.logpsi(configs, out)
+        fctx.nctx = nctx
+        fctx.save_for_backward(configs)
+        return out
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        (configs,) = fctx.saved_tensors
+        nctx = fctx.nctx
+        n = configs.shape[0]
+        g = grad_out.detach().to(torch.float32).contiguous()
+        stats = torch.zeros(5, dtype=torch.float64, device=configs.device)   # E = 0
+        force = torch.empty(nctx.P, dtype=torch.float64, device=configs.device)
+        ws = torch.empty(max(nctx.logpsi_grad_workspace(n), 1), dtype=torch.uint8, device=configs.device)
+        nctx.logpsi_grad(configs, None, g, stats, force, ws)
+        return None, force.mul_(float(n)), None
+
+
 def selftest_tc_gemm(A, B, a_transposed=False, b_transposed=False):
     """D = A B^T on the tensor cores (tcgen05).  A [128 x K] (or [K x 128] when a_transposed),
     B [N x K] (or [K x N] when b_transposed), BF16 CUDA tensors."""
