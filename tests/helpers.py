@@ -10,8 +10,14 @@ if ROOT not in sys.path:
 
 
 def ensure_built():
-    from paper_2601_20782_b300 import build as b
-    return b.build()
+    """Builds libnqs.so if needed; build.py is loaded by path, since importing the package
+    needs the library."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_nqs_build", os.path.join(ROOT, "paper_2601_20782_b300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()
 
 
 def nqs():
