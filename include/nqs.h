@@ -290,9 +290,8 @@ typedef struct {
 /* Builds the work list for n_sweeps sweeps (burn_in of them not kept) per call.  One CTA
  * per SM; each warp runs one chain of the CTA's current item.  warps_per_cta > 0 fixes the
  * CTA width (F16: the register-capped kernel variant); 0 runs the autotuner: for every
- * kernel variant (F16: registers capped at 128 with up to 16 warps, capped at 80 with up
- * to 24 warps, or the widest case's registers with up to 8 warps; F32: one) and candidate
- * width (4 .. 24 warps, within the
+ * kernel variant (F16: registers capped at 128 with up to 16 warps, or the widest case's
+ * registers with up to 8 warps; F32: one) and candidate width (4 .. 24 warps, within the
  * variant's register limit) it times one sweep of every instance on scratch copies of the
  * chains with CUDA events on `stream`, and keeps the fastest (synchronises the stream; the
  * chains are not changed).  Allocates the work list and descriptors; the states must be
@@ -314,7 +313,7 @@ nqs_status nqs_batch_step(nqs_batch *b, uint32_t sweep_offset, nqs_stream stream
 
 typedef struct {
   int32_t warps_per_cta, max_warps_per_cta, ctas;
-  int32_t variant;         /* 0: F32; F16 with registers capped at 128 (1), at 80 (3), or the widest case's (2) */
+  int32_t variant;         /* 0: F32; F16 with registers capped at 128 (1) or the widest case's (2) */
   int32_t n_work_items;
   int32_t n_staged;        /* instances whose table is staged in shared memory */
   int64_t stage_bytes;     /* dynamic shared memory per CTA */

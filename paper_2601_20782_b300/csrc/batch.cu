@@ -34,7 +34,7 @@ struct nqs_batch {
   int warps = 0;       // warps (chains) per CTA
   int variant = 0;     // kernel variant (kernel_for)
   int max_warps = 0;   // register limit of the chosen variant
-  int max_warps_v[4] = {0, 0, 0, 0};
+  int max_warps_v[3] = {0, 0, 0};
   int n_staged = 0;
   uint32_t table_cap = 0, ak_cap = 0;
   std::vector<nqs::BatchInst> inst_h;
@@ -64,15 +64,13 @@ nqs_status bcuda(nqs_batch *b, cudaError_t e, const char *where) {
   return NQS_ECUDA;
 }
 
-// variant 0: FP32; FP16 with registers capped at 128 (1), at 80 (3), or those of the widest case (2)
+// variant 0: FP32; FP16 with registers capped at 128 (1) or those of the widest case (2)
 const void *kernel_for(int variant) {
   switch (variant) {
     case 1:
       return nqs::batchk::batch_kernel_f16_capped();
     case 2:
       return nqs::batchk::batch_kernel_f16_wide();
-    case 3:
-      return nqs::batchk::batch_kernel_f16_narrow();
     default:
       return nqs::batchk::batch_kernel_f32();
   }
@@ -218,7 +216,7 @@ nqs_status nqs_batch_create(nqs_batch **out, const nqs_batch_item *items, int32_
     nqs_batch_destroy(b);
     return NQS_ECUDA;
   }
-  const std::vector<int> variants = b->dtype == NQS_F16 ? std::vector<int>{1, 2, 3} : std::vector<int>{0};
+  const std::vector<int> variants = b->dtype == NQS_F16 ? std::vector<int>{1, 2} : std::vector<int>{0};
   for (int v : variants) {  // CTA width limit of each variant from its register use
     cudaFuncAttributes fa;
     if ((e = cudaFuncSetAttribute(kernel_for(v), cudaFuncAttributeMaxDynamicSharedMemorySize, shm)) != cudaSuccess ||

@@ -112,9 +112,7 @@ __global__ void __launch_bounds__(MAXT > 0 ? MAXT : 256, 1) rbm_batch_sweep_kern
 const void *batch_kernel_f32();
 const void *batch_kernel_f16_capped();
 const void *batch_kernel_f16_wide();
-const void *batch_kernel_f16_narrow();
 constexpr int BATCH_CAPPED_THREADS = 512;  // registers <= 128
-constexpr int BATCH_NARROW_THREADS = 768;  // registers <= 80
 
 }  // namespace batchk
 }  // namespace nqs
