@@ -1,18 +1,35 @@
 // Force of the RBM (App. I, Eq. forces) on the tensor cores:
 //     F_k = (1/n) sum_x O_k(x) (eloc(x) - E),  O_a = s, O_b = tanh(theta), O_W[j, i] = tanh(theta_j) s_i.
 //
-// Block (jt, chunk) owns hidden units j0 = 128 jt .. j0 + 127 and one chunk of rows; per
-// tile of 128 rows (samples x) it runs two tcgen05 products with FP32 accumulation in TMEM:
-//   GEMM1  theta[x, j] = sum_i s[x, i] W[j, i]             A1 = spins (exact in BF16),
-//                                                          B1 = W as three BF16 terms (hi + mid + lo)
-//   GEMM2  G[j, i]    += sum_x a[x, j] s[x, i]             a = tanh(theta + b) (eloc - E), three BF16 terms
-// Column i = N of the spin tile is a constant +1 (its W column is zero), so G[j, N] = sum_x a[x, j]
-// gives the b-entries; the extra hidden row j = M carries a = eloc - E, so G[M, i] gives the a-entries.
-// The spin tile serves as the K-major A of GEMM1 and, read MN-major, as the B of GEMM2.
-// The hi term of a accumulates in one TMEM accumulator and the mid + lo terms in a second one,
-// so that the small terms are not rounded away against the large running sum.  Every DRAIN
-// tiles both are added into the block's FP64 slice of the workspace (rows chunk * P ...),
-// which force_reduce_kernel then sums over chunks in a fixed order.
+// Block (jt, chunk) owns hidden units j0 = 64 jt .. j0 + 63 and one chunk of rows; per tile
+// of 128 rows (samples x) it runs two tcgen05 products with FP32 accumulation in TMEM:
+//   GEMM1  theta_s[x, j] = sum_i s[x, i] W_s[j, i]      M = 128 rows, N = 3 x 64, K = 128 sites
+//          A = spins (exact in BF16), B = the three BF16 terms W_s of W (hi, mid, lo) stacked
+//          along N, so that one product per K step gives the three partial thetas, summed
+//          in the epilogue as (hi + mid) + lo
+//   GEMM2  G[i, j]  += sum_x s[x, i] a[x, j]           M = 128 sites, K = 128 rows
+//          a = tanh(theta + b) (eloc - E) as three BF16 terms; a_hi and a_mid side by side
+//          (N = 128) into the accumulator pair (hi, lo), then a_lo (N = 64) into lo
+// Column i = N of the spin tile is a constant +1 whose W column holds the hidden bias, so GEMM1
+// gives theta = W s + b and G[N, j] = sum_x a[x, j] gives the b-entries; the extra hidden unit
+// j = M carries a = eloc - E, so G[i, M] gives the a-entries.  The spin tile is the K-major A of GEMM1 and, read MN-major, the A of GEMM2.
+// The hi term of a accumulates apart from the mid + lo terms, so that the small terms are not
+// rounded away against the large running sum.
+//
+// The block is warp-specialised so that staging, the tensor core and the epilogue overlap:
+//   warp 0 (one thread)  issues GEMM1 of tile t, then GEMM2 of tile t - 1;
+//   warps 4-7            stage the spin tile (thread x: row x) from the packed configurations,
+//                        one byte of spins at a time through a 256-entry table of BF16 +-1,
+//                        up to three tiles ahead;
+//   warps 8-15           read theta from TMEM, form the three a-terms in registers, store them
+//                        once GEMM2 of the previous tile has read its terms, and every DRAIN
+//                        tiles add the accumulators into the block's FP64 slice of the workspace
+//                        (rows chunk * P ...), which force_reduce_kernel then sums over chunks
+//                        in a fixed order.
+// Buffers: three spin tiles and one set of a-terms in shared memory; theta and two accumulator
+// pairs (one drained while the other accumulates) in TMEM; mbarriers hand each buffer between the
+// roles.  Every wait is bounded: a wait that gives up records STATUS_TIMEOUT and every role
+// leaves its loop.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -24,9 +41,19 @@
 namespace nqs {
 namespace {
 
-constexpr int FTC_THREADS = 256;
-constexpr int FTC_DRAIN = 16;  // tiles between FP64 drains of the accumulators
+constexpr int FTC_THREADS = 512;
+constexpr int FTC_HT = 64;       // hidden units per block
+constexpr int FTC_NS = 3;        // spin tiles in flight
+constexpr int FTC_DRAIN = 16;    // tiles per FP32 accumulation period before the FP64 drain
 constexpr uint32_t FTC_POLLS = 1u << 24;
+constexpr int FTC_KP = 128;      // padded site extent (N + 1 <= 128)
+constexpr uint32_t SPIN_BYTES = 128 * FTC_KP * 2;        // one spin tile: 2 K-blocks of 16 KB
+constexpr uint32_t WKB_BYTES = 3 * FTC_HT * 128;         // one K-block of the stacked W terms
+constexpr uint32_t ATERM_BYTES = 128 * FTC_HT * 2;       // one a term: 128 rows x 128 bytes
+constexpr size_t FTC_SMEM = 1024 + 2 * WKB_BYTES + FTC_NS * SPIN_BYTES + 3 * ATERM_BYTES + 256 * 16;
+// TMEM columns: theta_hi, theta_mid, theta_lo at 0, 64, 128; accumulator pair d at 256 + 128 d
+// (hi, then lo 64 columns later)
+constexpr uint32_t TM_G = 256;
 
 struct ForceTcParams {
   const uint32_t *cfg;
@@ -37,7 +64,7 @@ struct ForceTcParams {
   double *ws;       // [chunks][P]
   int *status;
   int64_t n, P;
-  int N, W, M, Kp, N2, n_chunks;
+  int N, W, M, n_chunks;
 };
 
 __device__ __forceinline__ void split3(float a, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
@@ -47,43 +74,127 @@ __device__ __forceinline__ void split3(float a, __nv_bfloat16 &h, __nv_bfloat16 
   l = __float2bfloat16_rn(r - __bfloat162float(m));
 }
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
-  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t *>(&v); }
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+// Paired FP32 arithmetic (fma.rn.f32x2 / mul.rn.f32x2): two operations per instruction, each
+// rounded as its scalar counterpart.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// The three BF16 terms of the pair a (a.x in the low half): the same split as split3, two values
+// per conversion; the residuals a - hi and r - mid are exact.
+__device__ __forceinline__ void split3_pair(float2 a, uint32_t &h, uint32_t &m, uint32_t &l) {
+  h = bf2_bits(__floats2bfloat162_rn(a.x, a.y));
+  const float2 r = ffma2(make_float2(bf_lo(h), bf_hi(h)), f2(-1.f), a);
+  m = bf2_bits(__floats2bfloat162_rn(r.x, r.y));
+  const float2 r2 = ffma2(make_float2(bf_lo(m), bf_hi(m)), f2(-1.f), r);
+  l = bf2_bits(__floats2bfloat162_rn(r2.x, r2.y));
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// tanh of the epilogue for a pair, from two textbook forms selected without a branch: the odd
+// Taylor series y (1 - y^2/3 + 2 y^4/15 - ...) through y^15 for |y| < 0.55 (truncation below
+// 4.1e-8 relative), and sign(y) (1 - 2 / (e^{2|y|} + 1)) beyond, with e^{2|y|} by ex2.approx and
+// the reciprocal by rcp.approx (a few ulp; e^{2|y|} = inf gives exactly 1).
+__device__ __forceinline__ float2 tanh_epi2(float2 y) {
+  const float2 y2 = fmul2(y, y);
+  float2 p = f2(-929569.f / 638512875.f);
+  p = ffma2(p, y2, f2(21844.f / 6081075.f));
+  p = ffma2(p, y2, f2(-1382.f / 155925.f));
+  p = ffma2(p, y2, f2(62.f / 2835.f));
+  p = ffma2(p, y2, f2(-17.f / 315.f));
+  p = ffma2(p, y2, f2(2.f / 15.f));
+  p = ffma2(p, y2, f2(-1.f / 3.f));
+  p = ffma2(p, y2, f2(1.f));
+  const float2 poly = fmul2(y, p);
+  const float2 t = make_float2(fabsf(y.x), fabsf(y.y));
+  const float2 g = fmul2(t, f2(2.8853900817779268f));
+  const float2 e1 = ffma2(make_float2(ex2_approx(g.x), ex2_approx(g.y)), f2(1.f), f2(1.f));
+  const float2 q = ffma2(f2(-2.f), make_float2(rcp_approx(e1.x), rcp_approx(e1.y)), f2(1.f));
+  return make_float2(t.x < 0.55f ? poly.x : copysignf(q.x, y.x), t.y < 0.55f ? poly.y : copysignf(q.y, y.y));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// byte offset of the 16-byte chunk c of row r in a 128-byte-swizzled tile of 128-byte rows
+__device__ __forceinline__ uint32_t sw_chunk(uint32_t r, uint32_t c) {
+  return (r >> 3) * 1024u + (r & 7u) * 128u + (((c ^ r) & 7u) << 4);
 }
 
 __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const ForceTcParams p) {
   extern __shared__ unsigned char smem_dyn[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t spin_full[FTC_NS], spin_free[FTC_NS], theta_full, theta_empty, a_full, a_free, g_full[2],
+      g_empty[2], fin_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const uint32_t raw = smem_addr(smem_dyn);
   unsigned char *base = smem_dyn + (((raw + 1023u) & ~1023u) - raw);
-  const int nkb = p.Kp / 64;
-  unsigned char *sA1 = base;                       // [128 x][Kp]            K-major, nkb x 16 KB
-  unsigned char *sB1 = sA1 + nkb * 16384;          // 3 x [128 j][Kp]        K-major
-  unsigned char *sA2 = sB1 + 3 * nkb * 16384;      // 3 x [128 x (K)][128 j] MN-major, 2 x 16 KB each
-  float *se = reinterpret_cast<float *>(sA2 + 3 * 32768);  // [128] eloc - E
-  float *sb = se + 128;                                    // [128] hidden bias of the tile
+  unsigned char *sW = base;                           // K-major [192 = 3 terms x 64 j][128 i]
+  unsigned char *sS = sW + 2 * WKB_BYTES;             // FTC_NS spin tiles, K-major [128 x][128 i]
+  unsigned char *sA = sS + FTC_NS * SPIN_BYTES;       // 3 a terms, MN-major [128 x][64 j]
+  uint4 *lut = reinterpret_cast<uint4 *>(sA + 3 * ATERM_BYTES);  // byte of 8 spins -> 8 BF16 (+-1)
 
   const int jt = blockIdx.x, chunk = blockIdx.y;
-  const int j0 = jt * 128;
-  const int N = p.N, M = p.M, Kp = p.Kp;
+  const int j0 = jt * FTC_HT;
+  const int N = p.N, M = p.M;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // ---- B1: W of the tile as three BF16 terms; sb: bias --------------------------------
-  for (int idx = tid; idx < 128 * Kp; idx += FTC_THREADS) {
-    const int jj = idx % 128, i = idx / 128;
-    const float w = (j0 + jj < M && i < N) ? p.Wm[(int64_t)i * M + j0 + jj] : 0.f;
+  // ---- W of the block as three stacked BF16 terms; bias; barriers; TMEM -----------------
+  for (int idx = tid; idx < FTC_HT * FTC_KP; idx += FTC_THREADS) {
+    const int jj = idx % FTC_HT, i = idx / FTC_HT;
+    // column N multiplies the constant +1 spin: the hidden bias enters theta through GEMM1
+    const float w = j0 + jj < M ? (i < N ? p.Wm[(int64_t)i * M + j0 + jj] : (i == N ? p.bm[j0 + jj] : 0.f)) : 0.f;
     __nv_bfloat16 h, m, l;
     split3(w, h, m, l);
-    const uint32_t off = (i / 64) * 16384 + tc::sw128_offset(jj, i % 64);
-    *reinterpret_cast<__nv_bfloat16 *>(sB1 + off) = h;
-    *reinterpret_cast<__nv_bfloat16 *>(sB1 + nkb * 16384 + off) = m;
-    *reinterpret_cast<__nv_bfloat16 *>(sB1 + 2 * nkb * 16384 + off) = l;
+    unsigned char *kb = sW + (i / 64) * WKB_BYTES;
+    *reinterpret_cast<__nv_bfloat16 *>(kb + tc::sw128_offset(jj, i % 64)) = h;
+    *reinterpret_cast<__nv_bfloat16 *>(kb + tc::sw128_offset(FTC_HT + jj, i % 64)) = m;
+    *reinterpret_cast<__nv_bfloat16 *>(kb + tc::sw128_offset(2 * FTC_HT + jj, i % 64)) = l;
   }
-  for (int jj = tid; jj < 128; jj += FTC_THREADS) sb[jj] = (j0 + jj < M) ? p.bm[j0 + jj] : 0.f;
+  for (int v = tid; v < 256; v += FTC_THREADS) {  // bit k of v set: spin 8c + k up (+1 = 0x3F80)
+    uint32_t w4[4];
+    for (int q = 0; q < 4; ++q)
+      w4[q] = (((v >> (2 * q)) & 1) ? 0x3F80u : 0xBF80u) | ((((v >> (2 * q + 1)) & 1) ? 0x3F80u : 0xBF80u) << 16);
+    lut[v] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+  }
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    for (int b = 0; b < FTC_NS; ++b) {
+      mbar_init(&spin_full[b], 128);
+      mbar_init(&spin_free[b], 1);
+    }
+    mbar_init(&theta_full, 1);
+    mbar_init(&theta_empty, 256);
+    mbar_init(&a_full, 256);
+    mbar_init(&a_free, 1);
+    for (int d = 0; d < 2; ++d) {
+      mbar_init(&g_full[d], 1);
+      mbar_init(&g_empty[d], 256);
+    }
+    mbar_init(&fin_bar, 1);
     fence_mbar_init();
     abort_flag = 0;
   }
@@ -95,160 +206,209 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tD1 = tmem_base, tD2 = tmem_base + 128, tD3 = tmem_base + 256;
-  const double E = p.stats[0];
+
+  const uint32_t tm = tmem_base;
   const int64_t rows_per_chunk = (p.n + p.n_chunks - 1) / p.n_chunks;
   const int64_t r0 = (int64_t)chunk * rows_per_chunk, r1 = min(p.n, r0 + rows_per_chunk);
-  const uint32_t id1 = tc::idesc_bf16_f32(128, 128);
-  const uint32_t id2 = tc::idesc_bf16_f32(128, (uint32_t)p.N2, 1, 1);
-  uint32_t phase = 0;
-  int tiles_since_drain = 0, drains = 0;
-  double *out = p.ws + (int64_t)chunk * p.P;
+  const int T = r1 > r0 ? (int)((r1 - r0 + 127) / 128) : 0;
+  volatile int *abort_v = &abort_flag;
 
-  // Waits for the products committed last; the result is uniform across the block.
-  auto wait_mma = [&]() -> bool {
-    const bool ok = mbar_wait_bounded(&bar, phase, FTC_POLLS);
-    phase ^= 1u;
-    const bool any_fail = __syncthreads_or(!ok);
-    if (any_fail && tid == 0) {
-      atomicOr(p.status, STATUS_TIMEOUT);
-      abort_flag = 1;
+  // Bounded wait by every thread of the calling role; false once the block aborts.
+  auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+    for (uint32_t it = 0; it < FTC_POLLS; ++it) {
+      if (mbar_try_wait(bar, parity)) return true;
+      if (*abort_v) return false;
     }
-    tc::fence_after_sync();
-    return !any_fail;
+    atomicOr(p.status, STATUS_TIMEOUT);
+    *abort_v = 1;
+    return false;
   };
+  // warp-uniform form (for roles that go on to warp-collective tcgen05.ld)
+  auto wait_warp = [&](uint64_t *bar, uint32_t parity) -> bool { return __all_sync(FULL_MASK, wait(bar, parity)); };
 
-  // Adds the FP32 accumulator G (TMEM columns 128 .. 128 + N2) into the FP64 slice
-  // (zero_only: writes zeros, for a chunk without rows).
-  auto drain = [&](bool zero_only) {
-    const int q = warp & 3, h = warp >> 2;
-    const int jj = 32 * q + lane, j = j0 + jj;
-    for (int c = 0; c < 2; ++c) {
-      const int i0 = 64 * h + 32 * c;
-      if (i0 >= p.N2) break;  // warp-uniform
+  if (warp == 0) {
+    // ================================ MMA issuer ===================================
+    if (lane == 0 && T > 0) {
+      const uint32_t id1 = tc::idesc_bf16_f32(128, 3 * FTC_HT);
+      const uint32_t id2 = tc::idesc_bf16_f32(128, 2 * FTC_HT, 1, 1);
+      const uint32_t id3 = tc::idesc_bf16_f32(128, FTC_HT, 1, 1);
+      auto gemm2 = [&](int u) -> bool {
+        const int sb_ = u % FTC_NS, per = u / FTC_DRAIN, d = per & 1;
+        const bool first = u % FTC_DRAIN == 0;
+        if (!wait(&a_full, u & 1)) return false;
+        if (first && per >= 2 && !wait(&g_empty[d], ((per - 2) >> 1) & 1)) return false;
+        tc::fence_after_sync();
+        const uint32_t gh = tm + TM_G + 128 * d;
+        unsigned char *spins = sS + sb_ * SPIN_BYTES;
+        for (int k0 = 0; k0 < 128; k0 += 16) {
+          const uint64_t ad = tc::desc_sw128(smem_addr(spins + k0 * 128), 16384);
+          // a_hi | a_mid (two 64-unit groups one term apart) -> hi | lo
+          tc::mma_bf16(gh, ad, tc::desc_sw128(smem_addr(sA + k0 * 128), ATERM_BYTES), id2, first && k0 == 0 ? 0u : 1u);
+          // a_lo -> lo
+          tc::mma_bf16(gh + FTC_HT, ad, tc::desc_sw128(smem_addr(sA + 2 * ATERM_BYTES + k0 * 128), ATERM_BYTES), id3, 1u);
+        }
+        tc::mma_commit(&spin_free[sb_]);
+        tc::mma_commit(&a_free);
+        if (u % FTC_DRAIN == FTC_DRAIN - 1 || u == T - 1) tc::mma_commit(&g_full[d]);
+        return true;
+      };
+      bool ok = true;
+      for (int t = 0; t < T && ok; ++t) {
+        const int sb_ = t % FTC_NS;
+        ok = wait(&spin_full[sb_], (t / FTC_NS) & 1);
+        if (ok && t >= 1) ok = wait(&theta_empty, (t - 1) & 1);
+        if (!ok) break;
+        tc::fence_after_sync();
+        unsigned char *spins = sS + sb_ * SPIN_BYTES;
+        for (int k0 = 0; k0 < FTC_KP; k0 += 16) {
+          const uint64_t ad = tc::desc_sw128(smem_addr(spins + (k0 / 64) * 16384 + (k0 % 64) * 2));
+          const uint64_t bd = tc::desc_sw128(smem_addr(sW + (k0 / 64) * WKB_BYTES + (k0 % 64) * 2));
+          tc::mma_bf16(tm, ad, bd, id1, k0 > 0 ? 1u : 0u);
+        }
+        tc::mma_commit(&theta_full);
+        if (t >= 1) ok = gemm2(t - 1);
+      }
+      if (ok) gemm2(T - 1);
+      // every product issued above has completed once fin_bar completes
+      tc::mma_commit(&fin_bar);
+      mbar_wait_bounded(&fin_bar, 0, FTC_POLLS);
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    // ============================= spin-tile producer ================================
+    const int x = tid - 128;  // row of the tile
+    // the packed row of tile t (zeros past the chunk), loaded one tile ahead of its use
+    auto load_row = [&](int t, uint32_t (&wd)[4]) {
+      const int64_t r = r0 + (int64_t)t * 128 + x;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) wd[w] = (r < r1 && w < p.W) ? p.cfg[r * p.W + w] : 0u;
+    };
+    uint32_t next[4];
+    if (T > 0) load_row(0, next);
+    for (int t = 0; t < T; ++t) {
+      const int sb_ = t % FTC_NS;
+      const bool live = r0 + (int64_t)t * 128 + x < r1;
+      const uint32_t words[4] = {next[0], next[1], next[2], next[3]};
+      if (t + 1 < T) load_row(t + 1, next);
+      if (t >= FTC_NS && !wait(&spin_free[sb_], ((t - FTC_NS) / FTC_NS) & 1)) break;
+      unsigned char *spins = sS + sb_ * SPIN_BYTES;
+#pragma unroll
+      for (int c = 0; c < FTC_KP / 8; ++c) {  // chunk c holds sites 8c .. 8c + 7
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (live && 8 * c <= N) {
+          v = lut[(words[c >> 2] >> (8 * (c & 3))) & 0xFFu];
+          if (8 * c + 8 > N) {  // the chunk of site N: +1 there, 0 beyond
+            uint32_t *e = &v.x;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int i = 8 * c + k;
+              if (i >= N) {
+                const uint32_t val = i == N ? 0x3F80u : 0u, sh = 16 * (k & 1);
+                e[k >> 1] = (e[k >> 1] & ~(0xFFFFu << sh)) | (val << sh);
+              }
+            }
+          }
+        }
+        *reinterpret_cast<uint4 *>(spins + (c / 8) * 16384 + sw_chunk(x, c & 7)) = v;
+      }
+      tc::fence_proxy_async_smem();
+      mbar_arrive(&spin_full[sb_]);
+    }
+  } else if (warp >= 8) {
+    // ================================== epilogue =====================================
+    const int q = warp & 3, h = (warp - 8) >> 2;  // TMEM lanes 32 q .. 32 q + 31; units 32 h .. 32 h + 31
+    const int x = 32 * q + lane;
+    const double E = p.stats[0];
+    const bool has_m = j0 <= M && M < j0 + FTC_HT;
+    double *out = p.ws + (int64_t)chunk * p.P;
+    int drains = 0;
+    // Adds the accumulator pair of period per into the FP64 slice (zero_only: writes zeros).
+    auto drain = [&](int per, bool zero_only) -> bool {
+      const int d = per & 1;
       float v[32], w[32];
       if (zero_only) {
         for (int t = 0; t < 32; ++t) v[t] = w[t] = 0.f;
       } else {
-        tc::tmem_ld32(tc::tmem_lane_addr(tD2, 32 * q, i0), v);
-        tc::tmem_ld32(tc::tmem_lane_addr(tD3, 32 * q, i0), w);
+        if (!wait_warp(&g_full[d], (per >> 1) & 1)) return false;
+        tc::fence_after_sync();
+        tc::tmem_ld32(tc::tmem_lane_addr(tm + TM_G + 128 * d, 32 * q, 32 * h), v);
+        tc::tmem_ld32(tc::tmem_lane_addr(tm + TM_G + 128 * d + FTC_HT, 32 * q, 32 * h), w);
+        tc::fence_before_sync();
+        mbar_arrive(&g_empty[d]);
       }
+      const int i = x;  // TMEM lane = site
       for (int t = 0; t < 32; ++t) {
-        const int i = i0 + t;
+        const int j = j0 + 32 * h + t;
         int64_t k = -1;
-        if (j < M && i < N) k = N + M + (int64_t)j * N + i;   // W entries
-        else if (j < M && i == N) k = N + j;                   // b entries
-        else if (j == M && i < N) k = i;                       // a entries
+        if (j < M && i < N) k = N + M + (int64_t)j * N + i;  // W entries
+        else if (j < M && i == N) k = N + j;                  // b entries
+        else if (j == M && i < N) k = i;                      // a entries
         if (k >= 0) out[k] = (drains ? out[k] : 0.0) + ((double)v[t] + (double)w[t]);
       }
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    ++drains;
-    tiles_since_drain = 0;
-  };
-
-  for (int64_t x0 = r0; x0 < r1; x0 += 128) {
-    const int nb = (int)(r1 - x0 < 128 ? r1 - x0 : 128);
-    // ---- stage the spin tile (row x: +-1 for i < N, +1 at i = N, 0 beyond) and e --------
-    if (tid < 128) {
-      const int x = tid;
-      uint32_t words[4] = {0u, 0u, 0u, 0u};
-      if (x < nb)
-        for (int w = 0; w < p.W; ++w) words[w] = p.cfg[(x0 + x) * p.W + w];
-      for (int c = 0; c < Kp / 8; ++c) {  // 16-byte chunk c holds sites 8c .. 8c + 7
-        uint32_t pk[4];
-        for (int q2 = 0; q2 < 4; ++q2) {
-          float f[2];
-          for (int e = 0; e < 2; ++e) {
-            const int i = 8 * c + 2 * q2 + e;
-            f[e] = (x >= nb) ? 0.f : (i < N ? (((words[i >> 5] >> (i & 31)) & 1u) ? 1.f : -1.f) : (i == N ? 1.f : 0.f));
-          }
-          pk[q2] = pack2(__float2bfloat16_rn(f[0]), __float2bfloat16_rn(f[1]));
-        }
-        const uint32_t off = (c / 8) * 16384 + (x >> 3) * 1024 + (x & 7) * 128 + ((((c & 7) ^ (x & 7)) & 7) << 4);
-        *reinterpret_cast<uint4 *>(sA1 + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-      }
-      se[x] = x < nb ? (float)((double)p.eloc[x0 + x] - E) : 0.f;
-    }
-    tc::fence_proxy_async_smem();
-    __syncthreads();
-    // ---- GEMM1: theta = spins * W^T (three W terms into one accumulator) ---------------
-    if (tid == 0) {
-      uint32_t acc = 0;
-      for (int s = 0; s < 3; ++s)
-        for (int k0 = 0; k0 < Kp; k0 += 16) {
-          const uint64_t ad = tc::desc_sw128(smem_addr(sA1 + (k0 / 64) * 16384 + (k0 % 64) * 2));
-          const uint64_t bd = tc::desc_sw128(smem_addr(sB1 + s * nkb * 16384 + (k0 / 64) * 16384 + (k0 % 64) * 2));
-          tc::mma_bf16(tD1, ad, bd, id1, acc);
-          acc = 1;
-        }
-      tc::mma_commit(&bar);
-    }
-    if (!wait_mma()) break;
-    // ---- epilogue: a = tanh(theta + b) e, three BF16 terms, MN-major rows x ---------------
-    {
-      const int q = warp & 3, h = warp >> 2;
-      const int x = 32 * q + lane;
-      const float ex = se[x];
-      for (int c = 0; c < 2; ++c) {
-        const int jb = 64 * h + 32 * c;  // 32 hidden units jb .. jb + 31
-        float v[32];
-        tc::tmem_ld32(tc::tmem_lane_addr(tD1, 32 * q, jb), v);
-        uint32_t ph[16], pm[16], pl[16];
-        for (int t = 0; t < 32; t += 2) {
-          __nv_bfloat16 h0, m0, l0, h1, m1, l1;
-          for (int u = 0; u < 2; ++u) {
-            const int jj = jb + t + u;
-            float a = tanhf(v[t + u] + sb[jj]) * ex;
-            if (j0 + jj == M) a = ex;
-            if (u == 0) split3(a, h0, m0, l0);
-            else split3(a, h1, m1, l1);
-          }
-          ph[t / 2] = pack2(h0, h1);
-          pm[t / 2] = pack2(m0, m1);
-          pl[t / 2] = pack2(l0, l1);
-        }
-        // row x, M-elements jb .. jb + 31: 64-element group jb / 64, chunks (jb % 64) / 8 .. + 3
-        for (int cc = 0; cc < 4; ++cc) {
-          const int chunk16 = ((jb & 63) >> 3) + cc;
-          const uint32_t off = (jb >> 6) * 16384 + (x >> 3) * 1024 + (x & 7) * 128 + (((chunk16 ^ (x & 7)) & 7) << 4);
-          *reinterpret_cast<uint4 *>(sA2 + off) = make_uint4(ph[4 * cc], ph[4 * cc + 1], ph[4 * cc + 2], ph[4 * cc + 3]);
-          *reinterpret_cast<uint4 *>(sA2 + 32768 + off) =
-              make_uint4(pm[4 * cc], pm[4 * cc + 1], pm[4 * cc + 2], pm[4 * cc + 3]);
-          *reinterpret_cast<uint4 *>(sA2 + 65536 + off) =
-              make_uint4(pl[4 * cc], pl[4 * cc + 1], pl[4 * cc + 2], pl[4 * cc + 3]);
+      ++drains;
+      return true;
+    };
+    auto eval = [&](int t) -> float {
+      const int64_t r = r0 + (int64_t)t * 128 + x;
+      return r < r1 ? (float)((double)p.eloc[r] - E) : 0.f;
+    };
+    float e_next = T > 0 ? eval(0) : 0.f;
+    bool ok = true;
+    for (int t = 0; t < T && ok; ++t) {
+      const float e = e_next;
+      if (t + 1 < T) e_next = eval(t + 1);
+      if (!wait_warp(&theta_full, t & 1)) { ok = false; break; }
+      tc::fence_after_sync();
+      float2 th[16];  // theta of units 32 h + 2 u, + 1 (bias included through GEMM1)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float vh[16], vm[16], vl[16];
+        const uint32_t col = 32 * h + 16 * r;
+        tc::tmem_ld16(tc::tmem_lane_addr(tm, 32 * q, col), vh);
+        tc::tmem_ld16(tc::tmem_lane_addr(tm, 32 * q, FTC_HT + col), vm);
+        tc::tmem_ld16(tc::tmem_lane_addr(tm, 32 * q, 2 * FTC_HT + col), vl);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float2 hm = ffma2(make_float2(vh[2 * u], vh[2 * u + 1]), f2(1.f), make_float2(vm[2 * u], vm[2 * u + 1]));
+          th[8 * r + u] = ffma2(hm, f2(1.f), make_float2(vl[2 * u], vl[2 * u + 1]));
         }
       }
-    }
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    // ---- GEMM2: G += a^T spins (a MN-major over j, spins MN-major over i) ---------------
-    if (tid == 0) {
-      for (int s = 0; s < 3; ++s)
-        for (int k0 = 0; k0 < 128; k0 += 16) {
-          const uint64_t ad = tc::desc_sw128(smem_addr(sA2 + s * 32768 + k0 * 128), 16384);
-          const uint64_t bd = tc::desc_sw128(smem_addr(sA1 + k0 * 128), 16384);
-          const bool first = tiles_since_drain == 0 && k0 == 0 && s < 2;  // s = 1 starts the second accumulator
-          tc::mma_bf16(s == 0 ? tD2 : tD3, ad, bd, id2, first ? 0u : 1u);
+      tc::fence_before_sync();
+      mbar_arrive(&theta_empty);
+      uint32_t ph[16], pm[16], pl[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        float2 a = fmul2(tanh_epi2(th[u]), f2(e));
+        if (has_m) {  // the block holding unit M: a = eloc - E there (a-entries)
+          const int j = j0 + 32 * h + 2 * u;
+          if (j == M) a.x = e;
+          if (j + 1 == M) a.y = e;
         }
-      tc::mma_commit(&bar);
+        split3_pair(a, ph[u], pm[u], pl[u]);
+      }
+      // the terms of tile t - 1 have been read by its GEMM2 once a_free completes
+      if (t >= 1 && !wait_warp(&a_free, (t - 1) & 1)) { ok = false; break; }
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {  // 16-byte chunk 4 h + cc: units 32 h + 8 cc .. + 7
+        const uint32_t off = sw_chunk(x, 4 * h + cc);
+        *reinterpret_cast<uint4 *>(sA + off) = make_uint4(ph[4 * cc], ph[4 * cc + 1], ph[4 * cc + 2], ph[4 * cc + 3]);
+        *reinterpret_cast<uint4 *>(sA + ATERM_BYTES + off) =
+            make_uint4(pm[4 * cc], pm[4 * cc + 1], pm[4 * cc + 2], pm[4 * cc + 3]);
+        *reinterpret_cast<uint4 *>(sA + 2 * ATERM_BYTES + off) =
+            make_uint4(pl[4 * cc], pl[4 * cc + 1], pl[4 * cc + 2], pl[4 * cc + 3]);
+      }
+      tc::fence_proxy_async_smem();
+      mbar_arrive(&a_full);
+      if (t >= 1 && (t - 1) % FTC_DRAIN == FTC_DRAIN - 1) ok = drain((t - 1) / FTC_DRAIN, false);
     }
-    if (!wait_mma()) break;
-    ++tiles_since_drain;
-    if (tiles_since_drain == FTC_DRAIN) drain(false);
-  }
-  __syncthreads();
-  if (!abort_flag) {
-    if (tiles_since_drain > 0) drain(false);
-    else if (drains == 0) drain(true);
-  } else {
-    mbar_wait_bounded(&bar, phase, FTC_POLLS);  // let a pending product finish before freeing TMEM
+    if (ok) {
+      if (T > 0) drain((T - 1) / FTC_DRAIN, false);
+      else drain(0, true);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
+  tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tmem_base, 512);
 }
 
@@ -257,7 +417,7 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
 bool rbm_force_tc_supported(const nqs_ctx *c) { return c->N <= 127; }
 
 int rbm_force_tc_chunks(const nqs_ctx *c, int64_t n) {
-  const int jt = (c->M + 1 + 127) / 128;
+  const int jt = (c->M + 1 + FTC_HT - 1) / FTC_HT;
   int64_t ch = std::max<int64_t>(1, c->num_sms / jt);
   ch = std::min<int64_t>(ch, (n + 127) / 128);
   return (int)std::max<int64_t>(1, ch);
@@ -278,14 +438,11 @@ cudaError_t rbm_force_tc(const nqs_ctx *c, const uint32_t *cfg, int64_t n, const
   p.N = c->N;
   p.W = c->W;
   p.M = c->M;
-  p.Kp = ((c->N + 1 + 63) / 64) * 64;
-  p.N2 = ((c->N + 1 + 15) / 16) * 16;
   p.n_chunks = chunks;
-  const int jt = (c->M + 1 + 127) / 128;
-  const size_t shm = 1024 + (size_t)(p.Kp / 64) * 16384 * 4 + 3 * 32768 + 2 * 128 * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(rbm_force_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  const int jt = (c->M + 1 + FTC_HT - 1) / FTC_HT;
+  cudaError_t e = cudaFuncSetAttribute(rbm_force_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FTC_SMEM);
   if (e != cudaSuccess) return e;
-  rbm_force_tc_kernel<<<dim3(jt, chunks), FTC_THREADS, shm, s>>>(p);
+  rbm_force_tc_kernel<<<dim3(jt, chunks), FTC_THREADS, FTC_SMEM, s>>>(p);
   return cudaGetLastError();
 }
 

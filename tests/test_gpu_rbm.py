@@ -167,11 +167,12 @@ def _oracle_force_blocked(model, s, eps, block=50000):
     return np.concatenate([Fa / n, Fb / n, (FW / n).ravel()])
 
 
-def test_force_many_tiles_matches_oracle():
-    """600k rows of the 10x10 alpha = 4 shape: every block accumulates > 64 tiles, so the
-    periodic FP64 drain of the tensor-core accumulator is exercised."""
+@pytest.mark.parametrize("n", [600_000, 98_700])
+def test_force_many_tiles_matches_oracle(n):
+    """Many rows of the 10x10 alpha = 4 shape.  600k: every block accumulates 224 tiles (14
+    FP32 periods drained to FP64, both accumulator pairs reused); 98,700: 37 tiles per block,
+    an odd count that ends in a partial period and a ragged tile."""
     ctx, model, _ = make(10, 10, 400, 0.05, 17)
-    n = 600_000
     rng = np.random.default_rng(18)
     s = rng.choice([-1, 1], size=(n, 100)).astype(np.int8)
     eps = rng.normal(-310.0, 5.0, n).astype(np.float32)
