@@ -413,15 +413,15 @@ class DenseStep:
     O rows and force of a dense-ansatz workload.  `T` overrides the sweep count (the 16 x 16
     workload times a bounded number of its sweeps)."""
 
-    def __init__(self, nqs, torch, dev, wl, C=None, T=None, B=None, n_grad=None, minsr_lambda=None):
+    def __init__(self, nqs, torch, dev, wl, C=None, T=None, B=None, n_grad=None, minsr_lambda=None, dtype="bf16"):
         lat = wl.ham.lattice
-        self.wl, self.torch = wl, torch
+        self.wl, self.torch, self.dtype = wl, torch, dtype
         self.N = lat.n_sites
         self.C, self.T = C or wl.n_chains, T or wl.n_sweeps
         self.B = min(wl.burn_in, self.T - 1) if B is None else B
         self.S = (self.T - self.B) * self.C
         self.ctx = nqs.Context("heisenberg", lat.Lx, lat.Ly, J1=wl.ham.J1, J2=wl.ham.J2, marshall=wl.ham.marshall,
-                               model="dense", widths=wl.widths, dtype="bf16")
+                               model="dense", widths=wl.widths, dtype=dtype)
         if self.C > 262144:
             self.ctx.set_option(nqs.OPT_MAX_ROWS, self.C)
         P = self.ctx.P
@@ -477,12 +477,16 @@ class DenseStep:
 
     def describe(self, ms, accepts, peaks_, n_sm):
         w, N = list(self.wl.widths), self.N
+        f8 = self.dtype == "fp8"
         kp = [((h + 63) // 64) * 64 for h in w]
-        gemm_row = sum(2.0 * kp[l - 1] * w[l] for l in range(1, len(w)))     # tensor-core FLOP per row
+        gemm_row = sum(2.0 * kp[l - 1] * w[l] for l in range(1, len(w)))     # tensor-core FLOP per row (BF16 copy)
+        kp8 = [((h + 127) // 128) * 128 for h in w]
+        gemm_row_s = sum(2.0 * kp8[l - 1] * w[l] for l in range(1, len(w))) if f8 else gemm_row  # sampling copy
         n_conn = self.ctx.n_bonds
-        sweep_flop = gemm_row * self.units()
+        sweep_flop = gemm_row_s * self.units()
         ach = sweep_flop / (ms["sweep"] / 1e3) / 1e12
-        peak = float(peaks_.get("bf16_tflops_sustained", 1400.0))
+        # FP8 products: the measured sustained BF16 rate x 2 (nominal dense FP8 / BF16 ratio)
+        peak = float(peaks_.get("bf16_tflops_sustained", 1400.0)) * (2.0 if f8 else 1.0)
         eloc_flop = gemm_row * self.S * (1 + n_conn)
         lat = self.wl.ham.lattice
         return {
@@ -502,8 +506,12 @@ class DenseStep:
                                   "as 6 BF16 products over the upper triangle"}} if self.lam else {}),
             "roofline": {"bound": "tensor", "kernel": "dense_gemm_kernel (sampler steps)", "achieved": ach,
                          "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                         "note": "BF16 GEMM FLOP of layers >= 2 over all proposals / sweep time, vs measured "
-                                 "sustained cuBLAS BF16"},
+                         "note": ("FP8 (E4M3) GEMM FLOP of layers >= 2 over all proposals / sweep time, vs 2 x the "
+                                  "measured sustained cuBLAS BF16" if f8 else
+                                  "BF16 GEMM FLOP of layers >= 2 over all proposals / sweep time, vs measured "
+                                  "sustained cuBLAS BF16")},
+            "energy": {"E": float(self.stats[0].item()), "err": float(self.stats[2].item()),
+                       "note": "last timed step; local energy on the BF16 copy"},
         }
 
 
@@ -644,7 +652,8 @@ def run_workload(args, rank, world, dist):
     if args.workload == "tfim1d":
         st = RbmStep(nqs, torch, dev, workloads.TFIM_1D_N16, "f32", C, T, B)
     elif args.workload == "heis2d-dense":
-        st = DenseStep(nqs, torch, dev, workloads.HEIS_2D_10x10, C, T, B)
+        st = DenseStep(nqs, torch, dev, workloads.HEIS_2D_10x10, C, T, B,
+                       dtype="fp8" if args.dtype == "fp8" else "bf16")
     elif args.workload == "j1j2-dense":
         wl = workloads.J1J2_2D_16x16
         st = DenseStep(nqs, torch, dev, wl, C, T or 2, 1 if B is None else B,
@@ -694,7 +703,9 @@ def run_workload(args, rank, world, dist):
     line = {"metric": METRIC, "value": world * units * args.steps / t_dev, "unit": "proposals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"tfim1d": "f32", "heis2d-dense": "bf16 (fp32 accumulate, fp32 layer-0 cache)",
+            "dtype": {"tfim1d": "f32",
+                      "heis2d-dense": ("fp8 e4m3 sampling (bf16 local energy, " if args.dtype == "fp8" else "bf16 (")
+                      + "fp32 accumulate, fp32 layer-0 cache)",
                       "j1j2-dense": "bf16 (fp32 accumulate, fp32 layer-0 cache)",
                       "batched": "f16 sampling (f32 caches, accept, statistics)"}[args.workload],
             "data": "synthetic (seeded random-init networks, random initial spins)"}
@@ -768,7 +779,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--dtype", default="f16", choices=["f32", "bf16", "f16"],
+    ap.add_argument("--dtype", default="f16", choices=["f32", "bf16", "f16", "fp8"],
                     help="sampling copy of the timed step (the mixed-precision path by default)")
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the FP32 / other-dtype comparison steps and the bias statement")
@@ -782,6 +793,8 @@ def main():
                     help="tfim2d: the 10x10 alpha=4 RBM workload (default); the others measure the other "
                          "workloads' steps with the same line")
     args = ap.parse_args()
+    if args.dtype == "fp8" and args.workload != "heis2d-dense":
+        ap.error("--dtype fp8 is the dense ansatz's FP8 sampling copy (--workload heis2d-dense)")
     world = int(os.environ.get("WORLD_SIZE", args.gpus))
     rank = int(os.environ.get("RANK", 0))
 

@@ -52,7 +52,11 @@ typedef enum {
   NQS_EUNSUPPORTED = 5  /* combination not implemented */
 } nqs_status;
 
-/* Arithmetic type of the sampling copy (Table tab:precision; FP8 is an extension). */
+/* Arithmetic type of the sampling copy (Table tab:precision).  RBM: F32, BF16, F16.
+ * Dense ansatz: BF16, or NQS_FP8E4M3, an extension beyond the paper's formats: every
+ * weight matrix in E4M3 scaled by a per-layer power of two (max |W_l| s_l <= 448),
+ * E4M3 activations between layers, biases and w_out as in the BF16 copy; the sampler
+ * and nqs_logpsi run on that copy, nqs_local_energy on the BF16 copy. */
 typedef enum { NQS_F32 = 0, NQS_BF16 = 1, NQS_F16 = 2, NQS_FP8E4M3 = 3 } nqs_dtype;
 
 enum { NQS_RBM = 0, NQS_DENSE = 1 };
@@ -75,7 +79,8 @@ typedef struct {
  * BF16 or F16; TFIM only.
  * DENSE: n_layers (2..8) hidden widths in widths[] (host array, copied; multiples of
  * 16), a_1 = log cosh(W1 s + b1), a_l = tanh(W_l a_{l-1} + b_l), log psi = w_out . a_L
- * + b_out; sampling copy BF16 (layers >= 2 on the tensor cores, FP32 accumulation);
+ * + b_out; sampling copy BF16 or FP8 E4M3 (layers >= 2 on the tensor cores, FP32
+ * accumulation);
  * TFIM (single flips) or HEISENBERG (exchange moves).  nqs_logpsi_grad of a dense
  * context is FP32 from the FP32 rounding of the master and needs no workspace. */
 typedef struct {

@@ -13,6 +13,7 @@
 // the cached z0 of a source configuration plus the move's column difference, then
 // log cosh -> BF16 -> GEMM chain (dense_gemm.cu) -> log psi.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cmath>
@@ -33,6 +34,15 @@ __device__ __forceinline__ float log_cosh_f(float z) {
 __device__ __forceinline__ float log_cosh_fast(float z) {
   z = fabsf(z);
   return z + __logf(1.f + __expf(-2.f * z)) - LN2;
+}
+
+// Two adjacent activations of a layer's input row, in the activation type of the copy:
+// BF16 (the BF16 copy) or E4M3 (the FP8 copy).
+__device__ __forceinline__ void store_act2(__nv_bfloat16 *row, int k, float v0, float v1) {
+  *reinterpret_cast<__nv_bfloat162 *>(row + k) = __floats2bfloat162_rn(v0, v1);
+}
+__device__ __forceinline__ void store_act2(uint8_t *row, int k, float v0, float v1) {
+  *reinterpret_cast<uint16_t *>(row + k) = __nv_cvt_float2_to_fp8x2(make_float2(v0, v1), __NV_SATFINITE, __NV_E4M3);
 }
 
 // ------------------------------------------------------------------------------------
@@ -62,6 +72,49 @@ __global__ void dense_prepare_layer_kernel(const double *__restrict__ p, int64_t
       bl[n] = __bfloat162float(__double2bfloat16(p[off + total + n]));
       if (last) w_out[n] = __bfloat162float(__double2bfloat16(w_out_src[n]));
     }
+  }
+}
+
+// FP8 copy.  max |W_l| of each weight matrix (l = 0: W_0 [H0 x N] at 0; l >= 1 at its offset),
+// as FP32 bits (non-negative floats order as integers)
+__global__ void dense_wmax_kernel(const double *__restrict__ p, int64_t off, int64_t count, unsigned *wmax) {
+  float m = 0.f;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf((float)p[off + k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(wmax, __float_as_uint(m));
+}
+// s_l = the largest power of two with max |W_l| s_l <= 448 (the E4M3 maximum); 1 for W_l = 0
+__global__ void dense_scale8_kernel(const unsigned *wmax, int L, float *scale) {
+  const int l = threadIdx.x;
+  if (l >= L) return;
+  const float m = __uint_as_float(wmax[l]);
+  const float sc = m > 0.f ? exp2f(floorf(log2f(448.f / m))) : 1.f;
+  scale[l] = sc;
+  scale[L + l] = 1.f / sc;
+}
+__device__ __forceinline__ float e4m3_round(float v) {
+  const __nv_fp8_e4m3 q(v);  // round to nearest even, saturating
+  return (float)q;
+}
+// layer 0 of the FP8 copy: W1t8[i][j] = E4M3(W_0[j][i] s_0) / s_0 (FP32 values, site-major)
+__global__ void dense_prepare8_l0_kernel(const double *__restrict__ p, int N, int H0, const float *scale,
+                                         float *W1t8) {
+  const float s0 = scale[0];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < (int64_t)H0 * N; k += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(k / N), i = (int)(k % N);
+    W1t8[(int64_t)i * H0 + j] = e4m3_round((float)p[k] * s0) / s0;
+  }
+}
+// layer l >= 1: W_l [H x K] (flat at off) -> E4M3 of W_l s_l, [H][Kp8] (padding stays zero)
+__global__ void dense_prepare8_layer_kernel(const double *__restrict__ p, int64_t off, int H, int K, int Kp8,
+                                            const float *scale_l, uint8_t *Wl8) {
+  const float sl = *scale_l;
+  const int64_t total = (int64_t)H * K;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(k / K), kk = (int)(k % K);
+    Wl8[(int64_t)n * Kp8 + kk] = __nv_cvt_float_to_fp8((float)p[off + k] * sl, __NV_SATFINITE, __NV_E4M3);
   }
 }
 
@@ -130,7 +183,7 @@ struct A1Args {
   const float *z0;
   const float *W1t;
   const int2 *bonds;
-  __nv_bfloat16 *act;
+  void *act;  // BF16 or E4M3 rows (the kernel's activation type)
   int64_t R;
   int N, W, H0, Kp1, nconn, mode, exchange;
 };
@@ -154,6 +207,7 @@ __device__ __forceinline__ bool row_move(const A1Args &a, int64_t r, int64_t *sr
   return true;
 }
 
+template <typename TA>
 __global__ void dense_a1_kernel(const A1Args a) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -166,7 +220,7 @@ __global__ void dense_a1_kernel(const A1Args a) {
     const float *zr = a.z0 + src * a.H0;
     const float *wi = a.W1t + (int64_t)mv.i * a.H0;
     const float *wj = a.W1t + (int64_t)(mv.j < 0 ? 0 : mv.j) * a.H0;
-    __nv_bfloat16 *out = a.act + r * a.Kp1;
+    TA *out = static_cast<TA *>(a.act) + r * a.Kp1;
     for (int k = 2 * lane; k < a.H0; k += 64) {  // two units per lane per step (H0 even)
       float z0v = zr[k], z1v = zr[k + 1];
       if (moved) {
@@ -176,7 +230,7 @@ __global__ void dense_a1_kernel(const A1Args a) {
         z0v = fmaf(-2.f * si, d0, z0v);
         z1v = fmaf(-2.f * si, d1, z1v);
       }
-      *reinterpret_cast<__nv_bfloat162 *>(out + k) = __floats2bfloat162_rn(log_cosh_fast(z0v), log_cosh_fast(z1v));
+      store_act2(out, k, log_cosh_fast(z0v), log_cosh_fast(z1v));
     }
   }
 }
@@ -254,7 +308,7 @@ struct ProposeArgs {
   int32_t *prop;
   float *thr;
   float *lp;
-  __nv_bfloat16 *act;
+  void *act;  // BF16 or E4M3 rows (the kernel's activation type)
   const float *part;
   const float *b_out;
   int n_ranges;
@@ -271,7 +325,7 @@ struct ProposeArgs {
   uint32_t sweep_id, k0, k1;
 };
 
-template <int NJ>  // column block of 64 * NJ units held in registers, two per lane per j
+template <int NJ, typename TA>  // column block of 64 * NJ units held in registers, two per lane per j
 __global__ void __launch_bounds__(256, 4) dense_propose_kernel(const ProposeArgs a) {
   const int lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
@@ -358,7 +412,7 @@ __global__ void __launch_bounds__(256, 4) dense_propose_kernel(const ProposeArgs
     float *zr = a.z0 + c * a.H0;
     const float *pi = a.W1t + (int64_t)pb.x * a.H0, *pj = a.W1t + (int64_t)(pb.y < 0 ? 0 : pb.y) * a.H0;
     const float *ni = a.W1t + (int64_t)nb.x * a.H0, *nj = a.W1t + (int64_t)(nb.y < 0 ? 0 : nb.y) * a.H0;
-    __nv_bfloat16 *out = a.act + c * a.Kp1;
+    TA *out = static_cast<TA *>(a.act) + c * a.Kp1;
     const bool use_new = a.propose && moved;
     for (int kb = 0; kb < a.H0; kb += 64 * NJ) {
       // all loads of the block (z row, the two moves' weight differences) before any store
@@ -398,7 +452,7 @@ __global__ void __launch_bounds__(256, 4) dense_propose_kernel(const ProposeArgs
           }
           if (a.propose) {
             const float vx = fmaf(gn, dn[j].x, z[j].x), vy = fmaf(gn, dn[j].y, z[j].y);
-            *reinterpret_cast<__nv_bfloat162 *>(out + k) = __floats2bfloat162_rn(log_cosh_fast(vx), log_cosh_fast(vy));
+            store_act2(out, k, log_cosh_fast(vx), log_cosh_fast(vy));
           }
         }
       }
@@ -553,21 +607,27 @@ int grid_for(int64_t work, int per_block, int num_sms) {
 // (out == nullptr: leaves the last layer's partials in d_part and returns their range count).
 // With fewer row tiles than half the SMs each layer uses its split configuration (N-ranges
 // of half the width) so that more CTAs share the work.
+// f8: the FP8 copy's E4M3 activations, weights and scales.
 cudaError_t run_chain(const nqs_ctx *c, int64_t R, float *out, const float *b_out_dev, cudaStream_t s,
-                      int *n_ranges_out = nullptr) {
+                      int *n_ranges_out = nullptr, bool f8 = false) {
   int cur = 0;
   cudaError_t e;
   const bool split = (R + 127) / 128 < c->num_sms / 2;
   int n_ranges = 1;
   for (int l = 1; l < c->L; ++l) {
     const bool last = l == c->L - 1;
-    const int ld_out = last ? 0 : c->Kp[l + 1];
+    const std::vector<int> &Kp = f8 ? c->Kp8 : c->Kp;
+    const int ld_out = last ? 0 : Kp[l + 1];
     const bool sp = split && c->NRs[l] > 0;
     const int NR = sp ? c->NRs[l] : c->NR[l];
-    if ((e = dense_gemm(c, c->d_act[cur], (int)R, c->Kp[l], sp ? c->mBs0[l] : c->mB0[l], sp ? c->mBs1[l] : c->mB1[l],
-                        c->H[l], NR, sp ? c->p0s[l] : c->p0[l], sp ? c->p1s[l] : c->p1[l], last ? 1 : 0, c->d_bl[l],
-                        last ? c->d_wout : nullptr, last ? nullptr : c->d_act[cur ^ 1], ld_out,
-                        last ? c->d_part : nullptr, s)) != cudaSuccess)
+    const CUtensorMap &m0 = f8 ? (sp ? c->mBs0_8[l] : c->mB0_8[l]) : (sp ? c->mBs0[l] : c->mB0[l]);
+    const CUtensorMap &m1 = f8 ? (sp ? c->mBs1_8[l] : c->mB1_8[l]) : (sp ? c->mBs1[l] : c->mB1[l]);
+    const void *A = f8 ? (const void *)c->d_act8[cur] : (const void *)c->d_act[cur];
+    void *next = f8 ? (void *)c->d_act8[cur ^ 1] : (void *)c->d_act[cur ^ 1];
+    if ((e = dense_gemm(c, A, (int)R, Kp[l], m0, m1, c->H[l], NR, sp ? c->p0s[l] : c->p0[l],
+                        sp ? c->p1s[l] : c->p1[l], last ? 1 : 0, c->d_bl[l], last ? c->d_wout : nullptr,
+                        last ? nullptr : next, ld_out, last ? c->d_part : nullptr, s,
+                        f8 ? c->d_scale8 + c->L + l : nullptr)) != cudaSuccess)
       return e;
     if (last) n_ranges = (c->H[l] + NR - 1) / NR;
     cur ^= 1;
@@ -578,18 +638,18 @@ cudaError_t run_chain(const nqs_ctx *c, int64_t R, float *out, const float *b_ou
   return cudaGetLastError();
 }
 
-A1Args a1_args(const nqs_ctx *c, const uint32_t *cfg, int64_t R, int mode) {
+A1Args a1_args(const nqs_ctx *c, const uint32_t *cfg, int64_t R, int mode, bool f8 = false) {
   A1Args a;
   a.cfg = cfg;
   a.z0 = c->d_z1;
-  a.W1t = c->d_W1t;
+  a.W1t = f8 ? c->d_W1t8 : c->d_W1t;
   a.bonds = c->d_bonds;
-  a.act = c->d_act[0];
+  a.act = f8 ? (void *)c->d_act8[0] : (void *)c->d_act[0];
   a.R = R;
   a.N = c->N;
   a.W = c->W;
   a.H0 = c->H[0];
-  a.Kp1 = c->Kp[1];
+  a.Kp1 = f8 ? c->Kp8[1] : c->Kp[1];
   a.nconn = c->ham_kind == NQS_HEISENBERG ? c->n_bonds : c->N;
   a.mode = mode;
   a.exchange = c->ham_kind == NQS_HEISENBERG;
@@ -598,12 +658,13 @@ A1Args a1_args(const nqs_ctx *c, const uint32_t *cfg, int64_t R, int mode) {
 
 cudaError_t launch_propose(const nqs_ctx *c, const ProposeArgs &a, cudaStream_t s) {
   const dim3 grid = grid_for(a.C, 8, c->num_sms);
+  const bool f8 = c->dtype == NQS_FP8E4M3;
   if (a.H0 <= 128)
-    dense_propose_kernel<2><<<grid, 256, 0, s>>>(a);
+    f8 ? dense_propose_kernel<2, uint8_t><<<grid, 256, 0, s>>>(a) : dense_propose_kernel<2, __nv_bfloat16><<<grid, 256, 0, s>>>(a);
   else if (a.H0 <= 256)
-    dense_propose_kernel<4><<<grid, 256, 0, s>>>(a);
+    f8 ? dense_propose_kernel<4, uint8_t><<<grid, 256, 0, s>>>(a) : dense_propose_kernel<4, __nv_bfloat16><<<grid, 256, 0, s>>>(a);
   else
-    dense_propose_kernel<8><<<grid, 256, 0, s>>>(a);
+    f8 ? dense_propose_kernel<8, uint8_t><<<grid, 256, 0, s>>>(a) : dense_propose_kernel<8, __nv_bfloat16><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -615,13 +676,14 @@ bool dense_setup(nqs_ctx *c, const nqs_model_desc *m, std::string *why) {
     *why = "dense ansatz needs 2..8 hidden layers";
     return false;
   }
-  if (c->dtype != NQS_BF16) {
-    *why = "the dense ansatz is built for a BF16 sampling copy";
+  if (c->dtype != NQS_BF16 && c->dtype != NQS_FP8E4M3) {
+    *why = "the dense ansatz is built for BF16 and FP8 (E4M3) sampling copies";
     return false;
   }
   c->L = m->n_layers;
   c->H.assign(m->widths, m->widths + c->L);
   c->Kp.assign(c->L, 0);
+  c->Kp8.assign(c->L, 0);
   int64_t P = 0;
   int fan = c->N;
   for (int l = 0; l < c->L; ++l) {
@@ -629,7 +691,10 @@ bool dense_setup(nqs_ctx *c, const nqs_model_desc *m, std::string *why) {
       *why = "dense widths must be multiples of 16 in [16, 4096]";
       return false;
     }
-    if (l >= 1) c->Kp[l] = ((c->H[l - 1] + 63) / 64) * 64;
+    if (l >= 1) {
+      c->Kp[l] = ((c->H[l - 1] + 63) / 64) * 64;
+      c->Kp8[l] = ((c->H[l - 1] + 127) / 128) * 128;
+    }
     P += (int64_t)c->H[l] * fan + c->H[l];
     fan = c->H[l];
   }
@@ -665,12 +730,19 @@ void dense_free(nqs_ctx *c) {
     if (p) cudaFree(p);
   for (auto p : c->d_bl)
     if (p) cudaFree(p);
+  void *p8[] = {c->d_W1t8, c->d_scale8, c->d_wmax8, c->d_act8[0], c->d_act8[1]};
+  for (void *p : p8)
+    if (p) cudaFree(p);
+  for (auto p : c->d_Wl8)
+    if (p) cudaFree(p);
 }
 
 cudaError_t dense_alloc_rows(nqs_ctx *c, int64_t rows) {
-  void *old[] = {c->d_act[0], c->d_act[1], c->d_part, c->d_out, c->d_z1, c->d_lp, c->d_prop, c->d_thr};
+  void *old[] = {c->d_act[0], c->d_act[1], c->d_part, c->d_out, c->d_z1, c->d_lp, c->d_prop, c->d_thr,
+                 c->d_act8[0], c->d_act8[1]};
   for (void *p : old)
     if (p) cudaFree(p);
+  c->d_act8[0] = c->d_act8[1] = nullptr;
   int maxKp = 64, max_ranges = 1;
   for (int l = 1; l < c->L; ++l) {
     maxKp = std::max(maxKp, c->Kp[l]);
@@ -685,6 +757,14 @@ cudaError_t dense_alloc_rows(nqs_ctx *c, int64_t rows) {
       (e = cudaMalloc(&c->d_prop, (size_t)rows * 4)) || (e = cudaMalloc(&c->d_thr, (size_t)rows * 4)))
     return e;
   if ((e = cudaMemset(c->d_act[0], 0, act)) || (e = cudaMemset(c->d_act[1], 0, act))) return e;
+  if (c->dtype == NQS_FP8E4M3) {  // E4M3 rows; the padding columns stay zero
+    int maxKp8 = 128;
+    for (int l = 1; l < c->L; ++l) maxKp8 = std::max(maxKp8, c->Kp8[l]);
+    const size_t act8 = (size_t)rows * maxKp8;
+    if ((e = cudaMalloc(&c->d_act8[0], act8)) || (e = cudaMalloc(&c->d_act8[1], act8)) ||
+        (e = cudaMemset(c->d_act8[0], 0, act8)) || (e = cudaMemset(c->d_act8[1], 0, act8)))
+      return e;
+  }
   c->max_rows = rows;
   return cudaSuccess;
 }
@@ -714,6 +794,27 @@ cudaError_t dense_alloc_params(nqs_ctx *c) {
          !make_tmap_bf16_2d(&c->mBs1[l], c->d_Wl[l], c->H[l], c->Kp[l], c->p1s[l] ? c->p1s[l] : c->p0s[l])))
       return cudaErrorInvalidValue;
   }
+  if (c->dtype == NQS_FP8E4M3) {
+    c->d_Wl8.assign(c->L, nullptr);
+    c->mB0_8.resize(c->L);
+    c->mB1_8.resize(c->L);
+    c->mBs0_8.resize(c->L);
+    c->mBs1_8.resize(c->L);
+    if ((e = cudaMalloc(&c->d_W1t8, (size_t)c->N * c->H[0] * 4)) || (e = cudaMalloc(&c->d_scale8, 2 * c->L * 4)) ||
+        (e = cudaMalloc(&c->d_wmax8, c->L * 4)))
+      return e;
+    for (int l = 1; l < c->L; ++l) {
+      const size_t wbytes = (size_t)c->H[l] * c->Kp8[l];
+      if ((e = cudaMalloc(&c->d_Wl8[l], wbytes)) || (e = cudaMemset(c->d_Wl8[l], 0, wbytes))) return e;
+      if (!make_tmap_u8_2d(&c->mB0_8[l], c->d_Wl8[l], c->H[l], c->Kp8[l], c->p0[l]) ||
+          !make_tmap_u8_2d(&c->mB1_8[l], c->d_Wl8[l], c->H[l], c->Kp8[l], c->p1[l] ? c->p1[l] : c->p0[l]))
+        return cudaErrorInvalidValue;
+      if (c->NRs[l] &&
+          (!make_tmap_u8_2d(&c->mBs0_8[l], c->d_Wl8[l], c->H[l], c->Kp8[l], c->p0s[l]) ||
+           !make_tmap_u8_2d(&c->mBs1_8[l], c->d_Wl8[l], c->H[l], c->Kp8[l], c->p1s[l] ? c->p1s[l] : c->p0s[l])))
+        return cudaErrorInvalidValue;
+    }
+  }
   const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(256, (int64_t)(256u << 20) / (c->P * 4)));
   c->grad_chunk = chunk;
   if ((e = cudaMalloc(&c->d_grad_scratch, (size_t)chunk * c->P * 4))) return e;
@@ -736,22 +837,50 @@ cudaError_t dense_prepare(nqs_ctx *c, const double *params, cudaStream_t s) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     off += (int64_t)c->H[l] * K + c->H[l];
   }
+  if (c->dtype == NQS_FP8E4M3) {  // the FP8 copy: per-layer scales, then E4M3 weights
+    if ((e = cudaMemsetAsync(c->d_wmax8, 0, c->L * 4, s)) != cudaSuccess) return e;
+    int64_t o = 0;
+    for (int l = 0; l < c->L; ++l) {
+      const int64_t cnt = (int64_t)c->H[l] * (l == 0 ? c->N : c->H[l - 1]);
+      dense_wmax_kernel<<<grid_for(cnt, 256, c->num_sms), 256, 0, s>>>(params, o, cnt, c->d_wmax8 + l);
+      o += cnt + c->H[l];
+    }
+    dense_scale8_kernel<<<1, 32, 0, s>>>(c->d_wmax8, c->L, c->d_scale8);
+    dense_prepare8_l0_kernel<<<grid_for((int64_t)H0 * c->N, 256, c->num_sms), 256, 0, s>>>(params, c->N, H0, c->d_scale8,
+                                                                                         c->d_W1t8);
+    o = (int64_t)H0 * c->N + H0;
+    for (int l = 1; l < c->L; ++l) {
+      const int K = c->H[l - 1];
+      dense_prepare8_layer_kernel<<<grid_for((int64_t)c->H[l] * K, 256, c->num_sms), 256, 0, s>>>(
+          params, o, c->H[l], K, c->Kp8[l], c->d_scale8 + l, c->d_Wl8[l]);
+      o += (int64_t)c->H[l] * K + c->H[l];
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   // b_out (= master[P - 1]) is kept on the device right after w_out
   return cudaMemcpyAsync(c->d_wout + c->H[c->L - 1], c->d_master + (c->P - 1), sizeof(float), cudaMemcpyDeviceToDevice,
                          s);
 }
 
+// log psi of rows through the sampling copy (BF16, or the FP8 copy of an FP8 context)
+static cudaError_t logpsi_rows(const nqs_ctx *c, const uint32_t *cfg, int64_t R, float *out, cudaStream_t s) {
+  const bool f8 = c->dtype == NQS_FP8E4M3;
+  const float *b_out = c->d_wout + c->H[c->L - 1];
+  dense_z0_kernel<<<z0_grid(R, c->H[0], c->num_sms), Z0_COLS, 0, s>>>(cfg, R, f8 ? c->d_W1t8 : c->d_W1t, c->d_b1, c->N,
+                                                                     c->W, c->H[0], c->d_z1);
+  const A1Args a = a1_args(c, cfg, R, 0, f8);
+  if (f8) dense_a1_kernel<uint8_t><<<grid_for(R, 8, c->num_sms), 256, 0, s>>>(a);
+  else dense_a1_kernel<__nv_bfloat16><<<grid_for(R, 8, c->num_sms), 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return run_chain(c, R, out, b_out, s, nullptr, f8);
+}
+
 cudaError_t dense_logpsi(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *out, cudaStream_t s) {
   cudaError_t e;
-  const float *b_out = c->d_wout + c->H[c->L - 1];
   for (int64_t x0 = 0; x0 < n; x0 += c->max_rows) {
     const int64_t R = std::min<int64_t>(c->max_rows, n - x0);
-    dense_z0_kernel<<<z0_grid(R, c->H[0], c->num_sms), Z0_COLS, 0, s>>>(cfg + x0 * c->W, R, c->d_W1t, c->d_b1, c->N, c->W,
-                                                               c->H[0], c->d_z1);
-    A1Args a = a1_args(c, cfg + x0 * c->W, R, 0);
-    dense_a1_kernel<<<grid_for(R, 8, c->num_sms), 256, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = run_chain(c, R, out + x0, b_out, s)) != cudaSuccess) return e;
+    if ((e = logpsi_rows(c, cfg + x0 * c->W, R, out + x0, s)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -768,8 +897,8 @@ cudaError_t dense_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n,
     const uint32_t *cx = cfg + x0 * c->W;
     dense_z0_kernel<<<z0_grid(ns, c->H[0], c->num_sms), Z0_COLS, 0, s>>>(cx, ns, c->d_W1t, c->d_b1, c->N, c->W, c->H[0],
                                                                 c->d_z1);
-    A1Args a = a1_args(c, cx, ns * per, 1);
-    dense_a1_kernel<<<grid_for(ns * per, 8, c->num_sms), 256, 0, s>>>(a);
+    A1Args a = a1_args(c, cx, ns * per, 1);  // the BF16 copy (also for an FP8 context)
+    dense_a1_kernel<__nv_bfloat16><<<grid_for(ns * per, 8, c->num_sms), 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = run_chain(c, ns * per, c->d_out, b_out, s)) != cudaSuccess) return e;
     dense_eloc_combine_kernel<<<grid_for(ns, 8, c->num_sms), 256, 0, s>>>(
@@ -787,25 +916,18 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swee
   const float *b_out = c->d_wout + c->H[c->L - 1];
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   cudaError_t e;
-  auto refresh = [&]() -> cudaError_t {  // z0 and log psi of the chains from scratch
-    dense_z0_kernel<<<z0_grid(C, c->H[0], c->num_sms), Z0_COLS, 0, s>>>(state, C, c->d_W1t, c->d_b1, c->N, c->W, c->H[0],
-                                                               c->d_z1);
-    A1Args a = a1_args(c, state, C, 0);
-    dense_a1_kernel<<<grid_for(C, 8, c->num_sms), 256, 0, s>>>(a);
-    cudaError_t e2 = cudaGetLastError();
-    if (e2 != cudaSuccess) return e2;
-    return run_chain(c, C, c->d_lp, b_out, s);
-  };
+  const bool f8 = c->dtype == NQS_FP8E4M3;  // the sampler runs on the FP8 copy
+  auto refresh = [&]() -> cudaError_t { return logpsi_rows(c, state, C, c->d_lp, s); };  // z0, log psi from scratch
   if ((e = refresh()) != cudaSuccess) return e;
   ProposeArgs a;
   a.state = state;
   a.z0 = c->d_z1;
-  a.W1t = c->d_W1t;
+  a.W1t = f8 ? c->d_W1t8 : c->d_W1t;
   a.bonds = c->d_bonds;
   a.prop = c->d_prop;
   a.thr = c->d_thr;
   a.lp = c->d_lp;
-  a.act = c->d_act[0];
+  a.act = f8 ? (void *)c->d_act8[0] : (void *)c->d_act[0];
   a.part = c->d_part;
   a.b_out = b_out;
   a.n_ranges = 1;
@@ -818,7 +940,7 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swee
   a.N = c->N;
   a.W = c->W;
   a.H0 = c->H[0];
-  a.Kp1 = c->Kp[1];
+  a.Kp1 = f8 ? c->Kp8[1] : c->Kp[1];
   a.exchange = c->ham_kind == NQS_HEISENBERG;
   a.n_moves = a.exchange ? c->n_bonds : c->N;
   a.n_sweeps = n_sweeps;
@@ -836,7 +958,7 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swee
       if ((e = launch_propose(c, a, s)) != cudaSuccess) return e;
       if (a.decide) a.first = 0;
       a.emit_row = -1;
-      if ((e = run_chain(c, C, nullptr, b_out, s, &a.n_ranges)) != cudaSuccess) return e;
+      if ((e = run_chain(c, C, nullptr, b_out, s, &a.n_ranges, f8)) != cudaSuccess) return e;
       a.decide = 1;
       a.t_prev = t;
       a.p_prev = p;

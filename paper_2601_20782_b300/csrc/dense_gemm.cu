@@ -15,7 +15,13 @@
 // tanh is the MUFU tanh.approx (relative error ~2^-11, below the BF16 rounding of the
 // activations).  The CTA loops over row tiles; stage and accumulator hand-offs use
 // mbarriers, every wait bounded.
+//
+// F8 = true is the FP8 sampling copy: A and B in E4M3 (tcgen05.mma kind::f8f6f4, K = 32 per
+// instruction), B = W_l * s_l with a per-layer power-of-two scale s_l, so the epilogue takes
+// z = acc / s_l; STORE writes E4M3 activations.  A K-block is then 128 elements (still 128
+// bytes per row), so the shared-memory tiles and descriptors are those of the BF16 kernel.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -48,6 +54,28 @@ bool make_tmap_bf16_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool make_tmap_u8_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  using Fn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                          const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                          CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Fn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return false;
+    fn = reinterpret_cast<Fn>(p);
+  }
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols};
+  const cuuint32_t box[2] = {128, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 namespace {
 
 constexpr int GEMM_THREADS = 320;
@@ -63,13 +91,14 @@ struct GemmArgs {
   int R, Kpad, NR, p0, p1, n_ranges, N, mode;
   const float *bias;
   const float *w;
-  __nv_bfloat16 *out_act;
+  void *out_act;             // BF16 or (F8) E4M3 [R][ld_out]
+  const float *inv_scale;    // F8: 1 / s_l of the layer (device scalar)
   int ld_out;
   float *out_part;
   int *status;
 };
 
-template <int STAGES>
+template <int STAGES, bool F8>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     dense_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB0,
                       const __grid_constant__ CUtensorMap mB1, const GemmArgs g) {
@@ -116,7 +145,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   };
 
   const int n_tiles = (g.R + 127) / 128;
-  const int kb_n = g.Kpad / 64;
+  constexpr int KB = F8 ? 128 : 64;  // elements per 128-byte K-block
+  const int kb_n = g.Kpad / KB;
   const int range = blockIdx.y;
   const int nbase = range * g.NR;
 
@@ -129,15 +159,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           if (!wait(&empty[s], ((it / STAGES) & 1u) ^ 1u)) break;
           unsigned char *st = base + s * stage_bytes;
           mbar_expect_tx(&full[s], stage_bytes);
-          tma_load_2d(st, &mA, kb * 64, tile * 128, &full[s]);
-          tma_load_2d(st + a_bytes, &mB0, kb * 64, nbase, &full[s]);
-          if (g.p1) tma_load_2d(st + a_bytes + g.p0 * 128, &mB1, kb * 64, nbase + g.p0, &full[s]);
+          tma_load_2d(st, &mA, kb * KB, tile * 128, &full[s]);
+          tma_load_2d(st + a_bytes, &mB0, kb * KB, nbase, &full[s]);
+          if (g.p1) tma_load_2d(st + a_bytes + g.p0 * 128, &mB1, kb * KB, nbase + g.p0, &full[s]);
         }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
-      const uint32_t id0 = tc::idesc_bf16_f32(128, (uint32_t)g.p0);
-      const uint32_t id1 = tc::idesc_bf16_f32(128, (uint32_t)(g.p1 ? g.p1 : 16));
+      const uint32_t id0 = F8 ? tc::idesc_e4m3_f32(128, (uint32_t)g.p0) : tc::idesc_bf16_f32(128, (uint32_t)g.p0);
+      const uint32_t n1 = (uint32_t)(g.p1 ? g.p1 : 16);
+      const uint32_t id1 = F8 ? tc::idesc_e4m3_f32(128, n1) : tc::idesc_bf16_f32(128, n1);
       uint32_t it = 0, t = 0;
       for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x, ++t) {
         if (!wait(&tempty, (t & 1u) ^ 1u)) break;
@@ -155,10 +186,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             const uint64_t ad = tc::desc_sw128(smem_addr(st + kk * 32));
             const uint64_t b0 = tc::desc_sw128(smem_addr(st + a_bytes + kk * 32));
             const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-            tc::mma_bf16(tmem, ad, b0, id0, acc);
+            if constexpr (F8) tc::mma_f8(tmem, ad, b0, id0, acc);
+            else tc::mma_bf16(tmem, ad, b0, id0, acc);
             if (g.p1) {
               const uint64_t b1 = tc::desc_sw128(smem_addr(st + a_bytes + g.p0 * 128 + kk * 32));
-              tc::mma_bf16(tmem + (uint32_t)g.p0, ad, b1, id1, acc);
+              if constexpr (F8) tc::mma_f8(tmem + (uint32_t)g.p0, ad, b1, id1, acc);
+              else tc::mma_bf16(tmem + (uint32_t)g.p0, ad, b1, id1, acc);
             }
           }
           tc::mma_commit(&empty[s]);  // stage free once these products are done
@@ -170,6 +203,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   } else {  // ---- epilogue warps 2..9: row = TMEM lane, every other 32-column chunk
     const int q = warp & 3, half = (warp - 2) >> 2;
     const int row_in_tile = 32 * q + lane;
+    const float sc = F8 ? *g.inv_scale : 1.f;
     uint32_t t = 0;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
       if (!wait(&tfull, t & 1u)) break;
@@ -181,24 +215,41 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         tc::tmem_ld32(tc::tmem_lane_addr(tmem, 32 * q, c0), v);
         if (r < g.R) {
           if (g.mode == 0) {
-            uint32_t pk[16];
+            float a[32];
 #pragma unroll
-            for (int e = 0; e < 32; e += 2) {
+            for (int e = 0; e < 32; ++e) {
               const int n = nbase + c0 + e;  // columns of this CTA's range only
-              const float a0 = (n < g.N && c0 + e < g.NR) ? tanh_fast(v[e] + g.bias[n]) : 0.f;
-              const float a1 = (n + 1 < g.N && c0 + e + 1 < g.NR) ? tanh_fast(v[e + 1] + g.bias[n + 1]) : 0.f;
-              const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
-              pk[e / 2] = *reinterpret_cast<const uint32_t *>(&h);
+              a[e] = (n < g.N && c0 + e < g.NR) ? tanh_fast(fmaf(v[e], sc, g.bias[n])) : 0.f;
             }
             const int n0 = nbase + c0;
-            uint4 *dst = reinterpret_cast<uint4 *>(g.out_act + (int64_t)r * g.ld_out + n0);
-            const int nv = min(4, (min(g.N - n0, g.NR - c0) + 7) / 8);
-            for (int u = 0; u < nv; ++u) dst[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+            if constexpr (F8) {  // 32 E4M3 values: two 16-byte stores
+              uint32_t pk[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a[4 * u], a[4 * u + 1]), __NV_SATFINITE, __NV_E4M3);
+                const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(a[4 * u + 2], a[4 * u + 3]), __NV_SATFINITE, __NV_E4M3);
+                pk[u] = lo | (hi << 16);
+              }
+              uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint8_t *>(g.out_act) + (int64_t)r * g.ld_out + n0);
+              const int nv = min(2, (min(g.N - n0, g.NR - c0) + 15) / 16);
+              for (int u = 0; u < nv; ++u) dst[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+            } else {
+              uint32_t pk[16];
+#pragma unroll
+              for (int e = 0; e < 32; e += 2) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(a[e], a[e + 1]);
+                pk[e / 2] = *reinterpret_cast<const uint32_t *>(&h);
+              }
+              uint4 *dst =
+                  reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(g.out_act) + (int64_t)r * g.ld_out + n0);
+              const int nv = min(4, (min(g.N - n0, g.NR - c0) + 7) / 8);
+              for (int u = 0; u < nv; ++u) dst[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+            }
           } else {
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
               const int n = nbase + c0 + e;
-              if (n < g.N && c0 + e < g.NR) dot = fmaf(tanh_fast(v[e] + g.bias[n]), g.w[n], dot);
+              if (n < g.N && c0 + e < g.NR) dot = fmaf(tanh_fast(fmaf(v[e], sc, g.bias[n])), g.w[n], dot);
             }
           }
         }
@@ -222,12 +273,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 
 // Host side of one layer product.  Weight maps (box rows p0 / p1) are passed in; the
 // activation map is encoded here (its address and row count change per call).
-cudaError_t dense_gemm(const nqs_ctx *c, const __nv_bfloat16 *A, int R, int Kpad, const CUtensorMap &mB0,
+cudaError_t dense_gemm(const nqs_ctx *c, const void *A, int R, int Kpad, const CUtensorMap &mB0,
                        const CUtensorMap &mB1, int N, int NR, int p0, int p1, int mode, const float *bias,
-                       const float *w, __nv_bfloat16 *out_act, int ld_out, float *out_part, cudaStream_t s) {
+                       const float *w, void *out_act, int ld_out, float *out_part, cudaStream_t s,
+                       const float *inv_scale) {
   if (R <= 0) return cudaSuccess;
+  const bool f8 = inv_scale != nullptr;
   CUtensorMap mA;
-  if (!make_tmap_bf16_2d(&mA, A, (uint64_t)R, (uint64_t)Kpad, 128)) return cudaErrorInvalidValue;
+  if (!(f8 ? make_tmap_u8_2d(&mA, A, (uint64_t)R, (uint64_t)Kpad, 128)
+           : make_tmap_bf16_2d(&mA, A, (uint64_t)R, (uint64_t)Kpad, 128)))
+    return cudaErrorInvalidValue;
   GemmArgs g;
   g.R = R;
   g.Kpad = Kpad;
@@ -240,6 +295,7 @@ cudaError_t dense_gemm(const nqs_ctx *c, const __nv_bfloat16 *A, int R, int Kpad
   g.bias = bias;
   g.w = w;
   g.out_act = out_act;
+  g.inv_scale = inv_scale;
   g.ld_out = ld_out;
   g.out_part = out_part;
   g.status = c->d_status;
@@ -252,7 +308,7 @@ cudaError_t dense_gemm(const nqs_ctx *c, const __nv_bfloat16 *A, int R, int Kpad
   cudaError_t e;
 #define NQS_LAUNCH(S)                                                                                        \
   {                                                                                                          \
-    auto k = dense_gemm_kernel<S>;                                                                           \
+    auto k = f8 ? dense_gemm_kernel<S, true> : dense_gemm_kernel<S, false>;                                  \
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) != cudaSuccess) \
       return e;                                                                                              \
     k<<<grid, GEMM_THREADS, shm, s>>>(mA, mB0, mB1, g);                                                      \

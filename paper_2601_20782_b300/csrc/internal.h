@@ -77,6 +77,16 @@ struct nqs_ctx {
   float *d_lp = nullptr;           // [max_rows] log psi per sample / chain
   int32_t *d_prop = nullptr;       // [max_rows] proposed bond (or -1) per chain
   float *d_thr = nullptr;          // [max_rows] log u per chain
+  // FP8 sampling copy (dtype NQS_FP8E4M3; the BF16 copy above then serves the local energy):
+  // every weight matrix W_l in E4M3 scaled by a per-layer power of two s_l (max |W_l| s_l <= 448),
+  // biases and w_out as in the BF16 copy, E4M3 activations between layers.
+  std::vector<int> Kp8;             // layer l >= 1: padded input width, a multiple of 128
+  std::vector<uint8_t *> d_Wl8;     // layer l >= 1: [H[l]][Kp8[l]] E4M3 of W_l s_l
+  std::vector<CUtensorMap> mB0_8, mB1_8, mBs0_8, mBs1_8;
+  float *d_W1t8 = nullptr;          // [N][H0] FP32 values of E4M3(W_0 s_0) / s_0, site-major
+  float *d_scale8 = nullptr;        // [2 L]: s_l, then 1 / s_l
+  unsigned *d_wmax8 = nullptr;      // [L] max |W_l| (FP32 bits)
+  uint8_t *d_act8[2] = {nullptr, nullptr};  // E4M3 activations [max_rows][max Kp8]
   float *d_grad_scratch = nullptr; // O rows for the force when the caller gives none
   void *d_force_part = nullptr;    // FP64 force partials [slices][P]
   int grad_chunk = 0;
@@ -142,9 +152,13 @@ cudaError_t dense_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, 
                               const double *stats, double *force, cudaStream_t s);
 // dense_gemm.cu
 bool make_tmap_bf16_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);
-cudaError_t dense_gemm(const nqs_ctx *c, const __nv_bfloat16 *A, int R, int Kpad, const CUtensorMap &mB0,
+bool make_tmap_u8_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);
+// inv_scale == nullptr: BF16 operands and activations; otherwise E4M3 (FP8 sampling copy) with
+// z = acc * (*inv_scale)
+cudaError_t dense_gemm(const nqs_ctx *c, const void *A, int R, int Kpad, const CUtensorMap &mB0,
                        const CUtensorMap &mB1, int N, int NR, int p0, int p1, int mode, const float *bias,
-                       const float *w, __nv_bfloat16 *out_act, int ld_out, float *out_part, cudaStream_t s);
+                       const float *w, void *out_act, int ld_out, float *out_part, cudaStream_t s,
+                       const float *inv_scale = nullptr);
 
 // minsr.cu
 size_t minsr_workspace(const nqs_ctx *c, int64_t n);

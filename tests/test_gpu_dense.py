@@ -154,3 +154,117 @@ def test_dense_heisenberg_4x4_energy_against_enumeration():
     e_exact = pi @ eps_all
     # the GPU evaluates the BF16 copy with BF16 activations: allow 5 % of |E| for that bias
     assert abs(E - e_exact) <= 4 * err + 0.05 * abs(e_exact), (E, e_exact, err)
+
+
+# ---------------------------------------------------------------------------------------
+# FP8 (E4M3) sampling copy: weights W_l in E4M3 scaled by s_l = 2^floor(log2(448 / max|W_l|)),
+# biases and w_out as in the BF16 copy, E4M3 activations between layers; the local energy runs
+# on the BF16 copy.
+
+def _e4m3(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(torch.float8_e4m3fn).double().numpy()
+
+
+def _bf16(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(torch.bfloat16).double().numpy()
+
+
+def fp8_copy_logpsi(params, N, widths, s):
+    """log psi of the FP8 copy, written from its definition in FP64 with every quantisation
+    point of the copy (E4M3 weights with the per-layer power-of-two scale, E4M3 activations
+    into layers 1 .. L-1, BF16 biases and w_out)."""
+    m = Dense(N, widths, params)
+    Wq = []
+    for W in m.Ws:
+        sc = 2.0 ** np.floor(np.log2(448.0 / np.abs(W).max()))
+        Wq.append(_e4m3(W * sc) / sc)
+    a = np.asarray(s, dtype=np.float64)
+    L = len(widths)
+    for l in range(L):
+        z = a @ Wq[l].T + _bf16(m.bs[l])
+        a = np.logaddexp(z, -z) - np.log(2.0) if l == 0 else np.tanh(z)
+        if l < L - 1:
+            a = _e4m3(a)
+    return a @ _bf16(m.w_out) + m.b_out
+
+
+def make_fp8(Lx, Ly, widths, seed, ham="heisenberg", bias=0.1):
+    p = nqs()
+    N = Lx * Ly
+    params = dense_params(N, widths, seed, bias_sigma=bias)
+    ctx = p.Context(ham, Lx, Ly, J1=1.0, h=1.0, marshall=(ham == "heisenberg"), model="dense", widths=widths,
+                    dtype="fp8")
+    ctx.set_params(torch.from_numpy(params).cuda())
+    return ctx, params
+
+
+@pytest.mark.parametrize("Lx,Ly,widths", [(10, 10, (400, 400)), (4, 4, (64, 48)), (6, 6, (128, 96, 64)),
+                                          (16, 1, (1024, 512))])
+def test_dense_fp8_logpsi_matches_its_definition(Lx, Ly, widths):
+    """The FP8 copy's log psi against its FP64 definition with the same quantisation points.
+    What remains are single-ulp E4M3 flips of activations that lie within the MUFU
+    tanh / log cosh error of a rounding boundary (about 1 % of them); an error anywhere in the
+    quantised path (scale, byte order, K blocking) moves log psi by O(1)."""
+    ctx, params = make_fp8(Lx, Ly, widths, 3)
+    N = Lx * Ly
+    n = 1000
+    s = np.random.default_rng(1).choice([-1, 1], size=(n, N)).astype(np.int8)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx.logpsi(to_words_tensor(pack_np(s)), out)
+    got = out.cpu().numpy().astype(np.float64)
+    d = got - fp8_copy_logpsi(params, N, widths, s)
+    full = np.abs(got - Dense(N, widths, params).logpsi(s))
+    assert np.abs(d).mean() < 0.02 and np.abs(d).max() < 0.15, (np.abs(d).mean(), np.abs(d).max())
+    assert np.abs(d).mean() < 0.25 * full.mean(), (np.abs(d).mean(), full.mean())  # the quantisation is resolved
+
+
+def test_dense_fp8_sampler_targets_its_distribution():
+    """4 x 4 Heisenberg, FP8 copy: the sampled energy equals the exact expectation under the
+    FP8 copy's own distribution pi~ = |psi~|^2 (enumerated through the context's log psi over
+    the zero-magnetisation sector) within 4 sigma of the Monte Carlo error; each recorded
+    decision follows the MH rule on the sampler's increment; magnetisation stays zero."""
+    ctx, params = make_fp8(4, 4, (64, 48), 21, bias=0.2)
+    C, T, B = 2048, 40, 10
+    state = torch.zeros((C, 1), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, 5)
+    S = torch.zeros(((T - B) * C, 1), dtype=torch.int32, device="cuda")
+    ctx.sweep(state, T, B, 6, 0, S)
+    e = torch.empty((T - B) * C, dtype=torch.float32, device="cuda")
+    ctx.local_energy(S, e)
+    st = torch.empty(5, dtype=torch.float64, device="cuda")
+    ctx.stats(e, C, st)
+    E, var, err = st.cpu().numpy()[:3]
+    allc = exact.all_configs(16)
+    sec = allc[allc.sum(axis=1) == 0]
+    cfg = to_words_tensor(pack_np(sec.astype(np.int8)))
+    lp = torch.empty(len(sec), dtype=torch.float32, device="cuda")
+    ctx.logpsi(cfg, lp)
+    es = torch.empty(len(sec), dtype=torch.float32, device="cuda")
+    ctx.local_energy(cfg, es)
+    w = 2.0 * lp.cpu().numpy().astype(np.float64)
+    pi = np.exp(w - w.max())
+    pi /= pi.sum()
+    e_exact = pi @ es.cpu().numpy().astype(np.float64)
+    assert abs(E - e_exact) <= 4 * err, (E, e_exact, err)
+    assert np.all(unpack_np(words_from_tensor(state), 16).sum(axis=1) == 0)
+    # decisions against the recorded increments and the Philox thresholds
+    C2, T2 = 128, 2
+    st2 = torch.zeros((C2, 1), dtype=torch.int32, device="cuda")
+    ctx.init_chains(st2, 9)
+    bits = torch.zeros((C2, T2, 1), dtype=torch.int32, device="cuda")
+    delta = torch.zeros((C2, T2, 16), dtype=torch.float32, device="cuda")
+    ctx.sweep(st2, T2, T2 - 1, 10, 0, torch.zeros((C2, 1), dtype=torch.int32, device="cuda"), None, None,
+              accept_bits=bits, delta=delta)
+    acc = unpack_accept_bits(words_from_tensor(bits), 16)
+    d = delta.cpu().numpy().astype(np.float64)
+    from oracle.lattice import nn_bonds
+    from oracle.philox import sweep_draws
+    n_checked = 0
+    for t in range(T2):
+        _, u = sweep_draws(10, np.arange(C2), t, 16, len(nn_bonds(4, 4)))
+        with np.errstate(divide="ignore"):
+            margin = 2.0 * d[:, t, :] - np.log(u)
+        real = (d[:, t, :] != 0.0) & (np.abs(margin) > 1e-5)   # moved, outside FP32 rounding of log u
+        np.testing.assert_array_equal(acc[:, t, :][real], margin[real] > 0)
+        n_checked += int(real.sum())
+    assert n_checked > 1000, n_checked

@@ -248,13 +248,17 @@ def test_histogram_tv_against_exact_distribution_4x4():
     assert tv < max(floors) * 1.15, (tv, floors)
 
 
-@pytest.mark.parametrize("Lx,Ly,M,dtype", [(10, 10, 400, "f16"), (16, 1, 16, "f32"), (37, 1, 50, "f32")])
-def test_local_energy_chains_matches_per_sample(Lx, Ly, M, dtype):
+@pytest.mark.parametrize("Lx,Ly,M,dtype,refresh", [(10, 10, 400, "f16", 20), (10, 10, 400, "f32", 7),
+                                                   (16, 1, 16, "f32", 20), (37, 1, 50, "f32", 20)])
+def test_local_energy_chains_matches_per_sample(Lx, Ly, M, dtype, refresh):
     """Chain-ordered local energies (incremental theta over each chain's sweep-major samples,
-    rebuilt every 20 samples) equal the per-sample evaluation up to FP32 rounding."""
+    taken two at a time, rebuilt every `refresh` samples: an odd interval rebuilds at the
+    second sample of a pair; 45 samples leave a last pair of one) equal the per-sample
+    evaluation up to FP32 rounding."""
     p = nqs()
     N = Lx * Ly
     ctx = p.Context("tfim", Lx, Ly, J1=1.0, h=2.0, model="rbm", n_hidden=M, dtype=dtype)
+    ctx.set_option(p.OPT_REFRESH, refresh)
     ctx.set_params(torch.from_numpy(rbm_params(N, M, 0.1, 3)).cuda())
     C, K = 2500, 45                      # >= 16 chains per SM: the chain-ordered kernel runs
     state = torch.zeros((C, ctx.W), dtype=torch.int32, device="cuda")
