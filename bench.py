@@ -657,7 +657,8 @@ def run_workload(args, rank, world, dist):
     elif args.workload == "j1j2-dense":
         wl = workloads.J1J2_2D_16x16
         st = DenseStep(nqs, torch, dev, wl, C, T or 2, 1 if B is None else B,
-                       n_grad=args.grad_rows or wl.extra["minsr_samples"], minsr_lambda=1e-3)
+                       n_grad=args.grad_rows or wl.extra["minsr_samples"], minsr_lambda=1e-3,
+                       dtype="fp8" if args.dtype == "fp8" else "bf16")
     else:
         st = BatchStep(nqs, torch, dev)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
@@ -706,7 +707,8 @@ def run_workload(args, rank, world, dist):
             "dtype": {"tfim1d": "f32",
                       "heis2d-dense": ("fp8 e4m3 sampling (bf16 local energy, " if args.dtype == "fp8" else "bf16 (")
                       + "fp32 accumulate, fp32 layer-0 cache)",
-                      "j1j2-dense": "bf16 (fp32 accumulate, fp32 layer-0 cache)",
+                      "j1j2-dense": ("fp8 e4m3 sampling (bf16 local energy, " if args.dtype == "fp8" else "bf16 (")
+                      + "fp32 accumulate, fp32 layer-0 cache)",
                       "batched": "f16 sampling (f32 caches, accept, statistics)"}[args.workload],
             "data": "synthetic (seeded random-init networks, random initial spins)"}
     line.update(d)
@@ -793,8 +795,8 @@ def main():
                     help="tfim2d: the 10x10 alpha=4 RBM workload (default); the others measure the other "
                          "workloads' steps with the same line")
     args = ap.parse_args()
-    if args.dtype == "fp8" and args.workload != "heis2d-dense":
-        ap.error("--dtype fp8 is the dense ansatz's FP8 sampling copy (--workload heis2d-dense)")
+    if args.dtype == "fp8" and args.workload not in ("heis2d-dense", "j1j2-dense"):
+        ap.error("--dtype fp8 is the dense ansatz's FP8 sampling copy (--workload heis2d-dense or j1j2-dense)")
     world = int(os.environ.get("WORLD_SIZE", args.gpus))
     rank = int(os.environ.get("RANK", 0))
 

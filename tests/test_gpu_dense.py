@@ -40,7 +40,7 @@ def make(Lx, Ly, widths, seed, ham="heisenberg", bias=0.1, marshall=True, J2=0.0
 
 
 @pytest.mark.parametrize("Lx,Ly,widths", [(10, 10, (400, 400)), (4, 4, (64, 48)), (6, 6, (128, 96, 64)),
-                                          (16, 1, (1024, 512))])
+                                          (16, 1, (1024, 512)), (16, 16, (1024, 1024, 1024))])
 def test_dense_logpsi_matches_oracle(Lx, Ly, widths):
     ctx, _, m_r, _ = make(Lx, Ly, widths, 3)
     N = Lx * Ly
@@ -53,12 +53,15 @@ def test_dense_logpsi_matches_oracle(Lx, Ly, widths):
     assert np.abs(d).mean() < 0.01, np.abs(d).mean()
 
 
-@pytest.mark.parametrize("Lx,Ly,widths,ham,J2", [(10, 10, (400, 400), "heisenberg", 0.0), (4, 4, (64, 48), "heisenberg", 0.5),
-                                                 (6, 1, (32, 32), "tfim", 0.0)])
-def test_dense_local_energy_matches_oracle(Lx, Ly, widths, ham, J2):
+@pytest.mark.parametrize("Lx,Ly,widths,ham,J2,n", [(10, 10, (400, 400), "heisenberg", 0.0, 300),
+                                                   (4, 4, (64, 48), "heisenberg", 0.5, 300),
+                                                   (6, 1, (32, 32), "tfim", 0.0, 300),
+                                                   (16, 16, (1024, 1024, 1024), "heisenberg", 0.5, 6)])
+def test_dense_local_energy_matches_oracle(Lx, Ly, widths, ham, J2, n):
+    """(16 x 16, 1024^3, J2 = 0.5: the J1-J2 workload's network; up to 1024 connected
+    configurations per sample.)"""
     ctx, _, m_r, _ = make(Lx, Ly, widths, 5, ham=ham, J2=J2)
     N = Lx * Ly
-    n = 300
     rng = np.random.default_rng(2)
     if ham == "heisenberg":
         s = init_spins_balanced(9, np.arange(n), N)
@@ -199,7 +202,7 @@ def make_fp8(Lx, Ly, widths, seed, ham="heisenberg", bias=0.1):
 
 
 @pytest.mark.parametrize("Lx,Ly,widths", [(10, 10, (400, 400)), (4, 4, (64, 48)), (6, 6, (128, 96, 64)),
-                                          (16, 1, (1024, 512))])
+                                          (16, 1, (1024, 512)), (16, 16, (1024, 1024, 1024))])
 def test_dense_fp8_logpsi_matches_its_definition(Lx, Ly, widths):
     """The FP8 copy's log psi against its FP64 definition with the same quantisation points.
     What remains are single-ulp E4M3 flips of activations that lie within the MUFU

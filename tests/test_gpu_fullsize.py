@@ -110,3 +110,48 @@ def test_bench_workload_full_size_sampled_parity():
 
     Fref = _force_blocked(model, words, e, N)
     np.testing.assert_allclose(force.cpu().numpy(), Fref, rtol=0, atol=1e-5 * np.abs(Fref).max())
+
+
+def test_batched_48_instances_full_size_against_single_context():
+    """The batched workload as the bench runs it: 48 TFIM instances (N from 36 to 256, alpha
+    1 / 2 / 4, 256 to 8192 chains, FP16 copies), autotuned persistent sweep and the captured
+    step graph (sweep -> local energy -> statistics -> last-sweep O rows).  Four instances
+    (the largest lattice, the most chains, a 1D one and one drawn at random) are run again
+    through the single-context calls from the same initial chains: every output is
+    bit-identical."""
+    insts = workloads.batched_tfim_instances()
+    T, B = insts[0].n_sweeps, insts[0].burn_in
+    K = T - B
+    p = nqs()
+    z = lambda *sh, dt=torch.int32: torch.zeros(sh, dtype=dt, device="cuda")
+    items, twins = [], []
+    for w in insts:
+        lat = w.ham.lattice
+        N, M, C = lat.n_sites, w.n_hidden, w.n_chains
+        ctx = p.Context("tfim", lat.Lx, lat.Ly, J1=w.ham.J1, h=w.ham.h, model="rbm", n_hidden=M, dtype="f16")
+        ctx.set_params(torch.from_numpy(workloads.rbm_params(N, M, w.weight_sigma, w.seed)).cuda())
+        st = z(C, ctx.W)
+        ctx.init_chains(st, w.seed + 1)
+        twins.append(st.clone())
+        items.append(dict(ctx=ctx, state=st, seed=w.seed + 1, samples=z(K * C, ctx.W), n_accepted=z(C, dt=torch.int64),
+                          eloc=z(K * C, dt=torch.float32), stats=z(5, dt=torch.float64),
+                          O=z(C, ctx.P, dt=torch.float32), N=N, C=C, oned=lat.Ly == 1))
+    keys = ("ctx", "state", "seed", "samples", "n_accepted", "eloc", "stats", "O")
+    b = p.Batch([{k: it[k] for k in keys} for it in items], T, B, warps_per_cta=0)
+    b.step(0)
+    torch.cuda.synchronize()
+    picks = {max(range(48), key=lambda k: items[k]["N"]), max(range(48), key=lambda k: items[k]["C"]),
+             next(k for k in range(48) if items[k]["oned"]), int(np.random.default_rng(3).integers(0, 48))}
+    for k in sorted(picks):
+        it, tw = items[k], twins[k]
+        c, C, N = it["ctx"], it["C"], it["N"]
+        r = dict(samples=z(K * C, c.W), n_accepted=z(C, dt=torch.int64), eloc=z(K * C, dt=torch.float32),
+                 stats=z(5, dt=torch.float64), O=z(C, c.P, dt=torch.float32))
+        c.sweep(tw, T, B, it["seed"], 0, r["samples"], None, r["n_accepted"])
+        c.local_energy(r["samples"], r["eloc"])
+        c.stats(r["eloc"], C, r["stats"], r["n_accepted"], T * N)
+        c.logpsi_grad(r["samples"][(K - 1) * C:], r["O"])
+        torch.cuda.synchronize()
+        assert torch.equal(it["state"], tw), k
+        for key in ("samples", "n_accepted", "eloc", "stats", "O"):
+            assert torch.equal(it[key], r[key]), (k, key)
