@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                       const __grid_constant__ CUtensorMap mB1, const GemmArgs g) {
   extern __shared__ unsigned char smem_dyn[];
   __shared__ uint64_t full[STAGES], empty[STAGES], tfull, tempty;
+  __shared__ float s_bias[512], s_w[512];  // the range's bias and (DOT) w_out, read once
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const uint32_t raw = smem_addr(smem_dyn);
@@ -127,6 +128,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   if (warp == 1) {
     tc::tmem_alloc(&tmem_base, 512);
     tc::tmem_relinquish();
+  }
+  for (int c = tid; c < g.NR; c += GEMM_THREADS) {
+    const int n = blockIdx.y * g.NR + c;
+    s_bias[c] = n < g.N ? g.bias[n] : 0.f;
+    s_w[c] = (g.mode == 1 && n < g.N) ? g.w[n] : 0.f;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
               const int n = nbase + c0 + e;  // columns of this CTA's range only
-              a[e] = (n < g.N && c0 + e < g.NR) ? tanh_fast(fmaf(v[e], sc, g.bias[n])) : 0.f;
+              a[e] = (n < g.N && c0 + e < g.NR) ? tanh_fast(fmaf(v[e], sc, s_bias[c0 + e])) : 0.f;
             }
             const int n0 = nbase + c0;
             if constexpr (F8) {  // 32 E4M3 values: two 16-byte stores
@@ -249,7 +255,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
               const int n = nbase + c0 + e;
-              if (n < g.N && c0 + e < g.NR) dot = fmaf(tanh_fast(fmaf(v[e], sc, g.bias[n])), g.w[n], dot);
+              if (n < g.N && c0 + e < g.NR) dot = fmaf(tanh_fast(fmaf(v[e], sc, s_bias[c0 + e])), s_w[c0 + e], dot);
             }
           }
         }
@@ -300,7 +306,7 @@ cudaError_t dense_gemm(const nqs_ctx *c, const void *A, int R, int Kpad, const C
   g.out_part = out_part;
   g.status = c->d_status;
   const size_t stage = 16384 + (size_t)NR * 128;
-  const int stages = (int)std::min<size_t>(4, (size_t)(c->smem_optin - 2048) / stage);
+  const int stages = (int)std::min<size_t>(4, (size_t)(c->smem_optin - 2048 - 4096) / stage);  // - static bias / w_out
   const size_t shm = 1024 + stages * stage;
   const int n_tiles = (R + 127) / 128;
   const int gx = std::max(1, std::min(n_tiles, c->num_sms / g.n_ranges));
