@@ -44,8 +44,11 @@ struct nqs_batch {
   unsigned *d_next = nullptr;
   std::vector<float> tune_ms;  // autotuner: time of one sweep per candidate (variant, width)
   std::vector<int> tune_warps, tune_variant;
-  // step graph
+  // step graph: the capture stream plus BRANCHES streams on which the per-instance work forks
+  static constexpr int BRANCHES = 3;
   cudaStream_t cap = nullptr;
+  cudaStream_t branch[BRANCHES] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[BRANCHES] = {};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t sweep_node = nullptr;
@@ -302,24 +305,42 @@ nqs_status nqs_batch_sweep(nqs_batch *b, uint32_t sweep_offset, nqs_stream strea
   return e == cudaSuccess ? NQS_OK : bcuda(b, e, "nqs_batch_sweep");
 }
 
-// The step graph: sweep (one launch) -> per instance local energies, statistics, O rows.
+// The step graph: sweep (one launch) -> per instance local energies, statistics, O rows.  The
+// instances' chains of kernels are independent: they fork over the capture stream and the
+// branch streams (instance k on lane k mod (BRANCHES + 1), each instance's kernels in order),
+// so that one instance's kernels fill the SMs another's tail leaves idle; the lanes join
+// before the graph ends.
 static cudaError_t capture_step(nqs_batch *b) {
   cudaError_t e;
   if (!b->cap && (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  for (int j = 0; j < nqs_batch::BRANCHES; ++j)
+    if (!b->branch[j] && ((e = cudaStreamCreateWithFlags(&b->branch[j], cudaStreamNonBlocking)) != cudaSuccess ||
+                          (e = cudaEventCreateWithFlags(&b->join_ev[j], cudaEventDisableTiming)) != cudaSuccess))
+      return e;
+  if (!b->fork_ev && (e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming)) != cudaSuccess) return e;
   if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
   b->graph_params = params_for(b, 0, b->n_sweeps, b->burn_in);
   cudaError_t le = launch_sweep(b, b->graph_params, b->cap);
+  if (le == cudaSuccess) le = cudaEventRecord(b->fork_ev, b->cap);
+  for (int j = 0; j < nqs_batch::BRANCHES && le == cudaSuccess; ++j) le = cudaStreamWaitEvent(b->branch[j], b->fork_ev, 0);
   const int64_t K = b->n_sweeps - b->burn_in;
   for (size_t k = 0; k < b->items.size() && le == cudaSuccess; ++k) {
     const nqs_batch_item &it = b->items[k];
     const nqs_ctx *c = it.ctx;
     const int64_t S = K * it.n_chains;
-    if (it.eloc && it.samples && S > 0) le = nqs::rbm_local_energy(c, it.samples, S, it.eloc, b->cap);
+    const int lane = (int)(k % (nqs_batch::BRANCHES + 1));
+    cudaStream_t st = lane == 0 ? b->cap : b->branch[lane - 1];
+    if (it.eloc && it.samples && S > 0) le = nqs::rbm_local_energy(c, it.samples, S, it.eloc, st);
     if (le == cudaSuccess && it.stats && it.eloc && it.samples && S > 0)
-      le = nqs::energy_stats(c, it.eloc, S, it.n_chains, it.n_accepted, (int64_t)b->n_sweeps * c->N, it.stats, b->cap);
+      le = nqs::energy_stats(c, it.eloc, S, it.n_chains, it.n_accepted, (int64_t)b->n_sweeps * c->N, it.stats, st);
     if (le == cudaSuccess && it.O && it.samples && K > 0)
       le = nqs::rbm_logpsi_grad(c, it.samples + (size_t)(K - 1) * it.n_chains * c->W, it.n_chains, it.O, nullptr,
-                                nullptr, nullptr, nullptr, b->cap);
+                                nullptr, nullptr, nullptr, st);
+  }
+  for (int j = 0; j < nqs_batch::BRANCHES; ++j) {  // join every lane, also after an error, so the capture can end
+    cudaError_t je = cudaEventRecord(b->join_ev[j], b->branch[j]);
+    if (je == cudaSuccess) je = cudaStreamWaitEvent(b->cap, b->join_ev[j], 0);
+    if (le == cudaSuccess) le = je;
   }
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(b->cap, &g);
@@ -388,6 +409,11 @@ void nqs_batch_destroy(nqs_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int j = 0; j < nqs_batch::BRANCHES; ++j) {
+    if (b->branch[j]) cudaStreamDestroy(b->branch[j]);
+    if (b->join_ev[j]) cudaEventDestroy(b->join_ev[j]);
+  }
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   if (b->d_inst) cudaFree(b->d_inst);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_next) cudaFree(b->d_next);
