@@ -212,18 +212,17 @@ nqs_status nqs_batch_create(nqs_batch **out, const nqs_batch_item *items, int32_
     in.p.k1 = (uint32_t)(items[k].seed >> 32);
   }
   b->table_cap = (b->table_cap + 127u) & ~127u;
-  cudaError_t e;
   const int shm = (int)(b->table_cap + b->ak_cap);
-  if ((e = cudaSetDevice(b->device)) != cudaSuccess || (e = cudaMalloc(&b->d_next, 16)) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_inst, n_items * sizeof(nqs::BatchInst))) != cudaSuccess) {
+  if (cudaSetDevice(b->device) != cudaSuccess || cudaMalloc(&b->d_next, 16) != cudaSuccess ||
+      cudaMalloc(&b->d_inst, n_items * sizeof(nqs::BatchInst)) != cudaSuccess) {
     nqs_batch_destroy(b);
     return NQS_ECUDA;
   }
   const std::vector<int> variants = b->dtype == NQS_F16 ? std::vector<int>{1, 2} : std::vector<int>{0};
   for (int v : variants) {  // CTA width limit of each variant from its register use
     cudaFuncAttributes fa;
-    if ((e = cudaFuncSetAttribute(kernel_for(v), cudaFuncAttributeMaxDynamicSharedMemorySize, shm)) != cudaSuccess ||
-        (e = cudaFuncGetAttributes(&fa, kernel_for(v))) != cudaSuccess) {
+    if (cudaFuncSetAttribute(kernel_for(v), cudaFuncAttributeMaxDynamicSharedMemorySize, shm) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kernel_for(v)) != cudaSuccess) {
       nqs_batch_destroy(b);
       return NQS_ECUDA;
     }
@@ -288,7 +287,7 @@ nqs_status nqs_batch_create(nqs_batch **out, const nqs_batch_item *items, int32_
     b->warps = best_w;
   }
   b->max_warps = b->max_warps_v[b->variant];
-  if ((e = build_items(b, b->warps)) != cudaSuccess || (e = upload_instances(b, true, nullptr)) != cudaSuccess) {
+  if (build_items(b, b->warps) != cudaSuccess || upload_instances(b, true, nullptr) != cudaSuccess) {
     nqs_batch_destroy(b);
     return NQS_ECUDA;
   }
