@@ -33,7 +33,7 @@ METRIC = "MH proposals/sec and local-energy samples/sec on 1 B300, mixed vs FP32
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of the sweep kernel
 # (16384 chains x 500 sweeps of this workload), per sampling copy, for the kernel as built;
 # a copy without an entry reports None.
-SWEEP_TRAFFIC_BYTES = {"f16": 77.5e6}   # 2.4 MB read + 74.9 MB written
+SWEEP_TRAFFIC_BYTES = {"f16": 77.5e6}   # 2.38 MB read + 75.11 MB written
 WL = workloads.TFIM_2D_10x10
 
 
