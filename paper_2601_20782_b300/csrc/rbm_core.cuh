@@ -147,6 +147,18 @@ __device__ __forceinline__ void sigmoid_pair(float th, float &lam, float &mu) {
   mu = th >= 0.f ? q : p;
 }
 
+// The same pair from the MUFU forms: e^{-2|th|} as 2^{-2|th| log2 e} and the reciprocal by
+// rcp.approx.  The rounding of the exponent's argument puts a relative error of at most
+// 2|th| 2^-24 (plus a few ulp) on the smaller entry, e^{-2|th|} / (1 + e^{-2|th|}); the
+// larger is within a few ulp.  Used where the pairs are rebuilt for every sample (chain-ordered local energy).
+__device__ __forceinline__ void sigmoid_pair_fast(float th, float &lam, float &mu) {
+  const float e = ex2_approx(-2.8853900817779268f * fabsf(th));
+  const float p = rcp_approx(1.f + e);
+  const float q = e * p;
+  lam = th >= 0.f ? p : q;
+  mu = th >= 0.f ? q : p;
+}
+
 template <int L, int E>
 __device__ __forceinline__ void compute_theta(float2 (&th)[Lay<L, E>::H], uint32_t sw, const float *__restrict__ Wt,
                                               const float *__restrict__ b, int N, int W, int M_pad, int gl) {
@@ -441,8 +453,8 @@ struct ChainCache {
   __device__ __forceinline__ void from_theta(const float2 (&th)[LY::H]) {
 #pragma unroll
     for (int k = 0; k < LY::H; ++k) {
-      sigmoid_pair(th[k].x, lam[k].x, mu[k].x);
-      sigmoid_pair(th[k].y, lam[k].y, mu[k].y);
+      sigmoid_pair_fast(th[k].x, lam[k].x, mu[k].x);
+      sigmoid_pair_fast(th[k].y, lam[k].y, mu[k].y);
     }
     if constexpr (LP) make_shadows<LY::H, TT>(lam, mu, lh, mh);
     ls = 0.f;
