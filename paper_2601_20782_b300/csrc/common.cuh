@@ -10,6 +10,7 @@ constexpr uint32_t FULL_MASK = 0xffffffffu;
 constexpr uint32_t TAG_SWEEP = 0x53574550u;  // "SWEP"
 constexpr uint32_t TAG_INIT = 0x494E4954u;   // "INIT"
 constexpr float LN2F = 0.693147180559945309f;
+constexpr float LOG2EF = 1.442695040888963407f;  // 1 / ln 2
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64-bit
 // products by 0xD2511F53 / 0xCD9E8D57, a swap and an xor with the round key;

@@ -767,7 +767,9 @@ __device__ __forceinline__ float tfim_eloc_value(const ChainCache<L, E, TT> &cac
       } else if ((gl & 3) == 0 && i < N) {
         const bool up = (word >> (i & 31)) & 1u;
         const float2 ak = saK[i];
-        off += expf(2.f * (ak.y - (up ? ak.x : -ak.x)) + (t - cache.ls) * LN2F);
+        // e^{Delta} as 2^{Delta / ln 2} (ex2.approx: the argument's rounding adds at most
+        // |Delta| 2^-24 relative, a few ulp beyond)
+        off += ex2_approx(2.f * LOG2EF * (ak.y - (up ? ak.x : -ak.x)) + (t - cache.ls));
       }
     }
     off = group_allsum<L>(off);
