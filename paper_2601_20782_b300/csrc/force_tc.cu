@@ -17,15 +17,14 @@
 // rounded away against the large running sum.
 //
 // The block is warp-specialised so that staging, the tensor core and the epilogue overlap:
-//   warp 0 (one thread)  issues GEMM1 of tile t, then GEMM2 of tile t - 1;
-//   warps 4-7            stage the spin tile (thread x: row x) from the packed configurations,
-//                        one byte of spins at a time through a 256-entry table of BF16 +-1,
-//                        up to three tiles ahead;
-//   warps 8-15           read theta from TMEM, form the three a-terms in registers, store them
-//                        once GEMM2 of the previous tile has read its terms, and every DRAIN
-//                        tiles add the accumulators into the block's FP64 slice of the workspace
-//                        (rows chunk * P ...), which force_reduce_kernel then sums over chunks
-//                        in a fixed order.
+//   warp 16 (one thread) issues GEMM1 of tile t, then GEMM2 of tile t - 1;
+//   warps 0-15 (workers) read theta from TMEM (lanes 32 (w % 4) .., units 16 (w / 4) ..), form
+//                        the three a-terms in registers, store them once GEMM2 of the previous
+//                        tile has read its terms, then stage their own row's part of the spin
+//                        tile two tiles ahead (one byte of spins per 16-byte chunk through a
+//                        256-entry table of BF16 +-1), and every DRAIN tiles add the accumulators
+//                        into the block's FP64 slice of the workspace (rows chunk * P ...), which
+//                        force_reduce_kernel then sums over chunks in a fixed order.
 // Buffers: three spin tiles and one set of a-terms in shared memory; theta and two accumulator
 // pairs (one drained while the other accumulates) in TMEM; mbarriers hand each buffer between the
 // roles.  Every wait is bounded: a wait that gives up records STATUS_TIMEOUT and every role
@@ -41,7 +40,9 @@
 namespace nqs {
 namespace {
 
-constexpr int FTC_THREADS = 512;
+constexpr int FTC_WORKERS = 16;                  // warps 0-15: epilogue + spin tiles; warp 16: MMA
+constexpr int FTC_THREADS = 32 * (FTC_WORKERS + 1);
+constexpr int FTC_NW = 32 * FTC_WORKERS;         // worker threads
 constexpr int FTC_HT = 64;       // hidden units per block
 constexpr int FTC_NS = 3;        // spin tiles in flight
 constexpr int FTC_DRAIN = 16;    // tiles per FP32 accumulation period before the FP64 drain
@@ -183,22 +184,22 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
   }
   if (tid == 0) {
     for (int b = 0; b < FTC_NS; ++b) {
-      mbar_init(&spin_full[b], 128);
+      mbar_init(&spin_full[b], FTC_NW);
       mbar_init(&spin_free[b], 1);
     }
     mbar_init(&theta_full, 1);
-    mbar_init(&theta_empty, 256);
-    mbar_init(&a_full, 256);
+    mbar_init(&theta_empty, FTC_NW);
+    mbar_init(&a_full, FTC_NW);
     mbar_init(&a_free, 1);
     for (int d = 0; d < 2; ++d) {
       mbar_init(&g_full[d], 1);
-      mbar_init(&g_empty[d], 256);
+      mbar_init(&g_empty[d], FTC_NW);
     }
     mbar_init(&fin_bar, 1);
     fence_mbar_init();
     abort_flag = 0;
   }
-  if (warp == 0) {
+  if (warp == FTC_WORKERS) {
     tc::tmem_alloc(&tmem_base, 512);
     tc::tmem_relinquish();
   }
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
   // warp-uniform form (for roles that go on to warp-collective tcgen05.ld)
   auto wait_warp = [&](uint64_t *bar, uint32_t parity) -> bool { return __all_sync(FULL_MASK, wait(bar, parity)); };
 
-  if (warp == 0) {
+  if (warp == FTC_WORKERS) {
     // ================================ MMA issuer ===================================
     if (lane == 0 && T > 0) {
       const uint32_t id1 = tc::idesc_bf16_f32(128, 3 * FTC_HT);
@@ -274,30 +275,33 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
       mbar_wait_bounded(&fin_bar, 0, FTC_POLLS);
     }
     __syncwarp();
-  } else if (warp >= 4 && warp < 8) {
-    // ============================= spin-tile producer ================================
-    const int x = tid - 128;  // row of the tile
-    // the packed row of tile t (zeros past the chunk), loaded one tile ahead of its use
-    auto load_row = [&](int t, uint32_t (&wd)[4]) {
+  } else {
+    // =========================== workers: epilogue + spin tiles ===========================
+    // Warp w: TMEM lanes (rows) 32 q .. 32 q + 31 with q = w % 4, hidden units 16 g .. 16 g + 15
+    // and spin chunks 4 g .. 4 g + 3 (sites 32 g .. 32 g + 31: packed word g of the row) with
+    // g = w / 4.  A thread stages its own row's four chunks of tile t + 2 after storing the
+    // a-terms of tile t.
+    const int q = warp & 3, g = warp >> 2;
+    const int x = 32 * q + lane;
+    const double E = p.stats[0];
+    const bool has_m = j0 <= M && M < j0 + FTC_HT;
+    double *out = p.ws + (int64_t)chunk * p.P;
+    int drains = 0;
+    auto load_word = [&](int t) -> uint32_t {
       const int64_t r = r0 + (int64_t)t * 128 + x;
-#pragma unroll
-      for (int w = 0; w < 4; ++w) wd[w] = (r < r1 && w < p.W) ? p.cfg[r * p.W + w] : 0u;
+      return (r < r1 && g < p.W) ? p.cfg[r * p.W + g] : 0u;
     };
-    uint32_t next[4];
-    if (T > 0) load_row(0, next);
-    for (int t = 0; t < T; ++t) {
-      const int sb_ = t % FTC_NS;
+    // chunks 4 g .. 4 g + 3 of row x of tile t (BF16 +-1; site N is +1, sites beyond it 0)
+    auto produce = [&](int t, uint32_t word) {
+      unsigned char *spins = sS + (t % FTC_NS) * SPIN_BYTES;
       const bool live = r0 + (int64_t)t * 128 + x < r1;
-      const uint32_t words[4] = {next[0], next[1], next[2], next[3]};
-      if (t + 1 < T) load_row(t + 1, next);
-      if (t >= FTC_NS && !wait(&spin_free[sb_], ((t - FTC_NS) / FTC_NS) & 1)) break;
-      unsigned char *spins = sS + sb_ * SPIN_BYTES;
 #pragma unroll
-      for (int c = 0; c < FTC_KP / 8; ++c) {  // chunk c holds sites 8c .. 8c + 7
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = 4 * g + cc;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (live && 8 * c <= N) {
-          v = lut[(words[c >> 2] >> (8 * (c & 3))) & 0xFFu];
-          if (8 * c + 8 > N) {  // the chunk of site N: +1 there, 0 beyond
+          v = lut[(word >> (8 * cc)) & 0xFFu];
+          if (8 * c + 8 > N) {  // the chunk of site N
             uint32_t *e = &v.x;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -312,33 +316,25 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
         *reinterpret_cast<uint4 *>(spins + (c / 8) * 16384 + sw_chunk(x, c & 7)) = v;
       }
       tc::fence_proxy_async_smem();
-      mbar_arrive(&spin_full[sb_]);
-    }
-  } else if (warp >= 8) {
-    // ================================== epilogue =====================================
-    const int q = warp & 3, h = (warp - 8) >> 2;  // TMEM lanes 32 q .. 32 q + 31; units 32 h .. 32 h + 31
-    const int x = 32 * q + lane;
-    const double E = p.stats[0];
-    const bool has_m = j0 <= M && M < j0 + FTC_HT;
-    double *out = p.ws + (int64_t)chunk * p.P;
-    int drains = 0;
+      mbar_arrive(&spin_full[t % FTC_NS]);
+    };
     // Adds the accumulator pair of period per into the FP64 slice (zero_only: writes zeros).
     auto drain = [&](int per, bool zero_only) -> bool {
       const int d = per & 1;
-      float v[32], w[32];
+      float v[16], w[16];
       if (zero_only) {
-        for (int t = 0; t < 32; ++t) v[t] = w[t] = 0.f;
+        for (int t = 0; t < 16; ++t) v[t] = w[t] = 0.f;
       } else {
         if (!wait_warp(&g_full[d], (per >> 1) & 1)) return false;
         tc::fence_after_sync();
-        tc::tmem_ld32(tc::tmem_lane_addr(tm + TM_G + 128 * d, 32 * q, 32 * h), v);
-        tc::tmem_ld32(tc::tmem_lane_addr(tm + TM_G + 128 * d + FTC_HT, 32 * q, 32 * h), w);
+        tc::tmem_ld16(tc::tmem_lane_addr(tm + TM_G + 128 * d, 32 * q, 16 * g), v);
+        tc::tmem_ld16(tc::tmem_lane_addr(tm + TM_G + 128 * d + FTC_HT, 32 * q, 16 * g), w);
         tc::fence_before_sync();
         mbar_arrive(&g_empty[d]);
       }
       const int i = x;  // TMEM lane = site
-      for (int t = 0; t < 32; ++t) {
-        const int j = j0 + 32 * h + t;
+      for (int t = 0; t < 16; ++t) {
+        const int j = j0 + 16 * g + t;
         int64_t k = -1;
         if (j < M && i < N) k = N + M + (int64_t)j * N + i;  // W entries
         else if (j < M && i == N) k = N + j;                  // b entries
@@ -352,35 +348,35 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
       const int64_t r = r0 + (int64_t)t * 128 + x;
       return r < r1 ? (float)((double)p.eloc[r] - E) : 0.f;
     };
+    for (int t0 = 0; t0 < 2 && t0 < T; ++t0) produce(t0, load_word(t0));
     float e_next = T > 0 ? eval(0) : 0.f;
     bool ok = true;
     for (int t = 0; t < T && ok; ++t) {
       const float e = e_next;
       if (t + 1 < T) e_next = eval(t + 1);
+      const uint32_t word2 = t + 2 < T ? load_word(t + 2) : 0u;  // used after this tile's epilogue
       if (!wait_warp(&theta_full, t & 1)) { ok = false; break; }
       tc::fence_after_sync();
-      float2 th[16];  // theta of units 32 h + 2 u, + 1 (bias included through GEMM1)
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      float2 th[8];  // theta of units 16 g + 2 u, + 1 (bias included through GEMM1)
+      {
         float vh[16], vm[16], vl[16];
-        const uint32_t col = 32 * h + 16 * r;
-        tc::tmem_ld16(tc::tmem_lane_addr(tm, 32 * q, col), vh);
-        tc::tmem_ld16(tc::tmem_lane_addr(tm, 32 * q, FTC_HT + col), vm);
-        tc::tmem_ld16(tc::tmem_lane_addr(tm, 32 * q, 2 * FTC_HT + col), vl);
+        tc::tmem_ld16(tc::tmem_lane_addr(tm, 32 * q, 16 * g), vh);
+        tc::tmem_ld16(tc::tmem_lane_addr(tm, 32 * q, FTC_HT + 16 * g), vm);
+        tc::tmem_ld16(tc::tmem_lane_addr(tm, 32 * q, 2 * FTC_HT + 16 * g), vl);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const float2 hm = ffma2(make_float2(vh[2 * u], vh[2 * u + 1]), f2(1.f), make_float2(vm[2 * u], vm[2 * u + 1]));
-          th[8 * r + u] = ffma2(hm, f2(1.f), make_float2(vl[2 * u], vl[2 * u + 1]));
+          th[u] = ffma2(hm, f2(1.f), make_float2(vl[2 * u], vl[2 * u + 1]));
         }
       }
       tc::fence_before_sync();
       mbar_arrive(&theta_empty);
-      uint32_t ph[16], pm[16], pl[16];
+      uint32_t ph[8], pm[8], pl[8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
+      for (int u = 0; u < 8; ++u) {
         float2 a = fmul2(tanh_epi2(th[u]), f2(e));
         if (has_m) {  // the block holding unit M: a = eloc - E there (a-entries)
-          const int j = j0 + 32 * h + 2 * u;
+          const int j = j0 + 16 * g + 2 * u;
           if (j == M) a.x = e;
           if (j + 1 == M) a.y = e;
         }
@@ -389,8 +385,8 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
       // the terms of tile t - 1 have been read by its GEMM2 once a_free completes
       if (t >= 1 && !wait_warp(&a_free, (t - 1) & 1)) { ok = false; break; }
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {  // 16-byte chunk 4 h + cc: units 32 h + 8 cc .. + 7
-        const uint32_t off = sw_chunk(x, 4 * h + cc);
+      for (int cc = 0; cc < 2; ++cc) {  // 16-byte chunk 2 g + cc: units 16 g + 8 cc .. + 7
+        const uint32_t off = sw_chunk(x, 2 * g + cc);
         *reinterpret_cast<uint4 *>(sA + off) = make_uint4(ph[4 * cc], ph[4 * cc + 1], ph[4 * cc + 2], ph[4 * cc + 3]);
         *reinterpret_cast<uint4 *>(sA + ATERM_BYTES + off) =
             make_uint4(pm[4 * cc], pm[4 * cc + 1], pm[4 * cc + 2], pm[4 * cc + 3]);
@@ -399,6 +395,10 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
       }
       tc::fence_proxy_async_smem();
       mbar_arrive(&a_full);
+      if (t + 2 < T) {  // spin buffer of tile t + 2, last read by GEMM2 of tile t - 1
+        if (t >= 1 && !wait(&spin_free[(t + 2) % FTC_NS], ((t - 1) / FTC_NS) & 1)) { ok = false; break; }
+        produce(t + 2, word2);
+      }
       if (t >= 1 && (t - 1) % FTC_DRAIN == FTC_DRAIN - 1) ok = drain((t - 1) / FTC_DRAIN, false);
     }
     if (ok) {
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem_base, 512);
+  if (warp == FTC_WORKERS) tc::tmem_dealloc(tmem_base, 512);
 }
 
 }  // namespace
