@@ -13,4 +13,10 @@ Pins (tests/test_oracle_*.py) tie each part to something other than itself:
 cuRAND's host Philox4x32-10, the free-fermion closed form of the 1D TFIM,
 exact diagonalisation, exact MH transition matrices, product-state closed
 forms, central finite differences and numerical quadrature.
+
+``complex_rbm`` is the oracle of the complex-parameter RBM (App. G as written, with
+complex a, b, W): its pins are the reduction to the real RBM, the sign map of a visible
+phase i pi/2 between the TFIM with +h and -h, the Rayleigh quotient of the sparse
+Hamiltonian, and finite differences of the exact energy in both directions of each
+parameter.
 """
