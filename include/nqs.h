@@ -331,6 +331,69 @@ nqs_status nqs_batch_info(const nqs_batch *b, nqs_batch_info_t *info);
 const char *nqs_batch_last_error(const nqs_batch *b);
 void nqs_batch_destroy(nqs_batch *b);
 
+/* ---- Complex-parameter RBM ------------------------------------------------------------
+ * App. G with complex parameters a in C^N, b in C^M, W in C^{M x N}:
+ *   log psi(s) = a . s + sum_j log cosh(theta_j),  theta = W s + b.
+ * Sec. 2: the sampled density is |psi|^2, so proposals are decided on 2 Re(log psi(y) - log psi(x)).
+ * TFIM (Sec. 4.1, single flips) on the periodic lattices of nqs_ham_desc, N <= 256 sites,
+ * 1 <= n_hidden <= 512, FP32 arithmetic.  Parameters, O rows and the force are complex and
+ * interleaved (re, im), in the real RBM's order [a (N) | b (M) | W (M x N, row-major)].
+ * Configurations use the packed layout of the conventions above; arrays are device pointers
+ * owned by the caller; calls are asynchronous on `stream` unless stated; errors as above
+ * (nqs_crbm_last_error gives the text). */
+typedef struct nqs_crbm nqs_crbm;
+
+/* NQS_EUNSUPPORTED for a Hamiltonian other than TFIM, N > 256 or n_hidden > 512.  Synchronous. */
+nqs_status nqs_crbm_create(nqs_crbm **out, const nqs_ham_desc *ham, int32_t n_hidden);
+void nqs_crbm_destroy(nqs_crbm *c);
+const char *nqs_crbm_last_error(const nqs_crbm *c);  /* c may be NULL: last nqs_crbm_create error */
+int64_t nqs_crbm_n_params(const nqs_crbm *c);         /* P (complex parameters) */
+int32_t nqs_crbm_words_per_config(const nqs_crbm *c); /* W = ceil(N/32) */
+/* The sampler rebuilds its per-unit cache from theta every `refresh` sweeps (default 20). */
+nqs_status nqs_crbm_set_refresh(nqs_crbm *c, int32_t refresh);
+
+/* params: device, P complex values as 2P doubles (re, im).  Rounded to FP32; the sampler's
+ * tables are built from the rounded copy.  Range of the sampler: |Re W_ji| <= 1 and
+ * sum_i |Re W_ji| + |Re b_j| <= 10 for every j (NQS_EINVAL otherwise; parameters then
+ * count as unset).  Synchronises with the stream. */
+nqs_status nqs_crbm_set_params(nqs_crbm *c, const double *params, nqs_stream stream);
+
+/* As nqs_init_chains for a TFIM context (i.i.d. uniform spins, Philox4x32-10 keyed by seed). */
+nqs_status nqs_crbm_init_chains(nqs_crbm *c, uint32_t *state, int64_t n_chains, uint64_t seed, nqs_stream stream);
+
+/* nqs_sweep's proposals, counters, layouts and decision rule (u < exp(2 Re(log psi(y) -
+ * log psi(x))), u = 0 always accepts) with the complex psi.  trace->delta receives
+ * Re(log psi(y) - log psi(x)).  There is no log psi output. */
+nqs_status nqs_crbm_sweep(nqs_crbm *c, uint32_t *state, int64_t n_chains, int32_t n_sweeps, int32_t burn_in,
+                          uint64_t seed, uint32_t sweep_offset, uint32_t *samples, int64_t *n_accepted,
+                          const nqs_sweep_trace *trace, nqs_stream stream);
+
+/* out [n x 2] FP32: (Re log psi, Im log psi) with Im the sum of principal arguments (defined
+ * modulo 2 pi). */
+nqs_status nqs_crbm_logpsi(nqs_crbm *c, const uint32_t *configs, int64_t n, float *out, nqs_stream stream);
+
+/* App. I, Eq. local_energies with complex psi: eloc_re[x] + i eloc_im[x] =
+ * J sum_<ij> s_i s_j + h sum_i psi(flip_i x) / psi(x), FP32, two planar arrays [n]. */
+nqs_status nqs_crbm_local_energy(nqs_crbm *c, const uint32_t *configs, int64_t n, float *eloc_re, float *eloc_im,
+                                 nqs_stream stream);
+
+/* out: device, 6 doubles.  out[0..4] = nqs_stats over eloc_re (mean, variance, chain-blocked
+ * error, acceptance, n); out[5] = mean of eloc_im (zero in expectation: H is Hermitian). */
+nqs_status nqs_crbm_stats(nqs_crbm *c, const float *eloc_re, const float *eloc_im, int64_t n, int64_t n_chains,
+                          const int64_t *n_accepted, int64_t proposals_per_chain, double *out, nqs_stream stream);
+
+/* App. I, Eq. forces with the conjugated log-derivatives of the holomorphic log psi.
+ * O [n x P] complex FP32 interleaved, or NULL: O_a = s, O_b = tanh theta, O_W[j][i] = tanh(theta_j) s_i.
+ * force [P] complex FP64 interleaved, or NULL: F_k = (1/n) sum_x conj(O_k(x)) (eps(x) - E) with
+ * E = stats[0] + i stats[5] (nqs_crbm_stats); dE/dRe theta_k = 2 Re F_k, dE/dIm theta_k = 2 Im F_k.
+ * The force adds FP64 partials with atomics (the last bits depend on their order); n = 0
+ * sets it to zero. */
+nqs_status nqs_crbm_logpsi_grad(nqs_crbm *c, const uint32_t *configs, int64_t n, float *O, const float *eloc_re,
+                                const float *eloc_im, const double *stats, double *force, nqs_stream stream);
+
+/* nqs_check_status for the complex RBM's status word. */
+nqs_status nqs_crbm_check_status(nqs_crbm *c, nqs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,6 +98,20 @@ _SIGS = {
     "nqs_batch_info": (_i32, [_vp, ctypes.POINTER(BatchInfo)]),
     "nqs_batch_last_error": (ctypes.c_char_p, [_vp]),
     "nqs_batch_destroy": (None, [_vp]),
+    "nqs_crbm_create": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(HamDesc), _i32]),
+    "nqs_crbm_destroy": (None, [_vp]),
+    "nqs_crbm_last_error": (ctypes.c_char_p, [_vp]),
+    "nqs_crbm_n_params": (_i64, [_vp]),
+    "nqs_crbm_words_per_config": (_i32, [_vp]),
+    "nqs_crbm_set_refresh": (_i32, [_vp, _i32]),
+    "nqs_crbm_set_params": (_i32, [_vp, _vp, _vp]),
+    "nqs_crbm_init_chains": (_i32, [_vp, _vp, _i64, _u64, _vp]),
+    "nqs_crbm_sweep": (_i32, [_vp, _vp, _i64, _i32, _i32, _u64, _u32, _vp, _vp, _vp, _vp]),
+    "nqs_crbm_logpsi": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "nqs_crbm_local_energy": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "nqs_crbm_stats": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp]),
+    "nqs_crbm_logpsi_grad": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "nqs_crbm_check_status": (_i32, [_vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -385,3 +399,89 @@ def unpack_spins(words, N):
     w = words.to(torch.int64) & 0xFFFFFFFF
     bits = (w.unsqueeze(2) >> torch.arange(32, device=w.device, dtype=torch.int64)) & 1
     return (bits.view(words.shape[0], -1)[:, :N] * 2 - 1).to(torch.int8)
+
+
+class ComplexContext:
+    """One nqs_crbm: the complex-parameter RBM (App. G, complex a, b, W) on a TFIM.
+
+    Parameters and the force are complex128 tensors [P], O rows complex64 [n, P], log psi
+    complex64 [n]; local energies are two float32 tensors (real and imaginary parts)."""
+
+    def __init__(self, Lx=4, Ly=1, J1=1.0, h=0.0, n_hidden=4):
+        self._h = None
+        hd = HamDesc(HAMS["tfim"], Lx, Ly, J1, 0.0, h, 0)
+        out = ctypes.c_void_p()
+        st = _lib.nqs_crbm_create(ctypes.byref(out), ctypes.byref(hd), n_hidden)
+        if st != NQS_OK:
+            raise NQSError(st, _lib.nqs_crbm_last_error(None).decode())
+        self._h = out
+        self.N = Lx * Ly
+        self.M = n_hidden
+        self.W = _lib.nqs_crbm_words_per_config(out)
+        self.P = _lib.nqs_crbm_n_params(out)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.nqs_crbm_destroy(self._h)
+            self._h = None
+
+    def _check(self, st):
+        if st != NQS_OK:
+            raise NQSError(st, _lib.nqs_crbm_last_error(self._h).decode())
+
+    def set_refresh(self, refresh):
+        self._check(_lib.nqs_crbm_set_refresh(self._h, int(refresh)))
+
+    def set_params(self, params):
+        self._check(_lib.nqs_crbm_set_params(self._h, _ptr(params, (torch.complex128,), "params", (self.P,), False),
+                                             _stream()))
+
+    def init_chains(self, state, seed):
+        n = state.shape[0]
+        self._check(_lib.nqs_crbm_init_chains(self._h, _ptr(state, _WORD, "state", (n, self.W), False), n,
+                                              int(seed) & (2 ** 64 - 1), _stream()))
+
+    def sweep(self, state, n_sweeps, burn_in, seed, sweep_offset=0, samples=None, n_accepted=None,
+              accept_bits=None, delta=None):
+        C = state.shape[0]
+        K = max(n_sweeps - burn_in, 0)
+        tr = None
+        if accept_bits is not None or delta is not None:
+            tr = SweepTrace(_ptr(accept_bits, _WORD, "accept_bits", (C, n_sweeps, self.W)),
+                            _ptr(delta, (torch.float32,), "delta", (C, n_sweeps, self.N)))
+        self._check(_lib.nqs_crbm_sweep(
+            self._h, _ptr(state, _WORD, "state", (C, self.W), False), C, n_sweeps, burn_in,
+            int(seed) & (2 ** 64 - 1), int(sweep_offset), _ptr(samples, _WORD, "samples", (K * C, self.W)),
+            _ptr(n_accepted, (torch.int64,), "n_accepted", (C,)), ctypes.byref(tr) if tr is not None else None,
+            _stream()))
+
+    def logpsi(self, configs, out):
+        n = configs.shape[0]
+        self._check(_lib.nqs_crbm_logpsi(self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
+                                         _ptr(out, (torch.complex64,), "out", (n,), False), _stream()))
+
+    def local_energy(self, configs, eloc_re, eloc_im):
+        n = configs.shape[0]
+        self._check(_lib.nqs_crbm_local_energy(
+            self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
+            _ptr(eloc_re, (torch.float32,), "eloc_re", (n,), False),
+            _ptr(eloc_im, (torch.float32,), "eloc_im", (n,), False), _stream()))
+
+    def stats(self, eloc_re, eloc_im, n_chains, out, n_accepted=None, proposals_per_chain=0):
+        n = eloc_re.shape[0]
+        self._check(_lib.nqs_crbm_stats(
+            self._h, _ptr(eloc_re, (torch.float32,), "eloc_re", (n,), False),
+            _ptr(eloc_im, (torch.float32,), "eloc_im", (n,), False), n, n_chains,
+            _ptr(n_accepted, (torch.int64,), "n_accepted", (n_chains,)), int(proposals_per_chain),
+            _ptr(out, (torch.float64,), "out", (6,), False), _stream()))
+
+    def logpsi_grad(self, configs, O=None, eloc_re=None, eloc_im=None, stats=None, force=None):
+        n = configs.shape[0]
+        self._check(_lib.nqs_crbm_logpsi_grad(
+            self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
+            _ptr(O, (torch.complex64,), "O", (n, self.P)), _ptr(eloc_re, (torch.float32,), "eloc_re", (n,)),
+            _ptr(eloc_im, (torch.float32,), "eloc_im", (n,)), _ptr(stats, (torch.float64,), "stats", (6,)),
+            _ptr(force, (torch.complex128,), "force", (self.P,)), _stream()))
+
+    def check_status(self):
+        self._check(_lib.nqs_crbm_check_status(self._h, _stream()))

@@ -1,0 +1,860 @@
+// Complex-parameter RBM (App. G with a in C^N, b in C^M, W in C^{M x N}):
+//   log psi(s) = a . s + sum_j log cosh(theta_j),  theta = W s + b.
+// Sec. 2: the chains sample |psi|^2, so a single-flip proposal is decided on
+//   2 Re(log psi(y) - log psi(x)) = -4 s_i Re a_i + sum_j ln(D_j(y) / D_j(x)),
+//   D_j = |cosh theta_j|^2 = sinh^2(Re theta_j) + cos^2(Im theta_j)
+// (a sum of squares: no cancellation near the zeros of cosh, where the equal form
+// (cosh 2x + cos 2y) / 2 loses its accuracy and can even turn negative in FP32).
+// Local energies (App. I, Eq. local_energies) of the TFIM (Sec. 4.1) are complex:
+//   eps(x) = J sum_<ij> s_i s_j + h sum_i psi(flip_i x) / psi(x),
+//   psi(flip_i x) / psi(x) = exp(-2 s_i a_i) prod_j (cosh 2W_ji - s_i tanh(theta_j) sinh 2W_ji).
+// The force (App. I, Eq. forces) conjugates the holomorphic log-derivatives:
+//   F_k = E[O_k^* (eps - E[eps])],  O_a = s, O_b = tanh theta, O_W[j][i] = tanh(theta_j) s_i.
+//
+// Sampler cache.  Each lane of a chain's warp keeps, for its hidden units, the four numbers
+// sinh x, cosh x, cos y, sin y of theta = x + iy.  Flipping s_i moves x by -2 s_i Re W_ji and
+// y by -2 s_i Im W_ji, so the proposal's D_j follows from the addition formulas and a
+// per-(site, unit) table of cosh/sinh(2 Re W) and cos/sin(2 Im W): six FMA-type operations
+// per unit, no transcendental.  The cache is rebuilt from theta every `refresh` sweeps.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+struct nqs_crbm {
+  nqs_ctx base;  // device, SM count, sticky status word and statistics scratch
+  int N = 0, W = 0, M = 0, M_pad = 0, KU = 0, Lx = 0, Ly = 1;
+  double J = 1.0, h = 0.0;
+  int64_t P = 0;
+  int refresh = 20;
+  bool params_set = false;
+  float2 *d_a = nullptr;   // [N] visible bias
+  float2 *d_b = nullptr;   // [M_pad] hidden bias (zero beyond M)
+  float2 *d_Wt = nullptr;  // [N][M_pad] weights, site-major (W^T)
+  float4 *d_st = nullptr;  // [N][M_pad] (cosh 2 Re W, sinh 2 Re W, cos 2 Im W, sin 2 Im W)
+  float4 *d_et = nullptr;  // [M_pad][N] (cosh 2W, sinh 2W) as complex pairs, unit-major
+  int2 *d_nb = nullptr;    // [N] right and down neighbour (-1: none, a chain)
+  double *d_imstats = nullptr;  // [5] statistics of Im eps
+  std::string err;
+};
+
+namespace nqs {
+namespace {
+
+constexpr int CR_THREADS = 128;
+constexpr int CR_SPW = 4;            // samples per warp of the local-energy kernel
+constexpr int CR_FU = 16;            // hidden units per force tile
+constexpr int CR_FR = 32;            // rows per force block
+constexpr int CR_FTHREADS = 288;     // force kernel: sites 0 .. N (N <= 256) in phase B
+constexpr double CR_MAX_RE_THETA = 10.0;  // sum_i |Re W_ji| + |Re b_j| (products of D_j stay finite)
+constexpr double CR_MAX_RE_W = 1.0;       // |Re W_ji| (conditioning of the hyperbolic update)
+
+__device__ __forceinline__ float spin_of(uint32_t word, int bit) { return (word >> bit) & 1u ? 1.f : -1.f; }
+
+// tanh(x + iy) = (sinh x cosh x + i sin y cos y) / (sinh^2 x + cos^2 y); the denominator is
+// |cosh(x + iy)|^2 as a sum of squares (no cancellation near the zeros of cosh).
+__device__ __forceinline__ float2 tanh_c(float x, float y) {
+  float sy, cy;
+  sincosf(y, &sy, &cy);
+  const float shx = sinhf(x), chx = coshf(x);
+  const float inv = 1.f / fmaf(shx, shx, cy * cy);
+  return make_float2(shx * chx * inv, sy * cy * inv);
+}
+
+// ---- parameter preparation -----------------------------------------------------------
+__global__ void crbm_prepare_kernel(const double2 *__restrict__ p, int N, int M, int M_pad, float2 *a, float2 *b,
+                                    float2 *Wt, float4 *st, float4 *et, int *status) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)N * M_pad;
+  for (int64_t idx = t0; idx < total; idx += stride) {
+    const int i = (int)(idx / M_pad), j = (int)(idx % M_pad);
+    const double2 w = j < M ? p[N + M + (int64_t)j * N + i] : make_double2(0.0, 0.0);
+    Wt[idx] = make_float2((float)w.x, (float)w.y);
+    st[idx] = make_float4((float)cosh(2.0 * w.x), (float)sinh(2.0 * w.x), (float)cos(2.0 * w.y), (float)sin(2.0 * w.y));
+    // cosh(x + iy) = cosh x cos y + i sinh x sin y, sinh(x + iy) = sinh x cos y + i cosh x sin y
+    const double cx = cosh(2.0 * w.x), sx = sinh(2.0 * w.x), cy = cos(2.0 * w.y), sy = sin(2.0 * w.y);
+    et[(int64_t)j * N + i] = make_float4((float)(cx * cy), (float)(sx * sy), (float)(sx * cy), (float)(cx * sy));
+  }
+  for (int64_t i = t0; i < N; i += stride) a[i] = make_float2((float)p[i].x, (float)p[i].y);
+  for (int64_t j = t0; j < M_pad; j += stride) {
+    if (j >= M) {
+      b[j] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const double2 bj = p[N + j];
+    b[j] = make_float2((float)bj.x, (float)bj.y);
+    double s = fabs(bj.x), wmax = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double wr = fabs(p[N + M + j * (int64_t)N + i].x);
+      s += wr;
+      wmax = fmax(wmax, wr);
+    }
+    if (!(s <= CR_MAX_RE_THETA) || !(wmax <= CR_MAX_RE_W)) atomicOr(status, STATUS_RANGE);
+  }
+}
+
+// ---- sampler ---------------------------------------------------------------------------
+struct CSweepArgs {
+  uint32_t *state;
+  int64_t C;
+  int N, W, M_pad, T, B, refresh;
+  uint32_t k0, k1, sweep_offset;
+  const float2 *a, *b, *Wt;
+  const float4 *st;
+  uint32_t *samples;
+  int64_t *n_acc;
+  uint32_t *acc_bits;
+  float *delta;
+};
+
+// One warp per chain; lane q < W holds word q of the configuration and of the sweep's
+// accept bits; lane l holds hidden units l + 32k (k < KU).
+template <int KU>
+__global__ void __launch_bounds__(CR_THREADS) crbm_sweep_kernel(const CSweepArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t c = (blockIdx.x * (int64_t)CR_THREADS + threadIdx.x) >> 5;
+  if (c >= a.C) return;  // warp-uniform
+  uint32_t word = lane < a.W ? a.state[c * a.W + lane] : 0u;
+  float shx[KU], chx[KU], cy[KU], sy[KU];
+  float Lc = 0.f;  // this lane's sum of log2 D_j of the current configuration
+  int64_t nacc = 0;
+  for (int t = 0; t < a.T; ++t) {
+    if (t % a.refresh == 0) {
+      float x[KU], y[KU];
+#pragma unroll
+      for (int k = 0; k < KU; ++k) {
+        const float2 bj = a.b[lane + 32 * k];
+        x[k] = bj.x;
+        y[k] = bj.y;
+      }
+      for (int i = 0; i < a.N; ++i) {
+        const float s = spin_of(__shfl_sync(FULL_MASK, word, i >> 5), i & 31);
+        const float2 *row = a.Wt + (int64_t)i * a.M_pad + lane;
+#pragma unroll
+        for (int k = 0; k < KU; ++k) {
+          const float2 w = __ldg(row + 32 * k);
+          x[k] = fmaf(s, w.x, x[k]);
+          y[k] = fmaf(s, w.y, y[k]);
+        }
+      }
+      Lc = 0.f;
+      float prod = 1.f;
+#pragma unroll
+      for (int k = 0; k < KU; ++k) {
+        shx[k] = sinhf(x[k]);
+        chx[k] = coshf(x[k]);
+        sincosf(y[k], &sy[k], &cy[k]);
+        prod *= fmaf(shx[k], shx[k], cy[k] * cy[k]);
+        if ((k & 3) == 3 || k == KU - 1) {
+          Lc += lg2_approx(prod);
+          prod = 1.f;
+        }
+      }
+    }
+    uint32_t bits = 0u;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    for (int p = 0; p < a.N; ++p) {
+      if ((p & 1) == 0) r = philox4x32_10(make_uint4((uint32_t)(p >> 1), a.sweep_offset + t, (uint32_t)c, TAG_SWEEP), a.k0, a.k1);
+      const uint32_t w0 = (p & 1) ? r.z : r.x, w1 = (p & 1) ? r.w : r.y;
+      const int i = (int)index_from_word(w0, (uint32_t)a.N);
+      const float u = (float)(w1 >> 8) * 0x1p-24f;
+      const float sg = spin_of(__shfl_sync(FULL_MASK, word, i >> 5), i & 31);
+      const float4 *row = a.st + (int64_t)i * a.M_pad + lane;
+      float Ln = 0.f, prod = 1.f;
+#pragma unroll
+      for (int k = 0; k < KU; ++k) {
+        const float4 tb = __ldg(row + 32 * k);
+        // sinh(x - b) = sinh x cosh b - cosh x sinh b, cos(y - c) = cos y cos c + sin y sin c
+        const float shn = fmaf(shx[k], tb.x, -chx[k] * (sg * tb.y));
+        const float cyn = fmaf(cy[k], tb.z, sy[k] * (sg * tb.w));
+        prod *= fmaf(shn, shn, cyn * cyn);
+        if ((k & 3) == 3 || k == KU - 1) {
+          Ln += lg2_approx(prod);
+          prod = 1.f;
+        }
+      }
+      // every lane ends with the bitwise-identical sum, so the decision is warp-uniform
+      const float dsum = group_allsum<32>(Ln - Lc);
+      const float d2 = fmaf(LN2F, dsum, -4.f * sg * a.a[i].x);
+      const bool acc = (u == 0.f) || (u < ex2_approx(d2 * LOG2EF));
+      if (a.delta && lane == 0) a.delta[((int64_t)c * a.T + t) * a.N + p] = 0.5f * d2;
+      if (acc) {
+#pragma unroll
+        for (int k = 0; k < KU; ++k) {
+          const float4 tb = __ldg(row + 32 * k);
+          const float sb = sg * tb.y, ss = sg * tb.w;
+          const float shn = fmaf(shx[k], tb.x, -chx[k] * sb), chn = fmaf(chx[k], tb.x, -shx[k] * sb);
+          const float cyn = fmaf(cy[k], tb.z, sy[k] * ss), syn = fmaf(sy[k], tb.z, -cy[k] * ss);
+          shx[k] = shn;
+          chx[k] = chn;
+          cy[k] = cyn;
+          sy[k] = syn;
+        }
+        Lc = Ln;
+        if (lane == (i >> 5)) word ^= 1u << (i & 31);
+        if (lane == (p >> 5)) bits |= 1u << (p & 31);
+        ++nacc;
+      }
+    }
+    if (lane < a.W) {
+      if (a.samples && t >= a.B) a.samples[((int64_t)(t - a.B) * a.C + c) * a.W + lane] = word;
+      if (a.acc_bits) a.acc_bits[((int64_t)c * a.T + t) * a.W + lane] = bits;
+    }
+  }
+  if (lane < a.W) a.state[c * a.W + lane] = word;
+  if (a.n_acc && lane == 0) a.n_acc[c] = nacc;
+}
+
+// ---- log psi ---------------------------------------------------------------------------
+struct CRowArgs {
+  const uint32_t *cfg;
+  int64_t n;
+  int N, W, M, M_pad;
+  const float2 *a, *b, *Wt;
+};
+
+// One warp per configuration: out[2x] = Re log psi, out[2x + 1] = Im log psi (the sum of
+// principal arguments; defined modulo 2 pi).
+__global__ void __launch_bounds__(CR_THREADS) crbm_logpsi_kernel(const CRowArgs a, float *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * CR_THREADS) >> 5;
+  for (int64_t x = (blockIdx.x * (int64_t)CR_THREADS + threadIdx.x) >> 5; x < a.n; x += nw) {
+    const uint32_t word = lane < a.W ? a.cfg[x * a.W + lane] : 0u;
+    float re = 0.f, im = 0.f;
+    // padded units (W = b = 0) add log cosh 0 = 0; every lane runs every iteration
+    for (int j = lane; j < a.M_pad; j += 32) {
+      float tx = a.b[j].x, ty = a.b[j].y;
+      for (int i = 0; i < a.N; ++i) {
+        const float s = spin_of(__shfl_sync(FULL_MASK, word, i >> 5), i & 31);
+        const float2 w = a.Wt[(int64_t)i * a.M_pad + j];
+        tx = fmaf(s, w.x, tx);
+        ty = fmaf(s, w.y, ty);
+      }
+      float sy, cy;
+      sincosf(ty, &sy, &cy);
+      const float chx = coshf(tx), shx = sinhf(tx);
+      re += 0.5f * logf(fmaxf(chx * chx - sy * sy, 0.f));  // |cosh z|^2 = cosh^2 x - sin^2 y
+      im += atan2f(shx * sy, chx * cy);
+    }
+    for (int q = 0; q < (a.N + 31) / 32; ++q) {
+      const uint32_t wq = __shfl_sync(FULL_MASK, word, q);
+      const int i = 32 * q + lane;
+      if (i < a.N) {
+        const float s = spin_of(wq, lane);
+        re = fmaf(s, a.a[i].x, re);
+        im = fmaf(s, a.a[i].y, im);
+      }
+    }
+    re = group_allsum<32>(re);
+    im = group_allsum<32>(im);
+    if (lane == 0) {
+      out[2 * x] = re;
+      out[2 * x + 1] = im;
+    }
+  }
+}
+
+// ---- local energies ----------------------------------------------------------------------
+struct CElocArgs {
+  CRowArgs r;
+  const float4 *et;
+  const int2 *nb;
+  float J, h;
+  float *eloc_re, *eloc_im;
+};
+
+// |p| pulled into the log2 accumulator L; a zero product marks the ratio as zero.
+__device__ __forceinline__ void crbm_normalise(float2 &p, float &L, bool &dead) {
+  const float m = fmaf(p.x, p.x, p.y * p.y);
+  if (m > 0.f) {
+    L = fmaf(0.5f, lg2_approx(m), L);
+    const float inv = rsqrtf(m);
+    p.x *= inv;
+    p.y *= inv;
+  } else {
+    dead = true;
+    p = make_float2(1.f, 0.f);
+  }
+}
+
+// One warp per CR_SPW configurations.  Phase 1 (lanes over hidden units): theta and
+// tanh theta of every sample into the warp's shared-memory slice.  Phase 2 (lanes over
+// sites): the flip ratio of site i as a product over all units, read from the unit-major
+// (cosh 2W, sinh 2W) table once for the CR_SPW samples.
+template <int KU>
+__global__ void __launch_bounds__(CR_THREADS) crbm_eloc_kernel(const CElocArgs a) {
+  extern __shared__ float2 crbm_tanh[];  // [warps][CR_SPW][M_pad]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int M_pad = a.r.M_pad, N = a.r.N, W = a.r.W;
+  float2 *tw = crbm_tanh + (size_t)warp * CR_SPW * M_pad;
+  const int64_t nw = ((int64_t)gridDim.x * CR_THREADS) >> 5;
+  for (int64_t x0 = ((blockIdx.x * (int64_t)CR_THREADS + threadIdx.x) >> 5) * CR_SPW; x0 < a.r.n;
+       x0 += nw * CR_SPW) {
+    uint32_t wr[CR_SPW];
+#pragma unroll
+    for (int r = 0; r < CR_SPW; ++r) {
+      const int64_t x = std::min<int64_t>(x0 + r, a.r.n - 1);
+      wr[r] = lane < W ? a.r.cfg[x * W + lane] : 0u;
+      float tx[KU], ty[KU];
+#pragma unroll
+      for (int k = 0; k < KU; ++k) {
+        const float2 bj = a.r.b[lane + 32 * k];
+        tx[k] = bj.x;
+        ty[k] = bj.y;
+      }
+      for (int i = 0; i < N; ++i) {
+        const float s = spin_of(__shfl_sync(FULL_MASK, wr[r], i >> 5), i & 31);
+        const float2 *row = a.r.Wt + (int64_t)i * M_pad + lane;
+#pragma unroll
+        for (int k = 0; k < KU; ++k) {
+          const float2 w = __ldg(row + 32 * k);
+          tx[k] = fmaf(s, w.x, tx[k]);
+          ty[k] = fmaf(s, w.y, ty[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < KU; ++k) {
+        tw[r * M_pad + lane + 32 * k] = tanh_c(tx[k], ty[k]);
+      }
+    }
+    __syncwarp();
+    float er[CR_SPW], ei[CR_SPW];
+#pragma unroll
+    for (int r = 0; r < CR_SPW; ++r) er[r] = ei[r] = 0.f;
+    for (int q = 0; q < (N + 31) / 32; ++q) {
+      const int i = 32 * q + lane;
+      const bool active = i < N;
+      const int2 nb = a.nb[active ? i : 0];
+      float sg[CR_SPW], zz[CR_SPW];
+#pragma unroll
+      for (int r = 0; r < CR_SPW; ++r) {
+        sg[r] = spin_of(__shfl_sync(FULL_MASK, wr[r], q), lane);
+        const float sr = spin_of(__shfl_sync(FULL_MASK, wr[r], nb.x >> 5), nb.x & 31);
+        const int d = nb.y >= 0 ? nb.y : 0;
+        const float sd = nb.y >= 0 ? spin_of(__shfl_sync(FULL_MASK, wr[r], d >> 5), d & 31) : 0.f;
+        zz[r] = sg[r] * (sr + sd);
+      }
+      if (active) {
+        float2 p[CR_SPW];
+        float L[CR_SPW];
+        bool dead[CR_SPW];
+#pragma unroll
+        for (int r = 0; r < CR_SPW; ++r) {
+          p[r] = make_float2(1.f, 0.f);
+          L[r] = 0.f;
+          dead[r] = false;
+        }
+        const float4 *col = a.et + i;
+        for (int j0 = 0; j0 < M_pad; j0 += 8) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = j0 + jj;
+            const float4 cs = __ldg(col + (int64_t)j * N);  // (cosh 2W, sinh 2W) of (j, i)
+#pragma unroll
+            for (int r = 0; r < CR_SPW; ++r) {
+              const float2 t = tw[r * M_pad + j];
+              const float tsx = fmaf(t.x, cs.z, -t.y * cs.w), tsy = fmaf(t.x, cs.w, t.y * cs.z);
+              const float rx = fmaf(-sg[r], tsx, cs.x), ry = fmaf(-sg[r], tsy, cs.y);
+              const float px = fmaf(p[r].x, rx, -p[r].y * ry), py = fmaf(p[r].x, ry, p[r].y * rx);
+              p[r] = make_float2(px, py);
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < CR_SPW; ++r) crbm_normalise(p[r], L[r], dead[r]);
+        }
+        const float2 ai = a.r.a[i];
+#pragma unroll
+        for (int r = 0; r < CR_SPW; ++r) {
+          er[r] = fmaf(a.J, zz[r], er[r]);
+          if (!dead[r]) {
+            // exp(-2 s_i a_i) prod_j (...) = 2^(L - 2 s_i Re a_i log2 e) e^{-2 i s_i Im a_i} p
+            const float mag = ex2_approx(fmaf(-2.f * sg[r] * ai.x, LOG2EF, L[r]));
+            float sn, cn;
+            sincosf(-2.f * sg[r] * ai.y, &sn, &cn);
+            const float rx = fmaf(p[r].x, cn, -p[r].y * sn), ry = fmaf(p[r].x, sn, p[r].y * cn);
+            er[r] = fmaf(a.h * mag, rx, er[r]);
+            ei[r] = fmaf(a.h * mag, ry, ei[r]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < CR_SPW; ++r) {
+      const float vr = group_allsum<32>(er[r]), vi = group_allsum<32>(ei[r]);
+      if (lane == 0 && x0 + r < a.r.n) {
+        a.eloc_re[x0 + r] = vr;
+        a.eloc_im[x0 + r] = vi;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---- O rows ------------------------------------------------------------------------------
+// One CTA per row: O[x] = [s | tanh theta | tanh(theta_j) s_i], complex FP32 interleaved.
+__global__ void __launch_bounds__(CR_THREADS) crbm_grad_rows_kernel(const CRowArgs a, int64_t P, float2 *O) {
+  extern __shared__ float2 crbm_rowt[];  // [M_pad]
+  __shared__ uint32_t words[8];
+  for (int64_t x = blockIdx.x; x < a.n; x += gridDim.x) {
+    if (threadIdx.x < a.W) words[threadIdx.x] = a.cfg[x * a.W + threadIdx.x];
+    __syncthreads();
+    for (int j = threadIdx.x; j < a.M; j += CR_THREADS) {
+      float tx = a.b[j].x, ty = a.b[j].y;
+      for (int i = 0; i < a.N; ++i) {
+        const float s = spin_of(words[i >> 5], i & 31);
+        const float2 w = a.Wt[(int64_t)i * a.M_pad + j];
+        tx = fmaf(s, w.x, tx);
+        ty = fmaf(s, w.y, ty);
+      }
+      crbm_rowt[j] = tanh_c(tx, ty);
+    }
+    __syncthreads();
+    float2 *row = O + x * P;
+    for (int64_t k = threadIdx.x; k < P; k += CR_THREADS) {
+      float2 v;
+      if (k < a.N) {
+        v = make_float2(spin_of(words[k >> 5], (int)(k & 31)), 0.f);
+      } else if (k < a.N + a.M) {
+        v = crbm_rowt[k - a.N];
+      } else {
+        const int64_t q = k - a.N - a.M;
+        const int j = (int)(q / a.N), i = (int)(q % a.N);
+        const float s = spin_of(words[i >> 5], i & 31);
+        const float2 t = crbm_rowt[j];
+        v = make_float2(s * t.x, s * t.y);
+      }
+      row[k] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- force -------------------------------------------------------------------------------
+// The force as one contraction over rows x of the extended matrices
+//   G[x][j] = conj(t_j(x)) e(x) (j < M),  G[x][M] = e(x),     e = eps - E,
+//   S[x][i] = s_i(x) (i < N),             S[x][N] = 1,
+// Fsum = G^T S: F_W = Fsum[j][i], F_b = Fsum[j][N], F_a = Fsum[M][i].  CTA (row range,
+// tile of CR_FU units): phase A builds G for CR_FR rows, phase B accumulates thread i's
+// column in FP32 over the block and in FP64 across blocks, then adds to the FP64 output.
+struct CForceArgs {
+  CRowArgs r;
+  const float *eloc_re, *eloc_im;
+  const double *stats;
+  int64_t rows_per_cta;
+  double2 *force;
+};
+
+__global__ void __launch_bounds__(CR_FTHREADS) crbm_force_kernel(const CForceArgs a) {
+  __shared__ uint32_t sbits[CR_FR][8];
+  __shared__ float2 g[CR_FR][CR_FU];
+  const int tid = threadIdx.x;
+  const int N = a.r.N, M = a.r.M, W = a.r.W;
+  const int j0 = blockIdx.y * CR_FU;
+  const int64_t x_begin = blockIdx.x * a.rows_per_cta;
+  const int64_t x_end = std::min<int64_t>(a.r.n, x_begin + a.rows_per_cta);
+  const float Ere = (float)a.stats[0], Eim = (float)a.stats[5];
+  double accd[CR_FU][2];
+#pragma unroll
+  for (int u = 0; u < CR_FU; ++u) accd[u][0] = accd[u][1] = 0.0;
+  for (int64_t r0 = x_begin; r0 < x_end; r0 += CR_FR) {
+    for (int idx = tid; idx < CR_FR * W; idx += CR_FTHREADS) {
+      const int rr = idx / W, q = idx % W;
+      const int64_t x = r0 + rr;
+      sbits[rr][q] = x < x_end ? a.r.cfg[x * W + q] : 0u;
+    }
+    __syncthreads();
+    if (tid < CR_FR * (CR_FU / 2)) {
+      const int rr = tid / (CR_FU / 2), uu = 2 * (tid % (CR_FU / 2));
+      const int64_t x = r0 + rr;
+      const bool valid = x < x_end;
+      const float ex = valid ? a.eloc_re[x] - Ere : 0.f, ey = valid ? a.eloc_im[x] - Eim : 0.f;
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int j = j0 + uu + v;
+        float2 gv = make_float2(0.f, 0.f);
+        if (j < M) {
+          float tx = a.r.b[j].x, ty = a.r.b[j].y;
+          for (int i = 0; i < N; ++i) {
+            const float s = spin_of(sbits[rr][i >> 5], i & 31);
+            const float2 w = a.r.Wt[(int64_t)i * a.r.M_pad + j];
+            tx = fmaf(s, w.x, tx);
+            ty = fmaf(s, w.y, ty);
+          }
+          const float2 t = tanh_c(tx, ty);
+          // conj(t) e
+          gv = make_float2(fmaf(t.x, ex, t.y * ey), fmaf(t.x, ey, -t.y * ex));
+        } else if (j == M) {
+          gv = make_float2(ex, ey);
+        }
+        g[rr][uu + v] = gv;
+      }
+    }
+    __syncthreads();
+    if (tid <= N) {
+      float acc[CR_FU][2];
+#pragma unroll
+      for (int u = 0; u < CR_FU; ++u) acc[u][0] = acc[u][1] = 0.f;
+      for (int rr = 0; rr < CR_FR; ++rr) {
+        const float s = tid < N ? spin_of(sbits[rr][tid >> 5], tid & 31) : 1.f;
+#pragma unroll
+        for (int u = 0; u < CR_FU; ++u) {
+          const float2 gv = g[rr][u];
+          acc[u][0] = fmaf(s, gv.x, acc[u][0]);
+          acc[u][1] = fmaf(s, gv.y, acc[u][1]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CR_FU; ++u) {
+        accd[u][0] += (double)acc[u][0];
+        accd[u][1] += (double)acc[u][1];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid > N) return;
+  const int i = tid;
+#pragma unroll
+  for (int u = 0; u < CR_FU; ++u) {
+    const int j = j0 + u;
+    int64_t k = -1;
+    if (j < M && i < N) k = (int64_t)N + M + (int64_t)j * N + i;
+    else if (j < M) k = (int64_t)N + j;
+    else if (j == M && i < N) k = i;
+    if (k >= 0) {
+      atomicAdd(&a.force[k].x, accd[u][0]);
+      atomicAdd(&a.force[k].y, accd[u][1]);
+    }
+  }
+}
+
+__global__ void crbm_scale_kernel(double *v, int64_t n, double s) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    v[k] *= s;
+}
+
+// Largest instantiated units-per-lane width >= need.
+constexpr int KU_LIST[] = {1, 2, 3, 4, 6, 8, 10, 13, 16};
+
+template <int KU>
+cudaError_t launch_sweep(const nqs_crbm *c, const CSweepArgs &a, cudaStream_t s) {
+  const int64_t blocks = (a.C * 32 + CR_THREADS - 1) / CR_THREADS;
+  crbm_sweep_kernel<KU><<<(unsigned)blocks, CR_THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int KU>
+cudaError_t launch_eloc(const nqs_crbm *c, const CElocArgs &a, cudaStream_t s) {
+  const size_t smem = (size_t)(CR_THREADS / 32) * CR_SPW * c->M_pad * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(crbm_eloc_kernel<KU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t warps = (a.r.n + CR_SPW - 1) / CR_SPW;
+  const int64_t blocks = std::max<int64_t>(
+      1, std::min<int64_t>((warps * 32 + CR_THREADS - 1) / CR_THREADS, (int64_t)c->base.num_sms * 8));
+  crbm_eloc_kernel<KU><<<(unsigned)blocks, CR_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+#define CRBM_DISPATCH(KUV, FN, ...)        \
+  switch (KUV) {                           \
+    case 1: return FN<1>(__VA_ARGS__);     \
+    case 2: return FN<2>(__VA_ARGS__);     \
+    case 3: return FN<3>(__VA_ARGS__);     \
+    case 4: return FN<4>(__VA_ARGS__);     \
+    case 6: return FN<6>(__VA_ARGS__);     \
+    case 8: return FN<8>(__VA_ARGS__);     \
+    case 10: return FN<10>(__VA_ARGS__);   \
+    case 13: return FN<13>(__VA_ARGS__);   \
+    default: return FN<16>(__VA_ARGS__);   \
+  }
+
+cudaError_t dispatch_sweep(const nqs_crbm *c, const CSweepArgs &a, cudaStream_t s) {
+  CRBM_DISPATCH(c->KU, launch_sweep, c, a, s)
+}
+cudaError_t dispatch_eloc(const nqs_crbm *c, const CElocArgs &a, cudaStream_t s) {
+  CRBM_DISPATCH(c->KU, launch_eloc, c, a, s)
+}
+
+CRowArgs row_args(const nqs_crbm *c, const uint32_t *cfg, int64_t n) {
+  CRowArgs r;
+  r.cfg = cfg;
+  r.n = n;
+  r.N = c->N;
+  r.W = c->W;
+  r.M = c->M;
+  r.M_pad = c->M_pad;
+  r.a = c->d_a;
+  r.b = c->d_b;
+  r.Wt = c->d_Wt;
+  return r;
+}
+
+void crbm_free(nqs_crbm *c) {
+  void *ptrs[] = {c->d_a, c->d_b, c->d_Wt, c->d_st, c->d_et, c->d_nb, c->d_imstats, c->base.d_status,
+                  c->base.d_scratch};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+}
+
+}  // namespace
+}  // namespace nqs
+
+namespace {
+
+thread_local std::string g_crbm_error;
+
+nqs_status cfail(nqs_crbm *c, nqs_status st, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_crbm_error = msg;
+  return st;
+}
+nqs_status ccuda(nqs_crbm *c, cudaError_t e, const char *where) {
+  return cfail(c, NQS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *nqs_crbm_last_error(const nqs_crbm *c) { return c ? c->err.c_str() : g_crbm_error.c_str(); }
+int64_t nqs_crbm_n_params(const nqs_crbm *c) { return c ? c->P : 0; }
+int32_t nqs_crbm_words_per_config(const nqs_crbm *c) { return c ? c->W : 0; }
+
+nqs_status nqs_crbm_create(nqs_crbm **out, const nqs_ham_desc *ham, int32_t n_hidden) {
+  using namespace nqs;
+  if (!out || !ham) return cfail(nullptr, NQS_EINVAL, "nqs_crbm_create: null argument");
+  *out = nullptr;
+  if (ham->kind != NQS_TFIM) return cfail(nullptr, NQS_EUNSUPPORTED, "the complex RBM is built for the TFIM");
+  if (ham->Lx < 3 || !(ham->Ly == 1 || ham->Ly >= 3))
+    return cfail(nullptr, NQS_EINVAL, "periodic lattice needs Lx >= 3 and Ly == 1 or Ly >= 3");
+  const int64_t N64 = (int64_t)ham->Lx * ham->Ly;
+  if (N64 > 256) return cfail(nullptr, NQS_EUNSUPPORTED, "the complex RBM takes at most 256 sites");
+  if (n_hidden < 1 || n_hidden > 512) return cfail(nullptr, NQS_EUNSUPPORTED, "the complex RBM needs 1 <= n_hidden <= 512");
+  nqs_crbm *c = new (std::nothrow) nqs_crbm();
+  if (!c) return cfail(nullptr, NQS_ENOMEM, "host allocation failed");
+  c->N = (int)N64;
+  c->W = (c->N + 31) / 32;
+  c->M = n_hidden;
+  const int need = (c->M + 31) / 32;
+  c->KU = 16;
+  for (int v : KU_LIST)
+    if (v >= need) {
+      c->KU = v;
+      break;
+    }
+  c->M_pad = 32 * c->KU;
+  c->Lx = ham->Lx;
+  c->Ly = ham->Ly;
+  c->J = ham->J1;
+  c->h = ham->h;
+  c->P = (int64_t)c->N + c->M + (int64_t)c->M * c->N;
+  nqs_ctx &b = c->base;
+  b.model_kind = NQS_RBM;
+  b.ham_kind = NQS_TFIM;
+  b.N = c->N;
+  b.W = c->W;
+  b.Lx = c->Lx;
+  b.Ly = c->Ly;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&b.device)) != cudaSuccess) {
+    delete c;
+    return ccuda(nullptr, e, "cudaGetDevice");
+  }
+  cudaDeviceGetAttribute(&b.num_sms, cudaDevAttrMultiProcessorCount, b.device);
+  std::vector<int2> nb(c->N);
+  for (int y = 0; y < c->Ly; ++y)
+    for (int x = 0; x < c->Lx; ++x)
+      nb[x + c->Lx * y] = make_int2((x + 1) % c->Lx + c->Lx * y, c->Ly > 1 ? x + c->Lx * ((y + 1) % c->Ly) : -1);
+  const size_t NM = (size_t)c->N * c->M_pad;
+  if ((e = cudaMalloc(&c->d_a, c->N * sizeof(float2))) || (e = cudaMalloc(&c->d_b, c->M_pad * sizeof(float2))) ||
+      (e = cudaMalloc(&c->d_Wt, NM * sizeof(float2))) || (e = cudaMalloc(&c->d_st, NM * sizeof(float4))) ||
+      (e = cudaMalloc(&c->d_et, NM * sizeof(float4))) || (e = cudaMalloc(&c->d_nb, c->N * sizeof(int2))) ||
+      (e = cudaMalloc(&c->d_imstats, 5 * sizeof(double))) || (e = cudaMalloc(&b.d_status, sizeof(int))) ||
+      (e = cudaMalloc(&b.d_scratch, 5 * STATS_MAX_BLOCKS * sizeof(double))) ||
+      (e = cudaMemset(b.d_status, 0, sizeof(int))) ||
+      (e = cudaMemcpy(c->d_nb, nb.data(), nb.size() * sizeof(int2), cudaMemcpyHostToDevice))) {
+    crbm_free(c);
+    delete c;
+    return cfail(nullptr, NQS_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  *out = c;
+  return NQS_OK;
+}
+
+void nqs_crbm_destroy(nqs_crbm *c) {
+  if (!c) return;
+  nqs::crbm_free(c);
+  delete c;
+}
+
+nqs_status nqs_crbm_set_refresh(nqs_crbm *c, int32_t refresh) {
+  if (!c) return NQS_EINVAL;
+  if (refresh < 1) return cfail(c, NQS_EINVAL, "refresh must be >= 1");
+  c->refresh = refresh;
+  return NQS_OK;
+}
+
+nqs_status nqs_crbm_set_params(nqs_crbm *c, const double *params, nqs_stream stream) {
+  using namespace nqs;
+  if (!c) return NQS_EINVAL;
+  if (!params) return cfail(c, NQS_EINVAL, "nqs_crbm_set_params: null params");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int st = 0;
+  cudaError_t e = cudaMemsetAsync(c->base.d_status, 0, sizeof(int), s);
+  if (e != cudaSuccess) return ccuda(c, e, "nqs_crbm_set_params");
+  const int64_t total = (int64_t)c->N * c->M_pad;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)c->base.num_sms * 8));
+  crbm_prepare_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const double2 *>(params), c->N, c->M, c->M_pad, c->d_a,
+                                             c->d_b, c->d_Wt, c->d_st, c->d_et, c->base.d_status);
+  if ((e = cudaGetLastError()) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&st, c->base.d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return ccuda(c, e, "nqs_crbm_set_params");
+  if (st & STATUS_RANGE) {
+    c->params_set = false;
+    cudaMemsetAsync(c->base.d_status, 0, sizeof(int), s);
+    return cfail(c, NQS_EINVAL, "a weight is outside the complex sampler's range (|Re W| <= 1, sum_i |Re W_ji| + |Re b_j| <= 10)");
+  }
+  c->params_set = true;
+  return NQS_OK;
+}
+
+nqs_status nqs_crbm_init_chains(nqs_crbm *c, uint32_t *state, int64_t n, uint64_t seed, nqs_stream stream) {
+  if (!c) return NQS_EINVAL;
+  if (n < 0 || (n > 0 && !state)) return cfail(c, NQS_EINVAL, "nqs_crbm_init_chains: bad state/n");
+  if (n > (int64_t)UINT32_MAX) return cfail(c, NQS_EINVAL, "at most 2^32 chains");
+  if (n == 0) return NQS_OK;
+  cudaError_t e = nqs::init_chains(&c->base, state, n, seed, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? NQS_OK : ccuda(c, e, "nqs_crbm_init_chains");
+}
+
+nqs_status nqs_crbm_sweep(nqs_crbm *c, uint32_t *state, int64_t n_chains, int32_t n_sweeps, int32_t burn_in,
+                          uint64_t seed, uint32_t sweep_offset, uint32_t *samples, int64_t *n_accepted,
+                          const nqs_sweep_trace *trace, nqs_stream stream) {
+  using namespace nqs;
+  if (!c) return NQS_EINVAL;
+  if (!c->params_set) return cfail(c, NQS_EINVAL, "nqs_crbm_sweep: parameters not set");
+  if (n_chains < 0 || n_sweeps < 0 || burn_in < 0) return cfail(c, NQS_EINVAL, "nqs_crbm_sweep: negative size");
+  if (n_chains > (int64_t)UINT32_MAX) return cfail(c, NQS_EINVAL, "at most 2^32 chains");
+  if ((uint64_t)sweep_offset + (uint64_t)n_sweeps > (1ull << 32)) return cfail(c, NQS_EINVAL, "sweep counter overflow");
+  if (n_chains == 0 || n_sweeps == 0) return NQS_OK;
+  if (!state) return cfail(c, NQS_EINVAL, "nqs_crbm_sweep: null state");
+  CSweepArgs a;
+  a.state = state;
+  a.C = n_chains;
+  a.N = c->N;
+  a.W = c->W;
+  a.M_pad = c->M_pad;
+  a.T = n_sweeps;
+  a.B = burn_in;
+  a.refresh = c->refresh;
+  a.k0 = (uint32_t)seed;
+  a.k1 = (uint32_t)(seed >> 32);
+  a.sweep_offset = sweep_offset;
+  a.a = c->d_a;
+  a.b = c->d_b;
+  a.Wt = c->d_Wt;
+  a.st = c->d_st;
+  a.samples = samples;
+  a.n_acc = n_accepted;
+  a.acc_bits = trace ? trace->accept_bits : nullptr;
+  a.delta = trace ? trace->delta : nullptr;
+  cudaError_t e = dispatch_sweep(c, a, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? NQS_OK : ccuda(c, e, "nqs_crbm_sweep");
+}
+
+nqs_status nqs_crbm_logpsi(nqs_crbm *c, const uint32_t *cfg, int64_t n, float *out, nqs_stream stream) {
+  using namespace nqs;
+  if (!c) return NQS_EINVAL;
+  if (!c->params_set) return cfail(c, NQS_EINVAL, "nqs_crbm_logpsi: parameters not set");
+  if (n < 0 || (n > 0 && (!cfg || !out))) return cfail(c, NQS_EINVAL, "nqs_crbm_logpsi: bad arguments");
+  if (n == 0) return NQS_OK;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n * 32 + CR_THREADS - 1) / CR_THREADS, (int64_t)c->base.num_sms * 16));
+  crbm_logpsi_kernel<<<(unsigned)blocks, CR_THREADS, 0, reinterpret_cast<cudaStream_t>(stream)>>>(row_args(c, cfg, n), out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? NQS_OK : ccuda(c, e, "nqs_crbm_logpsi");
+}
+
+nqs_status nqs_crbm_local_energy(nqs_crbm *c, const uint32_t *cfg, int64_t n, float *eloc_re, float *eloc_im,
+                                 nqs_stream stream) {
+  using namespace nqs;
+  if (!c) return NQS_EINVAL;
+  if (!c->params_set) return cfail(c, NQS_EINVAL, "nqs_crbm_local_energy: parameters not set");
+  if (n < 0 || (n > 0 && (!cfg || !eloc_re || !eloc_im))) return cfail(c, NQS_EINVAL, "nqs_crbm_local_energy: bad arguments");
+  if (n == 0) return NQS_OK;
+  CElocArgs a;
+  a.r = row_args(c, cfg, n);
+  a.et = c->d_et;
+  a.nb = c->d_nb;
+  a.J = (float)c->J;
+  a.h = (float)c->h;
+  a.eloc_re = eloc_re;
+  a.eloc_im = eloc_im;
+  cudaError_t e = dispatch_eloc(c, a, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? NQS_OK : ccuda(c, e, "nqs_crbm_local_energy");
+}
+
+nqs_status nqs_crbm_stats(nqs_crbm *c, const float *eloc_re, const float *eloc_im, int64_t n, int64_t n_chains,
+                          const int64_t *n_accepted, int64_t proposals_per_chain, double *out, nqs_stream stream) {
+  if (!c) return NQS_EINVAL;
+  if (n <= 0 || n_chains <= 0 || n % n_chains != 0 || !eloc_re || !eloc_im || !out)
+    return cfail(c, NQS_EINVAL, "nqs_crbm_stats: need n > 0 a multiple of n_chains and non-null eloc/out");
+  if (n_accepted && proposals_per_chain <= 0) return cfail(c, NQS_EINVAL, "nqs_crbm_stats: proposals_per_chain must be > 0");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = nqs::energy_stats(&c->base, eloc_re, n, n_chains, n_accepted, proposals_per_chain, out, s);
+  if (e == cudaSuccess) e = nqs::energy_stats(&c->base, eloc_im, n, n_chains, nullptr, 1, c->d_imstats, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out + 5, c->d_imstats, sizeof(double), cudaMemcpyDeviceToDevice, s);
+  return e == cudaSuccess ? NQS_OK : ccuda(c, e, "nqs_crbm_stats");
+}
+
+nqs_status nqs_crbm_logpsi_grad(nqs_crbm *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc_re,
+                                const float *eloc_im, const double *stats, double *force, nqs_stream stream) {
+  using namespace nqs;
+  if (!c) return NQS_EINVAL;
+  if (!c->params_set) return cfail(c, NQS_EINVAL, "nqs_crbm_logpsi_grad: parameters not set");
+  if (n < 0 || (n > 0 && !cfg)) return cfail(c, NQS_EINVAL, "nqs_crbm_logpsi_grad: bad arguments");
+  if (force && n > 0 && (!eloc_re || !eloc_im || !stats))
+    return cfail(c, NQS_EINVAL, "nqs_crbm_logpsi_grad: the force needs eloc and stats");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (force) e = cudaMemsetAsync(force, 0, (size_t)c->P * 2 * sizeof(double), s);
+  if (e != cudaSuccess || n == 0) return e == cudaSuccess ? NQS_OK : ccuda(c, e, "nqs_crbm_logpsi_grad");
+  const CRowArgs r = row_args(c, cfg, n);
+  if (O) {
+    const int64_t blocks = std::min<int64_t>(n, (int64_t)c->base.num_sms * 16);
+    crbm_grad_rows_kernel<<<(unsigned)blocks, CR_THREADS, c->M_pad * sizeof(float2), s>>>(
+        r, c->P, reinterpret_cast<float2 *>(O));
+    if ((e = cudaGetLastError()) != cudaSuccess) return ccuda(c, e, "nqs_crbm_logpsi_grad");
+  }
+  if (force) {
+    CForceArgs a;
+    a.r = r;
+    a.eloc_re = eloc_re;
+    a.eloc_im = eloc_im;
+    a.stats = stats;
+    a.force = reinterpret_cast<double2 *>(force);
+    const int tiles = (c->M + 1 + CR_FU - 1) / CR_FU;
+    const int64_t blocks_rows = (n + CR_FR - 1) / CR_FR;
+    const int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(blocks_rows, ((int64_t)c->base.num_sms * 4 + tiles - 1) / tiles));
+    a.rows_per_cta = ((blocks_rows + chunks - 1) / chunks) * CR_FR;
+    const int64_t gx = (n + a.rows_per_cta - 1) / a.rows_per_cta;
+    crbm_force_kernel<<<dim3((unsigned)gx, (unsigned)tiles), CR_FTHREADS, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return ccuda(c, e, "nqs_crbm_logpsi_grad");
+    crbm_scale_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((2 * c->P + 255) / 256, 1024)), 256, 0, s>>>(
+        force, 2 * c->P, 1.0 / (double)n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return ccuda(c, e, "nqs_crbm_logpsi_grad");
+  }
+  return NQS_OK;
+}
+
+nqs_status nqs_crbm_check_status(nqs_crbm *c, nqs_stream stream) {
+  if (!c) return NQS_EINVAL;
+  nqs_status st = nqs_check_status(&c->base, stream);
+  if (st != NQS_OK) c->err = c->base.err;
+  return st;
+}
+
+}  // extern "C"
