@@ -322,7 +322,8 @@ def run_ours(args, rank, world, dist):
 
 # ------------------------------------------------------------------------------------------
 # The other workloads (--workload): the 1D N = 16 RBM, the dense 10 x 10 Heisenberg, the 48
-# batched TFIM instances and the dense 16 x 16 J1-J2 ansatz.  Each step is the whole hot path
+# batched TFIM instances, the dense 16 x 16 J1-J2 ansatz and the 10 x 10 complex-parameter RBM.
+# Each step is the whole hot path
 # of that workload; the line has the same keys as the default workload's.
 
 class _Phased:
@@ -404,6 +405,81 @@ class RbmStep:
             "roofline": {"bound": "alu", "kernel": "rbm_sweep_kernel", "achieved": ach, "peak": peak,
                          "unit": "T lane-ops/s", "frac": ach / peak, "traffic": None,
                          "note": "method arithmetic per proposal (2M + 3M per accept) vs SMs x 128 FP32 lanes "
+                                 "x max clock"},
+        }
+
+
+class ComplexRbmStep:
+    """The default workload's lattice, width and sizes with complex a, b, W (App. G): set_params,
+    init, sweeps on 2 Re delta, complex local energies, statistics, conjugate force and the
+    last sweep's O rows."""
+
+    def __init__(self, nqs, torch, dev, wl, C=None, T=None, B=None):
+        lat = wl.ham.lattice
+        self.wl, self.torch = wl, torch
+        self.N, self.M = lat.n_sites, wl.n_hidden
+        self.C, self.T, self.B = C or wl.n_chains, T or wl.n_sweeps, wl.burn_in if B is None else B
+        self.S = (self.T - self.B) * self.C
+        self.ctx = nqs.ComplexContext(lat.Lx, lat.Ly, J1=wl.ham.J1, h=wl.ham.h, n_hidden=self.M)
+        P = self.ctx.P
+        self.params_h = torch.from_numpy(
+            workloads.complex_rbm_params(self.N, self.M, wl.weight_sigma, wl.seed)).pin_memory()
+        self.params = self.params_h.to(dev)
+        z = lambda *sh, dt=torch.int32: torch.zeros(sh, dtype=dt, device=dev)
+        self.state, self.samples = z(self.C, self.ctx.W), z(self.S, self.ctx.W)
+        self.nacc = z(self.C, dt=torch.int64)
+        self.eloc_re, self.eloc_im = z(self.S, dt=torch.float32), z(self.S, dt=torch.float32)
+        self.stats, self.force = z(6, dt=torch.float64), z(P, dt=torch.complex128)
+        self.O = z(self.C, P, dt=torch.complex64)
+        self.out_h = torch.zeros(6 + 2 * P, dtype=torch.float64).pin_memory()
+        self.ph = _Phased(torch, ["set_params+init", "sweep", "local_energy", "stats+force", "O_rows"])
+        # prepare, init, sweep, local energy, 2 x (stats partial + final), force + scale, O rows
+        self.launches = 1 + 1 + 1 + 1 + 4 + 2 + 1
+        self.h2d, self.d2h = P * 16, (6 + 2 * P) * 8
+
+    def run(self, seed, host_io=False):
+        c, ph = self.ctx, self.ph
+        if host_io:
+            self.params.copy_(self.params_h, non_blocking=True)
+        ph.mark(0)
+        c.set_params(self.params)
+        c.init_chains(self.state, seed)
+        ph.mark(1)
+        c.sweep(self.state, self.T, self.B, seed + 1, 0, self.samples, self.nacc)
+        ph.mark(2)
+        c.local_energy(self.samples, self.eloc_re, self.eloc_im)
+        ph.mark(3)
+        c.stats(self.eloc_re, self.eloc_im, self.C, self.stats, self.nacc, self.T * self.N)
+        c.logpsi_grad(self.samples, None, self.eloc_re, self.eloc_im, self.stats, self.force)
+        ph.mark(4)
+        c.logpsi_grad(self.samples[self.S - self.C:], self.O)
+        ph.mark(5)
+        if host_io:
+            self.out_h[:6].copy_(self.stats, non_blocking=True)
+            self.out_h[6:].copy_(self.torch.view_as_real(self.force).reshape(-1), non_blocking=True)
+
+    def units(self):
+        return self.C * self.T * self.N
+
+    def describe(self, ms, accepts, peaks_, n_sm):
+        # per proposal and unit: two spin-signed table factors, two FMAs for sinh x' and cos y',
+        # the square sum and the running product (6); an accepted flip rewrites four values (8)
+        alg = 6.0 * self.M * self.units() + 8.0 * self.M * accepts
+        ach = alg / (ms["sweep"] / 1e3) / 1e12
+        peak = n_sm * 128 * float(peaks_.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+        lat = self.wl.ham.lattice
+        return {
+            "config": {"workload": self.wl.name + "_complex", "lattice": f"{lat.Lx}x{lat.Ly} periodic",
+                       "h": self.wl.ham.h, "n_hidden": self.M, "chains": self.C, "sweeps": self.T,
+                       "burn_in": self.B, "samples": self.S, "params": self.ctx.P,
+                       "weights": f"complex, re and im N(0, {self.wl.weight_sigma}^2)"},
+            "local_energy": {"value": self.S / (ms["local_energy"] / 1e3), "unit": "samples/s"},
+            "sweep": {"value": self.units() / (ms["sweep"] / 1e3), "unit": "proposals/s",
+                      "acceptance": accepts / self.units()},
+            "energy": float(self.stats[0].item()),
+            "roofline": {"bound": "alu", "kernel": "crbm_sweep_kernel", "achieved": ach, "peak": peak,
+                         "unit": "T lane-ops/s", "frac": ach / peak, "traffic": None,
+                         "note": "method arithmetic per proposal (6M + 8M per accept) vs SMs x 128 FP32 lanes "
                                  "x max clock"},
         }
 
@@ -659,6 +735,8 @@ def run_workload(args, rank, world, dist):
         st = DenseStep(nqs, torch, dev, wl, C, T or 2, 1 if B is None else B,
                        n_grad=args.grad_rows or wl.extra["minsr_samples"], minsr_lambda=1e-3,
                        dtype="fp8" if args.dtype == "fp8" else "bf16")
+    elif args.workload == "crbm-tfim2d":
+        st = ComplexRbmStep(nqs, torch, dev, WL, C, T, B)
     else:
         st = BatchStep(nqs, torch, dev)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
@@ -709,7 +787,8 @@ def run_workload(args, rank, world, dist):
                       + "fp32 accumulate, fp32 layer-0 cache)",
                       "j1j2-dense": ("fp8 e4m3 sampling (bf16 local energy, " if args.dtype == "fp8" else "bf16 (")
                       + "fp32 accumulate, fp32 layer-0 cache)",
-                      "batched": "f16 sampling (f32 caches, accept, statistics)"}[args.workload],
+                      "batched": "f16 sampling (f32 caches, accept, statistics)",
+                      "crbm-tfim2d": "complex f32 (f64 statistics and force accumulation)"}[args.workload],
             "data": "synthetic (seeded random-init networks, random initial spins)"}
     line.update(d)
     if args.chains or args.sweeps or args.burn_in is not None or args.grad_rows:
@@ -791,7 +870,7 @@ def main():
     ap.add_argument("--burn-in", type=int, default=None, help="profiling only: override the burn-in")
     ap.add_argument("--grad-rows", type=int, default=0, help="profiling only (j1j2-dense): O rows / minSR samples")
     ap.add_argument("--workload", default="tfim2d", choices=["tfim2d", "tfim1d", "heis2d-dense", "batched",
-                                                             "j1j2-dense", "noisy-rbm"],
+                                                             "j1j2-dense", "noisy-rbm", "crbm-tfim2d"],
                     help="tfim2d: the 10x10 alpha=4 RBM workload (default); the others measure the other "
                          "workloads' steps with the same line")
     args = ap.parse_args()

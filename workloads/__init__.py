@@ -69,6 +69,13 @@ def rbm_params(n, m, sigma, seed):
     return rng.normal(0.0, sigma, size=rbm_n_params(n, m)).astype(np.float64)
 
 
+def complex_rbm_params(n, m, sigma, seed):
+    """Complex a, b, W: the real parts are rbm_params(n, m, sigma, seed), the imaginary parts
+    N(0, sigma^2) i.i.d. from seed + 1 (complex128, order [a | b | W])."""
+    im = np.random.default_rng(seed + 1).normal(0.0, sigma, size=rbm_n_params(n, m))
+    return rbm_params(n, m, sigma, seed) + 1j * im
+
+
 def dense_params(n, widths, seed, bias_sigma=0.0):
     """He initialisation: W_l ~ N(0, 2 / fan_in); biases ~ N(0, bias_sigma^2) (0 by default)."""
     rng = np.random.default_rng(seed)
