@@ -438,8 +438,8 @@ __global__ void __launch_bounds__(CR_THREADS) crbm_grad_rows_kernel(const CRowAr
 //   G[x][j] = conj(t_j(x)) e(x) (j < M),  G[x][M] = e(x),     e = eps - E,
 //   S[x][i] = s_i(x) (i < N),             S[x][N] = 1,
 // Fsum = G^T S: F_W = Fsum[j][i], F_b = Fsum[j][N], F_a = Fsum[M][i].  CTA (row range,
-// tile of CR_FU units): phase A builds G for CR_FR rows, phase B accumulates thread i's
-// column in FP32 over the block and in FP64 across blocks, then adds to the FP64 output.
+// tile of CR_FU units): phase A builds G for CR_FR rows, phase B accumulates site columns
+// in FP32 over the block and in FP64 across blocks, then adds to the FP64 output.
 struct CForceArgs {
   CRowArgs r;
   const float *eloc_re, *eloc_im;
@@ -448,7 +448,11 @@ struct CForceArgs {
   double2 *force;
 };
 
+// HALVES = 2 (N + 1 <= 144): phase B thread (i, h) takes site i and units h*8 .. h*8 + 7 of
+// the tile, so 2 (N + 1) threads share the accumulation; HALVES = 1 otherwise.
+template <int HALVES>
 __global__ void __launch_bounds__(CR_FTHREADS) crbm_force_kernel(const CForceArgs a) {
+  constexpr int UPT = CR_FU / HALVES;  // units per phase-B thread
   __shared__ uint32_t sbits[CR_FR][8];
   __shared__ float2 g[CR_FR][CR_FU];
   const int tid = threadIdx.x;
@@ -457,9 +461,11 @@ __global__ void __launch_bounds__(CR_FTHREADS) crbm_force_kernel(const CForceArg
   const int64_t x_begin = blockIdx.x * a.rows_per_cta;
   const int64_t x_end = std::min<int64_t>(a.r.n, x_begin + a.rows_per_cta);
   const float Ere = (float)a.stats[0], Eim = (float)a.stats[5];
-  double accd[CR_FU][2];
+  const int i = tid % (N + 1), h = tid / (N + 1);
+  const bool worker = h < HALVES;
+  double accd[UPT][2];
 #pragma unroll
-  for (int u = 0; u < CR_FU; ++u) accd[u][0] = accd[u][1] = 0.0;
+  for (int u = 0; u < UPT; ++u) accd[u][0] = accd[u][1] = 0.0;
   for (int64_t r0 = x_begin; r0 < x_end; r0 += CR_FR) {
     for (int idx = tid; idx < CR_FR * W; idx += CR_FTHREADS) {
       const int rr = idx / W, q = idx % W;
@@ -472,19 +478,24 @@ __global__ void __launch_bounds__(CR_FTHREADS) crbm_force_kernel(const CForceArg
       const int64_t x = r0 + rr;
       const bool valid = x < x_end;
       const float ex = valid ? a.eloc_re[x] - Ere : 0.f, ey = valid ? a.eloc_im[x] - Eim : 0.f;
+      const int ja = j0 + uu, jb = ja + 1;
+      const int ca = std::min(ja, a.r.M_pad - 1), cb = std::min(jb, a.r.M_pad - 1);
+      float tax = a.r.b[ca].x, tay = a.r.b[ca].y, tbx = a.r.b[cb].x, tby = a.r.b[cb].y;
+#pragma unroll 4
+      for (int ii = 0; ii < N; ++ii) {
+        const float sp = spin_of(sbits[rr][ii >> 5], ii & 31);
+        const float2 wa = a.r.Wt[(int64_t)ii * a.r.M_pad + ca], wb = a.r.Wt[(int64_t)ii * a.r.M_pad + cb];
+        tax = fmaf(sp, wa.x, tax);
+        tay = fmaf(sp, wa.y, tay);
+        tbx = fmaf(sp, wb.x, tbx);
+        tby = fmaf(sp, wb.y, tby);
+      }
 #pragma unroll
       for (int v = 0; v < 2; ++v) {
-        const int j = j0 + uu + v;
+        const int j = v ? jb : ja;
         float2 gv = make_float2(0.f, 0.f);
         if (j < M) {
-          float tx = a.r.b[j].x, ty = a.r.b[j].y;
-          for (int i = 0; i < N; ++i) {
-            const float s = spin_of(sbits[rr][i >> 5], i & 31);
-            const float2 w = a.r.Wt[(int64_t)i * a.r.M_pad + j];
-            tx = fmaf(s, w.x, tx);
-            ty = fmaf(s, w.y, ty);
-          }
-          const float2 t = tanh_c(tx, ty);
+          const float2 t = v ? tanh_c(tbx, tby) : tanh_c(tax, tay);
           // conj(t) e
           gv = make_float2(fmaf(t.x, ex, t.y * ey), fmaf(t.x, ey, -t.y * ex));
         } else if (j == M) {
@@ -494,32 +505,31 @@ __global__ void __launch_bounds__(CR_FTHREADS) crbm_force_kernel(const CForceArg
       }
     }
     __syncthreads();
-    if (tid <= N) {
-      float acc[CR_FU][2];
+    if (worker) {
+      float acc[UPT][2];
 #pragma unroll
-      for (int u = 0; u < CR_FU; ++u) acc[u][0] = acc[u][1] = 0.f;
+      for (int u = 0; u < UPT; ++u) acc[u][0] = acc[u][1] = 0.f;
       for (int rr = 0; rr < CR_FR; ++rr) {
-        const float s = tid < N ? spin_of(sbits[rr][tid >> 5], tid & 31) : 1.f;
+        const float sp = i < N ? spin_of(sbits[rr][i >> 5], i & 31) : 1.f;
 #pragma unroll
-        for (int u = 0; u < CR_FU; ++u) {
-          const float2 gv = g[rr][u];
-          acc[u][0] = fmaf(s, gv.x, acc[u][0]);
-          acc[u][1] = fmaf(s, gv.y, acc[u][1]);
+        for (int u = 0; u < UPT; ++u) {
+          const float2 gv = g[rr][h * UPT + u];
+          acc[u][0] = fmaf(sp, gv.x, acc[u][0]);
+          acc[u][1] = fmaf(sp, gv.y, acc[u][1]);
         }
       }
 #pragma unroll
-      for (int u = 0; u < CR_FU; ++u) {
+      for (int u = 0; u < UPT; ++u) {
         accd[u][0] += (double)acc[u][0];
         accd[u][1] += (double)acc[u][1];
       }
     }
     __syncthreads();
   }
-  if (tid > N) return;
-  const int i = tid;
+  if (!worker) return;
 #pragma unroll
-  for (int u = 0; u < CR_FU; ++u) {
-    const int j = j0 + u;
+  for (int u = 0; u < UPT; ++u) {
+    const int j = j0 + h * UPT + u;
     int64_t k = -1;
     if (j < M && i < N) k = (int64_t)N + M + (int64_t)j * N + i;
     else if (j < M) k = (int64_t)N + j;
@@ -841,7 +851,10 @@ nqs_status nqs_crbm_logpsi_grad(nqs_crbm *c, const uint32_t *cfg, int64_t n, flo
     const int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(blocks_rows, ((int64_t)c->base.num_sms * 4 + tiles - 1) / tiles));
     a.rows_per_cta = ((blocks_rows + chunks - 1) / chunks) * CR_FR;
     const int64_t gx = (n + a.rows_per_cta - 1) / a.rows_per_cta;
-    crbm_force_kernel<<<dim3((unsigned)gx, (unsigned)tiles), CR_FTHREADS, 0, s>>>(a);
+    if (2 * (c->N + 1) <= CR_FTHREADS)
+      crbm_force_kernel<2><<<dim3((unsigned)gx, (unsigned)tiles), CR_FTHREADS, 0, s>>>(a);
+    else
+      crbm_force_kernel<1><<<dim3((unsigned)gx, (unsigned)tiles), CR_FTHREADS, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return ccuda(c, e, "nqs_crbm_logpsi_grad");
     crbm_scale_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((2 * c->P + 255) / 256, 1024)), 256, 0, s>>>(
         force, 2 * c->P, 1.0 / (double)n);
