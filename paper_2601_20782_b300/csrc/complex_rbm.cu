@@ -286,7 +286,7 @@ __device__ __forceinline__ void crbm_normalise(float2 &p, float &L, bool &dead) 
 // sites): the flip ratio of site i as a product over all units, read from the unit-major
 // (cosh 2W, sinh 2W) table once for the CR_SPW samples.
 template <int KU>
-__global__ void __launch_bounds__(CR_THREADS) crbm_eloc_kernel(const CElocArgs a) {
+__global__ void __launch_bounds__(CR_THREADS, 4) crbm_eloc_kernel(const CElocArgs a) {
   extern __shared__ float2 crbm_tanh[];  // [warps][CR_SPW][M_pad]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int M_pad = a.r.M_pad, N = a.r.N, W = a.r.W;
@@ -349,11 +349,24 @@ __global__ void __launch_bounds__(CR_THREADS) crbm_eloc_kernel(const CElocArgs a
           dead[r] = false;
         }
         const float4 *col = a.et + i;
+        // (cosh 2W, sinh 2W) of (j, i) for the current chunk of 8 units; the next chunk's
+        // loads are issued before the current one is consumed (load latency, not bandwidth,
+        // bounds this loop)
+        float4 cur[8], nxt[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) cur[jj] = __ldg(col + (int64_t)jj * N);
         for (int j0 = 0; j0 < M_pad; j0 += 8) {
+          if (j0 + 8 < M_pad) {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) nxt[jj] = __ldg(col + (int64_t)(j0 + 8 + jj) * N);
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) nxt[jj] = cur[jj];
+          }
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
             const int j = j0 + jj;
-            const float4 cs = __ldg(col + (int64_t)j * N);  // (cosh 2W, sinh 2W) of (j, i)
+            const float4 cs = cur[jj];
 #pragma unroll
             for (int r = 0; r < CR_SPW; ++r) {
               const float2 t = tw[r * M_pad + j];
@@ -365,6 +378,8 @@ __global__ void __launch_bounds__(CR_THREADS) crbm_eloc_kernel(const CElocArgs a
           }
 #pragma unroll
           for (int r = 0; r < CR_SPW; ++r) crbm_normalise(p[r], L[r], dead[r]);
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) cur[jj] = nxt[jj];
         }
         const float2 ai = a.r.a[i];
 #pragma unroll
