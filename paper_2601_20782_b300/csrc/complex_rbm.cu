@@ -47,7 +47,7 @@ namespace {
 constexpr int CR_THREADS = 128;
 constexpr int CR_SPW = 4;            // samples per warp of the local-energy kernel
 constexpr int CR_FU = 16;            // hidden units per force tile
-constexpr int CR_FR = 32;            // rows per force block
+constexpr int CR_FR = 64;            // rows per force block (phase A covers 32 rows per pass)
 constexpr int CR_FTHREADS = 288;     // force kernel: sites 0 .. N (N <= 256) in phase B
 constexpr double CR_MAX_RE_THETA = 10.0;  // sum_i |Re W_ji| + |Re b_j| (products of D_j stay finite)
 constexpr double CR_MAX_RE_W = 1.0;       // |Re W_ji| (conditioning of the hyperbolic update)
@@ -488,8 +488,10 @@ __global__ void __launch_bounds__(CR_FTHREADS) crbm_force_kernel(const CForceArg
       sbits[rr][q] = x < x_end ? a.r.cfg[x * W + q] : 0u;
     }
     __syncthreads();
-    if (tid < CR_FR * (CR_FU / 2)) {
-      const int rr = tid / (CR_FU / 2), uu = 2 * (tid % (CR_FU / 2));
+#pragma unroll 1
+    for (int rr0 = 0; rr0 < CR_FR; rr0 += 32) {
+      if (tid >= 32 * (CR_FU / 2)) break;
+      const int rr = rr0 + tid / (CR_FU / 2), uu = 2 * (tid % (CR_FU / 2));
       const int64_t x = r0 + rr;
       const bool valid = x < x_end;
       const float ex = valid ? a.eloc_re[x] - Ere : 0.f, ey = valid ? a.eloc_im[x] - Eim : 0.f;
