@@ -156,10 +156,16 @@ __global__ void __launch_bounds__(CR_THREADS) crbm_sweep_kernel(const CSweepArgs
       }
     }
     uint32_t bits = 0u;
+    // lane l draws the Philox block of proposal pair p/2 + l once per 64 proposals; the
+    // proposal's two words are then broadcast from that lane (same counters, same draws)
     uint4 r = make_uint4(0, 0, 0, 0);
     for (int p = 0; p < a.N; ++p) {
-      if ((p & 1) == 0) r = philox4x32_10(make_uint4((uint32_t)(p >> 1), a.sweep_offset + t, (uint32_t)c, TAG_SWEEP), a.k0, a.k1);
-      const uint32_t w0 = (p & 1) ? r.z : r.x, w1 = (p & 1) ? r.w : r.y;
+      if ((p & 63) == 0)
+        r = philox4x32_10(make_uint4((uint32_t)((p >> 1) + lane), a.sweep_offset + t, (uint32_t)c, TAG_SWEEP), a.k0,
+                          a.k1);
+      const int src = (p & 63) >> 1;
+      const uint32_t w0 = __shfl_sync(FULL_MASK, (p & 1) ? r.z : r.x, src);
+      const uint32_t w1 = __shfl_sync(FULL_MASK, (p & 1) ? r.w : r.y, src);
       const int i = (int)index_from_word(w0, (uint32_t)a.N);
       const float u = (float)(w1 >> 8) * 0x1p-24f;
       const float sg = spin_of(__shfl_sync(FULL_MASK, word, i >> 5), i & 31);
