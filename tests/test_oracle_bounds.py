@@ -102,3 +102,54 @@ def test_unit_roundoffs_against_the_printed_table():
         assert u == pytest.approx(printed, rel=2e-3)
     assert bounds.UNIT_ROUNDOFF["f16"] == np.finfo(np.float16).eps / 2
     assert bounds.UNIT_ROUNDOFF["f32"] == np.finfo(np.float32).eps / 2
+
+
+def test_reported_bound_recovers_the_delta_sigma_from_flip_increments():
+    # Theorem 3's statement takes eps ~ N(mu, 2 sigma^2) with sigma the std of delta (Sec. 3.1):
+    # for delta ~ N(0, sigma^2) drawn independently per configuration, the single-flip
+    # increments eps(x, y) = delta(y) - delta(x) have variance 2 sigma^2, so reported_bound
+    # (which takes std(eps)) must return min(Pinsker, Thm 3) at the sigma that made delta.
+    # Dropping the sqrt 2, or swapping (mu, std), moves the result by far more than the
+    # sampling tolerance used here.
+    N = 12
+    x = np.arange(2 ** N)
+    for sigma in (0.02, 0.3, 1.0):
+        delta = np.random.default_rng(7).normal(0.0, sigma, size=x.size)
+        eps = np.concatenate([delta[x ^ (1 << i)] - delta for i in range(N)])
+        got = bounds.reported_bound(eps.mean(), eps.std())
+        want = min(sigma / 2, bounds.thm3_bound(0.0, sigma))
+        assert got == pytest.approx(want, rel=0.03)
+        # and it bounds the exact distance of pi e^delta / Z from pi for an enumerated RBM whose
+        # pi spreads over the space (Pinsker's sigma / 2 uses KL = sigma^2 / 2, the expectation
+        # over delta, which a pi concentrated on a few configurations need not meet draw by draw)
+        model = RBM(N, N, rbm_params(N, N, 0.05, 11))
+        pi = exact.exact_pi(model.logpsi, N)
+        assert bounds.tv_distance(pi, bounds.perturbed_pi(pi, delta)) <= got
+
+
+@pytest.mark.parametrize("mu,sigma", [(0.1, 0.2), (-0.4, 0.6), (0.02, 0.01)])
+def test_reported_bound_with_a_mean_shift(mu, sigma):
+    # increments drawn as N(mu, 2 sigma^2) directly: the bound is min(sigma / 2, Thm 3(mu, sigma))
+    eps = np.random.default_rng(3).normal(mu, np.sqrt(2.0) * sigma, size=400_000)
+    got = bounds.reported_bound(eps.mean(), eps.std())
+    assert got == pytest.approx(min(sigma / 2, bounds.thm3_bound(mu, sigma)), rel=5e-3)
+    # Theorem 3 is the Gaussian expectation of Theorem 2's average: 1 - E[e^{-|eps|}]
+    assert bounds.thm2_bound(eps) == pytest.approx(bounds.thm3_bound(mu, sigma), rel=5e-3, abs=2e-4)
+
+
+def test_thm2_bound_on_chain_proposals_bounds_the_one_step_distance():
+    # Theorem 2: ||pi'(P~ - P)||_TV <= 1 - E_{x ~ pi', y ~ q}[e^{-|eps(x, y)|}], with the
+    # expectation estimated from proposals drawn as a chain would draw them (x ~ pi',
+    # y a uniform single flip of x).  Exact average and its Monte Carlo estimate agree.
+    pi, pi_t, delta, P, Pt = _kernels(N=5, sigma_delta=0.4, seed=3)
+    D, N = pi.size, 5
+    x = np.arange(D)
+    rng = np.random.default_rng(5)
+    for trial in range(3):
+        pip = rng.dirichlet(np.ones(D))
+        xs = rng.choice(D, size=200_000, p=pip)
+        ys = xs ^ (1 << rng.integers(0, N, size=xs.size))
+        est = bounds.thm2_bound(delta[ys] - delta[xs])
+        exact_avg = sum((pip * np.exp(-np.abs(delta[x ^ (1 << i)] - delta[x]))).sum() / N for i in range(N))
+        assert est == pytest.approx(1.0 - exact_avg, abs=4e-3)
+        assert bounds.tv_distance(0.0, pip @ (Pt - P)) <= 1.0 - exact_avg + 1e-15

@@ -193,3 +193,26 @@ def test_sample_force_and_stats():
     assert E == pytest.approx(eps.mean()) and var == pytest.approx(eps.var())
     cm = eps.reshape(5, 8).mean(axis=0)
     assert err == pytest.approx(cm.std(ddof=1) / np.sqrt(8))
+
+
+def test_energy_error_from_chain_blocks_matches_independent_routes():
+    # The error of E from per-chain means (statistics reading) against routes that do not use
+    # chain blocks: (i) i.i.d. draws, whose error of the mean is sigma / sqrt(n); (ii) AR(1)
+    # chains x_{t+1} = rho x_t + sqrt(1 - rho^2) z, whose long-chain error of the mean is
+    # sigma sqrt((1 + rho) / (1 - rho) / n).  The chain-block estimate must see the
+    # autocorrelation that the naive sqrt(Var / n) misses.
+    rng = np.random.default_rng(12)
+    K, C, sigma = 400, 512, 1.7
+    eps = rng.normal(3.0, sigma, size=(K, C)).reshape(-1)      # sweep-major rows k * C + c
+    E, var, err = energy_stats(eps, C)
+    assert var == pytest.approx(sigma ** 2, rel=0.01)
+    assert err == pytest.approx(sigma / np.sqrt(K * C), rel=0.08)
+    rho = 0.8
+    x = np.empty((K, C))
+    x[0] = rng.normal(size=C)
+    for k in range(1, K):
+        x[k] = rho * x[k - 1] + np.sqrt(1 - rho ** 2) * rng.normal(size=C)
+    E, var, err = energy_stats(sigma * x.reshape(-1), C)
+    want = sigma * np.sqrt((1 + rho) / (1 - rho) / (K * C))
+    assert err == pytest.approx(want, rel=0.1)
+    assert err > 2.5 * np.sqrt(var / (K * C))
