@@ -85,29 +85,32 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def reduce_stats_across_ranks(stats, n_local, dist):
-    """Energy statistics over all ranks' samples, in place: an FP64 all-reduce of
-    (n, n * mean, n * (var + mean^2), (n * err)^2).  Afterwards stats[0] is the global E,
-    so every rank's force (1/n_r) sum_x O(x) (eps(x) - E) uses the same E."""
-    import torch
-    n_r = float(n_local)
-    buf = torch.cat([torch.tensor([n_r], dtype=torch.float64, device=stats.device),
-                     stats[:1] * n_r, (stats[1:2] + stats[:1] ** 2) * n_r, (stats[2:3] * n_r) ** 2])
-    dist.all_reduce(buf)
-    n = buf[0]
-    mean = buf[1] / n
-    stats[0] = mean
-    stats[1] = buf[2] / n - mean ** 2
-    stats[2] = torch.sqrt(buf[3]) / n
-    return n
-
-
-def reduce_force_across_ranks(force, n_local, n_total, dist):
-    """F = (1/n) sum over all ranks of n_r F_r, exact when every F_r was centred on the
-    global E (reduce_stats_across_ranks first); in place."""
-    force.mul_(float(n_local))
-    dist.all_reduce(force)
-    force.div_(float(n_total))
+def measure_alu_peaks(nqs, torch, dev, target_ms=25.0):
+    """Issue rates of the instructions the RBM kernels use (nqs_probe_alu), in T lane-ops/s:
+    every SM full (4 CTAs x 512 threads), 8 independent chains per thread, best of three
+    launches of about target_ms each, timed with CUDA events on the launching stream.  The
+    SM clock is sampled while they run."""
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = n_sm * 4, 512
+    sink = torch.zeros(blocks, dtype=torch.float32, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    with ClockSampler(dev.index) as clk:
+        for kind in nqs.PROBE_KINDS:
+            def run(iters):
+                ev0.record()
+                nqs.probe_alu(kind, blocks, threads, iters, sink)
+                ev1.record()
+                torch.cuda.synchronize()
+                return ev0.elapsed_time(ev1)
+            run(64)
+            iters = max(64, int(2048 * target_ms / max(run(2048), 1e-3)))
+            best = min(run(iters) for _ in range(3))
+            ops = blocks * threads * iters * 8 * nqs.PROBE_OPS[kind]
+            out[kind] = ops / (best / 1e3) / 1e12
+    out["unit"] = "T lane-ops/s (FP32 / F16 / BF16 element operations, or MUFU results)"
+    out["clocks"] = clk.summary()
+    return out
 
 
 def thm3_bound(mu, sigma):
@@ -136,14 +139,16 @@ class Step:
         self.nacc = torch.zeros(C, dtype=torch.int64, device=dev)
         self.eloc = torch.zeros(self.S, dtype=torch.float32, device=dev)
         self.stats = torch.zeros(5, dtype=torch.float64, device=dev)
+        self.moments = torch.zeros(8, dtype=torch.float64, device=dev)
         self.force = torch.zeros(P, dtype=torch.float64, device=dev)
         self.O = torch.zeros((C, P), dtype=torch.float32, device=dev)
         self.ws = torch.zeros(self.ctx.logpsi_grad_workspace(self.S), dtype=torch.uint8, device=dev)
         self.out_h = torch.zeros(5 + P, dtype=torch.float64).pin_memory()
         self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         # set_params (prepare, colsum, bounds; a 16-bit copy adds the FP32 copy's prepare and colsum),
-        # init, sweep, local energy, stats (2), force (tensor-core kernel + reduction), O rows
-        self.launches = (3 if dtype == "f32" else 5) + 1 + 1 + 1 + 2 + 2 + 1
+        # init, sweep, local energy, stats (2; 3 with the multi-rank finalize), force (tensor-core
+        # kernel + reduction), O rows
+        self.launches = (3 if dtype == "f32" else 5) + 1 + 1 + 1 + (3 if dist else 2) + 2 + 1
 
     def run(self, seed, host_io=False):
         c, ev = self.ctx, self.ev
@@ -157,12 +162,15 @@ class Step:
         ev[2].record()
         c.local_energy_chains(self.samples, self.C, self.eloc)
         ev[3].record()
-        c.stats(self.eloc, self.C, self.stats, self.nacc, self.T * self.N)
-        if self.dist:   # the one exchange of the step: global E first, then the force
-            n_total = reduce_stats_across_ranks(self.stats, self.S, self.dist)
-        c.logpsi_grad(self.samples, None, self.eloc, self.stats, self.force, self.ws)
-        if self.dist:
-            reduce_force_across_ranks(self.force, self.S, n_total, self.dist)
+        if self.dist:   # the one exchange of the step: pooled statistics (global E) first, then the force
+            from paper_2601_20782_b300.distributed import exchange_stats, exchange_force
+            c.stats_moments(self.eloc, self.C, self.moments, self.nacc, self.T * self.N)
+            exchange_stats(c, self.moments, self.stats)
+            c.force_share(self.samples, self.eloc, self.stats, self.force, self.ws)
+            exchange_force(self.force)
+        else:
+            c.stats(self.eloc, self.C, self.stats, self.nacc, self.T * self.N)
+            c.logpsi_grad(self.samples, None, self.eloc, self.stats, self.force, self.ws)
         ev[4].record()
         c.logpsi_grad(self.samples[self.S - self.C:], self.O)
         ev[5].record()
@@ -269,15 +277,14 @@ def run_ours(args, rank, world, dist):
     r = results[args.dtype]
     ph = r["phase"]   # ms per phase: prep+init, sweep, eloc, stats+force, O rows
     value = world * proposals_step * args.steps / r["t_dev"]
-    pk = peaks()
-    sm_max = float(pk.get("sm_max_mhz", 2032.0))
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu = measure_alu_peaks(nqs, torch, dev)
     # Sweep roofline (arithmetic of the method per proposal): one FMA (factor) and one multiply
     # (product) per hidden unit, three multiplies per hidden unit per accepted flip, counted as
-    # lane operations; peak = SMs x 128 FP32 lanes x max SM clock.
+    # FP32 lane operations; peak = the measured issue rate of the paired FP32 FMA (fma.rn.f32x2)
+    # in the same units, the instruction those operations are issued as.
     alg_ops = 2.0 * M * proposals_step + 3.0 * M * r["accepts"]
     achieved = alg_ops / (ph[1] / 1e3) / 1e12
-    peak = n_sm * 128 * sm_max * 1e6 / 1e12
+    peak = alu["ffma2"]
     line = {
         "metric": METRIC,
         "value": value,
@@ -310,8 +317,13 @@ def run_ours(args, rank, world, dist):
         "bias": bias,
         "roofline": {"bound": "alu", "kernel": "rbm_sweep_kernel", "achieved": achieved, "peak": peak,
                      "unit": "T lane-ops/s", "frac": achieved / peak,
+                     "peak_source": "measured in this run: fma.rn.f32x2 issue rate (nqs_probe_alu), FP32 ops",
                      "traffic": SWEEP_TRAFFIC_BYTES.get(args.dtype) if (C, T) == (WL.n_chains, WL.n_sweeps) else None,
-                     "note": "method arithmetic per proposal (2M + 3M per accept) vs SMs x 128 FP32 lanes x max clock"},
+                     "traffic_source": "from profile (ncu dram bytes of this kernel at this size; null when the "
+                                       "kernel changed since the capture)",
+                     "note": "method arithmetic per proposal (2M + 3M per accept) vs the measured paired-FP32 "
+                             "issue rate"},
+        "alu_peaks": alu,
         "e2e": {"value": world * proposals_step * args.steps / t_e2e, "unit": "proposals/s",
                 "h2d_bytes_per_step": steps[args.dtype].ctx.P * 8, "d2h_bytes_per_step": (5 + steps[args.dtype].ctx.P) * 8},
         "gpu_launches": steps[args.dtype].launches * args.steps,
@@ -393,9 +405,10 @@ class RbmStep:
     def describe(self, ms, accepts, peaks_, n_sm):
         alg = 2.0 * self.M * self.units() + 3.0 * self.M * accepts
         ach = alg / (ms["sweep"] / 1e3) / 1e12
-        peak = n_sm * 128 * float(peaks_.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+        peak = peaks_["alu"]["ffma2"]
         lat = self.wl.ham.lattice
         return {
+            "alu_peaks": peaks_["alu"],
             "config": {"workload": self.wl.name, "lattice": f"{lat.Lx}x{lat.Ly} periodic", "h": self.wl.ham.h,
                        "n_hidden": self.M, "chains": self.C, "sweeps": self.T, "burn_in": self.B,
                        "samples": self.S, "params": self.ctx.P},
@@ -404,8 +417,8 @@ class RbmStep:
                       "acceptance": accepts / self.units()},
             "roofline": {"bound": "alu", "kernel": "rbm_sweep_kernel", "achieved": ach, "peak": peak,
                          "unit": "T lane-ops/s", "frac": ach / peak, "traffic": None,
-                         "note": "method arithmetic per proposal (2M + 3M per accept) vs SMs x 128 FP32 lanes "
-                                 "x max clock"},
+                         "note": "method arithmetic per proposal (2M + 3M per accept) vs the measured "
+                                 "fma.rn.f32x2 issue rate (FP32 ops)"},
         }
 
 
@@ -466,9 +479,10 @@ class ComplexRbmStep:
         # the square sum and the running product (6); an accepted flip rewrites four values (8)
         alg = 6.0 * self.M * self.units() + 8.0 * self.M * accepts
         ach = alg / (ms["sweep"] / 1e3) / 1e12
-        peak = n_sm * 128 * float(peaks_.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+        peak = peaks_["alu"]["ffma"]
         lat = self.wl.ham.lattice
         return {
+            "alu_peaks": peaks_["alu"],
             "config": {"workload": self.wl.name + "_complex", "lattice": f"{lat.Lx}x{lat.Ly} periodic",
                        "h": self.wl.ham.h, "n_hidden": self.M, "chains": self.C, "sweeps": self.T,
                        "burn_in": self.B, "samples": self.S, "params": self.ctx.P,
@@ -479,8 +493,8 @@ class ComplexRbmStep:
             "energy": float(self.stats[0].item()),
             "roofline": {"bound": "alu", "kernel": "crbm_sweep_kernel", "achieved": ach, "peak": peak,
                          "unit": "T lane-ops/s", "frac": ach / peak, "traffic": None,
-                         "note": "method arithmetic per proposal (6M + 8M per accept) vs SMs x 128 FP32 lanes "
-                                 "x max clock"},
+                         "note": "method arithmetic per proposal (6M + 8M per accept) vs the measured scalar "
+                                 "fma.rn.f32 issue rate (the complex sweep issues scalar FP32 operations)"},
         }
 
 
@@ -777,7 +791,10 @@ def run_workload(args, rank, world, dist):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_dev, t_e2e = tt.tolist()
     ms = {n: v / args.steps for n, v in tot.items()}
-    d = st.describe(ms, acc / args.steps, peaks(), torch.cuda.get_device_properties(dev).multi_processor_count)
+    pk = dict(peaks())
+    if isinstance(st, (RbmStep, ComplexRbmStep)):
+        pk["alu"] = measure_alu_peaks(nqs, torch, dev)
+    d = st.describe(ms, acc / args.steps, pk, torch.cuda.get_device_properties(dev).multi_processor_count)
     units = st.units()
     line = {"metric": METRIC, "value": world * units * args.steps / t_dev, "unit": "proposals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3,
@@ -804,17 +821,44 @@ def run_workload(args, rank, world, dist):
     return line
 
 
-def oracle_sample_subprocess(n_chains, n_sweeps, eloc_samples):
-    """oracle_sample in a fresh interpreter pinned to one BLAS / OpenMP thread."""
+def _oracle_cmd(n_chains, n_sweeps, eloc_samples, chain0=0):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = ("import json, bench; print(json.dumps(bench.oracle_sample(%d, %d, %d)))"
-            % (n_chains, n_sweeps, eloc_samples))
-    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, check=True)
+    code = ("import json, bench; print(json.dumps(bench.oracle_sample(%d, %d, %d, %d)))"
+            % (n_chains, n_sweeps, eloc_samples, chain0))
+    return [sys.executable, "-c", code], env
+
+
+def oracle_sample_subprocess(n_chains, n_sweeps, eloc_samples):
+    """oracle_sample in a fresh interpreter pinned to one BLAS / OpenMP thread."""
+    cmd, env = _oracle_cmd(n_chains, n_sweeps, eloc_samples)
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, check=True)
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_sample(n_chains, n_sweeps, eloc_samples):
+def oracle_sample_all_cores(n_chains, n_sweeps, eloc_samples, max_workers=64):
+    """The oracle on every host core at once: one single-threaded interpreter per core, each on
+    its own block of chains (distinct chain ids), started together.  The aggregate rate is the
+    sum of the workers' own rates, each measured inside the worker over its sampling (the
+    windows overlap; interpreter start-up is not counted)."""
+    workers = max(1, min(os.cpu_count() or 1, max_workers))
+    procs = []
+    for w in range(workers):
+        cmd, env = _oracle_cmd(n_chains, n_sweeps, eloc_samples, w * n_chains)
+        procs.append(subprocess.Popen(cmd, cwd=ROOT, env=env, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                      text=True))
+    outs = []
+    for pr in procs:
+        out, _ = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError("oracle worker failed")
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    return {"proposals_per_s": sum(o["proposals_per_s"] for o in outs),
+            "eloc_samples_per_s": sum(o["eloc_samples_per_s"] for o in outs), "cores": workers,
+            "sample": f"{workers} workers x ({outs[0]['sample']})"}
+
+
+def oracle_sample(n_chains, n_sweeps, eloc_samples, chain0=0):
     """The FP64 oracle on a bounded sample of the same workload; returns rates."""
     from oracle.estimators import local_energy
     from oracle.hamiltonian import make_hamiltonian
@@ -825,9 +869,10 @@ def oracle_sample(n_chains, n_sweeps, eloc_samples):
     N, M = lat.n_sites, WL.n_hidden
     model = RBM(N, M, workloads.rbm_params(N, M, WL.weight_sigma, WL.seed))
     ham = make_hamiltonian(WL.ham)
-    s0 = init_spins_random(WL.seed, np.arange(n_chains), N)
+    ids = chain0 + np.arange(n_chains)
+    s0 = init_spins_random(WL.seed, ids, N)
     t0 = time.perf_counter()
-    out = mh_sweeps(model.logpsi, s0, np.arange(n_chains), WL.seed + 1, n_sweeps, 0)
+    out = mh_sweeps(model.logpsi, s0, ids, WL.seed + 1, n_sweeps, 0)
     t_sweep = time.perf_counter() - t0
     t0 = time.perf_counter()
     local_energy(ham, model.logpsi, out["samples"][:eloc_samples])
@@ -905,10 +950,14 @@ def main():
     line = run_ours(args, rank, world, dist)
     if rank == 0:
         if not args.no_cpu_baseline:
-            cb = oracle_sample_subprocess(1024, 8, 1024)
-            line["cpu_baseline"] = {"value": cb["proposals_per_s"], "unit": "proposals/s", "cores": 1,
+            cb = oracle_sample_all_cores(256, 6, 256)
+            one = oracle_sample_subprocess(1024, 8, 1024)
+            line["cpu_baseline"] = {"value": cb["proposals_per_s"], "unit": "proposals/s", "cores": cb["cores"],
                                     "kind": "oracle", "sample": cb["sample"],
-                                    "local_energy_samples_per_s": cb["eloc_samples_per_s"]}
+                                    "local_energy_samples_per_s": cb["eloc_samples_per_s"],
+                                    "one_core": {"value": one["proposals_per_s"], "unit": "proposals/s",
+                                                 "local_energy_samples_per_s": one["eloc_samples_per_s"],
+                                                 "sample": one["sample"]}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -194,6 +194,31 @@ nqs_status nqs_stats(nqs_ctx *ctx, const float *eloc, int64_t n, int64_t n_chain
                      const int64_t *n_accepted, int64_t proposals_per_chain, double *out,
                      nqs_stream stream);
 
+/* Multi-rank step (chains split over processes, one per GPU; no paper passage: the
+ * statistics of Sec. 2 Eq. loss and the force of App. I Eq. forces over the pooled samples).
+ * nqs_stats_moments writes the additive moments of this rank's samples, moments[8] (device):
+ *   [n, sum eloc, sum eloc^2, n_chains, sum_c m_c, sum_c m_c^2, sum n_accepted,
+ *    n_chains * proposals_per_chain (0 if n_accepted is NULL)],  m_c the per-chain means.
+ * Summing the moments of all ranks (an all-reduce SUM) and passing the sum to
+ * nqs_stats_finalize gives out[5] exactly as nqs_stats gives it for all ranks' chains
+ * together; with one rank the two calls equal nqs_stats.  Same argument checks as
+ * nqs_stats; nqs_stats_finalize needs moments[0] > 0 (unchecked on the device). */
+nqs_status nqs_stats_moments(nqs_ctx *ctx, const float *eloc, int64_t n, int64_t n_chains,
+                             const int64_t *n_accepted, int64_t proposals_per_chain, double *moments,
+                             nqs_stream stream);
+nqs_status nqs_stats_finalize(const double *moments, double *out, nqs_stream stream);
+
+/* App. I, Eq. forces, one rank's share: force[k] = (1 / stats[4]) sum_{x < n} O_k(x) (eloc[x] - stats[0])
+ * with stats (device, 5 doubles) as nqs_stats_finalize writes them for the pooled samples
+ * (global E and total count).  The shares of all ranks sum (all-reduce SUM) to the force of
+ * the pooled samples, since every rank centres on the same E.  With one rank and stats
+ * from nqs_stats this equals nqs_logpsi_grad's force.  With stats = (0, ., ., ., 1) and
+ * eloc = g it is the vector-Jacobian product sum_x g_x O(x) of log psi.  Arguments,
+ * workspace and errors as nqs_logpsi_grad with O = NULL; n = 0 sets force to zero. */
+nqs_status nqs_force_share(nqs_ctx *ctx, const uint32_t *configs, int64_t n, const float *eloc,
+                           const double *stats, double *force, void *workspace, size_t workspace_bytes,
+                           nqs_stream stream);
+
 /* No counterpart in the paper.  The force F of nqs_logpsi_grad (same arguments and
  * result, no O rows) for callers that cannot allocate device memory when they need
  * it: code running under another framework's memory budget, plugins whose host
@@ -204,9 +229,31 @@ nqs_status nqs_stats(nqs_ctx *ctx, const float *eloc, int64_t n, int64_t n_chain
  * looks up that array's device address (cudaGetSymbolAddress); make that first call
  * before any stream capture.  The context's device must be current.  All calls share
  * the one array, so calls whose kernels overlap on the GPU (different streams, or
- * different contexts on one device) race; serialise them.  Allocates nothing. */
+ * different contexts on one device) race; serialise them.  n = 0 sets the force to zero
+ * and returns NQS_OK, as nqs_logpsi_grad does; n < 0 or a NULL force (or NULL configs,
+ * eloc or stats with n > 0) return NQS_EINVAL; dense contexts NQS_EUNSUPPORTED.
+ * Allocates nothing. */
 nqs_status nqs_force_noalloc(nqs_ctx *ctx, const uint32_t *configs, int64_t n, const float *eloc,
                              const double *stats, double *force, nqs_stream stream);
+
+/* Issue-rate probe (no counterpart in the paper): the peak that the RBM kernels' ALU
+ * roofline divides by is measured, not assumed.  Launches `blocks` x `threads` threads
+ * (32 <= threads <= 512, a multiple of 32), each running 8 independent dependency chains of
+ * one instruction for `iters` iterations:
+ *   NQS_PROBE_FFMA   fma.rn.f32      (1 FP32 FMA per lane per instruction)
+ *   NQS_PROBE_FFMA2  fma.rn.f32x2    (2 FP32 FMAs per lane)
+ *   NQS_PROBE_FMUL2  mul.rn.f32x2    (2 FP32 multiplies per lane)
+ *   NQS_PROBE_HFMA2  fma.rn.f16x2    (2 F16 FMAs per lane)
+ *   NQS_PROBE_BFMA2  fma.rn.bf16x2   (2 BF16 FMAs per lane)
+ *   NQS_PROBE_LG2    lg2.approx.f32  (1 MUFU op per lane, plus one FP32 add feeding it)
+ *   NQS_PROBE_EX2    ex2.approx.f32  (1 MUFU op per lane, chained)
+ * The caller times the launch on `stream`; instructions = blocks * threads * iters * 8.
+ * sink: device float [blocks] (written only in a practically impossible case).  Bad sizes
+ * or kind: NQS_EINVAL. */
+enum { NQS_PROBE_FFMA = 0, NQS_PROBE_FFMA2 = 1, NQS_PROBE_FMUL2 = 2, NQS_PROBE_HFMA2 = 3, NQS_PROBE_BFMA2 = 4,
+       NQS_PROBE_LG2 = 5, NQS_PROBE_EX2 = 6 };
+nqs_status nqs_probe_alu(int32_t kind, int64_t blocks, int32_t threads, int64_t iters, float *sink,
+                         nqs_stream stream);
 
 /* Self-test of the tensor-core building block used by the contraction kernels (no
  * counterpart in the paper): D [128 x N] FP32 = A [128 x K] * B [N x K]^T in BF16 with FP32

@@ -87,6 +87,10 @@ _SIGS = {
     "nqs_stats": (_i32, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp]),
     "nqs_check_status": (_i32, [_vp, _vp]),
     "nqs_force_noalloc": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "nqs_probe_alu": (_i32, [_i32, _i64, _i32, _i64, _vp, _vp]),
+    "nqs_stats_moments": (_i32, [_vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp]),
+    "nqs_stats_finalize": (_i32, [_vp, _vp, _vp]),
+    "nqs_force_share": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nqs_selftest_tc_gemm": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "nqs_set_noise": (_i32, [_vp, ctypes.c_double, _u64]),
     "nqs_local_energy_chains": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp]),
@@ -235,6 +239,30 @@ class Context:
                                    int(proposals_per_chain), _ptr(out, (torch.float64,), "out", (5,), False),
                                    _stream()))
 
+    def stats_moments(self, eloc, n_chains, moments, n_accepted=None, proposals_per_chain=0):
+        """nqs_stats_moments: the additive moments [8] of these chains' statistics."""
+        n = eloc.shape[0]
+        self._check(_lib.nqs_stats_moments(self._h, _ptr(eloc, (torch.float32,), "eloc", (n,), False), n, n_chains,
+                                           _ptr(n_accepted, (torch.int64,), "n_accepted", (n_chains,)),
+                                           int(proposals_per_chain),
+                                           _ptr(moments, (torch.float64,), "moments", (8,), False), _stream()))
+
+    def stats_finalize(self, moments, out):
+        """nqs_stats_finalize: statistics [5] from (summed) moments [8]."""
+        self._check(_lib.nqs_stats_finalize(_ptr(moments, (torch.float64,), "moments", (8,), False),
+                                            _ptr(out, (torch.float64,), "out", (5,), False), _stream()))
+
+    def force_share(self, configs, eloc, stats, force, workspace=None):
+        """nqs_force_share: (1 / stats[4]) sum_x O(x) (eloc[x] - stats[0]) over these rows."""
+        n = configs.shape[0]
+        ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+        self._check(_lib.nqs_force_share(
+            self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
+            _ptr(eloc, (torch.float32,), "eloc", (n,), n == 0), _ptr(stats, (torch.float64,), "stats", (5,), n == 0),
+            _ptr(force, (torch.float64,), "force", (self.P,), False),
+            _ptr(workspace, (torch.uint8, torch.float64, torch.float32, torch.int32), "workspace"), ws_bytes,
+            _stream()))
+
     def force_noalloc(self, configs, eloc, stats, force):
         """nqs_force_noalloc: the force without a workspace (built-in device scratch)."""
         n = configs.shape[0]
@@ -335,8 +363,8 @@ class LogPsi(torch.autograd.Function):
 
     forward: nqs_set_params(params), then nqs_logpsi(configs) -> FP32 [n].
     backward: d/dparams of sum_x g_x log psi(x) = sum_x g_x O(x), the hand-written backward
-    (App. I, Eq. forces) in the library's force kernel: with eloc = g and E = 0 the force is
-    (1/n) sum_x O(x) g_x, scaled here by n.  No O rows are materialised.  The derivative is
+    (App. I, Eq. forces) in the library's force kernel: nqs_force_share with eloc = g and
+    stats = (0, 0, 0, 0, 1) (no centring, divisor 1).  No O rows are materialised.  The derivative is
     that of the FP32 rounding of the master parameters; the forward of a 16-bit context is its
     sampling copy's log psi.
 
@@ -359,11 +387,27 @@ class LogPsi(torch.autograd.Function):
         nctx = fctx.nctx
         n = configs.shape[0]
         g = grad_out.detach().to(torch.float32).contiguous()
-        stats = torch.zeros(5, dtype=torch.float64, device=configs.device)   # E = 0
-        force = torch.empty(nctx.P, dtype=torch.float64, device=configs.device)
+        stats = torch.tensor([0.0, 0.0, 0.0, 0.0, 1.0], dtype=torch.float64, device=configs.device)
+        vjp = torch.empty(nctx.P, dtype=torch.float64, device=configs.device)
         ws = torch.empty(max(nctx.logpsi_grad_workspace(n), 1), dtype=torch.uint8, device=configs.device)
-        nctx.logpsi_grad(configs, None, g, stats, force, ws)
-        return None, force.mul_(float(n)), None
+        nctx.force_share(configs, g, stats, vjp, ws)
+        return None, vjp, None
+
+
+PROBE_KINDS = {"ffma": 0, "ffma2": 1, "fmul2": 2, "hfma2": 3, "bfma2": 4, "lg2": 5, "ex2": 6}
+# operations per lane per probed instruction
+PROBE_OPS = {"ffma": 1, "ffma2": 2, "fmul2": 2, "hfma2": 2, "bfma2": 2, "lg2": 1, "ex2": 1}
+
+
+def probe_alu(kind, blocks, threads, iters, sink):
+    """nqs_probe_alu: launches the issue-rate probe of one instruction on the current stream
+    (time it with CUDA events); sink is a CUDA float32 tensor of at least `blocks` elements."""
+    if sink.numel() < blocks:
+        raise ValueError("sink needs at least `blocks` elements")
+    st = _lib.nqs_probe_alu(PROBE_KINDS[kind], blocks, threads, iters, _ptr(sink, (torch.float32,), "sink"),
+                            _stream())
+    if st != NQS_OK:
+        raise NQSError(st, "nqs_probe_alu failed")
 
 
 def selftest_tc_gemm(A, B, a_transposed=False, b_transposed=False):

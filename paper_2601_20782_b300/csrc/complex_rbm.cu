@@ -38,6 +38,8 @@ struct nqs_crbm {
   float4 *d_et = nullptr;  // [M_pad][N] (cosh 2W, sinh 2W) as complex pairs, unit-major
   int2 *d_nb = nullptr;    // [N] right and down neighbour (-1: none, a chain)
   double *d_imstats = nullptr;  // [5] statistics of Im eps
+  double2 *d_fpart = nullptr;   // [force_chunks][P] per-row-chunk partial forces, added in a fixed order
+  int force_chunks = 1;
   std::string err;
 };
 
@@ -460,13 +462,16 @@ __global__ void __launch_bounds__(CR_THREADS) crbm_grad_rows_kernel(const CRowAr
 //   S[x][i] = s_i(x) (i < N),             S[x][N] = 1,
 // Fsum = G^T S: F_W = Fsum[j][i], F_b = Fsum[j][N], F_a = Fsum[M][i].  CTA (row range,
 // tile of CR_FU units): phase A builds G for CR_FR rows, phase B accumulates site columns
-// in FP32 over the block and in FP64 across blocks, then adds to the FP64 output.
+// in FP32 over the block and in FP64 across blocks, then writes its row chunk's slot of the
+// partial forces (every entry of a slot is written by exactly one CTA of that chunk);
+// crbm_force_reduce_kernel adds the slots in a fixed order, so the result is deterministic.
 struct CForceArgs {
   CRowArgs r;
   const float *eloc_re, *eloc_im;
   const double *stats;
   int64_t rows_per_cta;
-  double2 *force;
+  double2 *part;  // [gridDim.x][P]
+  int64_t P;
 };
 
 // HALVES = 2 (N + 1 <= 144): phase B thread (i, h) takes site i and units h*8 .. h*8 + 7 of
@@ -557,16 +562,20 @@ __global__ void __launch_bounds__(CR_FTHREADS) crbm_force_kernel(const CForceArg
     if (j < M && i < N) k = (int64_t)N + M + (int64_t)j * N + i;
     else if (j < M) k = (int64_t)N + j;
     else if (j == M && i < N) k = i;
-    if (k >= 0) {
-      atomicAdd(&a.force[k].x, accd[u][0]);
-      atomicAdd(&a.force[k].y, accd[u][1]);
-    }
+    if (k >= 0) a.part[blockIdx.x * a.P + k] = make_double2(accd[u][0], accd[u][1]);
   }
 }
 
-__global__ void crbm_scale_kernel(double *v, int64_t n, double s) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    v[k] *= s;
+__global__ void crbm_force_reduce_kernel(const double2 *part, int chunks, int64_t P, double inv_n, double2 *force) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int q = 0; q < chunks; ++q) {
+      const double2 v = part[q * P + k];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    force[k] = make_double2(s.x * inv_n, s.y * inv_n);
+  }
 }
 
 // Largest instantiated units-per-lane width >= need.
@@ -627,7 +636,7 @@ CRowArgs row_args(const nqs_crbm *c, const uint32_t *cfg, int64_t n) {
 
 void crbm_free(nqs_crbm *c) {
   void *ptrs[] = {c->d_a, c->d_b, c->d_Wt, c->d_st, c->d_et, c->d_nb, c->d_imstats, c->base.d_status,
-                  c->base.d_scratch};
+                  c->base.d_scratch, c->d_fpart};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -702,7 +711,10 @@ nqs_status nqs_crbm_create(nqs_crbm **out, const nqs_ham_desc *ham, int32_t n_hi
     for (int x = 0; x < c->Lx; ++x)
       nb[x + c->Lx * y] = make_int2((x + 1) % c->Lx + c->Lx * y, c->Ly > 1 ? x + c->Lx * ((y + 1) % c->Ly) : -1);
   const size_t NM = (size_t)c->N * c->M_pad;
-  if ((e = cudaMalloc(&c->d_a, c->N * sizeof(float2))) || (e = cudaMalloc(&c->d_b, c->M_pad * sizeof(float2))) ||
+  const int tiles = (c->M + 1 + CR_FU - 1) / CR_FU;
+  c->force_chunks = std::max(1, (b.num_sms * 4 + tiles - 1) / tiles);
+  if ((e = cudaMalloc(&c->d_fpart, (size_t)c->force_chunks * c->P * sizeof(double2))) ||
+      (e = cudaMalloc(&c->d_a, c->N * sizeof(float2))) || (e = cudaMalloc(&c->d_b, c->M_pad * sizeof(float2))) ||
       (e = cudaMalloc(&c->d_Wt, NM * sizeof(float2))) || (e = cudaMalloc(&c->d_st, NM * sizeof(float4))) ||
       (e = cudaMalloc(&c->d_et, NM * sizeof(float4))) || (e = cudaMalloc(&c->d_nb, c->N * sizeof(int2))) ||
       (e = cudaMalloc(&c->d_imstats, 5 * sizeof(double))) || (e = cudaMalloc(&b.d_status, sizeof(int))) ||
@@ -853,8 +865,10 @@ nqs_status nqs_crbm_logpsi_grad(nqs_crbm *c, const uint32_t *cfg, int64_t n, flo
     return cfail(c, NQS_EINVAL, "nqs_crbm_logpsi_grad: the force needs eloc and stats");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
-  if (force) e = cudaMemsetAsync(force, 0, (size_t)c->P * 2 * sizeof(double), s);
-  if (e != cudaSuccess || n == 0) return e == cudaSuccess ? NQS_OK : ccuda(c, e, "nqs_crbm_logpsi_grad");
+  if (n == 0) {
+    if (force) e = cudaMemsetAsync(force, 0, (size_t)c->P * 2 * sizeof(double), s);
+    return e == cudaSuccess ? NQS_OK : ccuda(c, e, "nqs_crbm_logpsi_grad");
+  }
   const CRowArgs r = row_args(c, cfg, n);
   if (O) {
     const int64_t blocks = std::min<int64_t>(n, (int64_t)c->base.num_sms * 16);
@@ -868,10 +882,11 @@ nqs_status nqs_crbm_logpsi_grad(nqs_crbm *c, const uint32_t *cfg, int64_t n, flo
     a.eloc_re = eloc_re;
     a.eloc_im = eloc_im;
     a.stats = stats;
-    a.force = reinterpret_cast<double2 *>(force);
+    a.part = c->d_fpart;
+    a.P = c->P;
     const int tiles = (c->M + 1 + CR_FU - 1) / CR_FU;
     const int64_t blocks_rows = (n + CR_FR - 1) / CR_FR;
-    const int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(blocks_rows, ((int64_t)c->base.num_sms * 4 + tiles - 1) / tiles));
+    const int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(blocks_rows, c->force_chunks));
     a.rows_per_cta = ((blocks_rows + chunks - 1) / chunks) * CR_FR;
     const int64_t gx = (n + a.rows_per_cta - 1) / a.rows_per_cta;
     if (2 * (c->N + 1) <= CR_FTHREADS)
@@ -879,8 +894,8 @@ nqs_status nqs_crbm_logpsi_grad(nqs_crbm *c, const uint32_t *cfg, int64_t n, flo
     else
       crbm_force_kernel<1><<<dim3((unsigned)gx, (unsigned)tiles), CR_FTHREADS, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return ccuda(c, e, "nqs_crbm_logpsi_grad");
-    crbm_scale_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((2 * c->P + 255) / 256, 1024)), 256, 0, s>>>(
-        force, 2 * c->P, 1.0 / (double)n);
+    crbm_force_reduce_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((c->P + 255) / 256, 1024)), 256, 0,
+                               s>>>(c->d_fpart, (int)gx, c->P, 1.0 / (double)n, reinterpret_cast<double2 *>(force));
     if ((e = cudaGetLastError()) != cudaSuccess) return ccuda(c, e, "nqs_crbm_logpsi_grad");
   }
   return NQS_OK;

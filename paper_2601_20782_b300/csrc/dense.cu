@@ -589,12 +589,14 @@ __global__ void __launch_bounds__(256) dense_force_part_kernel(const float *O, i
   }
   if (k < P) part[slice * P + k] = s;
 }
-__global__ void dense_force_sum_kernel(const double *part, int64_t P, int64_t n_total, int accumulate,
-                                       double *force) {
+// ndiv: when given, the divisor is *ndiv (stats[4], the total sample count of a multi-rank step)
+__global__ void dense_force_sum_kernel(const double *part, int64_t P, int64_t n_total, const double *ndiv,
+                                       int accumulate, double *force) {
+  const double d = ndiv ? *ndiv : (double)n_total;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int q = 0; q < FORCE_SLICES; ++q) s += part[q * P + k];
-    s /= (double)n_total;
+    s /= d;
     force[k] = accumulate ? force[k] + s : s;
   }
 }
@@ -978,16 +980,17 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swee
 }
 
 static cudaError_t force_rows(const nqs_ctx *c, const float *O, int64_t rows, const float *eloc, const double *stats,
-                              int64_t n_total, int accumulate, double *force, cudaStream_t s) {
+                              int64_t n_total, bool share, int accumulate, double *force, cudaStream_t s) {
   double *part = reinterpret_cast<double *>(c->d_force_part);
   dense_force_part_kernel<<<dim3((unsigned)((c->P + 255) / 256), FORCE_SLICES), 256, 0, s>>>(O, rows, c->P, eloc, stats,
                                                                                              part);
-  dense_force_sum_kernel<<<grid_for(c->P, 256, c->num_sms), 256, 0, s>>>(part, c->P, n_total, accumulate, force);
+  dense_force_sum_kernel<<<grid_for(c->P, 256, c->num_sms), 256, 0, s>>>(part, c->P, n_total, share ? stats + 4 : nullptr,
+                                                                        accumulate, force);
   return cudaGetLastError();
 }
 
 cudaError_t dense_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
-                              const double *stats, double *force, cudaStream_t s) {
+                              const double *stats, double *force, cudaStream_t s, bool share) {
   GradArgs g;
   g.cfg = cfg;
   g.master = c->d_master;
@@ -1019,9 +1022,10 @@ cudaError_t dense_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, 
     g.n = rows;
     dense_grad_kernel<<<(unsigned)std::min<int64_t>(rows, (int64_t)c->num_sms * 8), 256, shm, s>>>(g);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (force && !O && (e = force_rows(c, g.O, rows, eloc + x0, stats, n, x0 > 0, force, s)) != cudaSuccess) return e;
+    if (force && !O && (e = force_rows(c, g.O, rows, eloc + x0, stats, n, share, x0 > 0, force, s)) != cudaSuccess)
+      return e;
   }
-  if (force && O) return force_rows(c, O, n, eloc, stats, n, 0, force, s);
+  if (force && O) return force_rows(c, O, n, eloc, stats, n, share, 0, force, s);
   return cudaSuccess;
 }
 

@@ -114,8 +114,9 @@ cudaError_t rbm_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n, f
 cudaError_t rbm_local_energy_chains(const nqs_ctx *c, const uint32_t *cfg, int64_t n_chains, int64_t per_chain,
                                     float *eloc, cudaStream_t s);
 size_t rbm_grad_workspace(const nqs_ctx *c, int64_t n);
+// share = false: force = (1/n) sum_x O(x) (eps(x) - stats[0]); share = true: divided by stats[4]
 cudaError_t rbm_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
-                            const double *stats, double *force, void *ws, cudaStream_t s);
+                            const double *stats, double *force, void *ws, cudaStream_t s, bool share = false);
 bool rbm_supported(const nqs_ctx *c, std::string *why);
 cudaError_t rbm_flip_delta(const nqs_ctx *c, const uint32_t *cfg, const int32_t *sites, int64_t n, float *out,
                            cudaStream_t s);
@@ -149,7 +150,7 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t n_chains, int
                         uint32_t sweep_offset, uint32_t *samples, float *logpsi, int64_t *n_acc, uint32_t *acc_bits,
                         float *delta, cudaStream_t s);
 cudaError_t dense_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
-                              const double *stats, double *force, cudaStream_t s);
+                              const double *stats, double *force, cudaStream_t s, bool share = false);
 // dense_gemm.cu
 bool make_tmap_bf16_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);
 bool make_tmap_u8_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);
@@ -166,7 +167,11 @@ cudaError_t minsr(const nqs_ctx *c, const float *O, int64_t n, const float *eloc
                   double *dtheta, double *T_out, void *ws, cudaStream_t s);
 
 // stats.cu
+// moments == nullptr: out[5] = (E, Var, err, acceptance, n); otherwise the additive moments
+// [8] of stats_finalize are written to `moments` and out is unused
 cudaError_t energy_stats(const nqs_ctx *c, const float *eloc, int64_t n, int64_t n_chains,
-                         const int64_t *n_acc, int64_t proposals_per_chain, double *out, cudaStream_t s);
+                         const int64_t *n_acc, int64_t proposals_per_chain, double *out, cudaStream_t s,
+                         double *moments = nullptr);
+cudaError_t stats_finalize(const double *moments, double *out, cudaStream_t s);
 
 }  // namespace nqs

@@ -54,8 +54,14 @@ extern "C" nqs_status nqs_force_noalloc(nqs_ctx *c, const uint32_t *configs, int
   };
   if (!c->params_set) return fail(NQS_EINVAL, "nqs_force_noalloc: parameters not set");
   if (c->model_kind != NQS_RBM) return fail(NQS_EUNSUPPORTED, "nqs_force_noalloc: RBM contexts only");
-  if (n <= 0 || !configs || !eloc || !stats || !force)
-    return fail(NQS_EINVAL, "nqs_force_noalloc: needs n > 0 and non-null configs, eloc, stats, force");
+  if (n < 0 || !force) return fail(NQS_EINVAL, "nqs_force_noalloc: needs n >= 0 and a non-null force");
+  if (n == 0) {  // as nqs_logpsi_grad: the force of no rows is zero
+    const cudaError_t z = cudaMemsetAsync(force, 0, (size_t)c->P * sizeof(double),
+                                          reinterpret_cast<cudaStream_t>(stream));
+    return z == cudaSuccess ? NQS_OK : fail(NQS_ECUDA, std::string("nqs_force_noalloc: ") + cudaGetErrorString(z));
+  }
+  if (!configs || !eloc || !stats)
+    return fail(NQS_EINVAL, "nqs_force_noalloc: needs non-null configs, eloc and stats when n > 0");
   const size_t per_chunk = (size_t)c->P * sizeof(double);
   if (per_chunk > NOALLOC_SCRATCH_BYTES)
     return fail(NQS_EINVAL, "nqs_force_noalloc: the model has more than 4,194,304 parameters, beyond the "
@@ -67,6 +73,9 @@ extern "C" nqs_status nqs_force_noalloc(nqs_ctx *c, const uint32_t *configs, int
   cudaError_t e = scratch_for_current_device(&scratch);
   if (e != cudaSuccess) return fail(NQS_ECUDA, std::string("nqs_force_noalloc: cudaGetSymbolAddress: ") +
                                                    cudaGetErrorString(e));
+  // The kernel wants about 2 * SMs / ceil(M / 32) chunks of P doubles.  Within the RBM's limits
+  // (N <= 256, M <= 1024, so P <= 257 M + 256) that stays below the scratch's capacity of
+  // 4,194,304 / P chunks; the clamp only guards a future change of those limits.
   int chunks = nqs::rbm_force_chunks(c, n);
   const int cap = (int)(NOALLOC_SCRATCH_BYTES / per_chunk);
   if (chunks > cap) chunks = cap;

@@ -354,6 +354,43 @@ nqs_status nqs_stats(nqs_ctx *c, const float *eloc, int64_t n, int64_t n_chains,
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_stats");
 }
 
+nqs_status nqs_stats_moments(nqs_ctx *c, const float *eloc, int64_t n, int64_t n_chains, const int64_t *n_accepted,
+                             int64_t proposals_per_chain, double *moments, nqs_stream stream) {
+  if (!c) return NQS_EINVAL;
+  if (n <= 0 || n_chains <= 0 || n % n_chains != 0 || bad_ptr(eloc) || bad_ptr(moments))
+    return fail(c, NQS_EINVAL, "nqs_stats_moments: need n > 0 a multiple of n_chains and non-null eloc/moments");
+  if (n_accepted && proposals_per_chain <= 0)
+    return fail(c, NQS_EINVAL, "nqs_stats_moments: proposals_per_chain must be > 0");
+  cudaError_t e = nqs::energy_stats(c, eloc, n, n_chains, n_accepted, proposals_per_chain, nullptr,
+                                    reinterpret_cast<cudaStream_t>(stream), moments);
+  return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_stats_moments");
+}
+
+nqs_status nqs_stats_finalize(const double *moments, double *out, nqs_stream stream) {
+  if (bad_ptr(moments) || bad_ptr(out)) return NQS_EINVAL;
+  cudaError_t e = nqs::stats_finalize(moments, out, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? NQS_OK : cuda_fail(nullptr, e, "nqs_stats_finalize");
+}
+
+nqs_status nqs_force_share(nqs_ctx *c, const uint32_t *cfg, int64_t n, const float *eloc, const double *stats,
+                           double *force, void *ws, size_t ws_bytes, nqs_stream stream) {
+  if (!c) return NQS_EINVAL;
+  if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_force_share: parameters not set");
+  if (n < 0 || bad_ptr(force) || (n > 0 && (bad_ptr(cfg) || bad_ptr(eloc) || bad_ptr(stats))))
+    return fail(c, NQS_EINVAL, "nqs_force_share: bad arguments");
+  if (n > 0 && c->model_kind == NQS_RBM && (bad_ptr(ws) || ws_bytes < nqs::rbm_grad_workspace(c, n)))
+    return fail(c, NQS_EINVAL, "nqs_force_share: workspace too small");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(force, 0, (size_t)c->P * sizeof(double), s);
+    return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_force_share");
+  }
+  cudaError_t e = c->model_kind == NQS_DENSE
+                      ? nqs::dense_logpsi_grad(c, cfg, n, nullptr, eloc, stats, force, s, true)
+                      : nqs::rbm_logpsi_grad(c, cfg, n, nullptr, eloc, stats, force, ws, s, true);
+  return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_force_share");
+}
+
 nqs_status nqs_local_energy_chains(nqs_ctx *c, const uint32_t *samples, int64_t n_chains, int64_t per_chain,
                                    float *eloc, nqs_stream stream) {
   if (!c) return NQS_EINVAL;

@@ -317,11 +317,15 @@ __global__ void __launch_bounds__(FT_THREADS) rbm_force_partial_kernel(
   if (jt == 0 && threadIdx.x < N) out[threadIdx.x] = accA;
 }
 
-__global__ void force_reduce_kernel(const double *ws, int n_chunks, int64_t P, int64_t n, double *force) {
+// Adds the chunks' partial sums in a fixed order and divides by n, or by *ndiv when given
+// (the total sample count of a multi-rank step, held in stats[4]).
+__global__ void force_reduce_kernel(const double *ws, int n_chunks, int64_t P, int64_t n, const double *ndiv,
+                                    double *force) {
+  const double d = ndiv ? *ndiv : (double)n;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int c = 0; c < n_chunks; ++c) s += ws[(int64_t)c * P + k];
-    force[k] = s / (double)n;
+    force[k] = s / d;
   }
 }
 
@@ -557,7 +561,7 @@ cudaError_t rbm_force_into(const nqs_ctx *c, const uint32_t *cfg, int64_t n, con
                                                                      c->W, c->M, c->P, chunks, scratch);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int rb = (int)std::min<int64_t>((c->P + 255) / 256, (int64_t)c->num_sms * 8);
-  force_reduce_kernel<<<rb, 256, 0, s>>>(scratch, chunks, c->P, n, force);
+  force_reduce_kernel<<<rb, 256, 0, s>>>(scratch, chunks, c->P, n, nullptr, force);
   return cudaGetLastError();
 }
 
@@ -567,7 +571,7 @@ size_t rbm_grad_workspace(const nqs_ctx *c, int64_t n) {
 }
 
 cudaError_t rbm_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
-                            const double *stats, double *force, void *ws, cudaStream_t s) {
+                            const double *stats, double *force, void *ws, cudaStream_t s, bool share) {
   if (O) {
     const size_t shm = (size_t)(c->N + c->M) * sizeof(float);
     const int64_t blocks = std::min<int64_t>(n, (int64_t)c->num_sms * 8);
@@ -580,7 +584,7 @@ cudaError_t rbm_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, fl
     cudaError_t e = rbm_force_tc(c, cfg, n, eloc, stats, (double *)ws, chunks, s);
     if (e != cudaSuccess) return e;
     const int rb = (int)std::min<int64_t>((c->P + 255) / 256, (int64_t)c->num_sms * 8);
-    force_reduce_kernel<<<rb, 256, 0, s>>>((const double *)ws, chunks, c->P, n, force);
+    force_reduce_kernel<<<rb, 256, 0, s>>>((const double *)ws, chunks, c->P, n, share ? stats + 4 : nullptr, force);
     return cudaGetLastError();
   }
   if (force) {
@@ -594,7 +598,7 @@ cudaError_t rbm_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, fl
                                                                        c->W, c->M, c->P, chunks, (double *)ws);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int rb = (int)std::min<int64_t>((c->P + 255) / 256, (int64_t)c->num_sms * 8);
-    force_reduce_kernel<<<rb, 256, 0, s>>>((const double *)ws, chunks, c->P, n, force);
+    force_reduce_kernel<<<rb, 256, 0, s>>>((const double *)ws, chunks, c->P, n, share ? stats + 4 : nullptr, force);
     return cudaGetLastError();
   }
   return cudaSuccess;

@@ -178,7 +178,8 @@ def test_O_rows_and_force_match_oracle():
     F2 = torch.zeros_like(F)
     c.logpsi_grad(cfg, None, re, im, stats, F2)
     torch.cuda.synchronize()
-    np.testing.assert_allclose(F2.cpu().numpy(), Fg, rtol=0, atol=1e-12 * np.abs(Fg).max())
+    # the row chunks' partials are added in a fixed order: the same inputs give the same bits
+    assert torch.equal(F2, F)
 
 
 def test_stats_match_oracle_statistics():

@@ -272,3 +272,72 @@ def test_local_energy_chains_matches_per_sample(Lx, Ly, M, dtype, refresh):
     a, b = e1.cpu().numpy().astype(np.float64), e2.cpu().numpy().astype(np.float64)
     rel = np.abs(b - a) / (np.abs(a) + 2.0 * N)
     assert rel.max() <= 2e-5, (rel.max(), np.argmax(rel), a[np.argmax(rel)], b[np.argmax(rel)])
+
+
+@pytest.mark.parametrize("model_kind", ["rbm", "dense"])
+def test_moments_and_force_shares_of_split_chains(model_kind):
+    # A multi-rank step on one GPU: the chains split into two "ranks" of unequal size.  Each
+    # rank's moments (nqs_stats_moments), summed, give through nqs_stats_finalize the pooled
+    # statistics, which equal the oracle's on all chains; each rank's force share
+    # (nqs_force_share, centred on the pooled E and divided by the pooled count) sums to the
+    # pooled force of the oracle.  With one rank the two calls equal nqs_stats and the share
+    # equals nqs_logpsi_grad's force.
+    p = nqs()
+    rng = np.random.default_rng(61)
+    if model_kind == "rbm":
+        Lx, Ly, M = 6, 6, 72
+        ctx, model, _ = make(Lx, Ly, M, 0.1, 62)
+    else:
+        from oracle.models import Dense
+        from workloads import dense_params
+        Lx, Ly, widths = 4, 4, (64, 48)
+        params = dense_params(16, widths, 63, bias_sigma=0.1)
+        ctx = p.Context("heisenberg", Lx, Ly, J1=1.0, marshall=True, model="dense", widths=widths, dtype="bf16")
+        ctx.set_params(torch.from_numpy(params).cuda())
+        model = Dense(16, widths, params)
+    N, K, Cs = Lx * Ly, 5, (37, 91)
+    parts = []
+    for C in Cs:
+        s = rng.choice([-1, 1], size=(K * C, N)).astype(np.int8)
+        e = rng.normal(-10.0, 3.0, size=K * C).astype(np.float32)
+        acc = rng.integers(0, 50, size=C)
+        parts.append((s, e, acc, C))
+    mom = []
+    for s, e, acc, C in parts:
+        m = torch.zeros(8, dtype=torch.float64, device="cuda")
+        ctx.stats_moments(torch.from_numpy(e).cuda(), C, m, torch.from_numpy(acc).cuda(), 50)
+        mom.append(m)
+    total = mom[0] + mom[1]          # the all-reduce SUM
+    stats = torch.zeros(5, dtype=torch.float64, device="cuda")
+    ctx.stats_finalize(total, stats)
+    shares = []
+    for s, e, acc, C in parts:
+        f = torch.zeros(ctx.P, dtype=torch.float64, device="cuda")
+        ws = torch.empty(max(ctx.logpsi_grad_workspace(len(e)), 1), dtype=torch.uint8, device="cuda")
+        ctx.force_share(to_words_tensor(pack_np(s)), torch.from_numpy(e).cuda(), stats, f, ws)
+        shares.append(f)
+    force = (shares[0] + shares[1]).cpu().numpy()
+    torch.cuda.synchronize()
+    # pooled oracle: chains side by side, sweep-major
+    eps = np.concatenate([e.astype(np.float64).reshape(K, C) for s, e, acc, C in parts], axis=1).reshape(-1)
+    S = np.concatenate([s.reshape(K, C, N) for s, e, acc, C in parts], axis=1).reshape(-1, N)
+    E, var, err = energy_stats(eps, sum(Cs))
+    acc_rate = sum(a.sum() for _, _, a, _ in parts) / (sum(Cs) * 50)
+    np.testing.assert_allclose(stats.cpu().numpy(), [E, var, err, acc_rate, eps.size], rtol=1e-12)
+    F = oracle_force(model.grad(S), eps)
+    tol = 1e-5 if model_kind == "rbm" else 1e-4      # as the other RBM / dense force tests
+    np.testing.assert_allclose(force, F, rtol=0, atol=tol * np.abs(F).max())
+    # one rank: the two calls equal nqs_stats, and the share equals nqs_logpsi_grad's force
+    s, e, acc, C = parts[1]
+    e_t, acc_t = torch.from_numpy(e).cuda(), torch.from_numpy(acc).cuda()
+    one = torch.zeros(5, dtype=torch.float64, device="cuda")
+    ctx.stats(e_t, C, one, acc_t, 50)
+    fin = torch.zeros(5, dtype=torch.float64, device="cuda")
+    ctx.stats_finalize(mom[1], fin)
+    assert torch.equal(one, fin)
+    ref = torch.zeros(ctx.P, dtype=torch.float64, device="cuda")
+    ws = torch.empty(max(ctx.logpsi_grad_workspace(len(e)), 1), dtype=torch.uint8, device="cuda")
+    ctx.logpsi_grad(to_words_tensor(pack_np(s)), None, e_t, one, ref, ws)
+    sh = torch.zeros(ctx.P, dtype=torch.float64, device="cuda")
+    ctx.force_share(to_words_tensor(pack_np(s)), e_t, one, sh, ws)
+    assert torch.equal(ref, sh)

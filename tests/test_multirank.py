@@ -1,9 +1,12 @@
 """The step's exchange across ranks (two gloo ranks on the CPU): statistics and force of
-the pooled samples from per-rank partials, against the oracle on the pooled data.
+the pooled samples from per-rank buffers, against the oracle on the pooled data.
 
-Each rank stands in for one GPU: its local statistics and force are computed here in
-FP64 the way the product's kernels define them (mean, variance 1/n, force centred on
-the E held in stats[0]); the reduction code under test is bench.py's."""
+Each rank stands in for one GPU.  Its moments and force share are built here in FP64 the
+way nqs_stats_moments and nqs_force_share define them (include/nqs.h); the exchange under
+test is the package's (paper_2601_20782_b300.distributed).  nqs_stats_finalize is a GPU
+kernel, so the ranks' context here is a stand-in whose finalize applies the header's
+formula; the kernel itself is checked on the GPU against the pooled oracle
+(tests/test_gpu_rbm.py::test_moments_and_force_shares_of_split_chains)."""
 import os
 import socket
 
@@ -14,33 +17,53 @@ torch = pytest.importorskip("torch")
 import torch.distributed as td
 import torch.multiprocessing as mp
 
-import bench
+from oracle.estimators import energy_stats as oracle_stats
 from oracle.estimators import force as oracle_force
+
+K = 6   # samples per chain
 
 
 def _data(rank):
     rng = np.random.default_rng(100 + rank)
-    n = 300 + 137 * rank                       # uneven sample counts
-    O = rng.normal(size=(n, 7)) + rank         # rank-dependent means: E_r != E
-    eps = rng.normal(-3.0 + 2.0 * rank, 1.0 + rank, size=n)
-    return O, eps
+    C = 50 + 23 * rank                         # uneven chain counts
+    O = rng.normal(size=(K * C, 7)) + rank     # rank-dependent means: E_r != E
+    eps = rng.normal(-3.0 + 2.0 * rank, 1.0 + rank, size=K * C)
+    acc = rng.integers(0, 40, size=C)
+    return O, eps, acc, C
+
+
+def _moments(eps, acc, C, proposals):
+    m = eps.reshape(K, C).mean(axis=0)
+    return torch.tensor([eps.size, eps.sum(), (eps ** 2).sum(), C, m.sum(), (m ** 2).sum(), acc.sum(),
+                         C * proposals], dtype=torch.float64)
+
+
+class _FinalizeStandIn:
+    """nqs_stats_finalize's formula (include/nqs.h) for CPU ranks."""
+
+    def stats_finalize(self, m, out):
+        n, C = m[0], m[3]
+        mean = m[1] / n
+        mm = m[4] / C
+        out[:] = torch.stack([mean, m[2] / n - mean ** 2, torch.sqrt((m[5] - C * mm * mm) / (C - 1) / C),
+                              m[6] / m[7], n])
 
 
 def _worker(rank, world, port, out):
+    from paper_2601_20782_b300.distributed import exchange_force, exchange_stats
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     td.init_process_group("gloo", rank=rank, world_size=world)
-    O, eps = _data(rank)
-    n = len(eps)
-    stats = torch.tensor([eps.mean(), eps.var(), eps.std() / np.sqrt(n), 0.5, n], dtype=torch.float64)
-    n_total = bench.reduce_stats_across_ranks(stats, n, td)
-    E = float(stats[0])
-    force = torch.from_numpy(O.T @ (eps - E) / n)       # the force kernel's definition with stats[0]
-    bench.reduce_force_across_ranks(force, n, n_total, td)
-    out[rank] = (float(n_total), stats.numpy().copy(), force.numpy().copy())
+    O, eps, acc, C = _data(rank)
+    moments = _moments(eps, acc, C, 40)
+    stats = torch.zeros(5, dtype=torch.float64)
+    exchange_stats(_FinalizeStandIn(), moments, stats)
+    force = torch.from_numpy(O.T @ (eps - float(stats[0])) / float(stats[4]))   # nqs_force_share
+    exchange_force(force)
+    out[rank] = (stats.numpy().copy(), force.numpy().copy())
     td.destroy_process_group()
 
 
-def test_two_rank_reduction_matches_pooled_oracle():
+def test_two_rank_exchange_matches_pooled_oracle():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
@@ -53,14 +76,17 @@ def test_two_rank_reduction_matches_pooled_oracle():
     for p in procs:
         p.join(120)
         assert p.exitcode == 0
-    O = np.concatenate([_data(r)[0] for r in range(2)])
-    eps = np.concatenate([_data(r)[1] for r in range(2)])
+    d = [_data(r) for r in range(2)]
+    # pooled chains in one sweep-major array: row k * C_total + c
+    eps = np.concatenate([x[1].reshape(K, x[3]) for x in d], axis=1).reshape(-1)
+    C_tot = sum(x[3] for x in d)
+    E, var, err = oracle_stats(eps, C_tot)
+    acc_rate = sum(x[2].sum() for x in d) / (C_tot * 40)
+    O_pooled = np.concatenate([x[0].reshape(K, x[3], 7) for x in d], axis=1).reshape(-1, 7)
     for r in range(2):
-        n, stats, force = out[r]
-        assert n == len(eps)
-        np.testing.assert_allclose(stats[0], eps.mean(), rtol=1e-13)
-        np.testing.assert_allclose(stats[1], eps.var(), rtol=1e-12)
-        np.testing.assert_allclose(force, oracle_force(O, eps), rtol=1e-12, atol=1e-12)
+        stats, force = out[r]
+        np.testing.assert_allclose(stats, [E, var, err, acc_rate, eps.size], rtol=1e-12)
+        np.testing.assert_allclose(force, oracle_force(O_pooled, eps), rtol=1e-12, atol=1e-12)
     # centring each rank on its own E_r instead would be wrong by a visible margin
-    naive = sum(len(_data(r)[1]) * oracle_force(*_data(r)) for r in range(2)) / len(eps)
-    assert np.abs(naive - oracle_force(O, eps)).max() > 1e-2
+    naive = sum(len(x[1]) * oracle_force(x[0], x[1]) for x in d) / eps.size
+    assert np.abs(naive - oracle_force(O_pooled, eps)).max() > 1e-2
