@@ -89,6 +89,21 @@ def dense_params(n, widths, seed, bias_sigma=0.0):
     return np.concatenate(parts).astype(np.float64)
 
 
+def rescnn_params(n_filters, n_blocks, seed, gamma_sigma=0.25, bias_sigma=0.1):
+    """ResCNN (App. H) parameters in the oracle's flat order: kernels ~ N(0, 1 / fan_in) with
+    fan_in = 9 x input channels; conv biases and LN shifts ~ N(0, bias_sigma^2); LN scales
+    ~ 1 + N(0, gamma_sigma^2) (scales all equal to 1 would make the summed output constant)."""
+    rng = np.random.default_rng(seed)
+    F = n_filters
+    parts = [rng.normal(0.0, np.sqrt(1.0 / 9.0), size=9 * F), rng.normal(0.0, bias_sigma, size=F)]
+    for _ in range(n_blocks):
+        parts += [1.0 + rng.normal(0.0, gamma_sigma, size=F), rng.normal(0.0, bias_sigma, size=F)]
+        for _ in range(2):
+            parts += [rng.normal(0.0, np.sqrt(1.0 / (9.0 * F)), size=9 * F * F), rng.normal(0.0, bias_sigma, size=F)]
+    parts += [1.0 + rng.normal(0.0, gamma_sigma, size=F), rng.normal(0.0, bias_sigma, size=F)]
+    return np.concatenate(parts).astype(np.float64)
+
+
 # The five workloads the build is measured and checked on.
 TFIM_1D_N16 = Workload(
     name="tfim1d_n16_rbm_a1", ham=Hamiltonian("tfim", Lattice(16), J1=1.0, h=1.0),
