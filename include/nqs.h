@@ -59,7 +59,7 @@ typedef enum {
  * and nqs_logpsi run on that copy, nqs_local_energy on the BF16 copy. */
 typedef enum { NQS_F32 = 0, NQS_BF16 = 1, NQS_F16 = 2, NQS_FP8E4M3 = 3 } nqs_dtype;
 
-enum { NQS_RBM = 0, NQS_DENSE = 1 };
+enum { NQS_RBM = 0, NQS_DENSE = 1, NQS_RESCNN = 2 };
 enum { NQS_TFIM = 0, NQS_HEISENBERG = 1 };
 
 /* Hamiltonian on a periodic Lx x Ly lattice (Ly == 1: chain of Lx sites; Lx >= 3,
@@ -82,7 +82,15 @@ typedef struct {
  * + b_out; sampling copy BF16 or FP8 E4M3 (layers >= 2 on the tensor cores, FP32
  * accumulation);
  * TFIM (single flips) or HEISENBERG (exchange moves).  nqs_logpsi_grad of a dense
- * context is FP32 from the FP32 rounding of the master and needs no workspace. */
+ * context is FP32 from the FP32 rounding of the master and needs no workspace.
+ * RESCNN (App. H): n_hidden = 16 filters, n_layers = residual blocks (0 .. 8), widths unused;
+ * h(0) = Conv(s), h(l+1) = h(l) + Conv[GELU(Conv(GELU(LN(h(l)))))], log psi = sum over sites
+ * and channels of LN(h(n_layers)); 3 x 3 periodic cross-correlations with a bias per output
+ * channel, LN over the 16 channels of a site (eps 1e-6, scale and shift per channel), GELU
+ * in its tanh form.  Two-dimensional TFIM (Ly >= 3, N <= 512).  Parameter vector
+ *   [K0 (16 x 1 x 3 x 3) | b0 | per block: gamma | beta | K1 (16 x 16 x 3 x 3) | b1 | K2 | b2 |
+ *    final gamma | final beta]   (K[co][ci][dy][dx]; P = 192 + 4672 n_layers).
+ * Sampling copy F32 (CUDA cores).  nqs_logpsi_grad and the force are not built for it. */
 typedef struct {
   int32_t kind;
   int32_t n_hidden;

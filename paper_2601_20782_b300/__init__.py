@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 NQS_OK, NQS_EINVAL, NQS_ECUDA, NQS_ENOMEM, NQS_ETIMEOUT, NQS_EUNSUPPORTED = range(6)
 DTYPES = {"f32": 0, "bf16": 1, "f16": 2, "fp8": 3}
-MODELS = {"rbm": 0, "dense": 1}
+MODELS = {"rbm": 0, "dense": 1, "rescnn": 2}
 HAMS = {"tfim": 0, "heisenberg": 1}
 OPT_REFRESH, OPT_CHAINS_PER_WARP, OPT_MAX_ROWS = 0, 1, 2
 
@@ -147,14 +147,17 @@ def _stream():
 
 
 class Context:
-    """One nqs_ctx: a Hamiltonian, an ansatz and the dtype of its sampling copy."""
+    """One nqs_ctx: a Hamiltonian, an ansatz and the dtype of its sampling copy.
+
+    model="rbm" (n_hidden), "dense" (widths) or "rescnn" (n_hidden = filters, n_blocks)."""
 
     def __init__(self, ham="tfim", Lx=4, Ly=1, J1=1.0, J2=0.0, h=0.0, marshall=False,
-                 model="rbm", n_hidden=0, widths=(), dtype="f32"):
+                 model="rbm", n_hidden=0, widths=(), dtype="f32", n_blocks=0):
         self._h = None
         hd = HamDesc(HAMS[ham], Lx, Ly, J1, J2, h, int(bool(marshall)))
         self._widths = (ctypes.c_int32 * max(len(widths), 1))(*widths)
-        md = ModelDesc(MODELS[model], n_hidden, len(widths), self._widths)
+        n_layers = n_blocks if model == "rescnn" else len(widths)
+        md = ModelDesc(MODELS[model], n_hidden, n_layers, self._widths)
         out = ctypes.c_void_p()
         st = _lib.nqs_create(ctypes.byref(out), ctypes.byref(md), ctypes.byref(hd), DTYPES[dtype])
         if st != NQS_OK:

@@ -91,6 +91,14 @@ struct nqs_ctx {
   void *d_force_part = nullptr;    // FP64 force partials [slices][P]
   int grad_chunk = 0;
 
+  // ---- ResCNN (App. H): n_blocks residual blocks of 16 filters -------------------------
+  int n_blocks = 0;
+  float *d_cw = nullptr;           // [P] FP32 copy in kernel order (rescnn.cu)
+  float *d_cw_lp = nullptr;        // [P] FP32 values of the 16-bit copy in kernel order (rescnn_tc.cu)
+  uint16_t *d_ctile = nullptr;     // 16-bit convolution B tiles (rescnn_tc.cu)
+  float *d_clp = nullptr;          // [cnn_rows] log psi of local-energy configurations
+  int64_t cnn_rows = 0;
+
   std::string err;
 };
 
@@ -151,6 +159,16 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t n_chains, int
                         float *delta, cudaStream_t s);
 cudaError_t dense_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
                               const double *stats, double *force, cudaStream_t s, bool share = false);
+// rescnn.cu
+bool rescnn_setup(nqs_ctx *c, const nqs_model_desc *m, std::string *why);
+cudaError_t rescnn_alloc(nqs_ctx *c);
+void rescnn_free(nqs_ctx *c);
+cudaError_t rescnn_prepare(nqs_ctx *c, const double *params, cudaStream_t s);
+cudaError_t rescnn_logpsi(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *out, cudaStream_t s);
+cudaError_t rescnn_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *eloc, cudaStream_t s);
+cudaError_t rescnn_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_sweeps, int burn_in, uint64_t seed,
+                         uint32_t sweep_offset, uint32_t *samples, float *logpsi, int64_t *n_acc, uint32_t *acc_bits,
+                         float *delta, cudaStream_t s);
 // dense_gemm.cu
 bool make_tmap_bf16_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);
 bool make_tmap_u8_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows);

@@ -89,7 +89,8 @@ nqs_status nqs_create(nqs_ctx **out, const nqs_model_desc *model, const nqs_ham_
   if (ham->kind != NQS_TFIM && ham->kind != NQS_HEISENBERG) return fail(nullptr, NQS_EINVAL, "unknown Hamiltonian kind");
   if (ham->Lx < 3 || !(ham->Ly == 1 || ham->Ly >= 3))
     return fail(nullptr, NQS_EINVAL, "periodic lattice needs Lx >= 3 and Ly == 1 or Ly >= 3");
-  if (model->kind != NQS_RBM && model->kind != NQS_DENSE) return fail(nullptr, NQS_EINVAL, "unknown model kind");
+  if (model->kind != NQS_RBM && model->kind != NQS_DENSE && model->kind != NQS_RESCNN)
+    return fail(nullptr, NQS_EINVAL, "unknown model kind");
   if ((int)dtype < 0 || (int)dtype > 3) return fail(nullptr, NQS_EINVAL, "unknown dtype");
   const int64_t N64 = (int64_t)ham->Lx * ham->Ly;
   if (N64 > 1024) return fail(nullptr, NQS_EINVAL, "at most 1024 sites");
@@ -137,12 +138,19 @@ nqs_status nqs_create(nqs_ctx **out, const nqs_model_desc *model, const nqs_ham_
       delete c;
       return fail(nullptr, NQS_EUNSUPPORTED, why);
     }
-  } else {
+  } else if (model->kind == NQS_DENSE) {
     if (!nqs::dense_setup(c, model, &why)) {
       delete c;
       return fail(nullptr, NQS_EUNSUPPORTED, why);
     }
     c->M = 32;  // the RBM tables below are not used by a dense context (kept minimal)
+    c->M_pad = 32;
+  } else {
+    if (!nqs::rescnn_setup(c, model, &why)) {
+      delete c;
+      return fail(nullptr, NQS_EUNSUPPORTED, why);
+    }
+    c->M = 32;  // as for the dense ansatz, the RBM tables are not used
     c->M_pad = 32;
   }
   if (ham->kind == NQS_HEISENBERG && (c->N % 2) != 0) {
@@ -191,6 +199,12 @@ nqs_status nqs_create(nqs_ctx **out, const nqs_model_desc *model, const nqs_ham_
     delete c;
     return fail(nullptr, NQS_ENOMEM, std::string("dense allocation failed: ") + cudaGetErrorString(e));
   }
+  if (c->model_kind == NQS_RESCNN && (e = nqs::rescnn_alloc(c)) != cudaSuccess) {
+    nqs::rescnn_free(c);
+    free_all(c);
+    delete c;
+    return fail(nullptr, NQS_ENOMEM, std::string("ResCNN allocation failed: ") + cudaGetErrorString(e));
+  }
   *out = c;
   return NQS_OK;
 }
@@ -198,6 +212,7 @@ nqs_status nqs_create(nqs_ctx **out, const nqs_model_desc *model, const nqs_ham_
 void nqs_destroy(nqs_ctx *c) {
   if (!c) return;
   if (c->model_kind == NQS_DENSE) nqs::dense_free(c);
+  if (c->model_kind == NQS_RESCNN) nqs::rescnn_free(c);
   free_all(c);
   delete c;
 }
@@ -230,7 +245,9 @@ nqs_status nqs_set_params(nqs_ctx *c, const double *params, nqs_stream stream) {
   int zero = 0;
   cudaError_t e = cudaMemcpyAsync(c->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "nqs_set_params");
-  e = c->model_kind == NQS_DENSE ? nqs::dense_prepare(c, params, s) : nqs::rbm_prepare(c, params, s);
+  e = c->model_kind == NQS_DENSE    ? nqs::dense_prepare(c, params, s)
+      : c->model_kind == NQS_RESCNN ? nqs::rescnn_prepare(c, params, s)
+                                    : nqs::rbm_prepare(c, params, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "nqs_set_params");
   int st = 0;
   float bounds[2] = {0.f, 0.f};
@@ -275,6 +292,10 @@ nqs_status nqs_sweep(nqs_ctx *c, uint32_t *state, int64_t n_chains, int32_t n_sw
           ? nqs::dense_sweep(c, state, n_chains, n_sweeps, burn_in, seed, sweep_offset, samples, logpsi, n_accepted,
                              trace ? trace->accept_bits : nullptr, trace ? trace->delta : nullptr,
                              reinterpret_cast<cudaStream_t>(stream))
+      : c->model_kind == NQS_RESCNN
+          ? nqs::rescnn_sweep(c, state, n_chains, n_sweeps, burn_in, seed, sweep_offset, samples, logpsi, n_accepted,
+                              trace ? trace->accept_bits : nullptr, trace ? trace->delta : nullptr,
+                              reinterpret_cast<cudaStream_t>(stream))
           : nqs::rbm_sweep(c, state, n_chains, n_sweeps, burn_in, seed, sweep_offset, samples, logpsi, n_accepted,
                            trace ? trace->accept_bits : nullptr, trace ? trace->delta : nullptr,
                            reinterpret_cast<cudaStream_t>(stream));
@@ -286,8 +307,10 @@ nqs_status nqs_logpsi(nqs_ctx *c, const uint32_t *cfg, int64_t n, float *out, nq
   if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_logpsi: parameters not set");
   if (n < 0 || (n > 0 && (bad_ptr(cfg) || bad_ptr(out)))) return fail(c, NQS_EINVAL, "nqs_logpsi: bad arguments");
   if (n == 0) return NQS_OK;
-  cudaError_t e = c->model_kind == NQS_DENSE ? nqs::dense_logpsi(c, cfg, n, out, reinterpret_cast<cudaStream_t>(stream))
-                                             : nqs::rbm_logpsi(c, cfg, n, out, reinterpret_cast<cudaStream_t>(stream));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = c->model_kind == NQS_DENSE    ? nqs::dense_logpsi(c, cfg, n, out, s)
+                  : c->model_kind == NQS_RESCNN ? nqs::rescnn_logpsi(c, cfg, n, out, s)
+                                                : nqs::rbm_logpsi(c, cfg, n, out, s);
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_logpsi");
 }
 
@@ -296,9 +319,10 @@ nqs_status nqs_local_energy(nqs_ctx *c, const uint32_t *cfg, int64_t n, float *e
   if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_local_energy: parameters not set");
   if (n < 0 || (n > 0 && (bad_ptr(cfg) || bad_ptr(eloc)))) return fail(c, NQS_EINVAL, "nqs_local_energy: bad arguments");
   if (n == 0) return NQS_OK;
-  cudaError_t e = c->model_kind == NQS_DENSE
-                      ? nqs::dense_local_energy(c, cfg, n, eloc, reinterpret_cast<cudaStream_t>(stream))
-                      : nqs::rbm_local_energy(c, cfg, n, eloc, reinterpret_cast<cudaStream_t>(stream));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = c->model_kind == NQS_DENSE    ? nqs::dense_local_energy(c, cfg, n, eloc, s)
+                  : c->model_kind == NQS_RESCNN ? nqs::rescnn_local_energy(c, cfg, n, eloc, s)
+                                                : nqs::rbm_local_energy(c, cfg, n, eloc, s);
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_local_energy");
 }
 
@@ -316,7 +340,7 @@ nqs_status nqs_flip_delta(nqs_ctx *c, const uint32_t *cfg, const int32_t *sites,
 }
 
 size_t nqs_logpsi_grad_workspace(const nqs_ctx *c, int64_t n) {
-  if (!c || n <= 0 || c->model_kind == NQS_DENSE) return 0;
+  if (!c || n <= 0 || c->model_kind != NQS_RBM) return 0;
   return nqs::rbm_grad_workspace(c, n);
 }
 
@@ -324,6 +348,7 @@ nqs_status nqs_logpsi_grad(nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O,
                            const double *stats, double *force, void *ws, size_t ws_bytes, nqs_stream stream) {
   if (!c) return NQS_EINVAL;
   if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_logpsi_grad: parameters not set");
+  if (c->model_kind == NQS_RESCNN) return fail(c, NQS_EUNSUPPORTED, "nqs_logpsi_grad: not built for the ResCNN");
   if (n < 0 || (n > 0 && bad_ptr(cfg))) return fail(c, NQS_EINVAL, "nqs_logpsi_grad: bad arguments");
   if (force && n > 0 && (bad_ptr(eloc) || bad_ptr(stats)))
     return fail(c, NQS_EINVAL, "nqs_logpsi_grad: the force needs eloc and stats");
@@ -376,6 +401,7 @@ nqs_status nqs_force_share(nqs_ctx *c, const uint32_t *cfg, int64_t n, const flo
                            double *force, void *ws, size_t ws_bytes, nqs_stream stream) {
   if (!c) return NQS_EINVAL;
   if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_force_share: parameters not set");
+  if (c->model_kind == NQS_RESCNN) return fail(c, NQS_EUNSUPPORTED, "nqs_force_share: not built for the ResCNN");
   if (n < 0 || bad_ptr(force) || (n > 0 && (bad_ptr(cfg) || bad_ptr(eloc) || bad_ptr(stats))))
     return fail(c, NQS_EINVAL, "nqs_force_share: bad arguments");
   if (n > 0 && c->model_kind == NQS_RBM && (bad_ptr(ws) || ws_bytes < nqs::rbm_grad_workspace(c, n)))
@@ -399,8 +425,9 @@ nqs_status nqs_local_energy_chains(nqs_ctx *c, const uint32_t *samples, int64_t 
   if (n_chains == 0 || per_chain == 0) return NQS_OK;
   if (bad_ptr(samples) || bad_ptr(eloc)) return fail(c, NQS_EINVAL, "nqs_local_energy_chains: null argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = c->model_kind == NQS_DENSE ? nqs::dense_local_energy(c, samples, n_chains * per_chain, eloc, s)
-                                             : nqs::rbm_local_energy_chains(c, samples, n_chains, per_chain, eloc, s);
+  cudaError_t e = c->model_kind == NQS_DENSE    ? nqs::dense_local_energy(c, samples, n_chains * per_chain, eloc, s)
+                  : c->model_kind == NQS_RESCNN ? nqs::rescnn_local_energy(c, samples, n_chains * per_chain, eloc, s)
+                                                : nqs::rbm_local_energy_chains(c, samples, n_chains, per_chain, eloc, s);
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_local_energy_chains");
 }
 

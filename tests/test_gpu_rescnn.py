@@ -1,0 +1,143 @@
+"""Parity of the CUDA ResCNN path (App. H) with the FP64 oracle, through the C ABI.
+
+FP32 copy (CUDA cores): log psi within 1e-5 relative; local energies within the bound the
+log psi tolerance implies for the ratios psi(x') / psi(x); sweeps replayed in the oracle in
+lockstep (bit-exact proposals, samples and accept counts; decisions may differ only within
+tau of the threshold); the 4 x 3 sampled energy and histogram against exact enumeration.
+"""
+import numpy as np
+import pytest
+
+from helpers import nqs, pack_np, unpack_np, unpack_accept_bits, to_words_tensor, words_from_tensor
+from oracle import exact
+from oracle.estimators import local_energy as oracle_eloc
+from oracle.hamiltonian import TFIM
+from oracle.philox import init_spins_random
+from oracle.rescnn import ResCNN
+from oracle.sampler import mh_sweeps
+from workloads import rescnn_params
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+LOGPSI_RTOL = 1e-5
+
+
+def make(Lx, Ly, B, seed, h=3.04, dtype="f32"):
+    p = nqs()
+    ctx = p.Context("tfim", Lx, Ly, J1=1.0, h=h, model="rescnn", n_hidden=16, n_blocks=B, dtype=dtype)
+    params = rescnn_params(16, B, seed)
+    ctx.set_params(torch.from_numpy(params).cuda())
+    return ctx, ResCNN(Lx, Ly, 16, B, params), TFIM(Lx, Ly, 1.0, h)
+
+
+def rand_configs(n, N, seed):
+    return np.random.default_rng(seed).choice([-1, 1], size=(n, N)).astype(np.int8)
+
+
+@pytest.mark.parametrize("Lx,Ly,B,n", [(4, 4, 4, 517), (10, 10, 4, 131), (6, 5, 2, 77), (3, 7, 1, 40),
+                                       (16, 16, 3, 9), (5, 5, 0, 33)])
+def test_logpsi_fp32_matches_oracle(Lx, Ly, B, n):
+    ctx, model, _ = make(Lx, Ly, B, 100 + Lx * Ly)
+    s = rand_configs(n, Lx * Ly, 1)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx.logpsi(to_words_tensor(pack_np(s)), out)
+    ref = model.logpsi(s)
+    got = out.cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=LOGPSI_RTOL * np.maximum(1.0, np.abs(ref)).max())
+
+
+@pytest.mark.parametrize("Lx,Ly,B,n", [(4, 4, 4, 37), (10, 10, 4, 9), (6, 5, 2, 23)])
+def test_local_energy_fp32_matches_oracle(Lx, Ly, B, n):
+    ctx, model, ham = make(Lx, Ly, B, 7 + Lx)
+    s = rand_configs(n, Lx * Ly, 2)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx.local_energy(to_words_tensor(pack_np(s)), out)
+    ref = oracle_eloc(ham, model.logpsi, s)
+    # each ratio psi(x') / psi(x) = exp(dlp) carries at most the two log psi errors
+    lp = model.logpsi(s)
+    off = ref - ham.diagonal(s)
+    tol = 2 * LOGPSI_RTOL * np.abs(lp).max() * np.abs(off) + 1e-5 * np.abs(ref) + 1e-5
+    assert np.all(np.abs(out.cpu().numpy() - ref) <= tol)
+
+
+def _lockstep(Lx, Ly, B, C, T, burn, seed=5, tau=1e-3):
+    ctx, model, _ = make(Lx, Ly, B, 41, h=1.0)
+    N = Lx * Ly
+    state = torch.zeros((C, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, seed=seed + 1)
+    s0 = unpack_np(words_from_tensor(state), N)
+    np.testing.assert_array_equal(s0, init_spins_random(seed + 1, np.arange(C), N))
+    K = T - burn
+    samples = torch.zeros((K * C, ctx.W), dtype=torch.int32, device="cuda")
+    logpsi = torch.zeros(K * C, dtype=torch.float32, device="cuda")
+    nacc = torch.zeros(C, dtype=torch.int64, device="cuda")
+    bits = torch.zeros((C, T, ctx.W), dtype=torch.int32, device="cuda")
+    delta = torch.zeros((C, T, N), dtype=torch.float32, device="cuda")
+    ctx.sweep(state, T, burn, seed, 3, samples, logpsi, nacc, accept_bits=bits, delta=delta)
+    torch.cuda.synchronize()
+    acc = unpack_accept_bits(words_from_tensor(bits), N)
+    ref = mh_sweeps(model.logpsi, s0, np.arange(C), seed, T, burn, sweep_offset=3, replay_accepts=acc, tau=tau,
+                    record_deltas=True)
+    np.testing.assert_array_equal(unpack_np(words_from_tensor(state), N), ref["spins"])
+    np.testing.assert_array_equal(unpack_np(words_from_tensor(samples), N), ref["samples"])
+    np.testing.assert_array_equal(nacc.cpu().numpy(), acc.sum(axis=(1, 2)))
+    lp_ref = ref["logpsi"]
+    np.testing.assert_allclose(logpsi.cpu().numpy(), lp_ref, rtol=0,
+                               atol=LOGPSI_RTOL * np.maximum(1.0, np.abs(lp_ref)).max())
+    d = delta.cpu().numpy()
+    np.testing.assert_allclose(d, ref["deltas"], rtol=0, atol=2 * LOGPSI_RTOL * np.abs(lp_ref).max())
+    return ref, acc
+
+
+def test_sweep_lockstep_4x4_ragged_groups():
+    # 70 chains over groups of 32: two full groups and a ragged one
+    ref, acc = _lockstep(4, 4, 4, 70, 3, 1)
+    assert 0.05 < acc.mean() < 0.95
+
+
+def test_sweep_lockstep_10x10():
+    ref, acc = _lockstep(10, 10, 2, 7, 1, 0)
+    assert acc.mean() > 0.02
+
+
+def test_sampled_energy_4x3_matches_enumeration():
+    Lx, Ly, B = 4, 3, 2
+    ctx, model, ham = make(Lx, Ly, B, 77, h=1.0)
+    N = Lx * Ly
+    S = exact.all_configs(N)
+    pi = exact.exact_pi(model.logpsi, N)
+    E_exact = pi @ oracle_eloc(ham, model.logpsi, S)
+    C, T, burn = 4096, 40, 10
+    state = torch.zeros((C, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, seed=9)
+    samples = torch.zeros(((T - burn) * C, ctx.W), dtype=torch.int32, device="cuda")
+    nacc = torch.zeros(C, dtype=torch.int64, device="cuda")
+    ctx.sweep(state, T, burn, 123, 0, samples, None, nacc)
+    eloc = torch.empty((T - burn) * C, dtype=torch.float32, device="cuda")
+    ctx.local_energy(samples, eloc)
+    stats = torch.zeros(5, dtype=torch.float64, device="cuda")
+    ctx.stats(eloc, C, stats, nacc, T * N)
+    E, var, err, acc_rate, n = stats.cpu().numpy()
+    assert abs(E - E_exact) < 5 * err, (E, E_exact, err)
+    # the sampled histogram against the exact distribution, at the i.i.d. noise floor
+    idx = exact.config_index(unpack_np(words_from_tensor(samples[-C:]), N))
+    hist = np.bincount(idx, minlength=pi.size) / C
+    tv = 0.5 * np.abs(hist - pi).sum()
+    floor = np.mean([0.5 * np.abs(np.bincount(np.random.default_rng(k).choice(pi.size, C, p=pi),
+                                              minlength=pi.size) / C - pi).sum() for k in range(4)])
+    assert tv < 1.2 * floor + 0.01, (tv, floor)
+
+
+def test_rescnn_rejections():
+    p = nqs()
+    with pytest.raises(p.NQSError):
+        p.Context("tfim", 16, 1, h=1.0, model="rescnn", n_hidden=16, n_blocks=2)     # 1D
+    with pytest.raises(p.NQSError):
+        p.Context("tfim", 4, 4, h=1.0, model="rescnn", n_hidden=8, n_blocks=2)      # filters
+    with pytest.raises(p.NQSError):
+        p.Context("heisenberg", 4, 4, J1=1.0, model="rescnn", n_hidden=16, n_blocks=2)
+    ctx, _, _ = make(4, 4, 1, 3)
+    cfg = to_words_tensor(pack_np(rand_configs(4, 16, 3)))
+    with pytest.raises(p.NQSError):
+        ctx.logpsi_grad(cfg, torch.zeros((4, ctx.P), dtype=torch.float32, device="cuda"))
