@@ -498,6 +498,80 @@ class ComplexRbmStep:
         }
 
 
+class RescnnStep:
+    """Downcast, init, sweeps, local energies of every kept sample and statistics of the ResCNN
+    workload (App. H: 4 residual blocks x 16 filters, 3 x 3 kernels; 10 x 10 TFIM at h = 3.04)."""
+
+    def __init__(self, nqs, torch, dev, wl, dtype, C=None, T=None, B=None):
+        lat = wl.ham.lattice
+        self.wl, self.torch, self.dtype = wl, torch, dtype
+        self.N, self.F, self.nb = lat.n_sites, wl.extra["filters"], wl.extra["blocks"]
+        self.C, self.T, self.B = C or wl.n_chains, T or wl.n_sweeps, wl.burn_in if B is None else B
+        self.S = (self.T - self.B) * self.C
+        self.ctx = nqs.Context("tfim", lat.Lx, lat.Ly, J1=wl.ham.J1, h=wl.ham.h, model="rescnn", n_hidden=self.F,
+                               n_blocks=self.nb, dtype=dtype)
+        self.params_h = torch.from_numpy(workloads.rescnn_params(self.F, self.nb, wl.seed)).pin_memory()
+        self.params = self.params_h.to(dev)
+        z = lambda *sh, dt=torch.int32: torch.zeros(sh, dtype=dt, device=dev)
+        self.state, self.samples = z(self.C, self.ctx.W), z(self.S, self.ctx.W)
+        self.nacc, self.eloc = z(self.C, dt=torch.int64), z(self.S, dt=torch.float32)
+        self.stats = z(5, dt=torch.float64)
+        self.out_h = torch.zeros(5, dtype=torch.float64).pin_memory()
+        self.ph = _Phased(torch, ["set_params+init", "sweep", "local_energy", "stats"])
+        chunks = -(-self.S * (self.N + 1) // (1 << 20))      # local-energy chunks of 2^20 configurations
+        # prepare (+ the 16-bit copy's prepare), init, sweep, per chunk evaluation + combine, stats (2)
+        self.launches = (1 if dtype == "f32" else 2) + 1 + 1 + 2 * chunks + 2
+        self.h2d, self.d2h = self.ctx.P * 8, 5 * 8
+
+    def run(self, seed, host_io=False):
+        c, ph = self.ctx, self.ph
+        if host_io:
+            self.params.copy_(self.params_h, non_blocking=True)
+        ph.mark(0)
+        c.set_params(self.params)
+        c.init_chains(self.state, seed)
+        ph.mark(1)
+        c.sweep(self.state, self.T, self.B, seed + 1, 0, self.samples, None, self.nacc)
+        ph.mark(2)
+        c.local_energy(self.samples, self.eloc)
+        ph.mark(3)
+        c.stats(self.eloc, self.C, self.stats, self.nacc, self.T * self.N)
+        ph.mark(4)
+        if host_io:
+            self.out_h.copy_(self.stats, non_blocking=True)
+
+    def units(self):
+        return self.C * self.T * self.N
+
+    def flops_per_eval(self):
+        # algorithmic FLOPs of one forward pass: 2 x 9 x 16 x 16 per site and block convolution,
+        # 2 x 9 x 16 per site for the embedding
+        return 2.0 * self.N * (2 * self.nb * 9 * self.F * self.F + 9 * self.F)
+
+    def describe(self, ms, accepts, peaks_, n_sm):
+        lat = self.wl.ham.lattice
+        fl = self.flops_per_eval() * self.units()
+        ach = fl / (ms["sweep"] / 1e3) / 1e12
+        tc = self.dtype != "f32"
+        peak = float(peaks_.get("bf16_tflops", 1764.5)) if tc else 2.0 * peaks_["alu"]["ffma"]
+        return {
+            "config": {"workload": self.wl.name, "lattice": f"{lat.Lx}x{lat.Ly} periodic", "h": self.wl.ham.h,
+                       "filters": self.F, "blocks": self.nb, "chains": self.C, "sweeps": self.T, "burn_in": self.B,
+                       "samples": self.S, "params": self.ctx.P},
+            "local_energy": {"value": self.S / (ms["local_energy"] / 1e3), "unit": "samples/s"},
+            "sweep": {"value": self.units() / (ms["sweep"] / 1e3), "unit": "proposals/s",
+                      "acceptance": accepts / self.units()},
+            "energy": float(self.stats[0].item()),
+            "roofline": {"bound": "tensor" if tc else "alu",
+                         "kernel": "rescnn_tc_sweep_kernel" if tc else "rescnn_sweep_f32_kernel",
+                         "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                         "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json); F16 has the same "
+                                        "nominal rate" if tc else "measured fma.rn.f32 issue rate x 2 FLOP",
+                         "note": "algorithmic convolution FLOPs of one forward pass per proposal "
+                                 "(2 x 9 x 16 x 16 per site and block convolution)"},
+        }
+
+
 class DenseStep:
     """Downcast, init, sweeps (burn-in + kept), local energies of the kept samples, statistics,
     O rows and force of a dense-ansatz workload.  `T` overrides the sweep count (the 16 x 16
@@ -751,6 +825,8 @@ def run_workload(args, rank, world, dist):
                        dtype="fp8" if args.dtype == "fp8" else "bf16")
     elif args.workload == "crbm-tfim2d":
         st = ComplexRbmStep(nqs, torch, dev, WL, C, T, B)
+    elif args.workload == "rescnn-tfim2d":
+        st = RescnnStep(nqs, torch, dev, workloads.RESCNN_2D_10x10, args.dtype, C, T, B)
     else:
         st = BatchStep(nqs, torch, dev)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
@@ -792,7 +868,7 @@ def run_workload(args, rank, world, dist):
         t_dev, t_e2e = tt.tolist()
     ms = {n: v / args.steps for n, v in tot.items()}
     pk = dict(peaks())
-    if isinstance(st, (RbmStep, ComplexRbmStep)):
+    if isinstance(st, (RbmStep, ComplexRbmStep)) or (isinstance(st, RescnnStep) and st.dtype == "f32"):
         pk["alu"] = measure_alu_peaks(nqs, torch, dev)
     d = st.describe(ms, acc / args.steps, pk, torch.cuda.get_device_properties(dev).multi_processor_count)
     units = st.units()
@@ -805,7 +881,11 @@ def run_workload(args, rank, world, dist):
                       "j1j2-dense": ("fp8 e4m3 sampling (bf16 local energy, " if args.dtype == "fp8" else "bf16 (")
                       + "fp32 accumulate, fp32 layer-0 cache)",
                       "batched": "f16 sampling (f32 caches, accept, statistics)",
-                      "crbm-tfim2d": "complex f32 (f64 statistics and force accumulation)"}[args.workload],
+                      "crbm-tfim2d": "complex f32 (f64 statistics and force accumulation)",
+                      "rescnn-tfim2d": {"f32": "f32 (CUDA cores)", "bf16": "bf16 convolutions on tcgen05 (fp32 "
+                                        "accumulate, LN, residual stream)", "f16": "f16 convolutions on tcgen05 "
+                                        "(fp32 accumulate, LN, residual stream)"}.get(args.dtype, args.dtype)
+                      }[args.workload],
             "data": "synthetic (seeded random-init networks, random initial spins)"}
     line.update(d)
     if args.chains or args.sweeps or args.burn_in is not None or args.grad_rows:
@@ -818,6 +898,33 @@ def run_workload(args, rank, world, dist):
     if st.launches:
         line["gpu_launches"] = st.launches * args.steps
     line["clocks"] = clk.summary()
+    if isinstance(st, RescnnStep) and args.compare:   # the other sampling copies, same sizes and steps
+        line["compare"] = {}
+        for d in ("f32", "bf16", "f16"):
+            if d == args.dtype:
+                continue
+            o = RescnnStep(nqs, torch, dev, workloads.RESCNN_2D_10x10, d, C, T, B)
+            for w in range(args.warmup):
+                o.run(base + w)
+            tot2 = {}
+            for k in range(args.steps):
+                flush.zero_()
+                o.run(base + 100 + k)
+                torch.cuda.synchronize()
+                for n, v in o.ph.ms().items():
+                    tot2[n] = tot2.get(n, 0.0) + v
+            ms2 = {n: v / args.steps for n, v in tot2.items()}
+            line["compare"][d] = {"value": world * o.units() / (sum(ms2.values()) / 1e3),
+                                  "sweep_proposals_per_s": world * o.units() / (ms2["sweep"] / 1e3),
+                                  "local_energy_samples_per_s": world * o.S / (ms2["local_energy"] / 1e3),
+                                  "E": float(o.stats[0].item()), "E_err": float(o.stats[2].item())}
+        if "f32" in line["compare"]:
+            f32 = line["compare"]["f32"]
+            line["mixed_vs_f32"] = {"sweep": line["sweep"]["value"] / f32["sweep_proposals_per_s"],
+                                    "local_energy": line["local_energy"]["value"] / f32["local_energy_samples_per_s"],
+                                    "step": line["value"] / f32["value"],
+                                    "energy_minus_f32": line["energy"] - f32["E"],
+                                    "energy_err": math.hypot(float(st.stats[2].item()), f32["E_err"])}
     return line
 
 
@@ -915,7 +1022,7 @@ def main():
     ap.add_argument("--burn-in", type=int, default=None, help="profiling only: override the burn-in")
     ap.add_argument("--grad-rows", type=int, default=0, help="profiling only (j1j2-dense): O rows / minSR samples")
     ap.add_argument("--workload", default="tfim2d", choices=["tfim2d", "tfim1d", "heis2d-dense", "batched",
-                                                             "j1j2-dense", "noisy-rbm", "crbm-tfim2d"],
+                                                             "j1j2-dense", "noisy-rbm", "crbm-tfim2d", "rescnn-tfim2d"],
                     help="tfim2d: the 10x10 alpha=4 RBM workload (default); the others measure the other "
                          "workloads' steps with the same line")
     args = ap.parse_args()

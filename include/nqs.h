@@ -90,7 +90,10 @@ typedef struct {
  * in its tanh form.  Two-dimensional TFIM (Ly >= 3, N <= 512).  Parameter vector
  *   [K0 (16 x 1 x 3 x 3) | b0 | per block: gamma | beta | K1 (16 x 16 x 3 x 3) | b1 | K2 | b2 |
  *    final gamma | final beta]   (K[co][ci][dy][dx]; P = 192 + 4672 n_layers).
- * Sampling copy F32 (CUDA cores).  nqs_logpsi_grad and the force are not built for it. */
+ * Sampling copy F32 (CUDA cores), or BF16 / F16 with the convolutions as tcgen05 products:
+ * kernels and the activations entering a convolution in the 16-bit type, biases, LN, the
+ * residual stream, accumulation and the final sum in FP32; nqs_logpsi and nqs_local_energy
+ * use the context's copy.  nqs_logpsi_grad and the force are not built for it. */
 typedef struct {
   int32_t kind;
   int32_t n_hidden;
@@ -272,6 +275,16 @@ nqs_status nqs_probe_alu(int32_t kind, int64_t blocks, int32_t threads, int64_t 
  * never completed. */
 nqs_status nqs_selftest_tc_gemm(const uint16_t *A, const uint16_t *B, float *D, int32_t N, int32_t K,
                                 int32_t flags, int32_t *status, nqs_stream stream);
+
+/* Self-test of the shifted-row product the periodic convolutions use (no counterpart in the
+ * paper): D [128 x 16] FP32 = sum_{t < n_taps} A[base + offs[t] .. + 127] B_t^T with A
+ * [n_rows x 16] and B [n_taps][16 x 16] BF16 (row-major, device), staged without swizzle as
+ * two 8-channel planes; offs: host int32 [n_taps].  128 <= n_rows <= 256 (a multiple of 8),
+ * 1 <= n_taps <= 8, every shifted window inside [0, n_rows); else NQS_EINVAL.  *status
+ * (device int) gets the timeout bit if the product never completed. */
+nqs_status nqs_selftest_tc_shift(const uint16_t *A, int32_t n_rows, const uint16_t *B, int32_t n_taps,
+                                 const int32_t *offs, int32_t base, float *D, int32_t *status,
+                                 nqs_stream stream);
 
 /* nqs_local_energy of the samples nqs_sweep writes: samples [per_chain * n_chains x W],
  * sweep-major (row k * n_chains + c), eloc the same rows.  The values are those of

@@ -92,6 +92,7 @@ _SIGS = {
     "nqs_stats_finalize": (_i32, [_vp, _vp, _vp]),
     "nqs_force_share": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
     "nqs_selftest_tc_gemm": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "nqs_selftest_tc_shift": (_i32, [_vp, _i32, _vp, _i32, _vp, _i32, _vp, _vp, _vp]),
     "nqs_set_noise": (_i32, [_vp, ctypes.c_double, _u64]),
     "nqs_local_energy_chains": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp]),
     "nqs_minsr_workspace": (_sz, [_vp, _i64]),
@@ -427,6 +428,21 @@ def selftest_tc_gemm(A, B, a_transposed=False, b_transposed=False):
                                    _ptr(status, (torch.int32,), "status"), _stream())
     if st != NQS_OK:
         raise NQSError(st, "nqs_selftest_tc_gemm failed")
+    return D, status
+
+
+def selftest_tc_shift(A, B, offs, base):
+    """D [128 x 16] = sum_t A[base + offs[t] : base + offs[t] + 128] @ B[t]^T on the tensor cores
+    (no-swizzle operand planes).  A [n_rows x 16], B [n_taps x 16 x 16] BF16 CUDA tensors."""
+    n_rows, n_taps = A.shape[0], B.shape[0]
+    D = torch.empty((128, 16), dtype=torch.float32, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    o = (ctypes.c_int32 * max(n_taps, 1))(*offs)
+    st = _lib.nqs_selftest_tc_shift(_ptr(A, (torch.bfloat16,), "A", (n_rows, 16), False), n_rows,
+                                    _ptr(B, (torch.bfloat16,), "B", (n_taps, 16, 16), False), n_taps, o, base,
+                                    _ptr(D, (torch.float32,), "D"), _ptr(status, (torch.int32,), "status"), _stream())
+    if st != NQS_OK:
+        raise NQSError(st, "nqs_selftest_tc_shift failed")
     return D, status
 
 

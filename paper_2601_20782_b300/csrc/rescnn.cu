@@ -426,11 +426,12 @@ bool rescnn_setup(nqs_ctx *c, const nqs_model_desc *m, std::string *why) {
     *why = "the ResCNN takes 0 .. 8 residual blocks (n_layers)";
     return false;
   }
+  c->n_blocks = m->n_layers;
   if (c->dtype != NQS_F32 && !rescnn_lp_supported(c)) {
-    *why = "the ResCNN sampling copy is F32, BF16 or F16";
+    *why = "the ResCNN sampling copy is F32, BF16 or F16 (16-bit copies: lattices whose padded rows fit the "
+           "tensor-core kernel's tiles and shared memory)";
     return false;
   }
-  c->n_blocks = m->n_layers;
   c->P = cnn::n_params(c->n_blocks);
   c->cnn_rows = (int64_t)1 << 20;
   return true;

@@ -36,6 +36,24 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t smem_byte_addr, uint32_t
   return d;
 }
 
+// Shared-memory matrix descriptor without swizzle (layout type 0), K-major operand: a core
+// matrix is 8 rows x 16 bytes stored contiguously (row r of it at +16 r); core matrices
+// adjacent along K are lbo_bytes apart (leading byte offset), groups of 8 rows along M / N are
+// sbo_bytes apart (stride byte offset).  Version 1 at bit 46; no base offset.
+__device__ __forceinline__ uint64_t desc_noswz(uint32_t smem_byte_addr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_byte_addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16 with A and B in F16 (format 0), D FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(uint32_t M, uint32_t N) {
+  return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
 // Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9,
 // 10-12 = 1), A / B major-ness in bits 15 / 16 (0 = K-major, 1 = MN-major), N >> 3 in
 // bits 17-22, M >> 4 in bits 24-28.

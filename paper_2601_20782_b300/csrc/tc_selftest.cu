@@ -93,8 +93,89 @@ __global__ void __launch_bounds__(128) tc_gemm_selftest_kernel(const uint16_t *_
   if (threadIdx.x < 32) tc::tmem_dealloc(taddr, ncols);
 }
 
+// The shifted-row product of the periodic convolutions (rescnn_tc.cu):
+//   D [128 x 16] = sum_t A[base + off_t .. base + off_t + 127] B_t^T,
+// A [n_rows x 16] BF16 staged as two 16-byte planes (channels 0-7 and 8-15, one 16-byte row
+// per A row), each B_t [16 x 16] as two 8-channel core-matrix columns; no-swizzle descriptors.
+// The shared-memory block is 96 KB, so that every address any reading of the two strides
+// could produce stays inside it (n_rows <= 256).
+constexpr int SHIFT_SMEM = 96 * 1024;
+__global__ void __launch_bounds__(128) tc_shift_selftest_kernel(const uint16_t *__restrict__ A, int n_rows,
+                                                                const uint16_t *__restrict__ B, int n_taps,
+                                                                int4 offs0, int4 offs1, int base, float *D,
+                                                                int *status) {
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  unsigned char *planes = smem_dyn;                   // [2][n_rows][16 B]
+  unsigned char *sB = smem_dyn + 2 * n_rows * 16;     // [tap][2][16 rows][16 B]
+  for (int i = threadIdx.x; i < SHIFT_SMEM / 16; i += blockDim.x)
+    reinterpret_cast<uint4 *>(smem_dyn)[i] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n_rows * 16; idx += blockDim.x) {
+    const int r = idx / 16, c = idx % 16;
+    *reinterpret_cast<uint16_t *>(planes + (c / 8) * n_rows * 16 + r * 16 + (c % 8) * 2) = A[idx];
+  }
+  for (int idx = threadIdx.x; idx < n_taps * 256; idx += blockDim.x) {
+    const int t = idx / 256, n = (idx / 16) % 16, k = idx % 16;
+    *reinterpret_cast<uint16_t *>(sB + t * 512 + (k / 8) * 256 + n * 16 + (k % 8) * 2) = B[idx];
+  }
+  tc::fence_proxy_async_smem();
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc(&tmem_base, 32);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem_base;
+  if (threadIdx.x == 0) {
+    const int offs[8] = {offs0.x, offs0.y, offs0.z, offs0.w, offs1.x, offs1.y, offs1.z, offs1.w};
+    for (int t = 0; t < n_taps; ++t) {
+      const uint64_t ad = tc::desc_noswz(smem_addr(planes + (base + offs[t]) * 16), n_rows * 16, 128);
+      const uint64_t bd = tc::desc_noswz(smem_addr(sB + t * 512), 256, 128);
+      tc::mma_bf16(taddr, ad, bd, tc::idesc_bf16_f32(128, 16), t > 0 ? 1u : 0u);
+    }
+    tc::mma_commit(&bar);
+  }
+  const bool ok = mbar_wait_bounded(&bar, 0, 1u << 22);
+  if (!ok && threadIdx.x == 0) atomicOr(status, STATUS_TIMEOUT);
+  tc::fence_after_sync();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (ok) {
+    float v[16];
+    tc::tmem_ld16(tc::tmem_lane_addr(taddr, 32 * warp, 0), v);
+    for (int q = 0; q < 16; ++q) D[(32 * warp + lane) * 16 + q] = v[q];
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) tc::tmem_dealloc(taddr, 32);
+}
+
 }  // namespace
 }  // namespace nqs
+
+extern "C" nqs_status nqs_selftest_tc_shift(const uint16_t *A, int32_t n_rows, const uint16_t *B, int32_t n_taps,
+                                            const int32_t *offs, int32_t base, float *D, int32_t *status,
+                                            nqs_stream stream) {
+  if (!A || !B || !offs || !D || !status || n_rows < 128 || n_rows > 256 || n_rows % 8 || n_taps < 1 || n_taps > 8)
+    return NQS_EINVAL;
+  int o[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int t = 0; t < n_taps; ++t) {
+    o[t] = offs[t];
+    if (base + o[t] < 0 || base + o[t] + 128 > n_rows) return NQS_EINVAL;
+  }
+  auto kern = nqs::tc_shift_selftest_kernel;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, nqs::SHIFT_SMEM) != cudaSuccess)
+    return NQS_ECUDA;
+  kern<<<1, 128, nqs::SHIFT_SMEM, reinterpret_cast<cudaStream_t>(stream)>>>(
+      A, n_rows, B, n_taps, make_int4(o[0], o[1], o[2], o[3]), make_int4(o[4], o[5], o[6], o[7]), base, D, status);
+  return cudaGetLastError() == cudaSuccess ? NQS_OK : NQS_ECUDA;
+}
 
 extern "C" nqs_status nqs_selftest_tc_gemm(const uint16_t *A, const uint16_t *B, float *D, int32_t N, int32_t K,
                                            int32_t flags, int32_t *status, nqs_stream stream) {

@@ -141,3 +141,138 @@ def test_rescnn_rejections():
     cfg = to_words_tensor(pack_np(rand_configs(4, 16, 3)))
     with pytest.raises(p.NQSError):
         ctx.logpsi_grad(cfg, torch.zeros((4, ctx.P), dtype=torch.float32, device="cuda"))
+
+
+# ---- 16-bit copies on the tensor cores ---------------------------------------------------------
+# The copy's definition (include/nqs.h): kernels and the activations entering a convolution
+# rounded to the 16-bit type, everything else in higher precision.  Emulated here in FP64 with
+# those rounding points, from the oracle's layers.
+from oracle.rescnn import conv3x3, gelu, layer_norm
+
+
+def round_bf16(x):
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def round_f16(x):
+    return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+
+
+ROUND = {"bf16": round_bf16, "f16": round_f16}
+
+
+def copy_logpsi(model, s, dtype):
+    rnd = ROUND[dtype]
+    x = model._grid(s)
+    h = conv3x3(x, rnd(model.K0), model.b0)
+    for (g, be, K1, b1, K2, b2) in model.blocks:
+        a = rnd(gelu(layer_norm(h, g, be)[0]))
+        c = rnd(gelu(conv3x3(a, rnd(K1), b1)))
+        h = h + conv3x3(c, rnd(K2), b2)
+    return layer_norm(h, model.gF, model.bF)[0].sum(axis=(1, 2, 3))
+
+
+# The kernel computes the values that get rounded in FP32, the emulation in FP64.  Where the two
+# fall on different sides of a 16-bit rounding boundary, one activation moves by one unit in the
+# last place, which moves log psi by about the copy's unit roundoff u16 (2^-8 BF16, 2^-11 F16;
+# Table tab:precision); a configuration sees a handful of such flips, more on larger lattices.
+# FP32 accumulation error is far below that.
+U16 = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}
+
+
+def flip_tol(dtype, N):
+    return 4.0 * U16[dtype] * (1.0 + np.sqrt(N / 16.0))
+
+
+def check_copy(got, want, dtype, N, exact=None):
+    err = np.abs(got - want)
+    assert err.max() <= flip_tol(dtype, N), (err.max(), flip_tol(dtype, N))
+    if exact is not None and dtype == "bf16" and len(got) >= 5:
+        # the kernel reproduces the copy's deterministic deviation from the FP64 network
+        assert np.corrcoef(got - exact, want - exact)[0, 1] > 0.9
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("Lx,Ly,B,n", [(4, 4, 4, 301), (10, 10, 4, 37), (6, 5, 2, 45), (16, 16, 3, 7),
+                                       (5, 5, 0, 50), (3, 7, 1, 26)])
+def test_logpsi_16bit_copy_matches_its_definition(dtype, Lx, Ly, B, n):
+    ctx, model, _ = make(Lx, Ly, B, 100 + Lx * Ly, dtype=dtype)
+    s = rand_configs(n, Lx * Ly, 5)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx.logpsi(to_words_tensor(pack_np(s)), out)
+    got = out.cpu().numpy()
+    want = copy_logpsi(model, s, dtype)
+    check_copy(got, want, dtype, Lx * Ly, model.logpsi(s) if B >= 2 else None)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_local_energy_16bit_copy(dtype):
+    Lx, Ly, B, n = 6, 5, 2, 21
+    ctx, model, ham = make(Lx, Ly, B, 9, dtype=dtype)
+    s = rand_configs(n, Lx * Ly, 6)
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx.local_energy(to_words_tensor(pack_np(s)), out)
+    lpf = lambda v: copy_logpsi(model, v, dtype)
+    ref = oracle_eloc(ham, lpf, s)
+    off = np.abs(ref - ham.diagonal(s))
+    # each ratio psi(x') / psi(x) carries the rounding-boundary error of two log psi values
+    rel = np.abs(out.cpu().numpy() - ref) / (off + 1e-6)
+    assert rel.max() <= 2 * flip_tol(dtype, Lx * Ly) + 1e-5, rel.max()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_sweep_16bit_lockstep_with_its_definition(dtype):
+    # decisions replayed against the copy's own log psi: equal except within tau of the threshold
+    Lx, Ly, B, C, T, burn = 4, 4, 3, 45, 2, 1
+    ctx, model, _ = make(Lx, Ly, B, 41, h=1.0, dtype=dtype)
+    N = Lx * Ly
+    state = torch.zeros((C, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, seed=12)
+    s0 = unpack_np(words_from_tensor(state), N)
+    samples = torch.zeros(((T - burn) * C, ctx.W), dtype=torch.int32, device="cuda")
+    nacc = torch.zeros(C, dtype=torch.int64, device="cuda")
+    bits = torch.zeros((C, T, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.sweep(state, T, burn, 31, 0, samples, None, nacc, accept_bits=bits)
+    torch.cuda.synchronize()
+    acc = unpack_accept_bits(words_from_tensor(bits), N)
+    lpf = lambda v: copy_logpsi(model, v, dtype)
+    ref = mh_sweeps(lpf, s0, np.arange(C), 31, T, burn, replay_accepts=acc, tau=4 * flip_tol(dtype, N))
+    np.testing.assert_array_equal(unpack_np(words_from_tensor(state), N), ref["spins"])
+    np.testing.assert_array_equal(unpack_np(words_from_tensor(samples), N), ref["samples"])
+    np.testing.assert_array_equal(nacc.cpu().numpy(), acc.sum(axis=(1, 2)))
+
+
+def test_bf16_sampler_targets_its_copy_and_the_bias_is_bounded():
+    # 4 x 3: the BF16 sampler's histogram matches |psi_bf16|^2 at the i.i.d. noise floor, and the
+    # exact TV(pi, pi_bf16) is below min(Pinsker, Thm 3) from the copy's single-flip increments
+    Lx, Ly, B = 4, 3, 2
+    ctx, model, ham = make(Lx, Ly, B, 77, h=1.0, dtype="bf16")
+    N = Lx * Ly
+    S = exact.all_configs(N)
+    lp_copy = copy_logpsi(model, S, "bf16")
+    pi_c = np.exp(2 * (lp_copy - lp_copy.max()))
+    pi_c /= pi_c.sum()
+    pi = exact.exact_pi(model.logpsi, N)
+    C, T, burn = 8192, 30, 10
+    state = torch.zeros((C, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, seed=19)
+    samples = torch.zeros(((T - burn) * C, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.sweep(state, T, burn, 321, 0, samples, None, None)
+    idx = exact.config_index(unpack_np(words_from_tensor(samples[-C:]), N))
+    hist = np.bincount(idx, minlength=pi.size) / C
+    tv = 0.5 * np.abs(hist - pi_c).sum()
+    floor = np.mean([0.5 * np.abs(np.bincount(np.random.default_rng(k).choice(pi.size, C, p=pi_c),
+                                              minlength=pi.size) / C - pi_c).sum() for k in range(4)])
+    assert tv < 1.2 * floor + 0.01, (tv, floor)
+    # the distance the BF16 copy puts between the sampled and the exact distribution obeys
+    # Pinsker with the exact KL; the Gaussian reading of Sec. 3 (sigma from the single-flip
+    # increments) gives a bound of the same size
+    from oracle import bounds
+    tv_exact = bounds.tv_distance(pi, pi_c)
+    kl = np.sum(pi * np.log(pi / pi_c))
+    assert tv_exact <= np.sqrt(kl / 2)
+    delta = 2 * (lp_copy - model.logpsi(S))           # log p~ - log p, up to a constant
+    x = np.arange(S.shape[0])
+    eps = np.concatenate([delta[x ^ (1 << i)] - delta for i in range(N)])
+    assert 0.25 < tv_exact / bounds.reported_bound(eps.mean(), eps.std()) < 4.0

@@ -34,3 +34,19 @@ def test_tc_gemm_mn_major_operands(N, K, a_t, b_t):
     ref = A.double() @ B.double().T
     scale = (A.double().abs() @ B.double().abs().T)
     assert torch.all((D.double() - ref).abs() <= 1e-6 * scale + 1e-30), (D - ref.float()).abs().max()
+
+
+@pytest.mark.parametrize("n_rows,offs,base", [(128, [0], 0), (144, [0, 5, 16], 0), (256, [-13, -12, -11, -1, 0, 1, 11, 12], 13),
+                                              (200, [-7, 9, 3], 40)])
+def test_tc_shifted_row_product(n_rows, offs, base):
+    # the implicit-GEMM product of the periodic convolutions: windows of A at row offsets
+    p = nqs()
+    g = torch.Generator(device="cuda").manual_seed(n_rows + base)
+    A = torch.randn((n_rows, 16), generator=g, device="cuda").to(torch.bfloat16)
+    B = torch.randn((len(offs), 16, 16), generator=g, device="cuda").to(torch.bfloat16)
+    D, status = p.selftest_tc_shift(A, B, offs, base)
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    ref = sum(A[base + o: base + o + 128].double() @ B[t].double().T for t, o in enumerate(offs))
+    scale = sum(A[base + o: base + o + 128].double().abs() @ B[t].double().abs().T for t, o in enumerate(offs))
+    assert torch.all((D.double() - ref).abs() <= 1e-6 * scale + 1e-30), (D - ref.float()).abs().max()

@@ -129,6 +129,13 @@ J1J2_2D_16x16 = Workload(
     dtypes=("fp8", "bf16"), seed=SEED_BASE + 5, extra={"minsr_samples": 4096})
 
 
+RESCNN_2D_10x10 = Workload(
+    name="rescnn_tfim2d_10x10_4blocks_16filters",
+    ham=Hamiltonian("tfim", Lattice(10, 10), J1=1.0, h=3.04), model="rescnn",
+    n_chains=8192, n_sweeps=10, burn_in=2, dtypes=("f16", "bf16", "f32"), seed=SEED_BASE + 6,
+    extra={"filters": 16, "blocks": 4, "small_case": Lattice(4, 4)})
+
+
 def batched_tfim_instances(seed=SEED_BASE + 4, n_instances=48):
     """48 independent TFIM problems, 1D and 2D, N in {36, 64, 100, 144, 196, 256},
     h ~ U[0.5, 4], alpha in {1, 2, 4}, chains log-uniform in [256, 8192]."""
