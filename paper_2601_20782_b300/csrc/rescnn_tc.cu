@@ -15,10 +15,12 @@
 // tcgen05.mma (M 128, N 16, K 16) per tile and tap accumulates in TMEM (16 FP32 columns per
 // tile).  Halo and tail rows compute garbage that is never read.
 //
-// Threads own rows: warp w reads TMEM lane quarter w % 4 of the tiles t = w / 4 + 4k, so a
-// thread owns the same up to three rows through the whole pass and keeps their residual
-// streams in registers.  One thread issues the MMAs; an mbarrier (bounded waits) hands the
-// accumulators to the epilogue, which writes the next 16-bit planes.
+// The residual streams h live in TMEM beside the accumulators (columns 128 + 16 t of tile t),
+// so a thread needs few registers and two CTAs share an SM: one CTA's epilogue runs while the
+// other's products do.  Warp w reads TMEM lane quarter w % 4 of the tiles t = w / 4 + 4 k, so a
+// thread owns the same up to two padded rows through the whole pass.  One thread issues the
+// products of a convolution tile by tile, committing each tile to its own mbarrier, so the
+// epilogue of a tile starts while the later tiles' products run; every wait is bounded.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -35,10 +37,11 @@ namespace {
 
 constexpr int TC_THREADS = 512;  // 16 warps: four groups of four warps (one per TMEM lane quarter)
 constexpr int TC_GROUPS = TC_THREADS / 128;
-constexpr int MAX_TILES = 12;
+constexpr int MAX_TILES = 8;     // accumulators in columns 0 .. 127, residual streams in 128 .. 255
 constexpr int ROWS_PT = (MAX_TILES + TC_GROUPS - 1) / TC_GROUPS;  // rows owned per thread
 constexpr int TILE_BYTES = 512;                                 // one tap: 16 x 16 16-bit values
 constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t H_COL = 128;  // first TMEM column of the residual streams
 constexpr uint32_t TC_WAIT_POLLS = 1u << 22;
 constexpr int SMALL_FLOATS = 10 * CF;  // k0 (9 x 16) and b0
 
@@ -174,7 +177,7 @@ struct Cta {
   const TcGeom &gm;
   unsigned char *base;
   TcLayout L;
-  uint64_t *bar;
+  uint64_t *bars;  // [MAX_TILES]: products of tile t done
   uint32_t tmem;
   uint32_t phase;
 
@@ -189,6 +192,13 @@ struct Cta {
   __device__ float *lpx() const { return reinterpret_cast<float *>(base + L.chain) + 3 * gm.G; }
   __device__ uint4 *pw() const {
     return reinterpret_cast<uint4 *>(base + L.chain + ((16u * gm.G + 15u) & ~15u));
+  }
+  // TMEM addresses of this warp's lane quarter: accumulator and residual stream of tile t
+  __device__ uint32_t acc_addr(int t) const {
+    return tc::tmem_lane_addr(tmem, 32u * ((threadIdx.x >> 5) & 3u), 16u * (uint32_t)t);
+  }
+  __device__ uint32_t h_addr(int t) const {
+    return tc::tmem_lane_addr(tmem, 32u * ((threadIdx.x >> 5) & 3u), H_COL + 16u * (uint32_t)t);
   }
 
   // 16-bit activations of one padded row (plane row GR + R)
@@ -208,9 +218,10 @@ struct Cta {
   }
 
   // halo rows <- their periodic images (every configuration of the CTA), then make the planes
-  // visible to the tensor core
-  __device__ void fill_halo() const {
-    __syncthreads();
+  // visible to the tensor core.  Returns false if any thread saw a timed-out wait (`bad`).
+  __device__ bool fill_halo(bool bad) const {
+    tc::fence_before_sync();
+    if (__syncthreads_or(bad)) return false;
     uint4 *p = reinterpret_cast<uint4 *>(planes() + (size_t)gm.GR * 16u);
     const int Lxp = gm.Lxp;
     for (int e = threadIdx.x; e < gm.G * gm.Rp; e += blockDim.x) {
@@ -223,134 +234,172 @@ struct Cta {
       p[e + gm.plane_rows] = p[src + gm.plane_rows];
     }
     tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
+    __syncthreads();
+    return true;
+  }
+
+  // Issues one convolution (block l, w = 0 for K1, 1 for K2), tile by tile, each tile committed
+  // to bars[t].  Called by thread 0 after the CTA barrier of fill_halo.  A descriptor's address
+  // field counts 16-byte units, so a row offset r is added to it as the integer r.
+  __device__ void issue_conv(int l, int w) const {
+    tc::fence_after_sync();
+    const uint64_t a0 = tc::desc_noswz(smem_addr(planes()), (uint32_t)gm.plane_rows * 16u, 128u);
+    const uint64_t b0 = tc::desc_noswz(smem_addr(base + L.tiles) + (uint32_t)((l * 2 + w) * 9) * TILE_BYTES, 256u, 128u);
+    const int o0 = gm.GR - gm.Lxp - 1;  // row offset of tap (0, 0) from the tile start
+    for (int t = 0; t < gm.T; ++t) {
+      const uint32_t d = tmem + 16u * t;
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const uint64_t ad = a0 + (uint64_t)(o0 + 128 * t + (tap / 3) * gm.Lxp + tap % 3);
+        tc::mma_bf16(d, ad, b0 + (uint64_t)(tap * (TILE_BYTES / 16)), Cvt<TT>::idesc(), tap > 0 ? 1u : 0u);
+      }
+      tc::mma_commit(&bars[t]);
+    }
+  }
+
+  // Waits for the products of tile t (this warp's epilogue); false after the poll limit.
+  // The result is the same on every lane (the TMEM loads that follow are warp-collective).
+  __device__ bool wait_tile(int t, int *status) const {
+    const bool ok = __all_sync(FULL_MASK, mbar_wait_bounded(&bars[t], phase, TC_WAIT_POLLS));
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr(status, STATUS_TIMEOUT);
+    tc::fence_after_sync();
+    return ok;
+  }
+
+  // After a timed-out wait: give every product in flight the poll limit again before TMEM is freed.
+  __device__ void drain() const {
+    if (threadIdx.x == 0)
+      for (int t = 0; t < gm.T; ++t) mbar_wait_bounded(&bars[t], phase, TC_WAIT_POLLS);
     __syncthreads();
   }
-
-  // One convolution (block l, w = 0 for K1, 1 for K2) over every tile; returns false if the
-  // accumulators never arrived (STATUS_TIMEOUT recorded).
-  __device__ bool conv(int l, int w, int *status) {
-    if (threadIdx.x == 0) {
-      tc::fence_after_sync();
-      const uint32_t pa = smem_addr(planes());
-      const uint32_t tb = smem_addr(base + L.tiles) + (uint32_t)((l * 2 + w) * 9) * TILE_BYTES;
-      const uint32_t lbo = (uint32_t)gm.plane_rows * 16u;
-      for (int t = 0; t < gm.T; ++t)
-        for (int tap = 0; tap < 9; ++tap) {
-          const int off = (tap / 3 - 1) * gm.Lxp + (tap % 3 - 1);
-          const uint64_t ad = tc::desc_noswz(pa + (uint32_t)(gm.GR + 128 * t + off) * 16u, lbo, 128u);
-          const uint64_t bd = tc::desc_noswz(tb + (uint32_t)tap * TILE_BYTES, 256u, 128u);
-          tc::mma_bf16(tmem + 16u * t, ad, bd, Cvt<TT>::idesc(), tap > 0 ? 1u : 0u);
-        }
-      tc::mma_commit(bar);
-    }
-    bool ok = mbar_wait_bounded(bar, phase, TC_WAIT_POLLS);
-    if (!ok) {
-      if (threadIdx.x == 0) atomicOr(status, STATUS_TIMEOUT);
-      mbar_wait_bounded(bar, phase, TC_WAIT_POLLS);  // let products in flight finish before TMEM is freed
-    }
-    phase ^= 1u;
-    tc::fence_after_sync();
-    return !__syncthreads_or(!ok);
-  }
 };
 
-// Row bookkeeping of one thread: rows R_k = 128 t_k + 32 (warp % 4) + lane, t_k = warp / 4 + 4 k.
+// Row bookkeeping of one thread: rows R_k = 128 t_k + 32 (warp % 4) + lane, t_k = warp / 4 + 4 k;
+// per row one word: configuration << 16 | site for an interior row, NONE otherwise.
 struct OwnRows {
-  int R[ROWS_PT], site[ROWS_PT], g[ROWS_PT];  // site < 0: not an interior row
-  int tile[ROWS_PT];
+  static constexpr uint32_t NONE = 0xFFFFFFFFu;
+  uint32_t info[ROWS_PT];
+  __device__ static int tile(int k) { return (int)(threadIdx.x >> 7) + TC_GROUPS * k; }
+  __device__ static int row(int k) { return 128 * tile(k) + (int)(threadIdx.x & 127u); }
+  __device__ bool interior(int k) const { return info[k] != NONE; }
+  __device__ int site(int k) const { return (int)(info[k] & 0xFFFFu); }
+  __device__ int cfg(int k) const { return (int)(info[k] >> 16); }
   __device__ void init(const TcGeom &gm) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < ROWS_PT; ++k) {
-      tile[k] = warp / 4 + TC_GROUPS * k;
-      R[k] = 128 * tile[k] + 32 * (warp % 4) + lane;
-      const int g0 = R[k] / gm.Rp, pos = R[k] - g0 * gm.Rp;
+      const int R = row(k);
+      const int g0 = R / gm.Rp, pos = R - g0 * gm.Rp;
       const int py = pos / gm.Lxp, px = pos - py * gm.Lxp;
-      const bool in = tile[k] < gm.T && g0 < gm.G && px >= 1 && px <= gm.Lx && py >= 1 && py <= gm.Ly;
-      site[k] = in ? (px - 1) + gm.Lx * (py - 1) : -1;
-      g[k] = in ? g0 : 0;
+      const bool in = tile(k) < gm.T && g0 < gm.G && px >= 1 && px <= gm.Lx && py >= 1 && py <= gm.Ly;
+      info[k] = in ? ((uint32_t)g0 << 16) | (uint32_t)((px - 1) + gm.Lx * (py - 1)) : NONE;
     }
   }
 };
 
-// log psi of the CTA's G configurations (spins with flips) into lp(); false on a timed-out wait.
+// phi(LN(h)) of one row with the LN parameters at bp (gamma, beta), as 16-bit activations
 template <typename TT>
-__device__ bool forward_tc(Cta<TT> &cta, const OwnRows &own, int *status) {
+__device__ __forceinline__ void ln_gelu_store(const Cta<TT> &cta, int R, const float (&h)[CF], const float *bp) {
+  float y[CF];
+  ln16(h, bp, bp + CF, y);
+#pragma unroll
+  for (int c = 0; c < CF; ++c) y[c] = gelu_lp(y[c]);
+  cta.store_act(R, y);
+}
+
+// log psi of the CTA's G configurations (spins with flips) into lp(); false on a timed-out
+// wait (STATUS_TIMEOUT recorded, products drained).
+template <typename TT>
+__device__ __forceinline__ bool forward_tc(Cta<TT> &cta, const OwnRows &own, int *status) {
   const TcGeom &gm = cta.gm;
   const float *sp = cta.small();
-  float h[ROWS_PT][CF];
-  float v[CF], y[CF];
-  // embedding h = b0 + sum_tap k0[tap] s(neighbour), then phi(LN(h)) of block 0
+  // embedding h = b0 + sum_tap k0[tap] s(neighbour) into TMEM, then phi(LN(h)) of block 0
 #pragma unroll
   for (int k = 0; k < ROWS_PT; ++k) {
+    if (OwnRows::tile(k) >= gm.T) continue;  // uniform per warp
+    float h[CF];
 #pragma unroll
-    for (int c = 0; c < CF; ++c) h[k][c] = sp[9 * CF + c];
-    if (own.site[k] < 0) continue;
-    const int g = own.g[k], x = own.site[k] % gm.Lx, yy = own.site[k] / gm.Lx;
-    const int fl = cta.flip()[g];
-    const float *s = cta.spin() + g * gm.N;
+    for (int c = 0; c < CF; ++c) h[c] = sp[9 * CF + c];
+    if (own.interior(k)) {
+      const int g = own.cfg(k), x = own.site(k) % gm.Lx, yy = own.site(k) / gm.Lx;
+      const int fl = cta.flip()[g];
+      const float *s = cta.spin() + g * gm.N;
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      int xx = x + tap % 3 - 1, y2 = yy + tap / 3 - 1;
-      xx += xx < 0 ? gm.Lx : (xx >= gm.Lx ? -gm.Lx : 0);
-      y2 += y2 < 0 ? gm.Ly : (y2 >= gm.Ly ? -gm.Ly : 0);
-      const int j = xx + gm.Lx * y2;
-      const float sv = j == fl ? -s[j] : s[j];
+      for (int tap = 0; tap < 9; ++tap) {
+        int xx = x + tap % 3 - 1, y2 = yy + tap / 3 - 1;
+        xx += xx < 0 ? gm.Lx : (xx >= gm.Lx ? -gm.Lx : 0);
+        y2 += y2 < 0 ? gm.Ly : (y2 >= gm.Ly ? -gm.Ly : 0);
+        const int j = xx + gm.Lx * y2;
+        const float sv = j == fl ? -s[j] : s[j];
 #pragma unroll
-      for (int c = 0; c < CF; ++c) h[k][c] = fmaf(sp[tap * CF + c], sv, h[k][c]);
+        for (int c = 0; c < CF; ++c) h[c] = fmaf(sp[tap * CF + c], sv, h[c]);
+      }
+      if (gm.n_blocks > 0) ln_gelu_store(cta, OwnRows::row(k), h, cta.blockp(0));
     }
-    if (gm.n_blocks > 0) {
-      const float *bp = cta.blockp(0);
-      ln16(h[k], bp, bp + CF, y);
-#pragma unroll
-      for (int c = 0; c < CF; ++c) y[c] = gelu_lp(y[c]);
-      cta.store_act(own.R[k], y);
-    }
+    tc::tmem_st16(cta.h_addr(OwnRows::tile(k)), h);
   }
+  tc::tmem_wait_st();
+  bool bad = false;
   for (int l = 0; l < gm.n_blocks; ++l) {
     const float *bp = cta.blockp(l);
-    cta.fill_halo();
-    if (!cta.conv(l, 0, status)) return false;
-#pragma unroll
-    for (int k = 0; k < ROWS_PT; ++k) {
-      if (own.tile[k] >= gm.T) continue;  // uniform per warp
-      float acc[CF];
-      tc::tmem_ld16(tc::tmem_lane_addr(cta.tmem, 32 * ((threadIdx.x >> 5) % 4), 16 * own.tile[k]), acc);
-      if (own.site[k] < 0) continue;
-#pragma unroll
-      for (int c = 0; c < CF; ++c) v[c] = gelu_lp(acc[c] + bp[2 * CF + c]);
-      cta.store_act(own.R[k], v);
-    }
-    cta.fill_halo();
-    if (!cta.conv(l, 1, status)) return false;
-#pragma unroll
-    for (int k = 0; k < ROWS_PT; ++k) {
-      if (own.tile[k] >= gm.T) continue;
-      float acc[CF];
-      tc::tmem_ld16(tc::tmem_lane_addr(cta.tmem, 32 * ((threadIdx.x >> 5) % 4), 16 * own.tile[k]), acc);
-      if (own.site[k] < 0) continue;
-#pragma unroll
-      for (int c = 0; c < CF; ++c) h[k][c] += acc[c] + bp[3 * CF + c];
-      if (l + 1 < gm.n_blocks) {
-        const float *bn = cta.blockp(l + 1);
-        ln16(h[k], bn, bn + CF, y);
-#pragma unroll
-        for (int c = 0; c < CF; ++c) y[c] = gelu_lp(y[c]);
-        cta.store_act(own.R[k], y);
+    for (int w = 0; w < 2; ++w) {
+      if (!cta.fill_halo(bad)) {
+        cta.drain();
+        return false;
       }
+      if (threadIdx.x == 0) cta.issue_conv(l, w);
+#pragma unroll
+      for (int k = 0; k < ROWS_PT; ++k) {
+        const int t = OwnRows::tile(k);
+        if (t >= gm.T) continue;
+        if (!cta.wait_tile(t, status)) {
+          bad = true;
+          continue;
+        }
+        uint32_t ra[CF], rh[CF];
+        tc::tmem_ld16_async(cta.acc_addr(t), ra);
+        if (w == 1) tc::tmem_ld16_async(cta.h_addr(t), rh);
+        tc::tmem_wait_ld();
+        float v[CF];
+        if (w == 0) {  // c = phi(K1 * a + b1)
+          if (!own.interior(k)) continue;
+#pragma unroll
+          for (int c = 0; c < CF; ++c) v[c] = gelu_lp(__uint_as_float(ra[c]) + bp[2 * CF + c]);
+          cta.store_act(OwnRows::row(k), v);
+        } else {  // h += K2 * c + b2, then phi(LN(h)) of the next block
+#pragma unroll
+          for (int c = 0; c < CF; ++c) v[c] = __uint_as_float(rh[c]) + (__uint_as_float(ra[c]) + bp[3 * CF + c]);
+          tc::tmem_st16(cta.h_addr(t), v);  // warp-collective: every lane, halo rows included
+          if (own.interior(k) && l + 1 < gm.n_blocks) ln_gelu_store(cta, OwnRows::row(k), v, cta.blockp(l + 1));
+        }
+      }
+      if (w == 1) tc::tmem_wait_st();
+      cta.phase ^= 1u;
     }
   }
-  // final LN and the per-row sums
+  tc::fence_before_sync();
+  if (__syncthreads_or(bad)) {
+    cta.drain();
+    return false;
+  }
+  tc::fence_after_sync();
+  // final LN of the residual streams and the per-row sums
   const float *fp = cta.blockp(gm.n_blocks);
 #pragma unroll
   for (int k = 0; k < ROWS_PT; ++k) {
-    if (own.site[k] < 0) continue;
-    ln16(h[k], fp, fp + CF, y);
+    const int t = OwnRows::tile(k);
+    if (t >= gm.T) continue;
+    uint32_t rh[CF];
+    tc::tmem_ld16_async(cta.h_addr(t), rh);
+    tc::tmem_wait_ld();
+    if (!own.interior(k)) continue;
+    float h[CF], y[CF];
+#pragma unroll
+    for (int c = 0; c < CF; ++c) h[c] = __uint_as_float(rh[c]);
+    ln16(h, fp, fp + CF, y);
     float rs = 0.f;
 #pragma unroll
     for (int c = 0; c < CF; ++c) rs += y[c];
-    cta.rowsum()[own.R[k]] = rs;
+    cta.rowsum()[OwnRows::row(k)] = rs;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -390,7 +439,7 @@ __device__ void setup_cta(Cta<TT> &cta, const TcArgs &a, uint32_t *tmem_slot) {
     bp[i] = v;
   }
   if (threadIdx.x == 0) {
-    mbar_init(cta.bar, 1);
+    for (int t = 0; t < MAX_TILES; ++t) mbar_init(&cta.bars[t], 1);
     fence_mbar_init();
   }
   if (threadIdx.x < 32) {
@@ -425,12 +474,12 @@ __device__ __forceinline__ unsigned char *aligned_base(unsigned char *raw) {
 
 // MODE 0: log psi of cfg[q]; MODE 1: the N + 1 local-energy configurations of each sample.
 template <typename TT, int MODE>
-__global__ void __launch_bounds__(TC_THREADS, 1) rescnn_tc_eval_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 2) rescnn_tc_eval_kernel(const TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bars[MAX_TILES];
   __shared__ uint32_t tmem_slot;
   const TcGeom &gm = a.gm;
-  Cta<TT> cta{gm, aligned_base(smem_raw), TcLayout::make(gm), &bar, 0u, 0u};
+  Cta<TT> cta{gm, aligned_base(smem_raw), TcLayout::make(gm), bars, 0u, 0u};
   setup_cta(cta, a, &tmem_slot);
   OwnRows own;
   own.init(gm);
@@ -457,12 +506,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) rescnn_tc_eval_kernel(const TcA
 
 // Metropolis sweeps with the Philox layout, decision rule and traces of the FP32 path.
 template <typename TT>
-__global__ void __launch_bounds__(TC_THREADS, 1) rescnn_tc_sweep_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 2) rescnn_tc_sweep_kernel(const TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bars[MAX_TILES];
   __shared__ uint32_t tmem_slot;
   const TcGeom &gm = a.gm;
-  Cta<TT> cta{gm, aligned_base(smem_raw), TcLayout::make(gm), &bar, 0u, 0u};
+  Cta<TT> cta{gm, aligned_base(smem_raw), TcLayout::make(gm), bars, 0u, 0u};
   setup_cta(cta, a, &tmem_slot);
   OwnRows own;
   own.init(gm);
@@ -557,7 +606,7 @@ TcGeom geometry(const nqs_ctx *c) {
   g.Lxp = c->Lx + 2;
   g.Rp = (c->Lx + 2) * (c->Ly + 2);
   g.N = c->N;
-  g.G = std::max(1, (9 * 128) / g.Rp);
+  g.G = std::max(1, (MAX_TILES * 128) / g.Rp);
   while (g.G > 1 && (g.G * g.Rp + 127) / 128 > MAX_TILES) --g.G;
   g.T = (g.G * g.Rp + 127) / 128;
   g.GR = ((g.Lxp + 1 + 7) / 8) * 8;
@@ -582,7 +631,7 @@ cudaError_t launch_tc(const nqs_ctx *c, K kern, const TcArgs &a, int64_t groups,
   const size_t shm = TcLayout::make(a.gm).total + 128;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e != cudaSuccess) return e;
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(groups, c->num_sms));
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(groups, 2 * (int64_t)c->num_sms));  // two CTAs per SM
   kern<<<(unsigned)grid, TC_THREADS, shm, s>>>(a);
   return cudaGetLastError();
 }
