@@ -113,6 +113,37 @@ def measure_alu_peaks(nqs, torch, dev, target_ms=25.0):
     return out
 
 
+def enumerate_bias_4x4(nqs, torch, dev, dtype):
+    """The workload's 4 x 4 case (alpha = 4, the same weight distribution) by full enumeration:
+    delta(x) = 2 (log psi_copy(x) - log psi_FP32(x)) over all 2^16 configurations through
+    nqs_logpsi of the 16-bit and FP32 contexts, its standard deviation (Sec. 4.2, Fig. 2), the
+    exact TV(pi, pi~) and KL, and min(Pinsker, Thm 3) from the single-flip increments of delta."""
+    lat = WL.extra["small_case"]
+    N, M = lat.n_sites, 4 * lat.n_sites
+    params = torch.from_numpy(workloads.rbm_params(N, M, WL.weight_sigma, WL.seed)).to(dev)
+    x = np.arange(2 ** N, dtype=np.int64)
+    cfg = torch.from_numpy(x.astype(np.int32)).view(-1, 1).to(dev)
+    lps = {}
+    for d in (dtype, "f32"):
+        ctx = nqs.Context("tfim", lat.Lx, lat.Ly, J1=WL.ham.J1, h=WL.ham.h, model="rbm", n_hidden=M, dtype=d)
+        ctx.set_params(params)
+        out = torch.empty(x.size, dtype=torch.float32, device=dev)
+        ctx.logpsi(cfg, out)
+        lps[d] = out.double().cpu().numpy()
+    delta = 2.0 * (lps[dtype] - lps["f32"])
+    logp = 2.0 * lps["f32"]
+    pi = np.exp(logp - logp.max())
+    pi /= pi.sum()
+    pt = pi * np.exp(delta - delta.max())
+    pt /= pt.sum()
+    eps = np.concatenate([delta[x ^ (1 << i)] - delta for i in range(N)])
+    s = float(eps.std() / math.sqrt(2.0))
+    return {"sigma_delta": float(delta.std()), "tv_exact": float(0.5 * np.abs(pi - pt).sum()),
+            "kl_exact": float(np.sum(pi * np.log(pi / pt))),
+            "tv_bound": min(s / 2, thm3_bound(float(eps.mean()), s)),
+            "note": "16-bit copy against the FP32 copy, all 65536 configurations, log psi from scratch"}
+
+
 def thm3_bound(mu, sigma):
     """Theorem 3 (Eq. avg_bound) at r = 0 for log-density increments eps ~ N(mu, 2 sigma^2)."""
     if sigma <= 0:
@@ -271,6 +302,9 @@ def run_ours(args, rank, world, dist):
             bias[d] = {"eps_mean": mu, "eps_std": float(eps.std()), "sigma_delta": sig,
                        "pinsker_tv_bound": sig / 2, "thm3_tv_bound_r0": thm3_bound(mu, sig),
                        "tv_bound": min(sig / 2, thm3_bound(mu, sig)),
+                       # Theorem 2 on the same proposals (x from the copy's own chains, y a flip)
+                       "thm2_one_step_bound": float(1.0 - np.mean(np.exp(-np.abs(eps)))),
+                       "enumeration_4x4": enumerate_bias_4x4(nqs, torch, dev, d),
                        "energy_vs_f32": dE, "energy_err": math.hypot(results[d]["E_err"], results["f32"]["E_err"]),
                        "sweep_speed_vs_f32": (results["f32"]["phase"][1] / results[d]["phase"][1])}
 
