@@ -123,8 +123,13 @@ int32_t nqs_n_bonds(const nqs_ctx *ctx);           /* bonds of the Hamiltonian *
  * 0 = chosen by the built-in rule).
  * NQS_OPT_MAX_ROWS: dense contexts only -- rows of one forward pass held in the
  * context's workspace (default 262144); bounds the chains of nqs_sweep and sets the
- * chunk of nqs_logpsi / nqs_local_energy.  Reallocates (synchronous). */
-enum { NQS_OPT_REFRESH = 0, NQS_OPT_CHAINS_PER_WARP = 1, NQS_OPT_MAX_ROWS = 2 };
+ * chunk of nqs_logpsi / nqs_local_energy.  Reallocates (synchronous).
+ * NQS_OPT_DENSE_FUSED: dense contexts -- 1 (default): nqs_sweep of a BF16 copy with two
+ * hidden layers no wider than 448 runs the persistent fused sampler (a CTA owns a tile of
+ * chains for all sweeps; proposal rows, the layer product on the tensor cores, log psi and
+ * the decision in one kernel); 0: the multi-launch sampler (a producer kernel and the layer
+ * GEMM per Metropolis step).  Same draws and decision rule; log psi sums in another order. */
+enum { NQS_OPT_REFRESH = 0, NQS_OPT_CHAINS_PER_WARP = 1, NQS_OPT_MAX_ROWS = 2, NQS_OPT_DENSE_FUSED = 3 };
 nqs_status nqs_set_option(nqs_ctx *ctx, int32_t option, int64_t value);
 
 /* Sec. 4.2 (two-copy scheme): the FP64 master parameters (device, P doubles) are

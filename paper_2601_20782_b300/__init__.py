@@ -26,7 +26,7 @@ NQS_OK, NQS_EINVAL, NQS_ECUDA, NQS_ENOMEM, NQS_ETIMEOUT, NQS_EUNSUPPORTED = rang
 DTYPES = {"f32": 0, "bf16": 1, "f16": 2, "fp8": 3}
 MODELS = {"rbm": 0, "dense": 1, "rescnn": 2}
 HAMS = {"tfim": 0, "heisenberg": 1}
-OPT_REFRESH, OPT_CHAINS_PER_WARP, OPT_MAX_ROWS = 0, 1, 2
+OPT_REFRESH, OPT_CHAINS_PER_WARP, OPT_MAX_ROWS, OPT_DENSE_FUSED = 0, 1, 2, 3
 
 
 class NQSError(RuntimeError):

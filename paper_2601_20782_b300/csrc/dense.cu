@@ -725,7 +725,7 @@ bool dense_setup(nqs_ctx *c, const nqs_model_desc *m, std::string *why) {
 void dense_free(nqs_ctx *c) {
   void *ptrs[] = {c->d_W1t, c->d_b1,   c->d_wout, c->d_master,     c->d_act[0],     c->d_act[1], c->d_part,
                   c->d_out, c->d_z1,   c->d_lp,   c->d_prop,       c->d_thr,        c->d_grad_scratch,
-                  c->d_force_part};
+                  c->d_force_part, c->d_z1b};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto p : c->d_Wl)
@@ -741,10 +741,11 @@ void dense_free(nqs_ctx *c) {
 
 cudaError_t dense_alloc_rows(nqs_ctx *c, int64_t rows) {
   void *old[] = {c->d_act[0], c->d_act[1], c->d_part, c->d_out, c->d_z1, c->d_lp, c->d_prop, c->d_thr,
-                 c->d_act8[0], c->d_act8[1]};
+                 c->d_act8[0], c->d_act8[1], c->d_z1b};
   for (void *p : old)
     if (p) cudaFree(p);
   c->d_act8[0] = c->d_act8[1] = nullptr;
+  c->d_z1b = nullptr;
   int maxKp = 64, max_ranges = 1;
   for (int l = 1; l < c->L; ++l) {
     maxKp = std::max(maxKp, c->Kp[l]);
@@ -759,6 +760,7 @@ cudaError_t dense_alloc_rows(nqs_ctx *c, int64_t rows) {
       (e = cudaMalloc(&c->d_prop, (size_t)rows * 4)) || (e = cudaMalloc(&c->d_thr, (size_t)rows * 4)))
     return e;
   if ((e = cudaMemset(c->d_act[0], 0, act)) || (e = cudaMemset(c->d_act[1], 0, act))) return e;
+  if (dense_fused_supported(c) && (e = cudaMalloc(&c->d_z1b, (size_t)rows * c->H[0] * 4)) != cudaSuccess) return e;
   if (c->dtype == NQS_FP8E4M3) {  // E4M3 rows; the padding columns stay zero
     int maxKp8 = 128;
     for (int l = 1; l < c->L; ++l) maxKp8 = std::max(maxKp8, c->Kp8[l]);
@@ -921,6 +923,20 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swee
   const bool f8 = c->dtype == NQS_FP8E4M3;  // the sampler runs on the FP8 copy
   auto refresh = [&]() -> cudaError_t { return logpsi_rows(c, state, C, c->d_lp, s); };  // z0, log psi from scratch
   if ((e = refresh()) != cudaSuccess) return e;
+  if (!f8 && c->dense_fused && c->d_z1b && dense_fused_supported(c)) {
+    // persistent fused sampler, one launch per stretch of sweeps between two refreshes (the
+    // refresh points of the multi-launch path below: after sweep t when (t + 1) % refresh == 0)
+    for (int t = 0; t < n_sweeps;) {
+      const int next = (t / c->refresh + 1) * c->refresh;
+      const int t1 = next < n_sweeps ? next : n_sweeps;
+      if ((e = dense_fused_sweeps(c, state, C, n_sweeps, t, t1, burn_in, seed, sweep_offset, samples, logpsi, n_acc,
+                                  acc_bits, delta, t > 0, s)) != cudaSuccess)
+        return e;
+      if (t1 < n_sweeps && (e = refresh()) != cudaSuccess) return e;
+      t = t1;
+    }
+    return cudaSuccess;
+  }
   ProposeArgs a;
   a.state = state;
   a.z0 = c->d_z1;

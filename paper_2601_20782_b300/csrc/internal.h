@@ -23,6 +23,7 @@ struct nqs_ctx {
   int64_t P = 0;  // parameters
   int refresh = 20;
   int chains_per_warp = 0;  // 0: tuner
+  int dense_fused = 1;       // dense sampler: the persistent fused kernel where it applies (NQS_OPT_DENSE_FUSED)
   double noise_sigma = 0.0;  // noisy RBM (nqs_set_noise): 0 = off
   int renorm = 1;            // RBM sweep: accepted flips between cache normalisations (set_params)
   float *d_bounds = nullptr; // RBM: [max |W|, max_j (sum_i |W_ji| + |b_j|)] of the sampling copy
@@ -74,6 +75,7 @@ struct nqs_ctx {
   float *d_part = nullptr;         // [max_rows][max ranges] DOT partials
   float *d_out = nullptr;          // [max_rows] log psi of the rows
   float *d_z1 = nullptr;           // [max_rows][H0] FP32 layer-1 pre-activations (per sample / chain)
+  float *d_z1b = nullptr;          // [max_rows][H0] second buffer of the fused sampler (dense_fused.cu)
   float *d_lp = nullptr;           // [max_rows] log psi per sample / chain
   int32_t *d_prop = nullptr;       // [max_rows] proposed bond (or -1) per chain
   float *d_thr = nullptr;          // [max_rows] log u per chain
@@ -159,6 +161,11 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t n_chains, int
                         float *delta, cudaStream_t s);
 cudaError_t dense_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
                               const double *stats, double *force, cudaStream_t s, bool share = false);
+// dense_fused.cu
+bool dense_fused_supported(const nqs_ctx *c);
+cudaError_t dense_fused_sweeps(const nqs_ctx *c, uint32_t *state, int64_t C, int n_sweeps, int t0, int t1,
+                               int burn_in, uint64_t seed, uint32_t sweep_offset, uint32_t *samples, float *logpsi,
+                               int64_t *n_acc, uint32_t *acc_bits, float *delta, bool add_acc, cudaStream_t s);
 // rescnn.cu
 bool rescnn_setup(nqs_ctx *c, const nqs_model_desc *m, std::string *why);
 cudaError_t rescnn_alloc(nqs_ctx *c);

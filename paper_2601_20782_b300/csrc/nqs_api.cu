@@ -230,6 +230,11 @@ nqs_status nqs_set_option(nqs_ctx *c, int32_t option, int64_t value) {
     cudaError_t e = nqs::dense_alloc_rows(c, value);
     return e == cudaSuccess ? NQS_OK : fail(c, NQS_ENOMEM, "dense workspace allocation failed");
   }
+  if (option == NQS_OPT_DENSE_FUSED) {
+    if (value != 0 && value != 1) return fail(c, NQS_EINVAL, "dense fused sampler: 0 or 1");
+    c->dense_fused = (int)value;
+    return NQS_OK;
+  }
   if (option == NQS_OPT_CHAINS_PER_WARP) {
     if (value != 0 && value != 1 && value != 2 && value != 4) return fail(c, NQS_EINVAL, "chains per warp: 0, 1, 2 or 4");
     c->chains_per_warp = (int)value;

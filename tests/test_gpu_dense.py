@@ -168,10 +168,13 @@ def test_dense_sampler_replays_at_workload_shapes(Lx, Ly, widths, J2, dtype, T):
     assert np.all(final.sum(axis=1) == 0)
 
 
-def test_dense_exchange_sampler_replays_in_oracle():
+@pytest.mark.parametrize("fused", [1, 0])
+def test_dense_exchange_sampler_replays_in_oracle(fused):
     """4 x 4 Heisenberg: every decision of the BF16 sampler agrees with the FP64 rule outside
-    a band of 10 sigma of its increment error; magnetisation stays zero."""
+    a band of 10 sigma of its increment error; magnetisation stays zero.  fused = 1: the
+    persistent fused sampler (the default for two hidden layers); 0: the multi-launch one."""
     ctx, _, m_r, _ = make(4, 4, (64, 48), 7, bias=0.2)
+    ctx.set_option(nqs().OPT_DENSE_FUSED, fused)
     C, T = 256, 3
     state = torch.zeros((C, 1), dtype=torch.int32, device="cuda")
     ctx.init_chains(state, 11)
