@@ -34,6 +34,13 @@ METRIC = "MH proposals/sec and local-energy samples/sec on 1 B300, mixed vs FP32
 # (16384 chains x 500 sweeps of this workload), per sampling copy, for the kernel as built;
 # a copy without an entry reports None.
 SWEEP_TRAFFIC_BYTES = {"f16": 77.5e6}   # 2.38 MB read + 75.11 MB written
+# Warp instructions per proposal of the sweep kernel by pipe, from the ncu capture summarised in
+# profiles/rbm_sweep_pipe_mix.md (10-sweep launch of 4144 chains on this workload, kernel as profiled).
+SWEEP_PIPE_MIX = {
+    "f32": {"total": 88.7, "fma": 31.7, "fma_fp16": 1.2, "alu": 24.8, "lsu": 9.4, "cbu": 2.8, "xu": 2.7, "adu": 2.1},
+    "f16": {"total": 128.9, "fma": 55.3, "fma_fp16": 26.7, "alu": 30.3, "lsu": 13.4, "cbu": 5.6, "xu": 3.3, "adu": 3.4},
+    "bf16": {"total": 138.7, "fma": 36.8, "fma_fp16": 8.1, "alu": 58.0, "lsu": 14.5, "cbu": 5.6, "xu": 3.3, "adu": 2.9},
+}
 WL = workloads.TFIM_2D_10x10
 
 
@@ -358,6 +365,9 @@ def run_ours(args, rank, world, dist):
                      "note": "method arithmetic per proposal (2M + 3M per accept) vs the measured paired-FP32 "
                              "issue rate"},
         "alu_peaks": alu,
+        "sweep_instructions_per_proposal": {"source": "from profile (ncu per-pipe counts, profiles/rbm_sweep_pipe_mix.md)",
+                                            "method_arithmetic": 12.5, **{d: SWEEP_PIPE_MIX[d] for d in dtypes
+                                                                        if d in SWEEP_PIPE_MIX}},
         "e2e": {"value": world * proposals_step * args.steps / t_e2e, "unit": "proposals/s",
                 "h2d_bytes_per_step": steps[args.dtype].ctx.P * 8, "d2h_bytes_per_step": (5 + steps[args.dtype].ctx.P) * 8},
         "gpu_launches": steps[args.dtype].launches * args.steps,
