@@ -37,10 +37,10 @@ SWEEP_TRAFFIC_BYTES = {"f16": 77.5e6}   # 2.38 MB read + 75.11 MB written
 # Warp instructions per proposal of the sweep kernel by pipe, from the ncu capture summarised in
 # profiles/rbm_sweep_pipe_mix.md (10-sweep launch of 4144 chains on this workload, kernel as profiled).
 SWEEP_PIPE_MIX = {
-    "f32": {"total": 88.7, "fma": 31.7, "fma_fp16": 1.2, "alu": 24.8, "lsu": 9.4, "cbu": 2.8, "xu": 2.7, "adu": 2.1},
-    "f16": {"total": 128.9, "fma": 55.3, "fma_fp16": 26.7, "alu": 30.3, "lsu": 13.4, "cbu": 5.6, "xu": 3.3, "adu": 3.4},
-    "bf16": {"total": 138.7, "fma": 36.8, "fma_fp16": 8.1, "alu": 58.0, "lsu": 14.5, "cbu": 5.6, "xu": 3.3, "adu": 2.9},
-}
+    "f32": {"total": 90.2, "fma": 32.2, "fma_fp16": 1.3, "alu": 25.3, "lsu": 9.4, "cbu": 2.9, "xu": 2.7, "adu": 2.1},
+    "f16": {"total": 132.6, "fma": 57.0, "fma_fp16": 27.2, "alu": 31.3, "lsu": 13.6, "cbu": 5.8, "xu": 3.4, "adu": 3.4},
+    "bf16": {"total": 142.8, "fma": 38.0, "fma_fp16": 8.1, "alu": 59.9, "lsu": 14.7, "cbu": 5.8, "xu": 3.4, "adu": 2.9},
+}}
 WL = workloads.TFIM_2D_10x10
 
 
@@ -233,6 +233,8 @@ def run_ours(args, rank, world, dist):
     params_h = torch.from_numpy(workloads.rbm_params(N, M, WL.weight_sigma, WL.seed)).pin_memory()
     dtypes = [args.dtype] + ([d for d in ("f32", "bf16", "f16") if d != args.dtype] if args.compare else [])
     steps = {d: Step(nqs, torch, dev, d, C, T, B, params_h, dist) for d in dtypes}
+    if args.chains_per_warp and "f32" in steps:
+        steps["f32"].ctx.set_option(nqs.OPT_CHAINS_PER_WARP, args.chains_per_warp)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
     base_seed = WL.seed * 1000 + rank * 7919
     proposals_step = C * T * N
@@ -1065,6 +1067,8 @@ def main():
     ap.add_argument("--sweeps", type=int, default=0, help="profiling only: override the sweep count")
     ap.add_argument("--burn-in", type=int, default=None, help="profiling only: override the burn-in")
     ap.add_argument("--grad-rows", type=int, default=0, help="profiling only (j1j2-dense): O rows / minSR samples")
+    ap.add_argument("--chains-per-warp", type=int, default=0, choices=[0, 1, 2],
+                    help="profiling only (tfim2d): RBM sweep chains per warp of the FP32 copy (0: built-in rule)")
     ap.add_argument("--workload", default="tfim2d", choices=["tfim2d", "tfim1d", "heis2d-dense", "batched",
                                                              "j1j2-dense", "noisy-rbm", "crbm-tfim2d", "rescnn-tfim2d"],
                     help="tfim2d: the 10x10 alpha=4 RBM workload (default); the others measure the other "
