@@ -40,7 +40,7 @@ SWEEP_PIPE_MIX = {
     "f32": {"total": 90.2, "fma": 32.2, "fma_fp16": 1.3, "alu": 25.3, "lsu": 9.4, "cbu": 2.9, "xu": 2.7, "adu": 2.1},
     "f16": {"total": 132.6, "fma": 57.0, "fma_fp16": 27.2, "alu": 31.3, "lsu": 13.6, "cbu": 5.8, "xu": 3.4, "adu": 3.4},
     "bf16": {"total": 142.8, "fma": 38.0, "fma_fp16": 8.1, "alu": 59.9, "lsu": 14.7, "cbu": 5.8, "xu": 3.4, "adu": 2.9},
-}}
+}
 WL = workloads.TFIM_2D_10x10
 
 
