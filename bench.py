@@ -714,7 +714,9 @@ class DenseStep:
                           / (ms["minsr"] / 1e3) / 1e12,
                           "note": "whole solve (means, split, Gram, Cholesky, solves, dtheta); Gram FLOP counted "
                                   "as 6 BF16 products over the upper triangle"}} if self.lam else {}),
-            "roofline": {"bound": "tensor", "kernel": "dense_gemm_kernel (sampler steps)", "achieved": ach,
+            "roofline": {"bound": "tensor",
+                         "kernel": ("dense_gemm_kernel (sampler steps)" if f8 or len(w) != 2 or max(w) > 448
+                                    else "dense_fused_sweep_kernel"), "achieved": ach,
                          "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                          "note": ("FP8 (E4M3) GEMM FLOP of layers >= 2 over all proposals / sweep time, vs 2 x the "
                                   "measured sustained cuBLAS BF16" if f8 else

@@ -83,7 +83,12 @@ __device__ __forceinline__ bool worker_sync_or(bool v) {
   return r != 0;
 }
 
+// Tile row of chain r: chains go round the four TMEM lane quarters (row 32 (r % 4) + r / 4), so
+// that every epilogue warp has rows even when a tile holds fewer than 128 chains.
+__device__ __forceinline__ uint32_t tile_row(int r) { return 32u * (uint32_t)(r & 3) + (uint32_t)(r >> 2); }
+
 struct FusedSmem {
+  float b2[FU_MAX_K], wout[FU_MAX_K];  // layer-1 bias and w_out, staged once
   float part[128][2];
   float thr[128], lpx[128], gsign[128];
   int2 mv[128];    // move (i, j) (j = -1 for a flip); i = -1: the identity
@@ -128,6 +133,10 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
   }
   // the A tile starts (and its unused rows stay) zero
   for (int i = tid; i < kb_n * 16384 / 16; i += FU_THREADS) reinterpret_cast<uint4 *>(atile)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < FU_MAX_K; i += FU_THREADS) {
+    sm.b2[i] = i < a.H1 ? a.b2[i] : 0.f;
+    sm.wout[i] = i < a.H1 ? a.w_out[i] : 0.f;
+  }
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
               }
               const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
               *reinterpret_cast<__nv_bfloat162 *>(atile + kb * 16384 +
-                                                  tc::sw128_offset((uint32_t)r, (uint32_t)(2 * lane))) = h2;
+                                                  tc::sw128_offset(tile_row(r), (uint32_t)(2 * lane))) = h2;
             }
           }
         }
@@ -287,16 +296,17 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         // 3-4. the products, then the epilogue: rows of this warp's lane quarter, its column half
         const bool ok = __all_sync(FULL_MASK, wait(&acc_full, step_g & 1u));  // the TMEM loads are warp-collective
         tc::fence_after_sync();
-        if (ok && 32 * q < Rv) {
+        const int rq = 4 * lane + q;  // chain of this thread's TMEM row 32 q + lane
+        if (ok && q < Rv) {
           float dot = 0.f;
           for (int cb = 32 * half; cb < a.H1; cb += 64) {
             float v[32];
             tc::tmem_ld32(tc::tmem_lane_addr(tmem, 32 * q, cb), v);
 #pragma unroll
             for (int e = 0; e < 32; ++e)
-              if (cb + e < a.H1) dot = fmaf(tanh_approx(v[e] + a.b2[cb + e]), a.w_out[cb + e], dot);
+              if (cb + e < a.H1) dot = fmaf(tanh_approx(v[e] + sm.b2[cb + e]), sm.wout[cb + e], dot);
           }
-          sm.part[32 * q + lane][half] = dot;
+          if (rq < Rv) sm.part[rq][half] = dot;
         }
         tc::fence_before_sync();
         stop = worker_sync_or(!ok || abort_flag);
