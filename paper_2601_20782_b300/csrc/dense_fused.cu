@@ -13,7 +13,8 @@
 //      switches the chain's current buffer.  All loads of a row are issued before its
 //      arithmetic, two rows at a time;
 //   3. products: one thread issues tcgen05.mma kind::f16 over the A tile and W2 K-blocks that
-//      a TMA thread streams through a two-stage ring (W2 does not fit shared memory);
+//      a TMA thread streams through a two-stage ring (W2 does not fit shared memory); meanwhile
+//      a thread per chain draws the next step's move and log u;
 //   4. epilogue: the accumulator rows (TMEM) give log psi(y) = b_out + w_out . tanh(z2 + b2);
 //   5. decision: accept iff 2 (log psi(y) - log psi(x)) > log u (an exchange of equal spins is
 //      the identity, accepted without evaluation); an accepted move updates the spins and
@@ -37,6 +38,7 @@ constexpr int FU_THREADS = 320;  // warp 0: TMA, warp 1: MMA issuer + TMEM, warp
 constexpr int FU_WORKERS = 256;
 constexpr int FU_STAGES = 2;
 constexpr int FU_MAX_K = 448;   // layer-0 width (padded) and layer-1 width limits
+constexpr int FU_ROWS = 2;      // proposal rows a warp loads at once
 constexpr uint32_t FU_POLLS = 1u << 24;
 
 struct FusedArgs {
@@ -90,8 +92,8 @@ __device__ __forceinline__ uint32_t tile_row(int r) { return 32u * (uint32_t)(r 
 struct FusedSmem {
   float b2[FU_MAX_K], wout[FU_MAX_K];  // layer-1 bias and w_out, staged once
   float part[128][2];
-  float thr[128], lpx[128], gsign[128];
-  int2 mv[128];    // move (i, j) (j = -1 for a flip); i = -1: the identity
+  float lpx[128], gsign[128];
+  int2 mv[128];    // move (i, j) of this step (j = -1 for a flip); i = -1: the identity
   int cur[128];    // buffer holding the chain's z0 (0: z0, 1: z0b)
   int nacc[128];
   uint32_t abits[128];
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
   const int kb_n = a.Kp1 / 64;
   unsigned char *atile = base;                                   // kb_n x 16 KB
   unsigned char *ring = base + kb_n * 16384;                     // FU_STAGES x H1 x 128 B
-  uint32_t *spins = reinterpret_cast<uint32_t *>(ring + FU_STAGES * a.H1 * 128);  // [128][W]
+  uint32_t *spins = reinterpret_cast<uint32_t *>(ring + FU_STAGES * a.H1 * 128);  // [128][8]
   const uint32_t stage_bytes = (uint32_t)a.H1 * 128u;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -151,6 +153,19 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
     abort_flag = 1;
     atomicOr(a.status, STATUS_TIMEOUT);
     return false;
+  };
+
+  // draw of step st of tile chain r: the move (i, j) (j = -1 for a flip) and log u; the
+  // thread of chain r draws and decides, so both stay in its registers
+  auto draw = [&](int st, int64_t c0, int r, float &thr, int2 &nb) {
+    const int t = a.t0 + st / a.N, p = st % a.N;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)(p / 2), a.sweep_offset + (uint32_t)t, (uint32_t)(c0 + r), TAG_SWEEP),
+                                  a.k0, a.k1);
+    const uint32_t wm = (p & 1) ? w.z : w.x, wu = (p & 1) ? w.w : w.y;
+    const int m = (int)index_from_word(wm, (uint32_t)a.n_moves);
+    const uint32_t k = wu >> 8;
+    thr = k == 0u ? -INFINITY : logf((float)k * 5.9604644775390625e-8f);
+    nb = a.exchange ? a.bonds[m] : make_int2(m, -1);
   };
 
   const int64_t n_tiles = (a.C + a.R - 1) / a.R;
@@ -206,6 +221,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
     const int wt = tid - 64, wk = wt >> 5;  // worker thread 0..255, worker warp 0..7
     const int q = warp & 3, half = wk >> 2;  // TMEM lane quarter (warp w reads lanes 32 (w % 4) ..), column half
     bool stop = false;
+    float thr = 0.f, thr_next = 0.f;  // log u of this step and of the next (thread of chain wt)
+    int2 nb_next = make_int2(0, -1);   // the next step's drawn move
     for (int64_t tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
       const int64_t c0 = tile * a.R;
       const int Rv = (int)std::min<int64_t>(a.R, a.C - c0);
@@ -223,36 +240,31 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
       // steps 0 .. steps_per_tile - 1 are the proposals
       for (int st = -1; st < steps_per_tile; ++st, ++step_g) {
         const int t = a.t0 + (st < 0 ? 0 : st / a.N), p = st < 0 ? 0 : st % a.N;
-        // 1. draws (thread per chain)
+        // 1. moves (thread per chain): the move drawn during the previous step's products; the
+        //    chain's spins decide whether an exchange moves anything and the sign of the change
         if (st >= 0 && wt < Rv) {
           const int r = wt;
-          const uint4 w = philox4x32_10(make_uint4((uint32_t)(p / 2), a.sweep_offset + (uint32_t)t,
-                                                   (uint32_t)(c0 + r), TAG_SWEEP), a.k0, a.k1);
-          const uint32_t wm = (p & 1) ? w.z : w.x, wu = (p & 1) ? w.w : w.y;
-          const int m = (int)index_from_word(wm, (uint32_t)a.n_moves);
-          const uint32_t k = wu >> 8;
-          sm.thr[r] = k == 0u ? -INFINITY : logf((float)k * 5.9604644775390625e-8f);
-          const int2 nb = a.exchange ? a.bonds[m] : make_int2(m, -1);
+          const int2 nb = nb_next;
+          thr = thr_next;
           const uint32_t *sw = spins + r * 8;
           const int si = (sw[nb.x >> 5] >> (nb.x & 31)) & 1u;
-          bool moved = true;
-          if (nb.y >= 0) moved = si != (int)((sw[nb.y >> 5] >> (nb.y & 31)) & 1u);
+          const bool moved = nb.y < 0 || si != (int)((sw[nb.y >> 5] >> (nb.y & 31)) & 1u);
           sm.mv[r] = moved ? nb : make_int2(-1, -1);
           sm.gsign[r] = si ? -2.f : 2.f;
         }
         worker_sync();
-        // 2. proposal rows into the A tile (warp per chain, two rows at a time, every load of
-        //    both rows issued before their arithmetic); step -1 writes the unmoved rows
-        for (int r0 = wk; r0 < Rv; r0 += 16) {
-          float2 z[2][7], di[2][7], dj[2][7];
-          int rr[2];
-          bool live[2];
+        // 2. proposal rows into the A tile (warp per chain, FU_ROWS rows at a time, every load of
+        //    those rows issued before their arithmetic); step -1 writes the unmoved rows
+        for (int r0 = wk; r0 < Rv; r0 += 8 * FU_ROWS) {
+          float2 z[FU_ROWS][7], di[FU_ROWS][7], dj[FU_ROWS][7];
+          float g[FU_ROWS];
+          bool live[FU_ROWS];
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
+          for (int u = 0; u < FU_ROWS; ++u) {
             const int r = r0 + 8 * u;
-            rr[u] = r;
             live[u] = r < Rv && !(st >= 0 && sm.mv[r].x < 0);  // the identity is not evaluated
-            const int2 mv = live[u] ? sm.mv[r] : make_int2(-1, -1);
+            const int2 mv = live[u] && st >= 0 ? sm.mv[r] : make_int2(-1, -1);
+            g[u] = live[u] ? sm.gsign[r] : 0.f;
             const float *zr = (sm.cur[live[u] ? r : r0] ? a.z0b : a.z0) + (c0 + (live[u] ? r : r0)) * a.H0;
             const float *wi = a.W1t + (int64_t)(mv.x < 0 ? 0 : mv.x) * a.H0;
             const float *wj = a.W1t + (int64_t)(mv.y < 0 ? 0 : mv.y) * a.H0;
@@ -266,10 +278,9 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
             }
           }
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
+          for (int u = 0; u < FU_ROWS; ++u) {
             if (!live[u]) continue;
-            const int r = rr[u];
-            const float g = sm.gsign[r];
+            const int r = r0 + 8 * u;
             const bool moved = st >= 0;
             float *zn = (sm.cur[r] ? a.z0 : a.z0b) + (c0 + r) * a.H0;  // the other buffer
 #pragma unroll
@@ -278,8 +289,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
               const int k = kb * 64 + 2 * lane;
               float v0 = 0.f, v1 = 0.f;
               if (k < a.H0) {
-                const float2 zz = make_float2(fmaf(g, di[u][kb].x - dj[u][kb].x, z[u][kb].x),
-                                              fmaf(g, di[u][kb].y - dj[u][kb].y, z[u][kb].y));
+                const float2 zz = make_float2(fmaf(g[u], di[u][kb].x - dj[u][kb].x, z[u][kb].x),
+                                              fmaf(g[u], di[u][kb].y - dj[u][kb].y, z[u][kb].y));
                 if (moved) *reinterpret_cast<float2 *>(zn + k) = zz;
                 v0 = log_cosh_f(zz.x);
                 v1 = log_cosh_f(zz.y);
@@ -293,6 +304,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         tc::fence_proxy_async_smem();
         worker_sync();
         if (wt == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&a_full)) : "memory");
+        // 2. while the products run: the next step's draws (thread per chain)
+        if (st + 1 < steps_per_tile && wt < Rv) draw(st + 1, c0, wt, thr_next, nb_next);
         // 3-4. the products, then the epilogue: rows of this warp's lane quarter, its column half
         const bool ok = __all_sync(FULL_MASK, wait(&acc_full, step_g & 1u));  // the TMEM loads are warp-collective
         tc::fence_after_sync();
@@ -324,7 +337,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
             float dlt = 0.f;
             if (mv.x >= 0) {
               dlt = lpy - sm.lpx[r];
-              acc = 2.f * dlt > sm.thr[r];
+              acc = 2.f * dlt > thr;
             }
             if (acc) {
               sm.nacc[r] += 1;
@@ -411,7 +424,6 @@ cudaError_t dense_fused_sweeps(const nqs_ctx *c, uint32_t *state, int64_t C, int
   a.logpsi = logpsi;
   a.status = c->d_status;
   a.C = C;
-  a.R = (int)std::min<int64_t>(128, (C + c->num_sms - 1) / c->num_sms);
   a.N = c->N;
   a.W = c->W;
   a.H0 = c->H[0];
@@ -429,6 +441,7 @@ cudaError_t dense_fused_sweeps(const nqs_ctx *c, uint32_t *state, int64_t C, int
   a.sweep_offset = sweep_offset;
   a.k0 = (uint32_t)seed;
   a.k1 = (uint32_t)(seed >> 32);
+  a.R = (int)std::min<int64_t>(128, (C + c->num_sms - 1) / c->num_sms);
   CUtensorMap mB0, mB1;
   if (!make_tmap_bf16_2d(&mB0, c->d_Wl[1], (uint64_t)a.H1, (uint64_t)a.Kp1, (uint32_t)a.p0)) return cudaErrorInvalidValue;
   if (a.p1 && !make_tmap_bf16_2d(&mB1, c->d_Wl[1], (uint64_t)a.H1, (uint64_t)a.Kp1, (uint32_t)a.p1))

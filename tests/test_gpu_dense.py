@@ -203,6 +203,36 @@ def test_dense_exchange_sampler_replays_in_oracle(fused):
     np.testing.assert_array_equal(unpack_np(words_from_tensor(samples), 16), ref["samples"])
 
 
+def test_dense_fused_sampler_independent_of_tiling():
+    """The fused sampler at the 10 x 10, 400 x 400 shape: a chain's draws, products and sums do
+    not depend on how many chains share its CTA or on its row in the tile, so 20000 chains
+    (tiles of 128, more than one tile per CTA), 8192 (tiles of 56) and 1000 (tiles of 7) give
+    bit-identical samples, log psi, acceptance counts and increments for the chains they
+    share."""
+    ctx, params, _, _ = make(10, 10, (400, 400), 23)
+    W, N, T, B = ctx.W, 100, 3, 1
+    out = {}
+    for C in (20000, 8192, 1000):
+        state = torch.zeros((C, W), dtype=torch.int32, device="cuda")
+        ctx.init_chains(state, 41)
+        samples = torch.zeros(((T - B) * C, W), dtype=torch.int32, device="cuda")
+        logpsi = torch.zeros((T - B) * C, dtype=torch.float32, device="cuda")
+        nacc = torch.zeros(C, dtype=torch.int64, device="cuda")
+        delta = torch.zeros((C, T, N), dtype=torch.float32, device="cuda")
+        ctx.sweep(state, T, B, 42, 0, samples, logpsi, nacc, delta=delta)
+        torch.cuda.synchronize()
+        out[C] = (state.cpu(), samples.cpu().view(T - B, C, W), logpsi.cpu().view(T - B, C), nacc.cpu(), delta.cpu())
+    ref = out[20000]
+    for C in (8192, 1000):
+        got = out[C]
+        assert torch.equal(got[0], ref[0][:C])
+        assert torch.equal(got[1], ref[1][:, :C])
+        assert torch.equal(got[2], ref[2][:, :C])
+        assert torch.equal(got[3], ref[3][:C])
+        assert torch.equal(got[4], ref[4][:C])
+    assert ref[3].sum().item() > 0
+
+
 @pytest.mark.parametrize("Lx,Ly,widths", [(4, 4, (64, 48)), (10, 10, (400, 400))])
 def test_dense_grad_and_force_match_oracle(Lx, Ly, widths):
     ctx, params, _, m = make(Lx, Ly, widths, 13)
