@@ -459,8 +459,10 @@ nqs_status nqs_crbm_stats(nqs_crbm *c, const float *eloc_re, const float *eloc_i
  * O [n x P] complex FP32 interleaved, or NULL: O_a = s, O_b = tanh theta, O_W[j][i] = tanh(theta_j) s_i.
  * force [P] complex FP64 interleaved, or NULL: F_k = (1/n) sum_x conj(O_k(x)) (eps(x) - E) with
  * E = stats[0] + i stats[5] (nqs_crbm_stats); dE/dRe theta_k = 2 Re F_k, dE/dIm theta_k = 2 Im F_k.
- * The force adds FP64 partials with atomics (the last bits depend on their order); n = 0
- * sets it to zero. */
+ * With N <= 127 the force runs on the tensor cores (theta and the contraction as products of
+ * three-term BF16 splits, FP32 accumulation in TMEM, FP64 across row tiles), else on the CUDA
+ * cores; either way the partial forces of the row chunks are added in a fixed order, so the
+ * result does not depend on timing.  n = 0 sets it to zero. */
 nqs_status nqs_crbm_logpsi_grad(nqs_crbm *c, const uint32_t *configs, int64_t n, float *O, const float *eloc_re,
                                 const float *eloc_im, const double *stats, double *force, nqs_stream stream);
 

@@ -712,7 +712,8 @@ nqs_status nqs_crbm_create(nqs_crbm **out, const nqs_ham_desc *ham, int32_t n_hi
       nb[x + c->Lx * y] = make_int2((x + 1) % c->Lx + c->Lx * y, c->Ly > 1 ? x + c->Lx * ((y + 1) % c->Ly) : -1);
   const size_t NM = (size_t)c->N * c->M_pad;
   const int tiles = (c->M + 1 + CR_FU - 1) / CR_FU;
-  c->force_chunks = std::max(1, (b.num_sms * 4 + tiles - 1) / tiles);
+  // row chunks of the SIMT force, and of the tensor-core force (at most one per SM and unit tile)
+  c->force_chunks = std::max(std::max(1, (b.num_sms * 4 + tiles - 1) / tiles), b.num_sms);
   if ((e = cudaMalloc(&c->d_fpart, (size_t)c->force_chunks * c->P * sizeof(double2))) ||
       (e = cudaMalloc(&c->d_a, c->N * sizeof(float2))) || (e = cudaMalloc(&c->d_b, c->M_pad * sizeof(float2))) ||
       (e = cudaMalloc(&c->d_Wt, NM * sizeof(float2))) || (e = cudaMalloc(&c->d_st, NM * sizeof(float4))) ||
@@ -876,7 +877,12 @@ nqs_status nqs_crbm_logpsi_grad(nqs_crbm *c, const uint32_t *cfg, int64_t n, flo
         r, c->P, reinterpret_cast<float2 *>(O));
     if ((e = cudaGetLastError()) != cudaSuccess) return ccuda(c, e, "nqs_crbm_logpsi_grad");
   }
-  if (force) {
+  if (force && c->N <= 127) {  // tensor-core path: spins, the constant site and the weights in K = 128
+    const int chunks = std::min(c->force_chunks, crbm_force_tc_chunks(c->M, c->base.num_sms, n));
+    e = crbm_force_tc(cfg, n, c->N, c->W, c->M, c->M_pad, c->P, c->d_Wt, c->d_b, eloc_re, eloc_im, stats, c->d_fpart,
+                      chunks, reinterpret_cast<double2 *>(force), c->base.d_status, s);
+    if (e != cudaSuccess) return ccuda(c, e, "nqs_crbm_logpsi_grad");
+  } else if (force) {
     CForceArgs a;
     a.r = r;
     a.eloc_re = eloc_re;

@@ -29,6 +29,13 @@
 // pairs (one drained while the other accumulates) in TMEM; mbarriers hand each buffer between the
 // roles.  Every wait is bounded: a wait that gives up records STATUS_TIMEOUT and every role
 // leaves its loop.
+//
+// The complex-parameter RBM (CPLX) runs the same products with 32 complex hidden units per
+// block: the 64 columns of a term are Re of units j0 .. j0 + 31, then Im of the same units, so
+// GEMM1 gives Re theta and Im theta (spins are real), and the a-terms hold
+//     a = conj(tanh theta) (eloc - E)    (Re in columns 0-31, Im in 32-63; eloc and E complex),
+// so GEMM2 gives the real and imaginary parts of sum_x s_i conj(O_k) (eloc - E) (App. I, Eq.
+// forces with complex O_k); the partial forces go to a [chunks][P] array of complex entries.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -59,13 +66,16 @@ constexpr uint32_t TM_G = 256;
 struct ForceTcParams {
   const uint32_t *cfg;
   const float *eloc;
+  const float *eloc_im;  // CPLX: Im eloc (E = stats[0] + i stats[5])
   const double *stats;
   const float *Wm;  // [N][M] FP32 master, site-major
   const float *bm;  // [M]
-  double *ws;       // [chunks][P]
+  const float2 *Wc; // CPLX: [N][M_pad] complex weights, site-major
+  const float2 *bc; // CPLX: [M_pad] complex hidden bias
+  double *ws;       // [chunks][P] (CPLX: complex entries, Re then Im)
   int *status;
   int64_t n, P;
-  int N, W, M, n_chunks;
+  int N, W, M, M_pad, n_chunks;
 };
 
 __device__ __forceinline__ void split3(float a, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
@@ -137,6 +147,27 @@ __device__ __forceinline__ float2 tanh_epi2(float2 y) {
   return make_float2(t.x < 0.55f ? poly.x : copysignf(q.x, y.x), t.y < 0.55f ? poly.y : copysignf(q.y, y.y));
 }
 
+// tanh(x + iy) = (sinh x cosh x + i sin y cos y) / (sinh^2 x + cos^2 y): the denominator is
+// |cosh(x + iy)|^2 as a sum of squares, so there is no cancellation near the zeros of cosh.
+__device__ __forceinline__ float2 tanh_cplx(float x, float y) {
+  float sy, cy;
+  sincosf(y, &sy, &cy);
+  const float shx = sinhf(x), chx = coshf(x);
+  const float inv = 1.f / fmaf(shx, shx, cy * cy);
+  return make_float2(shx * chx * inv, sy * cy * inv);
+}
+
+// 8 consecutive FP32 columns of the warp's 32 TMEM lanes (lane rule of tc::tmem_ld32)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
@@ -146,7 +177,9 @@ __device__ __forceinline__ uint32_t sw_chunk(uint32_t r, uint32_t c) {
   return (r >> 3) * 1024u + (r & 7u) * 128u + (((c ^ r) & 7u) << 4);
 }
 
+template <bool CPLX>
 __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const ForceTcParams p) {
+  constexpr int UB = CPLX ? FTC_HT / 2 : FTC_HT;  // hidden units per block
   extern __shared__ unsigned char smem_dyn[];
   __shared__ uint64_t spin_full[FTC_NS], spin_free[FTC_NS], theta_full, theta_empty, a_full, a_free, g_full[2],
       g_empty[2], fin_bar;
@@ -160,7 +193,7 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
   uint4 *lut = reinterpret_cast<uint4 *>(sA + 3 * ATERM_BYTES);  // byte of 8 spins -> 8 BF16 (+-1)
 
   const int jt = blockIdx.x, chunk = blockIdx.y;
-  const int j0 = jt * FTC_HT;
+  const int j0 = jt * UB;
   const int N = p.N, M = p.M;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -168,7 +201,15 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
   for (int idx = tid; idx < FTC_HT * FTC_KP; idx += FTC_THREADS) {
     const int jj = idx % FTC_HT, i = idx / FTC_HT;
     // column N multiplies the constant +1 spin: the hidden bias enters theta through GEMM1
-    const float w = j0 + jj < M ? (i < N ? p.Wm[(int64_t)i * M + j0 + jj] : (i == N ? p.bm[j0 + jj] : 0.f)) : 0.f;
+    float w;
+    if (CPLX) {  // column jj: Re (jj < 32) or Im of unit j0 + jj % 32
+      const int j = j0 + jj % UB;
+      const float2 wc = j < M ? (i < N ? p.Wc[(int64_t)i * p.M_pad + j] : (i == N ? p.bc[j] : make_float2(0.f, 0.f)))
+                              : make_float2(0.f, 0.f);
+      w = jj < UB ? wc.x : wc.y;
+    } else {
+      w = j0 + jj < M ? (i < N ? p.Wm[(int64_t)i * M + j0 + jj] : (i == N ? p.bm[j0 + jj] : 0.f)) : 0.f;
+    }
     __nv_bfloat16 h, m, l;
     split3(w, h, m, l);
     unsigned char *kb = sW + (i / 64) * WKB_BYTES;
@@ -283,9 +324,9 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
     // a-terms of tile t.
     const int q = warp & 3, g = warp >> 2;
     const int x = 32 * q + lane;
-    const double E = p.stats[0];
-    const bool has_m = j0 <= M && M < j0 + FTC_HT;
-    double *out = p.ws + (int64_t)chunk * p.P;
+    const double E = p.stats[0], E_im = CPLX ? p.stats[5] : 0.0;
+    const bool has_m = j0 <= M && M < j0 + UB;
+    double *out = p.ws + (int64_t)chunk * p.P * (CPLX ? 2 : 1);
     int drains = 0;
     auto load_word = [&](int t) -> uint32_t {
       const int64_t r = r0 + (int64_t)t * 128 + x;
@@ -334,29 +375,83 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
       }
       const int i = x;  // TMEM lane = site
       for (int t = 0; t < 16; ++t) {
-        const int j = j0 + 16 * g + t;
+        // column 16 g + t: unit j0 + 16 g + t (CPLX: Re / Im part of unit j0 + (16 g + t) % 32)
+        const int j = CPLX ? j0 + (16 * g + t) % UB : j0 + 16 * g + t;
         int64_t k = -1;
         if (j < M && i < N) k = N + M + (int64_t)j * N + i;  // W entries
         else if (j < M && i == N) k = N + j;                  // b entries
         else if (j == M && i < N) k = i;                      // a entries
+        if (CPLX && k >= 0) k = 2 * k + (16 * g + t) / UB;
         if (k >= 0) out[k] = (drains ? out[k] : 0.0) + ((double)v[t] + (double)w[t]);
       }
       ++drains;
       return true;
     };
-    auto eval = [&](int t) -> float {
+    auto eval = [&](int t) -> float2 {
       const int64_t r = r0 + (int64_t)t * 128 + x;
-      return r < r1 ? (float)((double)p.eloc[r] - E) : 0.f;
+      if (r >= r1) return make_float2(0.f, 0.f);
+      return make_float2((float)((double)p.eloc[r] - E), CPLX ? (float)((double)p.eloc_im[r] - E_im) : 0.f);
     };
     for (int t0 = 0; t0 < 2 && t0 < T; ++t0) produce(t0, load_word(t0));
-    float e_next = T > 0 ? eval(0) : 0.f;
+    float2 e_next = T > 0 ? eval(0) : make_float2(0.f, 0.f);
     bool ok = true;
     for (int t = 0; t < T && ok; ++t) {
-      const float e = e_next;
+      const float2 ec = e_next;
+      const float e = ec.x;
       if (t + 1 < T) e_next = eval(t + 1);
       const uint32_t word2 = t + 2 < T ? load_word(t + 2) : 0u;  // used after this tile's epilogue
       if (!wait_warp(&theta_full, t & 1)) { ok = false; break; }
       tc::fence_after_sync();
+      if (CPLX) {
+        // units j0 + 8 g .. + 7: Re theta in columns 8 g .., Im theta in 32 + 8 g .. of each term
+        float re[8], im[8];
+        {
+          float h[8], m[8], l[8];
+          tmem_ld8(tc::tmem_lane_addr(tm, 32 * q, 8 * g), h);
+          tmem_ld8(tc::tmem_lane_addr(tm, 32 * q, FTC_HT + 8 * g), m);
+          tmem_ld8(tc::tmem_lane_addr(tm, 32 * q, 2 * FTC_HT + 8 * g), l);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) re[u] = (h[u] + m[u]) + l[u];
+          tmem_ld8(tc::tmem_lane_addr(tm, 32 * q, UB + 8 * g), h);
+          tmem_ld8(tc::tmem_lane_addr(tm, 32 * q, FTC_HT + UB + 8 * g), m);
+          tmem_ld8(tc::tmem_lane_addr(tm, 32 * q, 2 * FTC_HT + UB + 8 * g), l);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) im[u] = (h[u] + m[u]) + l[u];
+        }
+        tc::fence_before_sync();
+        mbar_arrive(&theta_empty);
+        uint32_t rh[4], rm[4], rl[4], ih[4], imd[4], il[4];
+#pragma unroll
+        for (int u2 = 0; u2 < 4; ++u2) {
+          float2 ar, ai;  // a of units 8 g + 2 u2, + 1: Re parts, Im parts
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            const int u = 2 * u2 + v;
+            const float2 th = tanh_cplx(re[u], im[u]);
+            // conj(t) e = (t.x e.x + t.y e.y) + i (t.x e.y - t.y e.x); the unit M carries e itself
+            float2 av = make_float2(fmaf(th.x, ec.x, th.y * ec.y), fmaf(th.x, ec.y, -th.y * ec.x));
+            if (has_m && j0 + 8 * g + u == M) av = ec;
+            if (v) {
+              ar.y = av.x;
+              ai.y = av.y;
+            } else {
+              ar.x = av.x;
+              ai.x = av.y;
+            }
+          }
+          split3_pair(ar, rh[u2], rm[u2], rl[u2]);
+          split3_pair(ai, ih[u2], imd[u2], il[u2]);
+        }
+        if (t >= 1 && !wait_warp(&a_free, (t - 1) & 1)) { ok = false; break; }
+        // 16-byte chunk g: Re of units 8 g .. 8 g + 7; chunk 4 + g: their Im
+        const uint32_t off_r = sw_chunk(x, g), off_i = sw_chunk(x, 4 + g);
+        *reinterpret_cast<uint4 *>(sA + off_r) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+        *reinterpret_cast<uint4 *>(sA + ATERM_BYTES + off_r) = make_uint4(rm[0], rm[1], rm[2], rm[3]);
+        *reinterpret_cast<uint4 *>(sA + 2 * ATERM_BYTES + off_r) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+        *reinterpret_cast<uint4 *>(sA + off_i) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+        *reinterpret_cast<uint4 *>(sA + ATERM_BYTES + off_i) = make_uint4(imd[0], imd[1], imd[2], imd[3]);
+        *reinterpret_cast<uint4 *>(sA + 2 * ATERM_BYTES + off_i) = make_uint4(il[0], il[1], il[2], il[3]);
+      } else {
       float2 th[8];  // theta of units 16 g + 2 u, + 1 (bias included through GEMM1)
       {
         float vh[16], vm[16], vl[16];
@@ -393,6 +488,7 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
         *reinterpret_cast<uint4 *>(sA + 2 * ATERM_BYTES + off) =
             make_uint4(pl[4 * cc], pl[4 * cc + 1], pl[4 * cc + 2], pl[4 * cc + 3]);
       }
+      }
       tc::fence_proxy_async_smem();
       mbar_arrive(&a_full);
       if (t + 2 < T) {  // spin buffer of tile t + 2, last read by GEMM2 of tile t - 1
@@ -410,6 +506,18 @@ __global__ void __launch_bounds__(FTC_THREADS, 1) rbm_force_tc_kernel(const Forc
   __syncthreads();
   tc::fence_after_sync();
   if (warp == FTC_WORKERS) tc::tmem_dealloc(tmem_base, 512);
+}
+
+__global__ void crbm_force_tc_reduce_kernel(const double2 *part, int chunks, int64_t P, double inv_n, double2 *force) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int q = 0; q < chunks; ++q) {  // fixed order: the result does not depend on timing
+      const double2 v = part[q * P + k];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    force[k] = make_double2(s.x * inv_n, s.y * inv_n);
+  }
 }
 
 }  // namespace
@@ -431,6 +539,9 @@ cudaError_t rbm_force_tc(const nqs_ctx *c, const uint32_t *cfg, int64_t n, const
   p.stats = stats;
   p.Wm = c->d_Wm;
   p.bm = c->d_bm;
+  p.eloc_im = nullptr;
+  p.Wc = nullptr;
+  p.bc = nullptr;
   p.ws = ws;
   p.status = c->d_status;
   p.n = n;
@@ -438,11 +549,52 @@ cudaError_t rbm_force_tc(const nqs_ctx *c, const uint32_t *cfg, int64_t n, const
   p.N = c->N;
   p.W = c->W;
   p.M = c->M;
+  p.M_pad = c->M;
   p.n_chunks = chunks;
   const int jt = (c->M + 1 + FTC_HT - 1) / FTC_HT;
-  cudaError_t e = cudaFuncSetAttribute(rbm_force_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FTC_SMEM);
+  cudaError_t e =
+      cudaFuncSetAttribute(rbm_force_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FTC_SMEM);
   if (e != cudaSuccess) return e;
-  rbm_force_tc_kernel<<<dim3(jt, chunks), FTC_THREADS, FTC_SMEM, s>>>(p);
+  rbm_force_tc_kernel<false><<<dim3(jt, chunks), FTC_THREADS, FTC_SMEM, s>>>(p);
+  return cudaGetLastError();
+}
+
+int crbm_force_tc_chunks(int M, int num_sms, int64_t n) {
+  const int jt = (M + 1 + FTC_HT / 2 - 1) / (FTC_HT / 2);
+  int64_t ch = std::max<int64_t>(1, num_sms / jt);
+  ch = std::min<int64_t>(ch, (n + 127) / 128);
+  return (int)std::max<int64_t>(1, ch);
+}
+
+cudaError_t crbm_force_tc(const uint32_t *cfg, int64_t n, int N, int W, int M, int M_pad, int64_t P, const float2 *Wt,
+                          const float2 *b, const float *eloc_re, const float *eloc_im, const double *stats,
+                          double2 *part, int chunks, double2 *force, int *status, cudaStream_t s) {
+  ForceTcParams p;
+  p.cfg = cfg;
+  p.eloc = eloc_re;
+  p.eloc_im = eloc_im;
+  p.stats = stats;
+  p.Wm = nullptr;
+  p.bm = nullptr;
+  p.Wc = Wt;
+  p.bc = b;
+  p.ws = reinterpret_cast<double *>(part);
+  p.status = status;
+  p.n = n;
+  p.P = P;
+  p.N = N;
+  p.W = W;
+  p.M = M;
+  p.M_pad = M_pad;
+  p.n_chunks = chunks;
+  const int jt = (M + 1 + FTC_HT / 2 - 1) / (FTC_HT / 2);
+  cudaError_t e =
+      cudaFuncSetAttribute(rbm_force_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FTC_SMEM);
+  if (e != cudaSuccess) return e;
+  rbm_force_tc_kernel<true><<<dim3(jt, chunks), FTC_THREADS, FTC_SMEM, s>>>(p);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  crbm_force_tc_reduce_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 1024)), 256, 0, s>>>(
+      part, chunks, P, 1.0 / (double)n, force);
   return cudaGetLastError();
 }
 

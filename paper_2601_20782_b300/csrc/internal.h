@@ -145,6 +145,12 @@ bool rbm_force_tc_supported(const nqs_ctx *c);
 int rbm_force_tc_chunks(const nqs_ctx *c, int64_t n);
 cudaError_t rbm_force_tc(const nqs_ctx *c, const uint32_t *cfg, int64_t n, const float *eloc, const double *stats,
                          double *ws, int chunks, cudaStream_t s);
+// the complex-parameter RBM's force on the same products (force_tc.cu): partial forces per row
+// chunk into part [chunks][P], then their fixed-order sum x 1/n into force [P]
+int crbm_force_tc_chunks(int M, int num_sms, int64_t n);
+cudaError_t crbm_force_tc(const uint32_t *cfg, int64_t n, int N, int W, int M, int M_pad, int64_t P, const float2 *Wt,
+                          const float2 *b, const float *eloc_re, const float *eloc_im, const double *stats,
+                          double2 *part, int chunks, double2 *force, int *status, cudaStream_t s);
 cudaError_t rbm_force_into(const nqs_ctx *c, const uint32_t *cfg, int64_t n, const float *eloc, const double *stats,
                            double *force, double *scratch, int chunks, cudaStream_t s);
 

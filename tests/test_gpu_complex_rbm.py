@@ -7,7 +7,9 @@ oracle ``oracle.complex_rbm``:
 * the |psi|^2 sampler replayed decision by decision in the oracle (decisions outside a
   10-sigma window of the FP32 increment agree with the FP64 rule, final chains and kept
   samples identical), traced equal to untraced, refresh every sweep equal in law;
-* O rows and the conjugate force (App. I, Eq. forces) over several unit tiles and row blocks;
+* O rows and the conjugate force (App. I, Eq. forces) over several unit tiles and row blocks,
+  at the workload's shape with a ragged row count, for one row, and beyond the tensor-core
+  path's site limit;
 * the FP64 statistics, including the mean of Im eps;
 * the sampled energy of a small chain against the exact Rayleigh quotient;
 * range checks and the empty cases.
@@ -180,6 +182,51 @@ def test_O_rows_and_force_match_oracle():
     torch.cuda.synchronize()
     # the row chunks' partials are added in a fixed order: the same inputs give the same bits
     assert torch.equal(F2, F)
+
+
+def _cforce_blocked(model, s, eps, block=20000):
+    """F = mean(conj(O) (eps - E)) over all rows, block by block: O_a = s, O_b = tanh theta,
+    O_W[j][i] = tanh(theta_j) s_i (the oracle's force without materialising the O rows)."""
+    e = eps - eps.mean()
+    Fa = np.zeros(model.N, complex); Fb = np.zeros(model.M, complex); FW = np.zeros((model.M, model.N), complex)
+    for b0 in range(0, len(eps), block):
+        sb = s[b0:b0 + block].astype(np.float64)
+        eb = e[b0:b0 + block]
+        ct = np.conj(np.tanh(model.theta(sb)))
+        Fa += sb.T @ eb
+        Fb += ct.T @ eb
+        FW += (ct * eb[:, None]).T @ sb
+    n = len(eps)
+    return np.concatenate([Fa / n, Fb / n, (FW / n).ravel()])
+
+
+@pytest.mark.parametrize("Lx,Ly,M,sigma,n", [(10, 10, 400, 0.04, 40077), (4, 4, 40, 0.2, 1), (16, 8, 32, 0.02, 3001)])
+def test_force_at_workload_shape_and_edges(Lx, Ly, M, sigma, n):
+    """The force over ragged row counts: the workload's 10 x 10, M = 400 shape (tensor-core
+    path: 13 unit tiles of 32, the last holding the a-entries; 313 full row tiles and a tail
+    of 13 rows), a single row, and N = 128 (beyond the tensor-core path's K, the CUDA-core path),
+    against the oracle's force accumulated block by block.  An FP32 rounding of theta reaches
+    tanh theta amplified by |1 - tanh^2 theta|, which is large near the poles at Im theta =
+    pi/2; the weights keep the std of Im theta at or below 0.4 so that few samples come near one
+    (at N = 128, std 0.05 put Im theta within reach of pi/2 and gave 1e-4 relative errors on
+    the CUDA-core path)."""
+    c, _, model, _ = make(Lx, Ly, M, sigma, 29)
+    N = Lx * Ly
+    s = rand_configs(n, N, 31)
+    cfg = to_words_tensor(pack_np(s))
+    re = torch.zeros(n, dtype=torch.float32, device="cuda")
+    im = torch.zeros_like(re)
+    c.local_energy(cfg, re, im)
+    stats = torch.zeros(6, dtype=torch.float64, device="cuda")
+    c.stats(re, im, 1, stats)
+    F = torch.zeros(c.P, dtype=torch.complex128, device="cuda")
+    c.logpsi_grad(cfg, None, re, im, stats, F)
+    torch.cuda.synchronize()
+    eps = re.cpu().numpy().astype(np.float64) + 1j * im.cpu().numpy().astype(np.float64)
+    Fref = _cforce_blocked(model, s, eps)
+    Fg = F.cpu().numpy()
+    scale = max(np.abs(Fref).max(), 1e-12 * np.abs(eps).max())
+    np.testing.assert_allclose(Fg, Fref, rtol=0, atol=2e-5 * scale)
 
 
 def test_stats_match_oracle_statistics():
