@@ -309,17 +309,53 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         // 3-4. the products, then the epilogue: rows of this warp's lane quarter, its column half
         const bool ok = __all_sync(FULL_MASK, wait(&acc_full, step_g & 1u));  // the TMEM loads are warp-collective
         tc::fence_after_sync();
-        const int rq = 4 * lane + q;  // chain of this thread's TMEM row 32 q + lane
+        // log psi(y) - b_out of chain r is part[r][0] + part[r][1]; the warp pair of lane quarter q
+        // takes the 64-column blocks 64 half + 128 j, and every chain's sum runs in one order
+        // whichever load serves it: per column residue j = c % 4, the columns in increasing order,
+        // then (S0 + S1) + (S2 + S3).  So results do not depend on the tiling.
         if (ok && q < Rv) {
-          float dot = 0.f;
-          for (int cb = 32 * half; cb < a.H1; cb += 64) {
-            float v[32];
-            tc::tmem_ld32(tc::tmem_lane_addr(tmem, 32 * q, cb), v);
+          if (a.R <= 64) {
+            // chains in lanes 32 q + i, i = r / 4 < 16: thread t holds the rows i = t / 4 and
+            // t / 4 + 8 at columns 4k + t % 4 (16-lane load), so no lane computes an empty row
+            const int ia = lane >> 2, cq = lane & 3;
+            float da = 0.f, db = 0.f;
+            for (int cb = 64 * half; cb < a.H1; cb += 128) {
+              float v[32];
+              tc::tmem_ld16x128b_x16(tc::tmem_lane_addr(tmem, 32 * q, cb), v);
 #pragma unroll
-            for (int e = 0; e < 32; ++e)
-              if (cb + e < a.H1) dot = fmaf(tanh_approx(v[e] + sm.b2[cb + e]), sm.wout[cb + e], dot);
+              for (int k = 0; k < 16; ++k) {
+                const int c = cb + 4 * k + cq;
+                if (c < a.H1) {
+                  const float bb = sm.b2[c], w = sm.wout[c];
+                  da = fmaf(tanh_approx(v[2 * k] + bb), w, da);
+                  db = fmaf(tanh_approx(v[2 * k + 1] + bb), w, db);
+                }
+              }
+            }
+            da += __shfl_xor_sync(FULL_MASK, da, 1);
+            db += __shfl_xor_sync(FULL_MASK, db, 1);
+            da += __shfl_xor_sync(FULL_MASK, da, 2);
+            db += __shfl_xor_sync(FULL_MASK, db, 2);
+            const int ra = 4 * ia + q, rb = 4 * (ia + 8) + q;
+            if (cq == 0 && ra < Rv) sm.part[ra][half] = da;
+            if (cq == 0 && rb < Rv) sm.part[rb][half] = db;
+          } else {
+            const int rq = 4 * lane + q;  // chain of this thread's TMEM row 32 q + lane
+            float s4[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int cb = 64 * half; cb < a.H1; cb += 128) {
+#pragma unroll
+              for (int sub = 0; sub < 2; ++sub) {
+                float v[32];
+                tc::tmem_ld32(tc::tmem_lane_addr(tmem, 32 * q, cb + 32 * sub), v);
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                  const int c = cb + 32 * sub + e;
+                  if (c < a.H1) s4[e & 3] = fmaf(tanh_approx(v[e] + sm.b2[c]), sm.wout[c], s4[e & 3]);
+                }
+              }
+            }
+            if (rq < Rv) sm.part[rq][half] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
           }
-          if (rq < Rv) sm.part[rq][half] = dot;
         }
         tc::fence_before_sync();
         stop = worker_sync_or(!ok || abort_flag);
