@@ -725,7 +725,7 @@ bool dense_setup(nqs_ctx *c, const nqs_model_desc *m, std::string *why) {
 void dense_free(nqs_ctx *c) {
   void *ptrs[] = {c->d_W1t, c->d_b1,   c->d_wout, c->d_master,     c->d_act[0],     c->d_act[1], c->d_part,
                   c->d_out, c->d_z1,   c->d_lp,   c->d_prop,       c->d_thr,        c->d_grad_scratch,
-                  c->d_force_part, c->d_z1b};
+                  c->d_force_part, c->d_z1b, c->d_W1d};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto p : c->d_Wl)
@@ -778,6 +778,9 @@ cudaError_t dense_alloc_params(nqs_ctx *c) {
   if ((e = cudaMalloc(&c->d_W1t, (size_t)c->N * c->H[0] * 4)) || (e = cudaMalloc(&c->d_b1, (size_t)c->H[0] * 4)) ||
       (e = cudaMalloc(&c->d_wout, (size_t)c->H[c->L - 1] * 4 + 16)) ||
       (e = cudaMalloc(&c->d_master, (size_t)c->P * 4)))
+    return e;
+  if (c->ham_kind == NQS_HEISENBERG && c->n_bonds > 0 && dense_fused_supported(c) &&
+      (e = cudaMalloc(&c->d_W1d, (size_t)c->n_bonds * c->H[0] * 4)))
     return e;
   c->d_Wl.assign(c->L, nullptr);
   c->d_bl.assign(c->L, nullptr);
@@ -861,6 +864,7 @@ cudaError_t dense_prepare(nqs_ctx *c, const double *params, cudaStream_t s) {
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  if (c->d_W1d && (e = dense_fused_prepare(c, s)) != cudaSuccess) return e;
   // b_out (= master[P - 1]) is kept on the device right after w_out
   return cudaMemcpyAsync(c->d_wout + c->H[c->L - 1], c->d_master + (c->P - 1), sizeof(float), cudaMemcpyDeviceToDevice,
                          s);

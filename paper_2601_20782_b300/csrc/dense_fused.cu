@@ -8,7 +8,9 @@
 //      (a bond for exchange moves, a site for flips) and log u;
 //   2. proposal rows: a warp per chain writes log cosh(z0 + move delta) (BF16) straight into
 //      the A tile in shared memory (128-byte swizzle, K-major), z0 being the chain's FP32
-//      layer-0 pre-activations.  z0 has two buffers per chain in global memory (read through
+//      layer-0 pre-activations and the delta +-2 times a row of W1t (a flip) or of the
+//      per-bond differences W1t[i] - W1t[j] (an exchange; the same FP32 difference the
+//      multi-launch sampler forms), so a proposal reads two rows, three chains at a time.  z0 has two buffers per chain in global memory (read through
 //      L2): the proposal's z0 + delta goes to the other one, and an accepted move only
 //      switches the chain's current buffer.  All loads of a row are issued before its
 //      arithmetic, two rows at a time;
@@ -38,7 +40,7 @@ constexpr int FU_THREADS = 320;  // warp 0: TMA, warp 1: MMA issuer + TMEM, warp
 constexpr int FU_WORKERS = 256;
 constexpr int FU_STAGES = 2;
 constexpr int FU_MAX_K = 448;   // layer-0 width (padded) and layer-1 width limits
-constexpr int FU_ROWS = 2;      // proposal rows a warp loads at once
+constexpr int FU_ROWS = 3;      // proposal rows a warp loads at once
 constexpr uint32_t FU_POLLS = 1u << 24;
 
 struct FusedArgs {
@@ -46,7 +48,7 @@ struct FusedArgs {
   float *z0;          // [C][H0]: the chains' z0 at launch
   float *z0b;         // [C][H0]: the second buffer
   float *lp;          // [C]
-  const float *W1t;   // [N][H0] site-major
+  const float *W1d;   // [n_moves][H0]: W1t rows (flips) or W1t[i_b] - W1t[j_b] (exchanges)
   const float *b2;    // [H1]
   const float *w_out; // [H1]
   float b_out;
@@ -94,6 +96,7 @@ struct FusedSmem {
   float part[128][2];
   float lpx[128], gsign[128];
   int2 mv[128];    // move (i, j) of this step (j = -1 for a flip); i = -1: the identity
+  int mi[128];     // its index (site or bond), -1: the identity
   int cur[128];    // buffer holding the chain's z0 (0: z0, 1: z0b)
   int nacc[128];
   uint32_t abits[128];
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
 
   // draw of step st of tile chain r: the move (i, j) (j = -1 for a flip) and log u; the
   // thread of chain r draws and decides, so both stay in its registers
-  auto draw = [&](int st, int64_t c0, int r, float &thr, int2 &nb) {
+  auto draw = [&](int st, int64_t c0, int r, float &thr, int2 &nb, int &mi) {
     const int t = a.t0 + st / a.N, p = st % a.N;
     const uint4 w = philox4x32_10(make_uint4((uint32_t)(p / 2), a.sweep_offset + (uint32_t)t, (uint32_t)(c0 + r), TAG_SWEEP),
                                   a.k0, a.k1);
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
     const uint32_t k = wu >> 8;
     thr = k == 0u ? -INFINITY : logf((float)k * 5.9604644775390625e-8f);
     nb = a.exchange ? a.bonds[m] : make_int2(m, -1);
+    mi = m;
   };
 
   const int64_t n_tiles = (a.C + a.R - 1) / a.R;
@@ -223,6 +227,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
     bool stop = false;
     float thr = 0.f, thr_next = 0.f;  // log u of this step and of the next (thread of chain wt)
     int2 nb_next = make_int2(0, -1);   // the next step's drawn move
+    int mi_next = 0;                   // and its index
     for (int64_t tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
       const int64_t c0 = tile * a.R;
       const int Rv = (int)std::min<int64_t>(a.R, a.C - c0);
@@ -250,31 +255,30 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
           const int si = (sw[nb.x >> 5] >> (nb.x & 31)) & 1u;
           const bool moved = nb.y < 0 || si != (int)((sw[nb.y >> 5] >> (nb.y & 31)) & 1u);
           sm.mv[r] = moved ? nb : make_int2(-1, -1);
+          sm.mi[r] = moved ? mi_next : -1;
           sm.gsign[r] = si ? -2.f : 2.f;
         }
         worker_sync();
         // 2. proposal rows into the A tile (warp per chain, FU_ROWS rows at a time, every load of
         //    those rows issued before their arithmetic); step -1 writes the unmoved rows
         for (int r0 = wk; r0 < Rv; r0 += 8 * FU_ROWS) {
-          float2 z[FU_ROWS][7], di[FU_ROWS][7], dj[FU_ROWS][7];
+          float2 z[FU_ROWS][7], d[FU_ROWS][7];
           float g[FU_ROWS];
           bool live[FU_ROWS];
 #pragma unroll
           for (int u = 0; u < FU_ROWS; ++u) {
             const int r = r0 + 8 * u;
             live[u] = r < Rv && !(st >= 0 && sm.mv[r].x < 0);  // the identity is not evaluated
-            const int2 mv = live[u] && st >= 0 ? sm.mv[r] : make_int2(-1, -1);
+            const int mi = live[u] && st >= 0 ? sm.mi[r] : -1;
             g[u] = live[u] ? sm.gsign[r] : 0.f;
             const float *zr = (sm.cur[live[u] ? r : r0] ? a.z0b : a.z0) + (c0 + (live[u] ? r : r0)) * a.H0;
-            const float *wi = a.W1t + (int64_t)(mv.x < 0 ? 0 : mv.x) * a.H0;
-            const float *wj = a.W1t + (int64_t)(mv.y < 0 ? 0 : mv.y) * a.H0;
+            const float *dr = a.W1d + (int64_t)(mi < 0 ? 0 : mi) * a.H0;
 #pragma unroll
             for (int kb = 0; kb < 7; ++kb) {
               const int k = kb * 64 + 2 * lane;
               const bool in = live[u] && kb < kb_n && k < a.H0;
               z[u][kb] = in ? *reinterpret_cast<const float2 *>(zr + k) : make_float2(0.f, 0.f);
-              di[u][kb] = in && mv.x >= 0 ? *reinterpret_cast<const float2 *>(wi + k) : make_float2(0.f, 0.f);
-              dj[u][kb] = in && mv.y >= 0 ? *reinterpret_cast<const float2 *>(wj + k) : make_float2(0.f, 0.f);
+              d[u][kb] = in && mi >= 0 ? *reinterpret_cast<const float2 *>(dr + k) : make_float2(0.f, 0.f);
             }
           }
 #pragma unroll
@@ -289,8 +293,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
               const int k = kb * 64 + 2 * lane;
               float v0 = 0.f, v1 = 0.f;
               if (k < a.H0) {
-                const float2 zz = make_float2(fmaf(g[u], di[u][kb].x - dj[u][kb].x, z[u][kb].x),
-                                              fmaf(g[u], di[u][kb].y - dj[u][kb].y, z[u][kb].y));
+                const float2 zz = make_float2(fmaf(g[u], d[u][kb].x, z[u][kb].x), fmaf(g[u], d[u][kb].y, z[u][kb].y));
                 if (moved) *reinterpret_cast<float2 *>(zn + k) = zz;
                 v0 = log_cosh_f(zz.x);
                 v1 = log_cosh_f(zz.y);
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         worker_sync();
         if (wt == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&a_full)) : "memory");
         // 2. while the products run: the next step's draws (thread per chain)
-        if (st + 1 < steps_per_tile && wt < Rv) draw(st + 1, c0, wt, thr_next, nb_next);
+        if (st + 1 < steps_per_tile && wt < Rv) draw(st + 1, c0, wt, thr_next, nb_next, mi_next);
         // 3-4. the products, then the epilogue: rows of this warp's lane quarter, its column half
         const bool ok = __all_sync(FULL_MASK, wait(&acc_full, step_g & 1u));  // the TMEM loads are warp-collective
         tc::fence_after_sync();
@@ -430,12 +433,29 @@ size_t fused_smem(const nqs_ctx *c) { return 1024 + (size_t)(c->Kp[1] / 64) * 16
 
 }  // namespace
 
+__global__ void dense_bond_diff_kernel(const float *__restrict__ W1t, const int2 *__restrict__ bonds, int n_bonds,
+                                       int H0, float *W1d) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)n_bonds * H0;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(q / H0), k = (int)(q % H0);
+    const int2 bd = bonds[b];
+    W1d[q] = W1t[(int64_t)bd.x * H0 + k] - W1t[(int64_t)bd.y * H0 + k];
+  }
+}
+
 bool dense_fused_supported(const nqs_ctx *c) {
   if (c->model_kind != NQS_DENSE || c->dtype != NQS_BF16 || c->L != 2) return false;
   const int H1 = c->H[1];
   const int p1 = H1 > 256 ? H1 - 256 : 0;
   return c->Kp[1] <= FU_MAX_K && H1 <= FU_MAX_K && H1 % 16 == 0 && p1 % 16 == 0 && c->W <= 8 &&
          fused_smem(c) + sizeof(FusedSmem) + 256 <= (size_t)c->smem_optin;
+}
+
+cudaError_t dense_fused_prepare(const nqs_ctx *c, cudaStream_t s) {
+  const int64_t n = (int64_t)c->n_bonds * c->H[0];
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8));
+  dense_bond_diff_kernel<<<grid, 256, 0, s>>>(c->d_W1t, c->d_bonds, c->n_bonds, c->H[0], c->d_W1d);
+  return cudaGetLastError();
 }
 
 // Sweeps [t0, t1) of the fused sampler; z0 and lp hold the chains' current layer-0
@@ -448,7 +468,8 @@ cudaError_t dense_fused_sweeps(const nqs_ctx *c, uint32_t *state, int64_t C, int
   a.z0 = c->d_z1;
   a.z0b = c->d_z1b;
   a.lp = c->d_lp;
-  a.W1t = c->d_W1t;
+  a.W1d = c->ham_kind == NQS_HEISENBERG ? c->d_W1d : c->d_W1t;
+  if (!a.W1d) return cudaErrorInvalidValue;
   a.b2 = c->d_bl[1];
   a.w_out = c->d_wout;
   a.b_out = c->b_out;

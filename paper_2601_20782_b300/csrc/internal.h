@@ -59,6 +59,7 @@ struct nqs_ctx {
   int L = 0;
   std::vector<int> H, Kp;          // Kp[l]: padded input width of layer l (Kp[0] unused)
   float *d_W1t = nullptr;          // [N][H0] FP32 sampling-copy layer-1 weights, site-major
+  float *d_W1d = nullptr;          // [n_bonds][H0] W1t[i_b] - W1t[j_b] per bond (fused exchange sampler)
   float *d_b1 = nullptr;           // [H0]
   std::vector<__nv_bfloat16 *> d_Wl;  // layer l >= 1: [H[l]][Kp[l]] BF16 sampling copy
   std::vector<float *> d_bl;       // layer l >= 1: [H[l]] bias (sampling copy, FP32 values)
@@ -169,6 +170,8 @@ cudaError_t dense_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, 
                               const double *stats, double *force, cudaStream_t s, bool share = false);
 // dense_fused.cu
 bool dense_fused_supported(const nqs_ctx *c);
+// per-bond differences of the layer-0 weights for the fused exchange sampler (after dense_prepare)
+cudaError_t dense_fused_prepare(const nqs_ctx *c, cudaStream_t s);
 cudaError_t dense_fused_sweeps(const nqs_ctx *c, uint32_t *state, int64_t C, int n_sweeps, int t0, int t1,
                                int burn_in, uint64_t seed, uint32_t sweep_offset, uint32_t *samples, float *logpsi,
                                int64_t *n_acc, uint32_t *acc_bits, float *delta, bool add_acc, cudaStream_t s);
