@@ -333,7 +333,13 @@ __global__ void __launch_bounds__(CR_THREADS, 4) crbm_eloc_kernel(const CElocArg
     float er[CR_SPW], ei[CR_SPW];
 #pragma unroll
     for (int r = 0; r < CR_SPW; ++r) er[r] = ei[r] = 0.f;
-    for (int q = 0; q < (N + 31) / 32; ++q) {
+    // full passes of 32 sites (every lane takes one site for all CR_SPW samples); a tail of
+    // rem < 32 sites with rem * CR_SPW <= 32 runs below as (site, sample) pairs instead, one
+    // pair per lane, so that it does not cost a full pass for a few active lanes
+    const int rem = N % 32;
+    const bool tail_pairs = rem > 0 && rem * CR_SPW <= 32;
+    const int n_full = tail_pairs ? N / 32 : (N + 31) / 32;
+    for (int q = 0; q < n_full; ++q) {
       const int i = 32 * q + lane;
       const bool active = i < N;
       const int2 nb = a.nb[active ? i : 0];
@@ -403,6 +409,76 @@ __global__ void __launch_bounds__(CR_THREADS, 4) crbm_eloc_kernel(const CElocArg
             ei[r] = fmaf(a.h * mag, ry, ei[r]);
           }
         }
+      }
+    }
+    if (tail_pairs) {
+      const bool act = lane < rem * CR_SPW;
+      const int rr = act ? lane / rem : 0;
+      const int i = 32 * (N / 32) + (act ? lane % rem : 0);
+      const int2 nb = a.nb[i];
+      const int d = nb.y >= 0 ? nb.y : 0;
+      // this lane's sample's words of sites i, nb.x, nb.y (the shuffles are warp-wide)
+      uint32_t wi = 0u, wx = 0u, wd = 0u;
+#pragma unroll
+      for (int r = 0; r < CR_SPW; ++r) {
+        const uint32_t vi = __shfl_sync(FULL_MASK, wr[r], i >> 5);
+        const uint32_t vx = __shfl_sync(FULL_MASK, wr[r], nb.x >> 5);
+        const uint32_t vd = __shfl_sync(FULL_MASK, wr[r], d >> 5);
+        if (r == rr) {
+          wi = vi;
+          wx = vx;
+          wd = vd;
+        }
+      }
+      if (act) {
+        const float sg = spin_of(wi, i & 31);
+        const float sr = spin_of(wx, nb.x & 31);
+        const float sd = nb.y >= 0 ? spin_of(wd, d & 31) : 0.f;
+        float2 pp = make_float2(1.f, 0.f);
+        float L = 0.f;
+        bool dead = false;
+        const float4 *col = a.et + i;
+        const float2 *tr = tw + rr * M_pad;
+        float4 cur[8], nxt[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) cur[jj] = __ldg(col + (int64_t)jj * N);
+        for (int j0 = 0; j0 < M_pad; j0 += 8) {
+          if (j0 + 8 < M_pad) {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) nxt[jj] = __ldg(col + (int64_t)(j0 + 8 + jj) * N);
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) nxt[jj] = cur[jj];
+          }
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const float4 cs = cur[jj];
+            const float2 t = tr[j0 + jj];
+            const float tsx = fmaf(t.x, cs.z, -t.y * cs.w), tsy = fmaf(t.x, cs.w, t.y * cs.z);
+            const float rx = fmaf(-sg, tsx, cs.x), ry = fmaf(-sg, tsy, cs.y);
+            const float px = fmaf(pp.x, rx, -pp.y * ry), py = fmaf(pp.x, ry, pp.y * rx);
+            pp = make_float2(px, py);
+          }
+          crbm_normalise(pp, L, dead);
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) cur[jj] = nxt[jj];
+        }
+        const float2 ai = a.r.a[i];
+        float dr = a.J * sg * (sr + sd), di = 0.f;
+        if (!dead) {
+          const float mag = ex2_approx(fmaf(-2.f * sg * ai.x, LOG2EF, L));
+          float sn, cn;
+          sincosf(-2.f * sg * ai.y, &sn, &cn);
+          const float rx = fmaf(pp.x, cn, -pp.y * sn), ry = fmaf(pp.x, sn, pp.y * cn);
+          dr = fmaf(a.h * mag, rx, dr);
+          di = a.h * mag * ry;
+        }
+#pragma unroll
+        for (int r = 0; r < CR_SPW; ++r)
+          if (r == rr) {
+            er[r] += dr;
+            ei[r] += di;
+          }
       }
     }
 #pragma unroll
