@@ -210,6 +210,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
             unsigned char *bs = ring + s * stage_bytes;
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
+              // K steps wholly beyond the layer-0 width multiply the A tile's zero columns: skipped
+              if (kb * 64 + kk * 16 >= a.H0) break;
               const uint64_t ad = tc::desc_sw128(smem_addr(atile + kb * 16384 + kk * 32));
               const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
               tc::mma_bf16(tmem, ad, tc::desc_sw128(smem_addr(bs + kk * 32)), id0, acc);
