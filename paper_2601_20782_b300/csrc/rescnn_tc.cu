@@ -266,6 +266,17 @@ struct Cta {
     return ok;
   }
 
+  // The planes hold the input of the convolution in flight, and the epilogue writes the next
+  // one's input into them: a tile's rows may be overwritten once no product still to finish
+  // reads them.  A tile's shifted windows reach Lx + 3 rows (< 128) either side, so only tile
+  // t + 1 reads rows of tile t; its barrier (tiles commit in order) covers every earlier tile.
+  __device__ bool wait_overwrite(int t, int *status) const {
+    if (t + 1 >= gm.T) return true;
+    const bool ok = __all_sync(FULL_MASK, mbar_wait_bounded(&bars[t + 1], phase, TC_WAIT_POLLS));
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr(status, STATUS_TIMEOUT);
+    return ok;
+  }
+
   // After a timed-out wait: give every product in flight the poll limit again before TMEM is freed.
   __device__ void drain() const {
     if (threadIdx.x == 0)
@@ -361,15 +372,24 @@ __device__ __forceinline__ bool forward_tc(Cta<TT> &cta, const OwnRows &own, int
         tc::tmem_wait_ld();
         float v[CF];
         if (w == 0) {  // c = phi(K1 * a + b1)
-          if (!own.interior(k)) continue;
 #pragma unroll
           for (int c = 0; c < CF; ++c) v[c] = gelu_lp(__uint_as_float(ra[c]) + bp[2 * CF + c]);
-          cta.store_act(OwnRows::row(k), v);
+          if (!cta.wait_overwrite(t, status)) {  // warp-uniform
+            bad = true;
+            continue;
+          }
+          if (own.interior(k)) cta.store_act(OwnRows::row(k), v);
         } else {  // h += K2 * c + b2, then phi(LN(h)) of the next block
 #pragma unroll
           for (int c = 0; c < CF; ++c) v[c] = __uint_as_float(rh[c]) + (__uint_as_float(ra[c]) + bp[3 * CF + c]);
           tc::tmem_st16(cta.h_addr(t), v);  // warp-collective: every lane, halo rows included
-          if (own.interior(k) && l + 1 < gm.n_blocks) ln_gelu_store(cta, OwnRows::row(k), v, cta.blockp(l + 1));
+          if (l + 1 < gm.n_blocks) {
+            if (!cta.wait_overwrite(t, status)) {  // warp-uniform
+              bad = true;
+              continue;
+            }
+            if (own.interior(k)) ln_gelu_store(cta, OwnRows::row(k), v, cta.blockp(l + 1));
+          }
         }
       }
       if (w == 1) tc::tmem_wait_st();
