@@ -307,26 +307,34 @@ __global__ void __launch_bounds__(CR_THREADS, 4) crbm_eloc_kernel(const CElocArg
     for (int r = 0; r < CR_SPW; ++r) {
       const int64_t x = std::min<int64_t>(x0 + r, a.r.n - 1);
       wr[r] = lane < W ? a.r.cfg[x * W + lane] : 0u;
-      float tx[KU], ty[KU];
+    }
+    // theta of two samples at a time: each weight row is loaded once for both
+#pragma unroll
+    for (int r = 0; r < CR_SPW; r += 2) {
+      float tx0[KU], ty0[KU], tx1[KU], ty1[KU];
 #pragma unroll
       for (int k = 0; k < KU; ++k) {
         const float2 bj = a.r.b[lane + 32 * k];
-        tx[k] = bj.x;
-        ty[k] = bj.y;
+        tx0[k] = tx1[k] = bj.x;
+        ty0[k] = ty1[k] = bj.y;
       }
       for (int i = 0; i < N; ++i) {
-        const float s = spin_of(__shfl_sync(FULL_MASK, wr[r], i >> 5), i & 31);
+        const float s0 = spin_of(__shfl_sync(FULL_MASK, wr[r], i >> 5), i & 31);
+        const float s1 = spin_of(__shfl_sync(FULL_MASK, wr[r + 1], i >> 5), i & 31);
         const float2 *row = a.r.Wt + (int64_t)i * M_pad + lane;
 #pragma unroll
         for (int k = 0; k < KU; ++k) {
           const float2 w = __ldg(row + 32 * k);
-          tx[k] = fmaf(s, w.x, tx[k]);
-          ty[k] = fmaf(s, w.y, ty[k]);
+          tx0[k] = fmaf(s0, w.x, tx0[k]);
+          ty0[k] = fmaf(s0, w.y, ty0[k]);
+          tx1[k] = fmaf(s1, w.x, tx1[k]);
+          ty1[k] = fmaf(s1, w.y, ty1[k]);
         }
       }
 #pragma unroll
       for (int k = 0; k < KU; ++k) {
-        tw[r * M_pad + lane + 32 * k] = tanh_c(tx[k], ty[k]);
+        tw[r * M_pad + lane + 32 * k] = tanh_c(tx0[k], ty0[k]);
+        tw[(r + 1) * M_pad + lane + 32 * k] = tanh_c(tx1[k], ty1[k]);
       }
     }
     __syncwarp();
