@@ -151,7 +151,7 @@ struct TcArgs {
 
 // Shared-memory carve (offsets in bytes from a 128-aligned base); the host uses the same.
 struct TcLayout {
-  uint32_t planes, tiles, small, blockp, spin, rowsum, chain, total;
+  uint32_t planes, tiles, small, blockp, spin, rowsum, chain, halo, total;
   __host__ __device__ static TcLayout make(const TcGeom &g) {
     TcLayout L;
     uint32_t o = 0;
@@ -167,6 +167,7 @@ struct TcLayout {
     L.spin = take((uint32_t)g.G * g.N * 4u);
     L.rowsum = take((uint32_t)g.T * 128u * 4u);
     L.chain = take((uint32_t)g.G * 40u);  // flip, lp, thr, lpx (4 x 4 B) + Philox block (16 B) + spare
+    L.halo = take((uint32_t)g.G * (uint32_t)(g.Rp - g.N) * 4u);  // halo row -> image row pairs
     L.total = o;
     return L;
   }
@@ -223,15 +224,12 @@ struct Cta {
     tc::fence_before_sync();
     if (__syncthreads_or(bad)) return false;
     uint4 *p = reinterpret_cast<uint4 *>(planes() + (size_t)gm.GR * 16u);
-    const int Lxp = gm.Lxp;
-    for (int e = threadIdx.x; e < gm.G * gm.Rp; e += blockDim.x) {
-      const int g = e / gm.Rp, pos = e - g * gm.Rp;
-      const int py = pos / Lxp, px = pos - py * Lxp;
-      if (px >= 1 && px <= gm.Lx && py >= 1 && py <= gm.Ly) continue;
-      const int sy = (py - 1 + gm.Ly) % gm.Ly + 1, sx = (px - 1 + gm.Lx) % gm.Lx + 1;
-      const int src = g * gm.Rp + sy * Lxp + sx;
-      p[e] = p[src];
-      p[e + gm.plane_rows] = p[src + gm.plane_rows];
+    const uint32_t *pairs = reinterpret_cast<const uint32_t *>(base + L.halo);
+    for (int e = threadIdx.x; e < gm.G * (gm.Rp - gm.N); e += blockDim.x) {
+      const uint32_t v = pairs[e];
+      const int dst = (int)(v >> 16), src = (int)(v & 0xFFFFu);
+      p[dst] = p[src];
+      p[dst + gm.plane_rows] = p[src + gm.plane_rows];
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
@@ -457,6 +455,18 @@ __device__ void setup_cta(Cta<TT> &cta, const TcArgs &a, uint32_t *tmem_slot) {
       v = a.cw[10 * CF + gm.n_blocks * BLOCK_FLOATS + q * CF + c];  // final gamma (q = 0), beta (q = 1)
     }
     bp[i] = v;
+  }
+  // the halo rows of every configuration with their periodic images, (row << 16 | image row)
+  // in rows from the first padded row: one thread per configuration, in position order
+  uint32_t *pairs = reinterpret_cast<uint32_t *>(cta.base + cta.L.halo);
+  for (int g = threadIdx.x; g < gm.G; g += blockDim.x) {
+    int q = g * (gm.Rp - gm.N);
+    for (int pos = 0; pos < gm.Rp; ++pos) {
+      const int py = pos / gm.Lxp, px = pos - py * gm.Lxp;
+      if (px >= 1 && px <= gm.Lx && py >= 1 && py <= gm.Ly) continue;
+      const int sy = (py - 1 + gm.Ly) % gm.Ly + 1, sx = (px - 1 + gm.Lx) % gm.Lx + 1;
+      pairs[q++] = ((uint32_t)(g * gm.Rp + pos) << 16) | (uint32_t)(g * gm.Rp + sy * gm.Lxp + sx);
+    }
   }
   if (threadIdx.x == 0) {
     for (int t = 0; t < MAX_TILES; ++t) mbar_init(&cta.bars[t], 1);
