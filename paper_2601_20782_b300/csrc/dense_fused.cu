@@ -4,26 +4,28 @@
 //
 // A CTA owns a tile of R <= 128 chains for all the sweeps of one launch; chains are
 // independent, so CTAs never wait on one another.  Each Metropolis step:
-//   1. draw: a thread per chain takes its Philox words (the layout of nqs_sweep), the move
-//      (a bond for exchange moves, a site for flips) and log u;
+//   1. moves: a thread per chain takes the move drawn during the previous step's products and
+//      looks up its spins (an exchange of equal spins is the identity, not evaluated);
 //   2. proposal rows: a warp per chain writes log cosh(z0 + move delta) (BF16) straight into
 //      the A tile in shared memory (128-byte swizzle, K-major), z0 being the chain's FP32
 //      layer-0 pre-activations and the delta +-2 times a row of W1t (a flip) or of the
 //      per-bond differences W1t[i] - W1t[j] (an exchange; the same FP32 difference the
-//      multi-launch sampler forms), so a proposal reads two rows, three chains at a time.  z0 has two buffers per chain in global memory (read through
-//      L2): the proposal's z0 + delta goes to the other one, and an accepted move only
-//      switches the chain's current buffer.  All loads of a row are issued before its
-//      arithmetic, two rows at a time;
+//      multi-launch sampler forms), so a proposal reads two rows.  z0 has two buffers per
+//      chain in global memory (read through L2): the proposal's z0 + delta goes to the other
+//      one, and an accepted move only switches the chain's current buffer.  All loads of a
+//      warp's rows are issued before their arithmetic, three rows at a time;
 //   3. products: one thread issues tcgen05.mma kind::f16 over the A tile and W2 K-blocks that
-//      a TMA thread streams through a two-stage ring (W2 does not fit shared memory); meanwhile
-//      a thread per chain draws the next step's move and log u;
+//      a TMA thread streams through a two-stage ring (W2 does not fit shared memory); K steps
+//      wholly beyond the layer-0 width (zero columns of the A tile) are skipped.  Meanwhile a
+//      thread per chain draws the next step's move and log u (Philox, the layout of
+//      nqs_sweep) into its registers;
 //   4. epilogue: the accumulator rows (TMEM) give log psi(y) = b_out + w_out . tanh(z2 + b2);
-//   5. decision: accept iff 2 (log psi(y) - log psi(x)) > log u (an exchange of equal spins is
-//      the identity, accepted without evaluation); an accepted move updates the spins and
-//      log psi and switches z0's buffer.
-// Rows of the tile beyond R stay zero and their outputs are not read.  Every wait is bounded;
-// on a timeout the kernel records STATUS_TIMEOUT and stops.  The host rebuilds z0 and log psi
-// from the spins between launches (every `refresh` sweeps), as the multi-launch sampler does.
+//   5. decision: accept iff 2 (log psi(y) - log psi(x)) > log u (the identity is accepted);
+//      an accepted move updates the spins and log psi and switches z0's buffer.
+// Rows of the tile beyond R hold stale or zero values whose outputs are not read.  Every wait
+// is bounded; on a timeout the kernel records STATUS_TIMEOUT and stops.  The host rebuilds z0
+// and log psi from the spins between launches (every `refresh` sweeps), as the multi-launch
+// sampler does.
 #include <cuda_bf16.h>
 
 #include <algorithm>
