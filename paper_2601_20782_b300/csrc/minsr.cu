@@ -6,7 +6,11 @@
 // Steps (all on the stream, FP64 wherever the solve's stability depends on it):
 //   1. minsr_colmean_kernel   FP64 column means of O (one pass over O).
 //   2. minsr_split_kernel     Obar' = O - mean (FP32), split into three BF16 terms
-//                             hi + mid + lo (exact to ~2^-24 relative), stored [3][n_pad][Pp].
+//                             hi + mid + lo (exact to ~2^-24 relative), stored K-block-major,
+//                             [Pp/64][3][n_pad][64]: the six boxes of one K block then lie in
+//                             3 n_pad 128 contiguous bytes.  (Row-major [3][n_pad][Pp] rows are
+//                             2 Pp bytes apart, one memory page per box row at P = 2.4M; the
+//                             Gram ran 1.4x slower from that layout.)
 //   3. minsr_gram_kernel      T' = Obar' Obar'^T on the tensor cores: TMA loads of the three
 //                             terms of a 128-row tile pair per 64-wide K block, six products
 //                             (hh into one TMEM accumulator; hm, mh, hl, lh, mm into a second,
@@ -14,8 +18,11 @@
 //                             accumulation for DRAIN K blocks, then FP64 partial sums per
 //                             (K part, tile pair).  Upper tile pairs only (T is symmetric).
 //   4. minsr_reduce_kernel    T = (1/n) sum over K parts, mirrored, + lambda on the diagonal.
-//   5. Cholesky T + lambda I = L L^T in FP64 (blocked: diagonal block, panel, trailing update).
-//   6. minsr_solve_kernel     L z = ebar, L^T y = z (one CTA), and sum_x y_x.
+//   5. Cholesky T + lambda I = L L^T in FP64 (blocked: diagonal block, panel, trailing update);
+//      minsr_reduce_kernel also writes ebar.
+//   6. L z = ebar along with the Cholesky (each diagonal block solves its triangle, each
+//      panel updates the later rows); minsr_back_kernel: L^T y = z in 64-row blocks from the
+//      last; minsr_ysum_kernel: sum_x y_x.
 //   7. minsr_dtheta_kernel    dtheta_k = (sum_x O_xk y_x - mean_k sum_x y_x) / sqrt(n), FP64.
 #include <cuda_bf16.h>
 
@@ -64,12 +71,11 @@ __device__ __forceinline__ void split3_bf16(float a, __nv_bfloat16 &h, __nv_bflo
   l = __float2bfloat16_rn(r - __bfloat162float(m));
 }
 
-// S3[t][x][k] for x < n_pad, k < Pp (pairs of k per thread); zero outside n x P.
+// S3[k / 64][t][x][k % 64] for x < n_pad, k < Pp (pairs of k per thread); zero outside n x P.
 __global__ void minsr_split_kernel(const float *__restrict__ O, int64_t n, int64_t P, int64_t n_pad, int64_t Pp,
                                    const float *__restrict__ mean_f, __nv_bfloat16 *S3) {
   const int64_t half_cols = Pp / 2;
   const int64_t total = n_pad * half_cols;
-  const int64_t term = n_pad * Pp;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x = q / half_cols, k = 2 * (q % half_cols);
     float v[2];
@@ -77,11 +83,36 @@ __global__ void minsr_split_kernel(const float *__restrict__ O, int64_t n, int64
     __nv_bfloat16 h0, m0, l0, h1, m1, l1;
     split3_bf16(v[0], h0, m0, l0);
     split3_bf16(v[1], h1, m1, l1);
-    const int64_t o = x * Pp + k;
+    const int64_t tb = n_pad * 64;
+    const int64_t o = (k >> 6) * 3 * tb + x * 64 + (k & 63);
     *reinterpret_cast<__nv_bfloat162 *>(S3 + o) = __halves2bfloat162(h0, h1);
-    *reinterpret_cast<__nv_bfloat162 *>(S3 + term + o) = __halves2bfloat162(m0, m1);
-    *reinterpret_cast<__nv_bfloat162 *>(S3 + 2 * term + o) = __halves2bfloat162(l0, l1);
+    *reinterpret_cast<__nv_bfloat162 *>(S3 + tb + o) = __halves2bfloat162(m0, m1);
+    *reinterpret_cast<__nv_bfloat162 *>(S3 + 2 * tb + o) = __halves2bfloat162(l0, l1);
   }
+}
+
+// The K-block-major copy of the split terms, S3[kb][t][x][c] (64-wide K blocks, three terms of
+// n_pad rows, 128-byte rows), as a 3D tensor map {c, t * n_pad + x, kb} with 128 x 64 boxes.
+bool make_tmap_kblocks(CUtensorMap *map, const void *base, uint64_t n_pad, uint64_t kb_total) {
+  using Fn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                          const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                          CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Fn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return false;
+    fn = reinterpret_cast<Fn>(p);
+  }
+  const cuuint64_t dims[3] = {64, 3 * n_pad, kb_total};
+  const cuuint64_t strides[2] = {128, 3 * n_pad * 128};
+  const cuuint32_t box[3] = {64, 128, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 struct GramArgs {
@@ -167,8 +198,8 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1)
           unsigned char *st = base + s * STAGE;
           mbar_expect_tx(&full[s], diag ? 3 * TILE : 6 * TILE);
           for (int t = 0; t < 3; ++t) {
-            tma_load_2d(st + t * TILE, &mS, kb * 64, (int32_t)(t * g.n_pad + ti * 128), &full[s]);
-            if (!diag) tma_load_2d(st + (3 + t) * TILE, &mS, kb * 64, (int32_t)(t * g.n_pad + tj * 128), &full[s]);
+            tma_load_3d(st + t * TILE, &mS, 0, (int32_t)(t * g.n_pad + ti * 128), kb, &full[s]);
+            if (!diag) tma_load_3d(st + (3 + t) * TILE, &mS, 0, (int32_t)(t * g.n_pad + tj * 128), kb, &full[s]);
           }
         }
       }
@@ -227,7 +258,12 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1)
       kb_range(item, &kb0, &kb1);
       const int part = item / g.n_pairs;
       const int64_t r = (int64_t)ti * 128 + 32 * q + lane;
-      double *row = g.Tpart + ((int64_t)part * g.n_pad + r) * g.n_pad + (int64_t)tj * 128;
+      double *row = g.Tpart + ((int64_t)part * g.n_pad + r) * g.n_pad + (int64_t)tj * 128 + 64 * h;
+      // this thread's 64 FP64 partial sums (row r, columns 64h..64h+63) stay in registers for
+      // the whole item and are stored once at its end
+      double acc[64];
+#pragma unroll
+      for (int e = 0; e < 64; ++e) acc[e] = 0.0;
       bool stop = false;
       for (int c0 = kb0; c0 < kb1; c0 += GRAM_DRAIN, ++d) {
         if (!wait(&tfull[d & 1u], (d >> 1) & 1u)) {
@@ -236,16 +272,14 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1)
         }
         tc::fence_after_sync();
         const uint32_t acc_hi = tmem + (d & 1u) * 256u, acc_lo = acc_hi + 128u;
-        for (int cc = 0; cc < 2; ++cc) {
-          const int col = 64 * h + 32 * cc;
-          float vh[32], vl[32];
-          tc::tmem_ld32(tc::tmem_lane_addr(acc_hi, 32 * q, col), vh);
-          tc::tmem_ld32(tc::tmem_lane_addr(acc_lo, 32 * q, col), vl);
 #pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const double v = (double)vh[e] + (double)vl[e];
-            row[col + e] = (c0 == kb0 ? 0.0 : row[col + e]) + v;
-          }
+        for (int cc = 0; cc < 4; ++cc) {
+          const int col = 64 * h + 16 * cc;
+          float vh[16], vl[16];
+          tc::tmem_ld16(tc::tmem_lane_addr(acc_hi, 32 * q, col), vh);
+          tc::tmem_ld16(tc::tmem_lane_addr(acc_lo, 32 * q, col), vl);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) acc[16 * cc + e] += (double)vh[e] + (double)vl[e];
         }
         tc::fence_before_sync();
         __syncwarp();
@@ -253,6 +287,8 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1)
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty[d & 1u])) : "memory");
       }
       if (stop) break;
+#pragma unroll
+      for (int e = 0; e < 64; e += 2) *reinterpret_cast<double2 *>(row + e) = make_double2(acc[e], acc[e + 1]);
     }
   }
   tc::fence_before_sync();
@@ -265,10 +301,12 @@ __global__ void __launch_bounds__(GRAM_THREADS, 1)
 }
 
 // T[x][y] = (1/n) sum_parts Tpart[min(x,y)][max(x,y)] + lam on the diagonal (x <= y lies in an
-// upper tile pair or a diagonal tile, the pairs the Gram kernel computed).
+// upper tile pair or a diagonal tile, the pairs the Gram kernel computed); on the diagonal pass
+// also the right-hand side w[x] = ebar_x = (eloc_x - E) / sqrt(n), E = stats[0].
 __global__ void minsr_reduce_kernel(const double *__restrict__ Tpart, int n_parts, int64_t n, int64_t n_pad,
-                                    double lam, double *T, double *T_out) {
-  const double inv_n = 1.0 / (double)n;
+                                    double lam, double *T, double *T_out, const float *__restrict__ eloc,
+                                    const double *__restrict__ stats, double *w) {
+  const double inv_n = 1.0 / (double)n, E = stats[0], rs = 1.0 / sqrt((double)n);
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * n; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x = q / n, y = q % n;
     const int64_t src = x <= y ? x * n_pad + y : y * n_pad + x;  // upper element, mirrored: T exactly symmetric
@@ -277,12 +315,19 @@ __global__ void minsr_reduce_kernel(const double *__restrict__ Tpart, int n_part
     s *= inv_n;
     if (T_out) T_out[q] = s;
     T[q] = s + (x == y ? lam : 0.0);
+    if (x == y) w[x] = ((double)eloc[x] - E) * rs;
   }
 }
 
 // ---- Cholesky (lower, in place in A [n x n] row-major), FP64 -------------------------------
-// Diagonal block [k0, k0 + nb) factored by one CTA in shared memory.
-__global__ void chol_diag_kernel(double *A, int64_t n, int64_t k0, int nb, int *status) {
+// The forward substitution L z = w runs along with it: when block [k0, k0 + nb) is factored,
+// the earlier panels have already subtracted their part from w over these rows, so the block
+// solves its own triangle (chol_diag_kernel) and its panel subtracts L[i][block] z_block from
+// w_i for every later row (chol_panel_kernel).  w holds z when the factorisation ends.
+//
+// Diagonal block [k0, k0 + nb) factored by one CTA in shared memory; then warp 0 solves
+// L_d z = w over the block's rows (lane l holds rows l and l + 32).
+__global__ void chol_diag_kernel(double *A, int64_t n, int64_t k0, int nb, int *status, double *w) {
   __shared__ double a[CHOL_NB][CHOL_NB + 1];
   for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) a[q / nb][q % nb] = A[(k0 + q / nb) * n + k0 + q % nb];
   __syncthreads();
@@ -305,14 +350,30 @@ __global__ void chol_diag_kernel(double *A, int64_t n, int64_t k0, int nb, int *
     }
     __syncthreads();
   }
+  __shared__ double rinv[CHOL_NB];  // 1 / L_jj, taken once per row before the sequential solve
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) rinv[j] = 1.0 / a[j][j];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+    double b0 = l < nb ? w[k0 + l] : 0.0, b1 = l + 32 < nb ? w[k0 + l + 32] : 0.0;
+    for (int j = 0; j < nb; ++j) {  // z_j = b_j / L_jj, then b_i -= L_ij z_j for the rows i > j
+      const double zj = __shfl_sync(FULL_MASK, j < 32 ? b0 : b1, j & 31) * rinv[j];
+      if (l == (j & 31)) (j < 32 ? b0 : b1) = zj;
+      if (l > j && l < nb) b0 -= a[l][j] * zj;
+      if (l + 32 > j && l + 32 < nb) b1 -= a[l + 32][j] * zj;
+    }
+    if (l < nb) w[k0 + l] = b0;
+    if (l + 32 < nb) w[k0 + l + 32] = b1;
+  }
   for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
     const int i = q / nb, k = q % nb;
     A[(k0 + i) * n + k0 + k] = k <= i ? a[i][k] : 0.0;
   }
 }
 
-// Panel rows i >= k0 + nb: L[i][k0 .. k0+nb) = A[i][..] L_d^-T (forward substitution per row).
-__global__ void chol_panel_kernel(double *A, int64_t n, int64_t k0, int nb) {
+// Panel rows i >= k0 + nb: L[i][k0 .. k0+nb) = A[i][..] L_d^-T (forward substitution per row),
+// then w_i -= L[i][k0 .. k0+nb) z_block (z_block = w[k0 .. k0+nb) from chol_diag_kernel).
+__global__ void chol_panel_kernel(double *A, int64_t n, int64_t k0, int nb, double *w) {
   __shared__ double l[CHOL_NB][CHOL_NB + 1];
   for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) l[q / nb][q % nb] = A[(k0 + q / nb) * n + k0 + q % nb];
   __syncthreads();
@@ -325,7 +386,12 @@ __global__ void chol_panel_kernel(double *A, int64_t n, int64_t k0, int nb) {
       for (int k = 0; k < j; ++k) s -= v[k] * l[j][k];
       v[j] = s / l[j][j];
     }
-    for (int j = 0; j < nb; ++j) row[j] = v[j];
+    double s = 0.0;
+    for (int j = 0; j < nb; ++j) {
+      row[j] = v[j];
+      s += v[j] * w[k0 + j];
+    }
+    w[i] -= s;
   }
 }
 
@@ -368,39 +434,49 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double *A, int64_t n, 
   }
 }
 
-// L z = ebar (row-oriented), L^T y = z (column-oriented over rows of L), one CTA; ebar from
-// eloc and E = stats[0].  work: [n] scratch; y: [n]; ysum: sum_x y_x.
-__global__ void __launch_bounds__(1024) minsr_solve_kernel(const double *__restrict__ L, int64_t n,
-                                                           const float *__restrict__ eloc,
-                                                           const double *__restrict__ stats, double *z, double *y,
-                                                           double *ysum) {
-  __shared__ double red[32];
-  __shared__ double bcast;
-  const double E = stats[0], rs = 1.0 / sqrt((double)n);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int64_t j = 0; j < n; ++j) {  // forward
-    double s = 0.0;
-    for (int64_t k = tid; k < j; k += blockDim.x) s += L[j * n + k] * z[k];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < nw; ++w) t += red[w];
-      z[j] = (((double)eloc[j] - E) * rs - t) / L[j * n + j];
-    }
-    __syncthreads();
-  }
-  for (int64_t i = tid; i < n; i += blockDim.x) y[i] = z[i];
+// Backward substitution L^T y = z over the block J = [j0, j0 + nb), the blocks taken from the
+// last: every CTA solves the block's triangle L_JJ^T y_J = w_J from a shared-memory copy of
+// L_JJ (warp 0; lane l holds rows l and l + 32), CTA 0 stores y_J, and the CTAs subtract
+// sum_{j in J} L[j][i] y_j from w_i for the columns i < j0, 64 columns per CTA (rows of L,
+// coalesced in i; the block's rows split over four quarters of the CTA).
+__global__ void __launch_bounds__(256) minsr_back_kernel(const double *__restrict__ L, int64_t n, int64_t j0, int nb,
+                                                         double *w, double *y) {
+  __shared__ double ld[CHOL_NB][CHOL_NB + 1];
+  __shared__ double yb[CHOL_NB], inv[CHOL_NB];
+  __shared__ double part[4][64];
+  const int tid = threadIdx.x;
+  for (int q = tid; q < nb * nb; q += blockDim.x) ld[q / nb][q % nb] = L[(j0 + q / nb) * n + j0 + q % nb];
+  for (int j = tid; j < nb; j += blockDim.x) inv[j] = 1.0 / L[(j0 + j) * n + j0 + j];
   __syncthreads();
-  for (int64_t j = n - 1; j >= 0; --j) {  // backward: y_j = w_j / L_jj, then w_i -= L_ji y_j (i < j)
-    if (tid == 0) bcast = y[j] / L[j * n + j];
-    __syncthreads();
-    const double yj = bcast;
-    for (int64_t i = tid; i < j; i += blockDim.x) y[i] -= L[j * n + i] * yj;
-    if (tid == 0) y[j] = yj;
-    __syncthreads();
+  if (tid < 32) {
+    const int l = tid;
+    double b0 = l < nb ? w[j0 + l] : 0.0, b1 = l + 32 < nb ? w[j0 + l + 32] : 0.0;
+    for (int j = nb - 1; j >= 0; --j) {  // y_j = b_j / L_jj, then b_i -= L_ji y_j for the rows i < j
+      const double yj = __shfl_sync(FULL_MASK, j < 32 ? b0 : b1, j & 31) * inv[j];
+      if (l == (j & 31)) (j < 32 ? b0 : b1) = yj;
+      if (l < j) b0 -= ld[j][l] * yj;
+      if (l + 32 < j) b1 -= ld[j][l + 32] * yj;
+    }
+    yb[l] = b0;
+    yb[l + 32] = b1;
   }
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int q = tid; q < nb; q += blockDim.x) y[j0 + q] = yb[q];
+  const int c = tid & 63, qtr = tid >> 6;
+  const int64_t i = (int64_t)blockIdx.x * 64 + c;
+  double s = 0.0;
+  if (i < j0)
+    for (int j = qtr; j < nb; j += 4) s += L[(j0 + j) * n + i] * yb[j];
+  part[qtr][c] = s;
+  __syncthreads();
+  if (qtr == 0 && i < j0) w[i] -= (part[0][c] + part[1][c]) + (part[2][c] + part[3][c]);
+}
+
+// ysum = sum_x y_x (one CTA, fixed order).
+__global__ void __launch_bounds__(1024) minsr_ysum_kernel(const double *__restrict__ y, int64_t n, double *ysum) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double s = 0.0;
   for (int64_t i = tid; i < n; i += blockDim.x) s += y[i];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
@@ -408,7 +484,7 @@ __global__ void __launch_bounds__(1024) minsr_solve_kernel(const double *__restr
   __syncthreads();
   if (tid == 0) {
     double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += red[w];
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
     *ysum = t;
   }
 }
@@ -511,7 +587,7 @@ cudaError_t minsr(const nqs_ctx *c, const float *O, int64_t n, const float *eloc
                                                                                  S3);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   CUtensorMap mS;
-  if (!make_tmap_bf16_2d(&mS, S3, (uint64_t)(3 * L.n_pad), (uint64_t)L.Pp, 128)) return cudaErrorInvalidValue;
+  if (!make_tmap_kblocks(&mS, S3, (uint64_t)L.n_pad, (uint64_t)L.kb_total)) return cudaErrorInvalidValue;
   GramArgs g;
   g.n_tiles = L.n_tiles;
   g.n_pairs = L.n_pairs;
@@ -528,21 +604,26 @@ cudaError_t minsr(const nqs_ctx *c, const float *O, int64_t n, const float *eloc
     return e;
   minsr_gram_kernel<<<std::min(g.n_items, c->num_sms), GRAM_THREADS, shm, s>>>(mS, g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  minsr_reduce_kernel<<<grid_n(n * n, 256, c->num_sms), 256, 0, s>>>(Tpart, L.n_parts, n, L.n_pad, lam, T, T_out);
+  minsr_reduce_kernel<<<grid_n(n * n, 256, c->num_sms), 256, 0, s>>>(Tpart, L.n_parts, n, L.n_pad, lam, T, T_out,
+                                                                    eloc, stats, z);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int64_t k0 = 0; k0 < n; k0 += CHOL_NB) {
     const int nb = (int)std::min<int64_t>(CHOL_NB, n - k0);
-    chol_diag_kernel<<<1, 256, 0, s>>>(T, n, k0, nb, c->d_status);
+    chol_diag_kernel<<<1, 256, 0, s>>>(T, n, k0, nb, c->d_status, z);
     const int64_t k1 = k0 + nb;
     if (k1 < n) {
-      chol_panel_kernel<<<grid_n(n - k1, 128, c->num_sms), 128, 0, s>>>(T, n, k0, nb);
+      chol_panel_kernel<<<grid_n(n - k1, 128, c->num_sms), 128, 0, s>>>(T, n, k0, nb, z);
       const int64_t tiles = (n - k1 + 63) / 64;
       chol_update_kernel<<<(unsigned)std::min<int64_t>(tiles * tiles, (int64_t)c->num_sms * 8), 256, 0, s>>>(
           T, n, k0, nb, k1);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  minsr_solve_kernel<<<1, 1024, 0, s>>>(T, n, eloc, stats, z, y, ys);
+  for (int64_t j0 = (n - 1) / CHOL_NB * CHOL_NB; j0 >= 0; j0 -= CHOL_NB) {
+    const int nb = (int)std::min<int64_t>(CHOL_NB, n - j0);
+    minsr_back_kernel<<<(unsigned)std::max<int64_t>(1, (j0 + 63) / 64), 256, 0, s>>>(T, n, j0, nb, z, y);
+  }
+  minsr_ysum_kernel<<<1, 1024, 0, s>>>(y, n, ys);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   minsr_dtheta_kernel<<<grid_n(c->P, 256, c->num_sms), 256, (size_t)n * sizeof(float), s>>>(O, n, c->P, mean_d, y,
                                                                                             ys, dtheta);
