@@ -608,19 +608,24 @@ int grid_for(int64_t work, int per_block, int num_sms) {
 // GEMM chain over layers 1..L-1 for R rows whose layer-0 output is in act[0]; writes log psi
 // (out == nullptr: leaves the last layer's partials in d_part and returns their range count).
 // With fewer row tiles than half the SMs each layer uses its split configuration (N-ranges
-// of half the width) so that more CTAs share the work.
+// of half the width) so that more CTAs share the work; with enough row tiles for every SM
+// to take two of them per N-range, the tall configuration (two row tiles per CTA on the
+// half-width ranges, more products per byte of operands).
 // f8: the FP8 copy's E4M3 activations, weights and scales.
 cudaError_t run_chain(const nqs_ctx *c, int64_t R, float *out, const float *b_out_dev, cudaStream_t s,
                       int *n_ranges_out = nullptr, bool f8 = false) {
   int cur = 0;
   cudaError_t e;
-  const bool split = (R + 127) / 128 < c->num_sms / 2;
+  const int64_t n_tiles = (R + 127) / 128;
+  const bool split = n_tiles < c->num_sms / 2;
   int n_ranges = 1;
   for (int l = 1; l < c->L; ++l) {
     const bool last = l == c->L - 1;
     const std::vector<int> &Kp = f8 ? c->Kp8 : c->Kp;
     const int ld_out = last ? 0 : Kp[l + 1];
-    const bool sp = split && c->NRs[l] > 0;
+    const bool tall = !split && c->NRs[l] > 0 && c->NRs[l] <= 256 &&
+                      (n_tiles / 2) * ((c->H[l] + c->NRs[l] - 1) / c->NRs[l]) >= c->num_sms;
+    const bool sp = (split || tall) && c->NRs[l] > 0;
     const int NR = sp ? c->NRs[l] : c->NR[l];
     const CUtensorMap &m0 = f8 ? (sp ? c->mBs0_8[l] : c->mB0_8[l]) : (sp ? c->mBs0[l] : c->mB0[l]);
     const CUtensorMap &m1 = f8 ? (sp ? c->mBs1_8[l] : c->mB1_8[l]) : (sp ? c->mBs1[l] : c->mB1[l]);
@@ -629,7 +634,7 @@ cudaError_t run_chain(const nqs_ctx *c, int64_t R, float *out, const float *b_ou
     if ((e = dense_gemm(c, A, (int)R, Kp[l], m0, m1, c->H[l], NR, sp ? c->p0s[l] : c->p0[l],
                         sp ? c->p1s[l] : c->p1[l], last ? 1 : 0, c->d_bl[l], last ? c->d_wout : nullptr,
                         last ? nullptr : next, ld_out, last ? c->d_part : nullptr, s,
-                        f8 ? c->d_scale8 + c->L + l : nullptr)) != cudaSuccess)
+                        f8 ? c->d_scale8 + c->L + l : nullptr, tall)) != cudaSuccess)
       return e;
     if (last) n_ranges = (c->H[l] + NR - 1) / NR;
     cur ^= 1;

@@ -98,7 +98,12 @@ struct GemmArgs {
   int *status;
 };
 
-template <int STAGES, bool F8>
+// TALL: a CTA owns two row tiles (256 rows) and an N-range of NR <= 256 columns: per K-block
+// it loads both A tiles and one B tile and issues one N = NR product per A tile, into TMEM
+// columns 0 and 256.  Per K-block that is 64 KB for 256 x 256 outputs instead of 80 KB for
+// 128 x 512, i.e. 25 % more products per byte delivered to the SM.  The epilogue warp pair
+// of a lane quarter then takes one tile each, over all of the range's columns.
+template <int STAGES, bool F8, bool TALL>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     dense_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB0,
                       const __grid_constant__ CUtensorMap mB1, const GemmArgs g) {
@@ -109,7 +114,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   __shared__ volatile int abort_flag;
   const uint32_t raw = smem_addr(smem_dyn);
   unsigned char *base = smem_dyn + (((raw + 1023u) & ~1023u) - raw);
-  const uint32_t a_bytes = 16384u, b_bytes = (uint32_t)g.NR * 128u, stage_bytes = a_bytes + b_bytes;
+  const uint32_t a_bytes = TALL ? 32768u : 16384u, b_bytes = (uint32_t)g.NR * 128u, stage_bytes = a_bytes + b_bytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
@@ -151,6 +156,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   };
 
   const int n_tiles = (g.R + 127) / 128;
+  const int n_steps = TALL ? (n_tiles + 1) / 2 : n_tiles;  // a step is one (TALL: two) row tile(s)
   constexpr int KB = F8 ? 128 : 64;  // elements per 128-byte K-block
   const int kb_n = g.Kpad / KB;
   const int range = blockIdx.y;
@@ -159,24 +165,30 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {  // ---- TMA producer
       uint32_t it = 0;
-      for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x)
+      for (int step = blockIdx.x; step < n_steps && !abort_flag; step += gridDim.x)
         for (int kb = 0; kb < kb_n; ++kb, ++it) {
           const int s = it % STAGES;
           if (!wait(&empty[s], ((it / STAGES) & 1u) ^ 1u)) break;
           unsigned char *st = base + s * stage_bytes;
           mbar_expect_tx(&full[s], stage_bytes);
-          tma_load_2d(st, &mA, kb * KB, tile * 128, &full[s]);
+          if constexpr (TALL) {  // the second tile may lie past R: TMA fills those rows with zeros
+            tma_load_2d(st, &mA, kb * KB, 2 * step * 128, &full[s]);
+            tma_load_2d(st + 16384, &mA, kb * KB, (2 * step + 1) * 128, &full[s]);
+          } else {
+            tma_load_2d(st, &mA, kb * KB, step * 128, &full[s]);
+          }
           tma_load_2d(st + a_bytes, &mB0, kb * KB, nbase, &full[s]);
           if (g.p1) tma_load_2d(st + a_bytes + g.p0 * 128, &mB1, kb * KB, nbase + g.p0, &full[s]);
         }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
-      const uint32_t id0 = F8 ? tc::idesc_e4m3_f32(128, (uint32_t)g.p0) : tc::idesc_bf16_f32(128, (uint32_t)g.p0);
+      const uint32_t id0 = F8 ? tc::idesc_e4m3_f32(128, (uint32_t)(TALL ? g.NR : g.p0))
+                              : tc::idesc_bf16_f32(128, (uint32_t)(TALL ? g.NR : g.p0));
       const uint32_t n1 = (uint32_t)(g.p1 ? g.p1 : 16);
       const uint32_t id1 = F8 ? tc::idesc_e4m3_f32(128, n1) : tc::idesc_bf16_f32(128, n1);
       uint32_t it = 0, t = 0;
-      for (int tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x, ++t) {
+      for (int step = blockIdx.x; step < n_steps && !abort_flag; step += gridDim.x, ++t) {
         if (!wait(&tempty, (t & 1u) ^ 1u)) break;
         tc::fence_after_sync();
         bool ok = true;
@@ -192,6 +204,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             const uint64_t ad = tc::desc_sw128(smem_addr(st + kk * 32));
             const uint64_t b0 = tc::desc_sw128(smem_addr(st + a_bytes + kk * 32));
             const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+            if constexpr (TALL) {  // B (both boxes, NR rows) against each A tile
+              const uint64_t ad1 = tc::desc_sw128(smem_addr(st + 16384 + kk * 32));
+              if constexpr (F8) {
+                tc::mma_f8(tmem, ad, b0, id0, acc);
+                tc::mma_f8(tmem + 256u, ad1, b0, id0, acc);
+              } else {
+                tc::mma_bf16(tmem, ad, b0, id0, acc);
+                tc::mma_bf16(tmem + 256u, ad1, b0, id0, acc);
+              }
+              continue;
+            }
             if constexpr (F8) tc::mma_f8(tmem, ad, b0, id0, acc);
             else tc::mma_bf16(tmem, ad, b0, id0, acc);
             if (g.p1) {
@@ -211,14 +234,18 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int row_in_tile = 32 * q + lane;
     const float sc = F8 ? *g.inv_scale : 1.f;
     uint32_t t = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++t) {
+    // TALL: this warp takes tile 2 step + half (accumulator at column 256 half), every chunk;
+    // otherwise tile step, every other 32-column chunk from 32 half
+    const int c_first = TALL ? 0 : 32 * half, c_step = TALL ? 32 : 64;
+    const uint32_t acc_col = TALL ? 256u * (uint32_t)half : 0u;
+    for (int step = blockIdx.x; step < n_steps; step += gridDim.x, ++t) {
       if (!wait(&tfull, t & 1u)) break;
       tc::fence_after_sync();
-      const int r = tile * 128 + row_in_tile;
+      const int r = (TALL ? 2 * step + half : step) * 128 + row_in_tile;
       float dot = 0.f;
-      for (int c0 = 32 * half; c0 < g.NR; c0 += 64) {
+      for (int c0 = c_first; c0 < g.NR; c0 += c_step) {
         float v[32];
-        tc::tmem_ld32(tc::tmem_lane_addr(tmem, 32 * q, c0), v);
+        tc::tmem_ld32(tc::tmem_lane_addr(tmem, 32 * q, acc_col + c0), v);
         if (r < g.R) {
           if (g.mode == 0) {
             float a[32];
@@ -260,7 +287,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           }
         }
       }
-      if (g.mode == 1 && r < g.R) g.out_part[((int64_t)r * g.n_ranges + range) * 2 + half] = dot;
+      if (g.mode == 1 && r < g.R) {
+        if constexpr (TALL) {  // the whole range's dot in one warp: slot 0, slot 1 zero
+          g.out_part[((int64_t)r * g.n_ranges + range) * 2] = dot;
+          g.out_part[((int64_t)r * g.n_ranges + range) * 2 + 1] = 0.f;
+        } else {
+          g.out_part[((int64_t)r * g.n_ranges + range) * 2 + half] = dot;
+        }
+      }
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty)) : "memory");
@@ -282,8 +316,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 cudaError_t dense_gemm(const nqs_ctx *c, const void *A, int R, int Kpad, const CUtensorMap &mB0,
                        const CUtensorMap &mB1, int N, int NR, int p0, int p1, int mode, const float *bias,
                        const float *w, void *out_act, int ld_out, float *out_part, cudaStream_t s,
-                       const float *inv_scale) {
+                       const float *inv_scale, bool tall) {
   if (R <= 0) return cudaSuccess;
+  if (tall && NR > 256) return cudaErrorInvalidValue;
   const bool f8 = inv_scale != nullptr;
   CUtensorMap mA;
   if (!(f8 ? make_tmap_u8_2d(&mA, A, (uint64_t)R, (uint64_t)Kpad, 128)
@@ -305,16 +340,17 @@ cudaError_t dense_gemm(const nqs_ctx *c, const void *A, int R, int Kpad, const C
   g.ld_out = ld_out;
   g.out_part = out_part;
   g.status = c->d_status;
-  const size_t stage = 16384 + (size_t)NR * 128;
+  const size_t stage = (tall ? 32768 : 16384) + (size_t)NR * 128;
   const int stages = (int)std::min<size_t>(4, (size_t)(c->smem_optin - 2048 - 4096) / stage);  // - static bias / w_out
   const size_t shm = 1024 + stages * stage;
-  const int n_tiles = (R + 127) / 128;
-  const int gx = std::max(1, std::min(n_tiles, c->num_sms / g.n_ranges));
+  const int n_steps = tall ? (R + 255) / 256 : (R + 127) / 128;
+  const int gx = std::max(1, std::min(n_steps, c->num_sms / g.n_ranges));
   const dim3 grid(gx, g.n_ranges);
   cudaError_t e;
 #define NQS_LAUNCH(S)                                                                                        \
   {                                                                                                          \
-    auto k = f8 ? dense_gemm_kernel<S, true> : dense_gemm_kernel<S, false>;                                  \
+    auto k = tall ? (f8 ? dense_gemm_kernel<S, true, true> : dense_gemm_kernel<S, false, true>)            \
+                  : (f8 ? dense_gemm_kernel<S, true, false> : dense_gemm_kernel<S, false, false>);          \
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) != cudaSuccess) \
       return e;                                                                                              \
     k<<<grid, GEMM_THREADS, shm, s>>>(mA, mB0, mB1, g);                                                      \

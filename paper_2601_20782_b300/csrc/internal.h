@@ -193,7 +193,7 @@ bool make_tmap_u8_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64_t
 cudaError_t dense_gemm(const nqs_ctx *c, const void *A, int R, int Kpad, const CUtensorMap &mB0,
                        const CUtensorMap &mB1, int N, int NR, int p0, int p1, int mode, const float *bias,
                        const float *w, void *out_act, int ld_out, float *out_part, cudaStream_t s,
-                       const float *inv_scale = nullptr);
+                       const float *inv_scale = nullptr, bool tall = false);
 
 // minsr.cu
 size_t minsr_workspace(const nqs_ctx *c, int64_t n);
