@@ -932,7 +932,7 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swee
   const bool f8 = c->dtype == NQS_FP8E4M3;  // the sampler runs on the FP8 copy
   auto refresh = [&]() -> cudaError_t { return logpsi_rows(c, state, C, c->d_lp, s); };  // z0, log psi from scratch
   if ((e = refresh()) != cudaSuccess) return e;
-  if (!f8 && c->dense_fused && c->d_z1b && dense_fused_supported(c)) {
+  if (c->dense_fused && c->d_z1b && dense_fused_supported(c)) {
     // persistent fused sampler, one launch per stretch of sweeps between two refreshes (the
     // refresh points of the multi-launch path below: after sweep t when (t + 1) % refresh == 0)
     for (int t = 0; t < n_sweeps;) {

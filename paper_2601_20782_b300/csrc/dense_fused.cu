@@ -1,6 +1,7 @@
 // Persistent Metropolis sampler of the dense ansatz with one tensor-core layer (two hidden
 // layers: a1 = log cosh(W1 s + b1), a2 = tanh(W2 a1 + b2), log psi = w_out . a2 + b_out; the
-// BF16 sampling copy), for layer widths up to 448.
+// BF16 sampling copy, or the FP8 copy: E4M3 a1 and W2 s2 with z2 = acc / s2, layer 0 on the
+// E4M3-rounded W1), for layer widths up to 448.
 //
 // A CTA owns a tile of R <= 128 chains for all the sweeps of one launch; chains are
 // independent, so CTAs never wait on one another.  Each Metropolis step:
@@ -14,7 +15,7 @@
 //      chain in global memory (read through L2): the proposal's z0 + delta goes to the other
 //      one, and an accepted move only switches the chain's current buffer.  All loads of a
 //      warp's rows are issued before their arithmetic, three rows at a time;
-//   3. products: one thread issues tcgen05.mma kind::f16 over the A tile and W2 K-blocks that
+//   3. products: one thread issues tcgen05.mma kind::f16 (FP8: kind::f8f6f4) over the A tile and W2 K-blocks that
 //      a TMA thread streams through a two-stage ring (W2 does not fit shared memory); K steps
 //      wholly beyond the layer-0 width (zero columns of the A tile) are skipped.  Meanwhile a
 //      thread per chain draws the next step's move and log u (Philox, the layout of
@@ -27,6 +28,7 @@
 // and log psi from the spins between launches (every `refresh` sweeps), as the multi-launch
 // sampler does.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -53,6 +55,7 @@ struct FusedArgs {
   const float *W1d;   // [n_moves][H0]: W1t rows (flips) or W1t[i_b] - W1t[j_b] (exchanges)
   const float *b2;    // [H1]
   const float *w_out; // [H1]
+  const float *inv_scale;  // FP8 copy: 1 / s2 (device scalar)
   float b_out;
   const int2 *bonds;
   int64_t *n_acc;
@@ -104,6 +107,10 @@ struct FusedSmem {
   uint32_t abits[128];
 };
 
+// F8: the FP8 copy.  A K-block is then 128 E4M3 elements (still 128 bytes per row), a lane
+// writes four activations per K-block (one 32-bit store at the byte offset of BF16 element
+// 2 lane), and the products are kind::f8f6f4 (K = 32 per instruction).
+template <bool F8>
 __global__ void __launch_bounds__(FU_THREADS, 1)
     dense_fused_sweep_kernel(const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
                              const FusedArgs a) {
@@ -114,7 +121,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
   __shared__ FusedSmem sm;
   const uint32_t raw = smem_addr(smem_dyn);
   unsigned char *base = smem_dyn + (((raw + 1023u) & ~1023u) - raw);
-  const int kb_n = a.Kp1 / 64;
+  constexpr int KB = F8 ? 128 : 64;  // elements per 128-byte K-block
+  const int kb_n = a.Kp1 / KB;
   unsigned char *atile = base;                                   // kb_n x 16 KB
   unsigned char *ring = base + kb_n * 16384;                     // FU_STAGES x H1 x 128 B
   uint32_t *spins = reinterpret_cast<uint32_t *>(ring + FU_STAGES * a.H1 * 128);  // [128][8]
@@ -188,14 +196,15 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
             if (!wait(&empty[s], ((it / FU_STAGES) & 1u) ^ 1u)) break;
             unsigned char *dst = ring + s * stage_bytes;
             mbar_expect_tx(&full[s], stage_bytes);
-            tma_load_2d(dst, &mB0, kb * 64, 0, &full[s]);
-            if (a.p1) tma_load_2d(dst + a.p0 * 128, &mB1, kb * 64, a.p0, &full[s]);
+            tma_load_2d(dst, &mB0, kb * KB, 0, &full[s]);
+            if (a.p1) tma_load_2d(dst + a.p0 * 128, &mB1, kb * KB, a.p0, &full[s]);
           }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // ---- MMA issuer
-      const uint32_t id0 = tc::idesc_bf16_f32(128, (uint32_t)a.p0);
-      const uint32_t id1 = tc::idesc_bf16_f32(128, (uint32_t)(a.p1 ? a.p1 : 16));
+      const uint32_t id0 = F8 ? tc::idesc_e4m3_f32(128, (uint32_t)a.p0) : tc::idesc_bf16_f32(128, (uint32_t)a.p0);
+      const uint32_t id1 = F8 ? tc::idesc_e4m3_f32(128, (uint32_t)(a.p1 ? a.p1 : 16))
+                              : tc::idesc_bf16_f32(128, (uint32_t)(a.p1 ? a.p1 : 16));
       uint32_t it = 0;
       for (int64_t tile = blockIdx.x; tile < n_tiles && !abort_flag; tile += gridDim.x)
         for (int st = 0; st < steps_per_tile + 1 && !abort_flag; ++st, ++step_g) {
@@ -213,11 +222,16 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
               // K steps wholly beyond the layer-0 width multiply the A tile's zero columns: skipped
-              if (kb * 64 + kk * 16 >= a.H0) break;
+              if (kb * KB + kk * (KB / 4) >= a.H0) break;
               const uint64_t ad = tc::desc_sw128(smem_addr(atile + kb * 16384 + kk * 32));
               const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-              tc::mma_bf16(tmem, ad, tc::desc_sw128(smem_addr(bs + kk * 32)), id0, acc);
-              if (a.p1) tc::mma_bf16(tmem + (uint32_t)a.p0, ad, tc::desc_sw128(smem_addr(bs + a.p0 * 128 + kk * 32)), id1, acc);
+              if constexpr (F8) {
+                tc::mma_f8(tmem, ad, tc::desc_sw128(smem_addr(bs + kk * 32)), id0, acc);
+                if (a.p1) tc::mma_f8(tmem + (uint32_t)a.p0, ad, tc::desc_sw128(smem_addr(bs + a.p0 * 128 + kk * 32)), id1, acc);
+              } else {
+                tc::mma_bf16(tmem, ad, tc::desc_sw128(smem_addr(bs + kk * 32)), id0, acc);
+                if (a.p1) tc::mma_bf16(tmem + (uint32_t)a.p0, ad, tc::desc_sw128(smem_addr(bs + a.p0 * 128 + kk * 32)), id1, acc);
+              }
             }
             tc::mma_commit(&empty[s]);
           }
@@ -228,6 +242,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
   } else {  // ---- workers
     const int wt = tid - 64, wk = wt >> 5;  // worker thread 0..255, worker warp 0..7
     const int q = warp & 3, half = wk >> 2;  // TMEM lane quarter (warp w reads lanes 32 (w % 4) ..), column half
+    const float sc = F8 ? *a.inv_scale : 1.f;  // FP8: z2 = acc / s2
     bool stop = false;
     float thr = 0.f, thr_next = 0.f;  // log u of this step and of the next (thread of chain wt)
     int2 nb_next = make_int2(0, -1);   // the next step's drawn move
@@ -265,46 +280,94 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
         worker_sync();
         // 2. proposal rows into the A tile (warp per chain, FU_ROWS rows at a time, every load of
         //    those rows issued before their arithmetic); step -1 writes the unmoved rows
-        for (int r0 = wk; r0 < Rv; r0 += 8 * FU_ROWS) {
-          float2 z[FU_ROWS][7], d[FU_ROWS][7];
-          float g[FU_ROWS];
-          bool live[FU_ROWS];
+        if constexpr (F8) {
+          for (int r0 = wk; r0 < Rv; r0 += 8 * FU_ROWS) {
+            float4 z[FU_ROWS][4], d[FU_ROWS][4];
+            float g[FU_ROWS];
+            bool live[FU_ROWS];
 #pragma unroll
-          for (int u = 0; u < FU_ROWS; ++u) {
-            const int r = r0 + 8 * u;
-            live[u] = r < Rv && !(st >= 0 && sm.mv[r].x < 0);  // the identity is not evaluated
-            const int mi = live[u] && st >= 0 ? sm.mi[r] : -1;
-            g[u] = live[u] ? sm.gsign[r] : 0.f;
-            const float *zr = (sm.cur[live[u] ? r : r0] ? a.z0b : a.z0) + (c0 + (live[u] ? r : r0)) * a.H0;
-            const float *dr = a.W1d + (int64_t)(mi < 0 ? 0 : mi) * a.H0;
+            for (int u = 0; u < FU_ROWS; ++u) {
+              const int r = r0 + 8 * u;
+              live[u] = r < Rv && !(st >= 0 && sm.mv[r].x < 0);  // the identity is not evaluated
+              const int mi = live[u] && st >= 0 ? sm.mi[r] : -1;
+              g[u] = live[u] ? sm.gsign[r] : 0.f;
+              const float *zr = (sm.cur[live[u] ? r : r0] ? a.z0b : a.z0) + (c0 + (live[u] ? r : r0)) * a.H0;
+              const float *dr = a.W1d + (int64_t)(mi < 0 ? 0 : mi) * a.H0;
 #pragma unroll
-            for (int kb = 0; kb < 7; ++kb) {
-              const int k = kb * 64 + 2 * lane;
-              const bool in = live[u] && kb < kb_n && k < a.H0;
-              z[u][kb] = in ? *reinterpret_cast<const float2 *>(zr + k) : make_float2(0.f, 0.f);
-              d[u][kb] = in && mi >= 0 ? *reinterpret_cast<const float2 *>(dr + k) : make_float2(0.f, 0.f);
+              for (int kb = 0; kb < 4; ++kb) {
+                const int k = kb * 128 + 4 * lane;
+                const bool in = live[u] && kb < kb_n && k < a.H0;
+                z[u][kb] = in ? *reinterpret_cast<const float4 *>(zr + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                d[u][kb] = in && mi >= 0 ? *reinterpret_cast<const float4 *>(dr + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < FU_ROWS; ++u) {
+              if (!live[u]) continue;
+              const int r = r0 + 8 * u;
+              const bool moved = st >= 0;
+              float *zn = (sm.cur[r] ? a.z0 : a.z0b) + (c0 + r) * a.H0;  // the other buffer
+#pragma unroll
+              for (int kb = 0; kb < 4; ++kb) {
+                if (kb >= kb_n) break;
+                const int k = kb * 128 + 4 * lane;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k < a.H0) {
+                  const float4 zz = make_float4(fmaf(g[u], d[u][kb].x, z[u][kb].x), fmaf(g[u], d[u][kb].y, z[u][kb].y),
+                                                fmaf(g[u], d[u][kb].z, z[u][kb].z), fmaf(g[u], d[u][kb].w, z[u][kb].w));
+                  if (moved) *reinterpret_cast<float4 *>(zn + k) = zz;
+                  v = make_float4(log_cosh_f(zz.x), log_cosh_f(zz.y), log_cosh_f(zz.z), log_cosh_f(zz.w));
+                }
+                const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v.x, v.y), __NV_SATFINITE, __NV_E4M3);
+                const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v.z, v.w), __NV_SATFINITE, __NV_E4M3);
+                // elements 4 lane .. 4 lane + 3 of the K-block: the bytes of BF16 element 2 lane
+                *reinterpret_cast<uint32_t *>(atile + kb * 16384 + tc::sw128_offset(tile_row(r), (uint32_t)(2 * lane))) =
+                    lo | (hi << 16);
+              }
             }
           }
-#pragma unroll
-          for (int u = 0; u < FU_ROWS; ++u) {
-            if (!live[u]) continue;
-            const int r = r0 + 8 * u;
-            const bool moved = st >= 0;
-            float *zn = (sm.cur[r] ? a.z0 : a.z0b) + (c0 + r) * a.H0;  // the other buffer
-#pragma unroll
-            for (int kb = 0; kb < 7; ++kb) {
-              if (kb >= kb_n) break;
-              const int k = kb * 64 + 2 * lane;
-              float v0 = 0.f, v1 = 0.f;
-              if (k < a.H0) {
-                const float2 zz = make_float2(fmaf(g[u], d[u][kb].x, z[u][kb].x), fmaf(g[u], d[u][kb].y, z[u][kb].y));
-                if (moved) *reinterpret_cast<float2 *>(zn + k) = zz;
-                v0 = log_cosh_f(zz.x);
-                v1 = log_cosh_f(zz.y);
+        } else {
+          for (int r0 = wk; r0 < Rv; r0 += 8 * FU_ROWS) {
+            float2 z[FU_ROWS][7], d[FU_ROWS][7];
+            float g[FU_ROWS];
+            bool live[FU_ROWS];
+  #pragma unroll
+            for (int u = 0; u < FU_ROWS; ++u) {
+              const int r = r0 + 8 * u;
+              live[u] = r < Rv && !(st >= 0 && sm.mv[r].x < 0);  // the identity is not evaluated
+              const int mi = live[u] && st >= 0 ? sm.mi[r] : -1;
+              g[u] = live[u] ? sm.gsign[r] : 0.f;
+              const float *zr = (sm.cur[live[u] ? r : r0] ? a.z0b : a.z0) + (c0 + (live[u] ? r : r0)) * a.H0;
+              const float *dr = a.W1d + (int64_t)(mi < 0 ? 0 : mi) * a.H0;
+  #pragma unroll
+              for (int kb = 0; kb < 7; ++kb) {
+                const int k = kb * 64 + 2 * lane;
+                const bool in = live[u] && kb < kb_n && k < a.H0;
+                z[u][kb] = in ? *reinterpret_cast<const float2 *>(zr + k) : make_float2(0.f, 0.f);
+                d[u][kb] = in && mi >= 0 ? *reinterpret_cast<const float2 *>(dr + k) : make_float2(0.f, 0.f);
               }
-              const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-              *reinterpret_cast<__nv_bfloat162 *>(atile + kb * 16384 +
-                                                  tc::sw128_offset(tile_row(r), (uint32_t)(2 * lane))) = h2;
+            }
+  #pragma unroll
+            for (int u = 0; u < FU_ROWS; ++u) {
+              if (!live[u]) continue;
+              const int r = r0 + 8 * u;
+              const bool moved = st >= 0;
+              float *zn = (sm.cur[r] ? a.z0 : a.z0b) + (c0 + r) * a.H0;  // the other buffer
+  #pragma unroll
+              for (int kb = 0; kb < 7; ++kb) {
+                if (kb >= kb_n) break;
+                const int k = kb * 64 + 2 * lane;
+                float v0 = 0.f, v1 = 0.f;
+                if (k < a.H0) {
+                  const float2 zz = make_float2(fmaf(g[u], d[u][kb].x, z[u][kb].x), fmaf(g[u], d[u][kb].y, z[u][kb].y));
+                  if (moved) *reinterpret_cast<float2 *>(zn + k) = zz;
+                  v0 = log_cosh_f(zz.x);
+                  v1 = log_cosh_f(zz.y);
+                }
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                *reinterpret_cast<__nv_bfloat162 *>(atile + kb * 16384 +
+                                                    tc::sw128_offset(tile_row(r), (uint32_t)(2 * lane))) = h2;
+              }
             }
           }
         }
@@ -334,8 +397,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
                 const int c = cb + 4 * k + cq;
                 if (c < a.H1) {
                   const float bb = sm.b2[c], w = sm.wout[c];
-                  da = fmaf(tanh_approx(v[2 * k] + bb), w, da);
-                  db = fmaf(tanh_approx(v[2 * k + 1] + bb), w, db);
+                  da = fmaf(tanh_approx(F8 ? fmaf(v[2 * k], sc, bb) : v[2 * k] + bb), w, da);
+                  db = fmaf(tanh_approx(F8 ? fmaf(v[2 * k + 1], sc, bb) : v[2 * k + 1] + bb), w, db);
                 }
               }
             }
@@ -357,7 +420,8 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
                   const int c = cb + 32 * sub + e;
-                  if (c < a.H1) s4[e & 3] = fmaf(tanh_approx(v[e] + sm.b2[c]), sm.wout[c], s4[e & 3]);
+                  if (c < a.H1)
+                    s4[e & 3] = fmaf(tanh_approx(F8 ? fmaf(v[e], sc, sm.b2[c]) : v[e] + sm.b2[c]), sm.wout[c], s4[e & 3]);
                 }
               }
             }
@@ -433,7 +497,11 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
   if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
-size_t fused_smem(const nqs_ctx *c) { return 1024 + (size_t)(c->Kp[1] / 64) * 16384 + 2 * (size_t)c->H[1] * 128 + 128 * 8 * 4; }
+// A tile (K-blocks of 64 BF16 or 128 E4M3 elements), the W2 ring and the spins
+size_t fused_smem(const nqs_ctx *c) {
+  const size_t kb_n = c->dtype == NQS_FP8E4M3 ? (size_t)c->Kp8[1] / 128 : (size_t)c->Kp[1] / 64;
+  return 1024 + kb_n * 16384 + 2 * (size_t)c->H[1] * 128 + 128 * 8 * 4;
+}
 
 }  // namespace
 
@@ -448,7 +516,8 @@ __global__ void dense_bond_diff_kernel(const float *__restrict__ W1t, const int2
 }
 
 bool dense_fused_supported(const nqs_ctx *c) {
-  if (c->model_kind != NQS_DENSE || c->dtype != NQS_BF16 || c->L != 2) return false;
+  if (c->model_kind != NQS_DENSE || (c->dtype != NQS_BF16 && c->dtype != NQS_FP8E4M3) || c->L != 2) return false;
+  if (c->dtype == NQS_FP8E4M3 && (c->H[0] % 4 != 0 || c->Kp8[1] > 512)) return false;  // float4 rows, 4 K-blocks
   const int H1 = c->H[1];
   const int p1 = H1 > 256 ? H1 - 256 : 0;
   return c->Kp[1] <= FU_MAX_K && H1 <= FU_MAX_K && H1 % 16 == 0 && p1 % 16 == 0 && c->W <= 8 &&
@@ -458,7 +527,9 @@ bool dense_fused_supported(const nqs_ctx *c) {
 cudaError_t dense_fused_prepare(const nqs_ctx *c, cudaStream_t s) {
   const int64_t n = (int64_t)c->n_bonds * c->H[0];
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8));
-  dense_bond_diff_kernel<<<grid, 256, 0, s>>>(c->d_W1t, c->d_bonds, c->n_bonds, c->H[0], c->d_W1d);
+  // the differences of the sampling copy's layer-0 rows (E4M3-rounded for the FP8 copy)
+  dense_bond_diff_kernel<<<grid, 256, 0, s>>>(c->dtype == NQS_FP8E4M3 ? c->d_W1t8 : c->d_W1t, c->d_bonds, c->n_bonds,
+                                              c->H[0], c->d_W1d);
   return cudaGetLastError();
 }
 
@@ -472,7 +543,9 @@ cudaError_t dense_fused_sweeps(const nqs_ctx *c, uint32_t *state, int64_t C, int
   a.z0 = c->d_z1;
   a.z0b = c->d_z1b;
   a.lp = c->d_lp;
-  a.W1d = c->ham_kind == NQS_HEISENBERG ? c->d_W1d : c->d_W1t;
+  const bool f8 = c->dtype == NQS_FP8E4M3;
+  a.W1d = c->ham_kind == NQS_HEISENBERG ? c->d_W1d : (f8 ? c->d_W1t8 : c->d_W1t);
+  a.inv_scale = f8 ? c->d_scale8 + c->L + 1 : nullptr;
   if (!a.W1d) return cudaErrorInvalidValue;
   a.b2 = c->d_bl[1];
   a.w_out = c->d_wout;
@@ -488,7 +561,7 @@ cudaError_t dense_fused_sweeps(const nqs_ctx *c, uint32_t *state, int64_t C, int
   a.N = c->N;
   a.W = c->W;
   a.H0 = c->H[0];
-  a.Kp1 = c->Kp[1];
+  a.Kp1 = f8 ? c->Kp8[1] : c->Kp[1];
   a.H1 = c->H[1];
   a.p0 = std::min(256, a.H1);
   a.p1 = a.H1 - a.p0;
@@ -504,16 +577,20 @@ cudaError_t dense_fused_sweeps(const nqs_ctx *c, uint32_t *state, int64_t C, int
   a.k1 = (uint32_t)(seed >> 32);
   a.R = (int)std::min<int64_t>(128, (C + c->num_sms - 1) / c->num_sms);
   CUtensorMap mB0, mB1;
-  if (!make_tmap_bf16_2d(&mB0, c->d_Wl[1], (uint64_t)a.H1, (uint64_t)a.Kp1, (uint32_t)a.p0)) return cudaErrorInvalidValue;
-  if (a.p1 && !make_tmap_bf16_2d(&mB1, c->d_Wl[1], (uint64_t)a.H1, (uint64_t)a.Kp1, (uint32_t)a.p1))
-    return cudaErrorInvalidValue;
+  auto tmap = [&](CUtensorMap *m, uint32_t box_rows) {
+    return f8 ? make_tmap_u8_2d(m, c->d_Wl8[1], (uint64_t)a.H1, (uint64_t)a.Kp1, box_rows)
+              : make_tmap_bf16_2d(m, c->d_Wl[1], (uint64_t)a.H1, (uint64_t)a.Kp1, box_rows);
+  };
+  if (!tmap(&mB0, (uint32_t)a.p0)) return cudaErrorInvalidValue;
+  if (a.p1 && !tmap(&mB1, (uint32_t)a.p1)) return cudaErrorInvalidValue;
   if (!a.p1) mB1 = mB0;
   const size_t shm = fused_smem(c);
-  cudaError_t e = cudaFuncSetAttribute(dense_fused_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  auto k = f8 ? dense_fused_sweep_kernel<true> : dense_fused_sweep_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e != cudaSuccess) return e;
   const int64_t n_tiles = (C + a.R - 1) / a.R;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(n_tiles, c->num_sms));
-  dense_fused_sweep_kernel<<<grid, FU_THREADS, shm, s>>>(mB0, mB1, a);
+  k<<<grid, FU_THREADS, shm, s>>>(mB0, mB1, a);
   return cudaGetLastError();
 }
 

@@ -128,15 +128,18 @@ def test_dense_local_energy_matches_oracle(Lx, Ly, widths, ham, J2, n):
     assert np.median(np.abs(ref64 - ref) / scale) > 3 * np.median(err / scale)
 
 
-@pytest.mark.parametrize("Lx,Ly,widths,J2,dtype,T", [(10, 10, (400, 400), 0.0, "bf16", 1),
-                                                     (16, 16, (1024, 1024, 1024), 0.5, "bf16", 1),
-                                                     (16, 16, (1024, 1024, 1024), 0.5, "fp8", 1)])
-def test_dense_sampler_replays_at_workload_shapes(Lx, Ly, widths, J2, dtype, T):
-    """The exchange sampler at the workloads' shapes (10 x 10 with 400 x 400; the 16 x 16
-    J1-J2 network 1024^3 in BF16 and FP8) and 8192 chains, in the launch configuration the
-    benchmark uses; a sampled subset of chains is replayed in the oracle against the copy's
-    own definition: every decision outside 10 sigma of the increment error agrees, and the
-    final configurations of those chains are reproduced."""
+@pytest.mark.parametrize("Lx,Ly,widths,J2,dtype,T,C", [(10, 10, (400, 400), 0.0, "bf16", 1, 8192),
+                                                       (10, 10, (400, 400), 0.0, "fp8", 1, 8192),
+                                                       (16, 16, (1024, 1024, 1024), 0.5, "bf16", 1, 8192),
+                                                       (16, 16, (1024, 1024, 1024), 0.5, "fp8", 1, 8192),
+                                                       (16, 16, (1024, 1024, 1024), 0.5, "bf16", 1, 65536)])
+def test_dense_sampler_replays_at_workload_shapes(Lx, Ly, widths, J2, dtype, T, C):
+    """The exchange sampler at the workloads' shapes (10 x 10 with 400 x 400, in BF16 and FP8:
+    the fused sampler; the 16 x 16 J1-J2 network 1024^3 in BF16 and FP8) with 8192 chains, and with the J1-J2 workload's
+    65,536 (whose products take the two-row-tile GEMM configuration); a sampled subset of
+    chains is replayed in the oracle against the copy's own definition: every decision
+    outside 10 sigma of the increment error agrees, and the final configurations of those
+    chains are reproduced."""
     from oracle.lattice import nn_bonds, nnn_bonds
     N = Lx * Ly
     if dtype == "fp8":
@@ -145,7 +148,6 @@ def test_dense_sampler_replays_at_workload_shapes(Lx, Ly, widths, J2, dtype, T):
     else:
         ctx, params, _, _ = make(Lx, Ly, widths, 17, J2=J2)
         lpf = lambda v: bf16_copy_logpsi(params, N, widths, v)
-    C = 8192
     W = ctx.W
     state = torch.zeros((C, W), dtype=torch.int32, device="cuda")
     ctx.init_chains(state, 31)
@@ -203,13 +205,14 @@ def test_dense_exchange_sampler_replays_in_oracle(fused):
     np.testing.assert_array_equal(unpack_np(words_from_tensor(samples), 16), ref["samples"])
 
 
-def test_dense_fused_sampler_independent_of_tiling():
-    """The fused sampler at the 10 x 10, 400 x 400 shape: a chain's draws, products and sums do
-    not depend on how many chains share its CTA or on its row in the tile, so 20000 chains
-    (tiles of 128, more than one tile per CTA), 8192 (tiles of 56) and 1000 (tiles of 7) give
-    bit-identical samples, log psi, acceptance counts and increments for the chains they
-    share."""
-    ctx, params, _, _ = make(10, 10, (400, 400), 23)
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_dense_fused_sampler_independent_of_tiling(dtype):
+    """The fused sampler at the 10 x 10, 400 x 400 shape (BF16 and FP8 copies): a chain's
+    draws, products and sums do not depend on how many chains share its CTA or on its row in
+    the tile, so 20000 chains (tiles of 128, more than one tile per CTA), 8192 (tiles of 56)
+    and 1000 (tiles of 7) give bit-identical samples, log psi, acceptance counts and
+    increments for the chains they share."""
+    ctx = make(10, 10, (400, 400), 23)[0] if dtype == "bf16" else make_fp8(10, 10, (400, 400), 23)[0]
     W, N, T, B = ctx.W, 100, 3, 1
     out = {}
     for C in (20000, 8192, 1000):
@@ -231,6 +234,39 @@ def test_dense_fused_sampler_independent_of_tiling():
         assert torch.equal(got[3], ref[3][:C])
         assert torch.equal(got[4], ref[4][:C])
     assert ref[3].sum().item() > 0
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_dense_fused_flip_sampler_replays_in_oracle(dtype):
+    """4 x 4 TFIM with two hidden layers (the fused sampler, flip moves: the proposal adds
+    -+2 times a row of the copy's layer-0 weights): every decision agrees with the MH rule on
+    the copy's own log psi (bf16_copy_logpsi / fp8_copy_logpsi) outside 10 sigma of the
+    increment error, and the final configurations and samples are reproduced."""
+    widths = (64, 48)
+    if dtype == "fp8":
+        ctx, params = make_fp8(4, 4, widths, 13, ham="tfim", bias=0.2)
+        lpf = lambda v: fp8_copy_logpsi(params, 16, widths, v)
+    else:
+        ctx, params, _, _ = make(4, 4, widths, 13, ham="tfim", bias=0.2, marshall=False)
+        lpf = lambda v: bf16_copy_logpsi(params, 16, widths, v)
+    C, T = 256, 3
+    state = torch.zeros((C, 1), dtype=torch.int32, device="cuda")
+    ctx.init_chains(state, 19)
+    s0 = unpack_np(words_from_tensor(state), 16)
+    bits = torch.zeros((C, T, 1), dtype=torch.int32, device="cuda")
+    delta = torch.zeros((C, T, 16), dtype=torch.float32, device="cuda")
+    samples = torch.zeros((C, 1), dtype=torch.int32, device="cuda")
+    ctx.sweep(state, T, T - 1, 14, 0, samples, None, None, accept_bits=bits, delta=delta)
+    acc = unpack_accept_bits(words_from_tensor(bits), 16)
+    ref = mh_sweeps(lpf, s0, np.arange(C), 14, T, T - 1, proposal="flip", replay_accepts=acc, tau=10.0,
+                    record_deltas=True)
+    d = delta.cpu().numpy().astype(np.float64)
+    sig = (2.0 * (d - ref["deltas"])).std()
+    assert sig < 0.05, sig
+    mh_sweeps(lpf, s0, np.arange(C), 14, T, T - 1, proposal="flip", replay_accepts=acc, tau=max(10 * sig, 1e-4))
+    np.testing.assert_array_equal(unpack_np(words_from_tensor(state), 16), ref["spins"])
+    np.testing.assert_array_equal(unpack_np(words_from_tensor(samples), 16), ref["samples"])
+    assert acc.mean() > 0.05
 
 
 @pytest.mark.parametrize("Lx,Ly,widths", [(4, 4, (64, 48)), (10, 10, (400, 400))])
