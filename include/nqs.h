@@ -124,8 +124,8 @@ int32_t nqs_n_bonds(const nqs_ctx *ctx);           /* bonds of the Hamiltonian *
  * NQS_OPT_MAX_ROWS: dense contexts only -- rows of one forward pass held in the
  * context's workspace (default 262144); bounds the chains of nqs_sweep and sets the
  * chunk of nqs_logpsi / nqs_local_energy.  Reallocates (synchronous).
- * NQS_OPT_DENSE_FUSED: dense contexts -- 1 (default): nqs_sweep of a BF16 copy with two
- * hidden layers no wider than 448 runs the persistent fused sampler (a CTA owns a tile of
+ * NQS_OPT_DENSE_FUSED: dense contexts -- 1 (default): nqs_sweep of a BF16 or FP8 copy with
+ * two hidden layers no wider than 448 runs the persistent fused sampler (a CTA owns a tile of
  * chains for all sweeps; proposal rows, the layer product on the tensor cores, log psi and
  * the decision in one kernel); 0: the multi-launch sampler (a producer kernel and the layer
  * GEMM per Metropolis step).  Same draws and decision rule; log psi sums in another order. */
