@@ -359,16 +359,17 @@ def make_fp8(Lx, Ly, widths, seed, ham="heisenberg", bias=0.1, J2=0.0):
     return ctx, params
 
 
-@pytest.mark.parametrize("Lx,Ly,widths", [(10, 10, (400, 400)), (4, 4, (64, 48)), (6, 6, (128, 96, 64)),
-                                          (16, 1, (1024, 512)), (16, 16, (1024, 1024, 1024))])
-def test_dense_fp8_logpsi_matches_its_definition(Lx, Ly, widths):
+@pytest.mark.parametrize("Lx,Ly,widths,n", [(10, 10, (400, 400), 1000), (4, 4, (64, 48), 1000),
+                                            (6, 6, (128, 96, 64), 1000), (16, 1, (1024, 512), 1000),
+                                            (16, 16, (1024, 1024, 1024), 1000), (16, 16, (1024, 1024, 1024), 20000)])
+def test_dense_fp8_logpsi_matches_its_definition(Lx, Ly, widths, n):
     """The FP8 copy's log psi against its FP64 definition with the same quantisation points.
     What remains are single-ulp E4M3 flips of activations that lie within the MUFU
     tanh / log cosh error of a rounding boundary (about 1 % of them); an error anywhere in the
-    quantised path (scale, byte order, K blocking) moves log psi by O(1)."""
+    quantised path (scale, byte order, K blocking) moves log psi by O(1).  20000 rows of the
+    1024^3 network take the layer products' two-row-tile configuration (ragged last pair)."""
     ctx, params = make_fp8(Lx, Ly, widths, 3)
     N = Lx * Ly
-    n = 1000
     s = np.random.default_rng(1).choice([-1, 1], size=(n, N)).astype(np.int8)
     out = torch.empty(n, dtype=torch.float32, device="cuda")
     ctx.logpsi(to_words_tensor(pack_np(s)), out)
