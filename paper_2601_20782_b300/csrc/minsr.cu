@@ -9,8 +9,8 @@
 //                             hi + mid + lo (exact to ~2^-24 relative), stored K-block-major,
 //                             [Pp/64][3][n_pad][64]: the six boxes of one K block then lie in
 //                             3 n_pad 128 contiguous bytes.  (Row-major [3][n_pad][Pp] rows are
-//                             2 Pp bytes apart, one memory page per box row at P = 2.4M; the
-//                             Gram ran 1.4x slower from that layout.)
+//                             2 Pp bytes apart, 4.7 MB at P = 2.4M, where the Gram ran 1.4x
+//                             slower from that layout; at P = 0.5M the two timed the same.)
 //   3. minsr_gram_kernel      T' = Obar' Obar'^T on the tensor cores: TMA loads of the three
 //                             terms of a 128-row tile pair per 64-wide K block, six products
 //                             (hh into one TMEM accumulator; hm, mh, hl, lh, mm into a second,
