@@ -48,8 +48,12 @@ def _run(ctx, O, eps, lam):
     return d.cpu().numpy(), T.cpu().numpy()
 
 
-@pytest.mark.parametrize("n,P,lam", [(300, 1000, 1e-3), (129, 4097, 1e-1), (256, 199_999, 1e-3)])
+@pytest.mark.parametrize("n,P,lam", [(300, 1000, 1e-3), (129, 4097, 1e-1), (256, 199_999, 1e-3),
+                                     (2, 1000, 1e-1), (65, 2999, 1e-3), (2200, 4999, 1e-3)])
 def test_minsr_matches_oracle_on_gaussian_rows(n, P, lam):
+    """Also the edges of the blocked Cholesky and triangular solves (64-row blocks): n = 2, one
+    block and a row (65), and 35 blocks with a 24-row last block and an odd count of 128-row
+    Gram tiles (2200)."""
     ctx = _ctx_with_P(P)
     P = ctx.P
     rng = np.random.default_rng(n + P)
