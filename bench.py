@@ -688,12 +688,11 @@ class DenseStep:
     def describe(self, ms, accepts, peaks_, n_sm):
         w, N = list(self.wl.widths), self.N
         f8 = self.dtype == "fp8"
-        kp = [((h + 63) // 64) * 64 for h in w]
-        gemm_row = sum(2.0 * kp[l - 1] * w[l] for l in range(1, len(w)))     # tensor-core FLOP per row (BF16 copy)
-        kp8 = [((h + 127) // 128) * 128 for h in w]
-        gemm_row_s = sum(2.0 * kp8[l - 1] * w[l] for l in range(1, len(w))) if f8 else gemm_row  # sampling copy
+        # algorithmic tensor-core FLOP per row: layers >= 1, unpadded widths (the padding of K to
+        # the tile is not counted)
+        gemm_row = sum(2.0 * w[l - 1] * w[l] for l in range(1, len(w)))
         n_conn = self.ctx.n_bonds
-        sweep_flop = gemm_row_s * self.units()
+        sweep_flop = gemm_row * self.units()
         ach = sweep_flop / (ms["sweep"] / 1e3) / 1e12
         # FP8 products: the measured sustained BF16 rate x 2 (nominal dense FP8 / BF16 ratio)
         peak = float(peaks_.get("bf16_tflops_sustained", 1400.0)) * (2.0 if f8 else 1.0)
@@ -715,7 +714,7 @@ class DenseStep:
                           "note": "whole solve (means, split, Gram, Cholesky, solves, dtheta); Gram FLOP counted "
                                   "as 6 BF16 products over the upper triangle"}} if self.lam else {}),
             "roofline": {"bound": "tensor",
-                         "kernel": ("dense_gemm_kernel (sampler steps)" if f8 or len(w) != 2 or max(w) > 448
+                         "kernel": ("dense_gemm_kernel (sampler steps)" if len(w) != 2 or max(w) > 448
                                     else "dense_fused_sweep_kernel"), "achieved": ach,
                          "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                          "note": ("FP8 (E4M3) GEMM FLOP of layers >= 2 over all proposals / sweep time, vs 2 x the "
