@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
             float2 z[FU_ROWS][7], d[FU_ROWS][7];
             float g[FU_ROWS];
             bool live[FU_ROWS];
-  #pragma unroll
+#pragma unroll
             for (int u = 0; u < FU_ROWS; ++u) {
               const int r = r0 + 8 * u;
               live[u] = r < Rv && !(st >= 0 && sm.mv[r].x < 0);  // the identity is not evaluated
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
               g[u] = live[u] ? sm.gsign[r] : 0.f;
               const float *zr = (sm.cur[live[u] ? r : r0] ? a.z0b : a.z0) + (c0 + (live[u] ? r : r0)) * a.H0;
               const float *dr = a.W1d + (int64_t)(mi < 0 ? 0 : mi) * a.H0;
-  #pragma unroll
+#pragma unroll
               for (int kb = 0; kb < 7; ++kb) {
                 const int k = kb * 64 + 2 * lane;
                 const bool in = live[u] && kb < kb_n && k < a.H0;
@@ -347,13 +347,13 @@ __global__ void __launch_bounds__(FU_THREADS, 1)
                 d[u][kb] = in && mi >= 0 ? *reinterpret_cast<const float2 *>(dr + k) : make_float2(0.f, 0.f);
               }
             }
-  #pragma unroll
+#pragma unroll
             for (int u = 0; u < FU_ROWS; ++u) {
               if (!live[u]) continue;
               const int r = r0 + 8 * u;
               const bool moved = st >= 0;
               float *zn = (sm.cur[r] ? a.z0 : a.z0b) + (c0 + r) * a.H0;  // the other buffer
-  #pragma unroll
+#pragma unroll
               for (int kb = 0; kb < 7; ++kb) {
                 if (kb >= kb_n) break;
                 const int k = kb * 64 + 2 * lane;
