@@ -506,7 +506,7 @@ class ComplexRbmStep:
         ph.mark(1)
         c.sweep(self.state, self.T, self.B, seed + 1, 0, self.samples, self.nacc)
         ph.mark(2)
-        c.local_energy(self.samples, self.eloc_re, self.eloc_im)
+        c.local_energy_chains(self.samples, self.C, self.eloc_re, self.eloc_im)
         ph.mark(3)
         c.stats(self.eloc_re, self.eloc_im, self.C, self.stats, self.nacc, self.T * self.N)
         c.logpsi_grad(self.samples, None, self.eloc_re, self.eloc_im, self.stats, self.force)

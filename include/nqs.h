@@ -422,7 +422,8 @@ void nqs_crbm_destroy(nqs_crbm *c);
 const char *nqs_crbm_last_error(const nqs_crbm *c);  /* c may be NULL: last nqs_crbm_create error */
 int64_t nqs_crbm_n_params(const nqs_crbm *c);         /* P (complex parameters) */
 int32_t nqs_crbm_words_per_config(const nqs_crbm *c); /* W = ceil(N/32) */
-/* The sampler rebuilds its per-unit cache from theta every `refresh` sweeps (default 20). */
+/* The sampler rebuilds its per-unit cache from theta every `refresh` sweeps (default 20);
+ * nqs_crbm_local_energy_chains rebuilds theta every `refresh` samples of a chain. */
 nqs_status nqs_crbm_set_refresh(nqs_crbm *c, int32_t refresh);
 
 /* params: device, P complex values as 2P doubles (re, im).  Rounded to FP32; the sampler's
@@ -449,6 +450,15 @@ nqs_status nqs_crbm_logpsi(nqs_crbm *c, const uint32_t *configs, int64_t n, floa
  * J sum_<ij> s_i s_j + h sum_i psi(flip_i x) / psi(x), FP32, two planar arrays [n]. */
 nqs_status nqs_crbm_local_energy(nqs_crbm *c, const uint32_t *configs, int64_t n, float *eloc_re, float *eloc_im,
                                  nqs_stream stream);
+
+/* nqs_crbm_local_energy of the samples nqs_crbm_sweep writes: samples [per_chain * n_chains x W],
+ * sweep-major (row k * n_chains + c), eloc_re / eloc_im the same rows.  The values are those of
+ * nqs_crbm_local_energy up to FP32 rounding: a warp walks each chain's samples in order and
+ * adds 2 s'_i W_i to theta = W s + b only for the spins that changed since the chain's
+ * previous sample (rebuilt from scratch every nqs_crbm_set_refresh samples).  With fewer than
+ * 16 chains per SM it evaluates the samples as nqs_crbm_local_energy does. */
+nqs_status nqs_crbm_local_energy_chains(nqs_crbm *c, const uint32_t *samples, int64_t n_chains, int64_t per_chain,
+                                        float *eloc_re, float *eloc_im, nqs_stream stream);
 
 /* out: device, 6 doubles.  out[0..4] = nqs_stats over eloc_re (mean, variance, chain-blocked
  * error, acceptance, n); out[5] = mean of eloc_im (zero in expectation: H is Hermitian). */

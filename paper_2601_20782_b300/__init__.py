@@ -114,6 +114,7 @@ _SIGS = {
     "nqs_crbm_sweep": (_i32, [_vp, _vp, _i64, _i32, _i32, _u64, _u32, _vp, _vp, _vp, _vp]),
     "nqs_crbm_logpsi": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "nqs_crbm_local_energy": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    "nqs_crbm_local_energy_chains": (_i32, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "nqs_crbm_stats": (_i32, [_vp, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _vp]),
     "nqs_crbm_logpsi_grad": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nqs_crbm_check_status": (_i32, [_vp, _vp]),
@@ -527,6 +528,16 @@ class ComplexContext:
         n = configs.shape[0]
         self._check(_lib.nqs_crbm_local_energy(
             self._h, _ptr(configs, _WORD, "configs", (n, self.W), False), n,
+            _ptr(eloc_re, (torch.float32,), "eloc_re", (n,), False),
+            _ptr(eloc_im, (torch.float32,), "eloc_im", (n,), False), _stream()))
+
+    def local_energy_chains(self, samples, n_chains, eloc_re, eloc_im):
+        """nqs_crbm_local_energy_chains: eloc of sweep-major samples of n_chains chains."""
+        n = samples.shape[0]
+        if n % n_chains:
+            raise ValueError("samples rows must be a multiple of n_chains")
+        self._check(_lib.nqs_crbm_local_energy_chains(
+            self._h, _ptr(samples, _WORD, "samples", (n, self.W), False), n_chains, n // n_chains,
             _ptr(eloc_re, (torch.float32,), "eloc_re", (n,), False),
             _ptr(eloc_im, (torch.float32,), "eloc_im", (n,), False), _stream()))
 

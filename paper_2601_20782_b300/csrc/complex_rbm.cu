@@ -273,6 +273,8 @@ struct CElocArgs {
   const int2 *nb;
   float J, h;
   float *eloc_re, *eloc_im;
+  int64_t n_chains;  // CHAIN: rows k C + c of chain c, k < r.n / n_chains (sweep-major samples)
+  int refresh;       // CHAIN: theta rebuilt from scratch every `refresh` samples of a chain
 };
 
 // |p| pulled into the log2 accumulator L; a zero product marks the ratio as zero.
@@ -293,21 +295,83 @@ __device__ __forceinline__ void crbm_normalise(float2 &p, float &L, bool &dead) 
 // tanh theta of every sample into the warp's shared-memory slice.  Phase 2 (lanes over
 // sites): the flip ratio of site i as a product over all units, read from the unit-major
 // (cosh 2W, sinh 2W) table once for the CR_SPW samples.
-template <int KU>
+// CHAIN: a warp walks one chain's sweep-major samples in order, CR_SPW at a time, and keeps
+// theta in registers from one sample to the next: it adds 2 s'_i W_i only for the spins that
+// changed since the chain's previous sample (theta rebuilt from scratch every `refresh`
+// samples).  Phase 2 is the same.
+template <int KU, bool CHAIN>
 __global__ void __launch_bounds__(CR_THREADS, 4) crbm_eloc_kernel(const CElocArgs a) {
   extern __shared__ float2 crbm_tanh[];  // [warps][CR_SPW][M_pad]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int M_pad = a.r.M_pad, N = a.r.N, W = a.r.W;
   float2 *tw = crbm_tanh + (size_t)warp * CR_SPW * M_pad;
+  const int64_t gw = (blockIdx.x * (int64_t)CR_THREADS + threadIdx.x) >> 5;  // global warp
   const int64_t nw = ((int64_t)gridDim.x * CR_THREADS) >> 5;
-  for (int64_t x0 = ((blockIdx.x * (int64_t)CR_THREADS + threadIdx.x) >> 5) * CR_SPW; x0 < a.r.n;
-       x0 += nw * CR_SPW) {
+  // work items: groups of CR_SPW rows (grid-stride), or (CHAIN) the blocks of chain gw in order
+  const int64_t K = CHAIN ? a.r.n / a.n_chains : 0;
+  const int64_t n_items = CHAIN ? (gw < a.n_chains ? (K + CR_SPW - 1) / CR_SPW : 0) : (a.r.n + CR_SPW - 1) / CR_SPW;
+  float cx[CHAIN ? KU : 1], cy[CHAIN ? KU : 1];  // CHAIN: the chain's theta after its previous sample
+  uint32_t prev = 0u;                            // CHAIN: the word of that sample held by this lane
+  for (int64_t it = CHAIN ? 0 : gw; it < n_items; it += CHAIN ? 1 : nw) {
     uint32_t wr[CR_SPW];
+    int64_t xr[CR_SPW];  // output row of sample r (clamped), valid when vr[r]
+    bool vr[CR_SPW];
 #pragma unroll
     for (int r = 0; r < CR_SPW; ++r) {
-      const int64_t x = std::min<int64_t>(x0 + r, a.r.n - 1);
-      wr[r] = lane < W ? a.r.cfg[x * W + lane] : 0u;
+      const int64_t q = it * CR_SPW + r;
+      if constexpr (CHAIN) {
+        vr[r] = q < K;
+        xr[r] = std::min<int64_t>(q, K - 1) * a.n_chains + gw;
+      } else {
+        vr[r] = q < a.r.n;
+        xr[r] = std::min<int64_t>(q, a.r.n - 1);
+      }
+      wr[r] = lane < W ? a.r.cfg[xr[r] * W + lane] : 0u;
     }
+    if constexpr (CHAIN) {
+#pragma unroll
+      for (int r = 0; r < CR_SPW; ++r) {
+        const int64_t k = std::min<int64_t>(it * CR_SPW + r, K - 1);
+        if (k % a.refresh == 0) {  // from scratch: b + sum_i s_i W_i
+#pragma unroll
+          for (int u = 0; u < KU; ++u) {
+            const float2 bj = a.r.b[lane + 32 * u];
+            cx[u] = bj.x;
+            cy[u] = bj.y;
+          }
+          for (int i = 0; i < N; ++i) {
+            const float si = spin_of(__shfl_sync(FULL_MASK, wr[r], i >> 5), i & 31);
+            const float2 *row = a.r.Wt + (int64_t)i * M_pad + lane;
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+              const float2 w = __ldg(row + 32 * u);
+              cx[u] = fmaf(si, w.x, cx[u]);
+              cy[u] = fmaf(si, w.y, cy[u]);
+            }
+          }
+        } else {  // the spins changed since the previous sample: theta += 2 s'_i W_i
+          for (int wi = 0; wi < W; ++wi) {
+            uint32_t m = __shfl_sync(FULL_MASK, wr[r] ^ prev, wi);
+            const uint32_t now = __shfl_sync(FULL_MASK, wr[r], wi);
+            while (m) {  // warp-uniform
+              const int bit = __ffs(m) - 1;
+              m &= m - 1u;
+              const float s2 = ((now >> bit) & 1u) ? 2.f : -2.f;
+              const float2 *row = a.r.Wt + (int64_t)(32 * wi + bit) * M_pad + lane;
+#pragma unroll
+              for (int u = 0; u < KU; ++u) {
+                const float2 w = __ldg(row + 32 * u);
+                cx[u] = fmaf(s2, w.x, cx[u]);
+                cy[u] = fmaf(s2, w.y, cy[u]);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < KU; ++u) tw[r * M_pad + lane + 32 * u] = tanh_c(cx[u], cy[u]);
+        prev = wr[r];
+      }
+    } else {
     // theta of two samples at a time: each weight row is loaded once for both
 #pragma unroll
     for (int r = 0; r < CR_SPW; r += 2) {
@@ -336,6 +400,7 @@ __global__ void __launch_bounds__(CR_THREADS, 4) crbm_eloc_kernel(const CElocArg
         tw[r * M_pad + lane + 32 * k] = tanh_c(tx0[k], ty0[k]);
         tw[(r + 1) * M_pad + lane + 32 * k] = tanh_c(tx1[k], ty1[k]);
       }
+    }
     }
     __syncwarp();
     float er[CR_SPW], ei[CR_SPW];
@@ -491,10 +556,10 @@ __global__ void __launch_bounds__(CR_THREADS, 4) crbm_eloc_kernel(const CElocArg
     }
 #pragma unroll
     for (int r = 0; r < CR_SPW; ++r) {
-      const float vr = group_allsum<32>(er[r]), vi = group_allsum<32>(ei[r]);
-      if (lane == 0 && x0 + r < a.r.n) {
-        a.eloc_re[x0 + r] = vr;
-        a.eloc_im[x0 + r] = vi;
+      const float sre = group_allsum<32>(er[r]), sim = group_allsum<32>(ei[r]);
+      if (lane == 0 && vr[r]) {
+        a.eloc_re[xr[r]] = sre;
+        a.eloc_im[xr[r]] = sim;
       }
     }
     __syncwarp();
@@ -675,12 +740,16 @@ cudaError_t launch_sweep(const nqs_crbm *c, const CSweepArgs &a, cudaStream_t s)
 template <int KU>
 cudaError_t launch_eloc(const nqs_crbm *c, const CElocArgs &a, cudaStream_t s) {
   const size_t smem = (size_t)(CR_THREADS / 32) * CR_SPW * c->M_pad * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(crbm_eloc_kernel<KU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const bool chain = a.n_chains > 0;
+  auto k = chain ? crbm_eloc_kernel<KU, true> : crbm_eloc_kernel<KU, false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t warps = (a.r.n + CR_SPW - 1) / CR_SPW;
-  const int64_t blocks = std::max<int64_t>(
-      1, std::min<int64_t>((warps * 32 + CR_THREADS - 1) / CR_THREADS, (int64_t)c->base.num_sms * 8));
-  crbm_eloc_kernel<KU><<<(unsigned)blocks, CR_THREADS, smem, s>>>(a);
+  // a warp per chain (CHAIN), else grid-stride warps over groups of CR_SPW rows
+  const int64_t warps = chain ? a.n_chains : (a.r.n + CR_SPW - 1) / CR_SPW;
+  const int64_t blocks = std::max<int64_t>(1, chain ? (warps * 32 + CR_THREADS - 1) / CR_THREADS
+                                                    : std::min<int64_t>((warps * 32 + CR_THREADS - 1) / CR_THREADS,
+                                                                        (int64_t)c->base.num_sms * 8));
+  k<<<(unsigned)blocks, CR_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -923,8 +992,36 @@ nqs_status nqs_crbm_local_energy(nqs_crbm *c, const uint32_t *cfg, int64_t n, fl
   a.h = (float)c->h;
   a.eloc_re = eloc_re;
   a.eloc_im = eloc_im;
+  a.n_chains = 0;
+  a.refresh = c->refresh;
   cudaError_t e = dispatch_eloc(c, a, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? NQS_OK : ccuda(c, e, "nqs_crbm_local_energy");
+}
+
+nqs_status nqs_crbm_local_energy_chains(nqs_crbm *c, const uint32_t *samples, int64_t n_chains, int64_t per_chain,
+                                        float *eloc_re, float *eloc_im, nqs_stream stream) {
+  using namespace nqs;
+  if (!c) return NQS_EINVAL;
+  if (!c->params_set) return cfail(c, NQS_EINVAL, "nqs_crbm_local_energy_chains: parameters not set");
+  if (n_chains < 0 || per_chain < 0) return cfail(c, NQS_EINVAL, "nqs_crbm_local_energy_chains: negative size");
+  if (n_chains == 0 || per_chain == 0) return NQS_OK;
+  if (!samples || !eloc_re || !eloc_im) return cfail(c, NQS_EINVAL, "nqs_crbm_local_energy_chains: null argument");
+  // a warp per chain: with fewer than 16 chains per SM that leaves the GPU mostly idle, so the
+  // per-sample evaluation (the same values to FP32 rounding) is used
+  if (n_chains < (int64_t)c->base.num_sms * 16)
+    return nqs_crbm_local_energy(c, samples, n_chains * per_chain, eloc_re, eloc_im, stream);
+  CElocArgs a;
+  a.r = row_args(c, samples, n_chains * per_chain);
+  a.et = c->d_et;
+  a.nb = c->d_nb;
+  a.J = (float)c->J;
+  a.h = (float)c->h;
+  a.eloc_re = eloc_re;
+  a.eloc_im = eloc_im;
+  a.n_chains = n_chains;
+  a.refresh = c->refresh;
+  cudaError_t e = dispatch_eloc(c, a, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? NQS_OK : ccuda(c, e, "nqs_crbm_local_energy_chains");
 }
 
 nqs_status nqs_crbm_stats(nqs_crbm *c, const float *eloc_re, const float *eloc_im, int64_t n, int64_t n_chains,

@@ -85,6 +85,45 @@ def test_local_energy_matches_oracle(Lx, Ly, M, sigma, n):
     assert not bad.any(), (np.flatnonzero(bad), got[bad], ref[bad], kappa[bad])
 
 
+@pytest.mark.parametrize("C,refresh", [(4096, 5), (4096, 20), (100, 5)])
+def test_local_energy_chains_matches_per_sample(C, refresh):
+    """nqs_crbm_local_energy_chains on the sweep-major samples of nqs_crbm_sweep (10 x 10,
+    M = 400): the chain-ordered theta updates (rebuilt every `refresh` samples, inside and
+    across the warp's blocks of four; 11 samples per chain, a ragged last block) give the
+    per-sample values to FP32 rounding, with the same pole widening as against the oracle; a
+    subset is also held to the oracle.  100 chains (fewer than 16 per SM) take the per-sample
+    path and match it exactly."""
+    c, _, model, ham = make(10, 10, 400, 0.04, 21, h=-0.9)
+    c.set_refresh(refresh)
+    N, W, T, B = 100, 4, 12, 1
+    st = torch.zeros((C, W), dtype=torch.int32, device="cuda")
+    c.init_chains(st, 31)
+    samples = torch.zeros(((T - B) * C, W), dtype=torch.int32, device="cuda")
+    c.sweep(st, T, B, 32, 0, samples)
+    n = samples.shape[0]
+    re1, im1 = torch.zeros(n, dtype=torch.float32, device="cuda"), torch.zeros(n, dtype=torch.float32, device="cuda")
+    re2, im2 = torch.zeros_like(re1), torch.zeros_like(re1)
+    c.local_energy(samples, re1, im1)
+    c.local_energy_chains(samples, C, re2, im2)
+    c.check_status()
+    if C < 2368:
+        assert torch.equal(re1, re2) and torch.equal(im1, im2)
+        return
+    a = re1.cpu().numpy().astype(np.float64) + 1j * im1.cpu().numpy().astype(np.float64)
+    b = re2.cpu().numpy().astype(np.float64) + 1j * im2.cpu().numpy().astype(np.float64)
+    s = unpack_np(words_from_tensor(samples), N)
+    kappa = (1.0 / np.abs(np.cosh(model.theta(s))) ** 2).max(axis=1)
+    scale = len(ham.bonds) + N * abs(ham.h)
+    rtol = 1e-4 + 8 * 2.0 ** -24 * kappa
+    bad = np.abs(a - b) > rtol * np.abs(a) + 2e-5 * scale
+    assert not bad.any(), (np.flatnonzero(bad)[:8], a[bad][:8], b[bad][:8])
+    assert np.abs(a - b).max() > 0 or refresh == 1   # the incremental path ran (not the per-sample one)
+    sub = np.random.default_rng(3).choice(n, 64, replace=False)
+    ref = local_energy_tfim(ham, model, s[sub])
+    bad = np.abs(b[sub] - ref) > rtol[sub] * np.abs(ref) + 2e-5 * scale
+    assert not bad.any(), (sub[bad], b[sub][bad], ref[bad])
+
+
 @pytest.mark.parametrize("refresh,sigma,strict", [(1, 0.3, True), (20, 0.1, True), (20, 0.3, False)])
 def test_sweep_replays_in_the_oracle(refresh, sigma, strict):
     Lx, Ly, M = 4, 4, 24
