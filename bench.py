@@ -854,6 +854,63 @@ def run_noisy_study(args, rank, world):
     }
 
 
+def run_rescnn_study(args, rank, world):
+    """App. H sampling study of the ResCNN (4 blocks x 16 filters, 3 x 3) on the 4 x 4 TFIM: the
+    sweep's proposals/s for the FP32, BF16 and F16 copies against the number of chains N_s,
+    and the 16-bit copies' speed-up over FP32.  The kernels have 16 channels, so the filter
+    count is not varied."""
+    import torch
+    import paper_2601_20782_b300 as nqs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    wl = workloads.RESCNN_2D_10x10
+    lat = wl.extra["small_case"]
+    F, nb = wl.extra["filters"], wl.extra["blocks"]
+    T = args.sweeps or 10
+    params = torch.from_numpy(workloads.rescnn_params(F, nb, wl.seed)).to(dev)
+    counts = [256, 1024, 4096, 16384, 65536] if not args.chains else [args.chains]
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    rows = []
+    with ClockSampler(dev.index) as clk:
+        for C in counts:
+            row = {"chains": C}
+            for dt in ("f32", "bf16", "f16"):
+                ctx = nqs.Context("tfim", lat.Lx, lat.Ly, J1=wl.ham.J1, h=wl.ham.h, model="rescnn", n_hidden=F,
+                                  n_blocks=nb, dtype=dt)
+                ctx.set_params(params)
+                state = torch.zeros((C, ctx.W), dtype=torch.int32, device=dev)
+                nacc = torch.zeros(C, dtype=torch.int64, device=dev)
+                times = []
+                for k in range(args.warmup + args.steps):
+                    flush.zero_()
+                    ctx.init_chains(state, wl.seed + 7)
+                    torch.cuda.synchronize()
+                    ev[0].record()
+                    ctx.sweep(state, T, T, wl.seed + 8, 0, None, None, nacc)
+                    ev[1].record()
+                    torch.cuda.synchronize()
+                    if k >= args.warmup:
+                        times.append(ev[0].elapsed_time(ev[1]))
+                row[dt] = C * T * lat.n_sites / (statistics.median(times) / 1e3)
+            row["speedup_bf16"] = row["bf16"] / row["f32"]
+            row["speedup_f16"] = row["f16"] / row["f32"]
+            rows.append(row)
+    top = rows[-1]
+    return {
+        "metric": METRIC, "value": top["f16"], "unit": "proposals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": top["chains"] * T * lat.n_sites / top["f16"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16 (convolutions on tcgen05, FP32 accumulation; FP32 and BF16 beside it)",
+        "data": "synthetic (seeded random-init ResCNN, random initial spins)",
+        "config": {"workload": "rescnn_tfim2d_4x4_4blocks_16filters_study", "lattice": "4x4 periodic",
+                   "filters": F, "blocks": nb, "sweeps": T, "chains": counts,
+                   "l2": "flushed between timed sweeps (256 MiB write)", "parallelism": "dp1 (chains)"},
+        "note": "value: F16 sweep proposals/s at the largest chain count; the study is in `rescnn_study`",
+        "rescnn_study": rows, "roofline": None, "clocks": clk.summary(),
+    }
+
+
 def run_workload(args, rank, world, dist):
     import torch
     import paper_2601_20782_b300 as nqs
@@ -1078,7 +1135,8 @@ def main():
     ap.add_argument("--chains-per-warp", type=int, default=0, choices=[0, 1, 2],
                     help="profiling only (tfim2d): RBM sweep chains per warp of the FP32 copy (0: built-in rule)")
     ap.add_argument("--workload", default="tfim2d", choices=["tfim2d", "tfim1d", "heis2d-dense", "batched",
-                                                             "j1j2-dense", "noisy-rbm", "crbm-tfim2d", "rescnn-tfim2d"],
+                                                             "j1j2-dense", "noisy-rbm", "crbm-tfim2d", "rescnn-tfim2d",
+                                                             "rescnn-study"],
                     help="tfim2d: the 10x10 alpha=4 RBM workload (default); the others measure the other "
                          "workloads' steps with the same line")
     args = ap.parse_args()
@@ -1102,6 +1160,10 @@ def main():
     if args.workload == "noisy-rbm":
         if rank == 0:
             print(json.dumps(run_noisy_study(args, rank, world)), flush=True)
+        return
+    if args.workload == "rescnn-study":
+        if rank == 0:
+            print(json.dumps(run_rescnn_study(args, rank, world)), flush=True)
         return
     if args.workload != "tfim2d":
         line = run_workload(args, rank, world, dist)
