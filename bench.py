@@ -854,6 +854,68 @@ def run_noisy_study(args, rank, world):
     }
 
 
+def run_rbm_grid(args, rank, world):
+    """The sampling grid of Sec. 4.2 (Fig. 4) on the 10 x 10 TFIM RBM: sweep proposals/s of the
+    FP32, BF16 and F16 copies against the number of samples N_s (N_s / 4 chains, four kept
+    samples per chain after four burn-in sweeps) and the hidden-unit density alpha, and the
+    16-bit copies' ratio to FP32 (the paper's ratios are to an FP64 copy, which is not built)."""
+    import torch
+    import paper_2601_20782_b300 as nqs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    lat = WL.ham.lattice
+    N = lat.n_sites
+    T, B = 8, 4
+    alphas = [1, 2, 4, 8]
+    n_samples = [4 * 1024, 4 * 4096, 4 * 16384, 4 * 65536] if not args.chains else [4 * args.chains]
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    rows = []
+    with ClockSampler(dev.index) as clk:
+        for alpha in alphas:
+            M = alpha * N
+            params = torch.from_numpy(workloads.rbm_params(N, M, WL.weight_sigma, WL.seed)).to(dev)
+            ctxs = {}
+            for dt in ("f32", "bf16", "f16"):
+                ctxs[dt] = nqs.Context("tfim", lat.Lx, lat.Ly, J1=WL.ham.J1, h=WL.ham.h, model="rbm", n_hidden=M,
+                                       dtype=dt)
+                ctxs[dt].set_params(params)
+            for ns in n_samples:
+                C = ns // 4
+                row = {"alpha": alpha, "n_samples": ns, "chains": C}
+                for dt, ctx in ctxs.items():
+                    state = torch.zeros((C, ctx.W), dtype=torch.int32, device=dev)
+                    samples = torch.zeros(((T - B) * C, ctx.W), dtype=torch.int32, device=dev)
+                    times = []
+                    for k in range(args.warmup + args.steps):
+                        flush.zero_()
+                        ctx.init_chains(state, WL.seed + 7)
+                        torch.cuda.synchronize()
+                        ev[0].record()
+                        ctx.sweep(state, T, B, WL.seed + 8, 0, samples)
+                        ev[1].record()
+                        torch.cuda.synchronize()
+                        if k >= args.warmup:
+                            times.append(ev[0].elapsed_time(ev[1]))
+                    row[dt] = C * T * N / (statistics.median(times) / 1e3)
+                row["bf16_over_f32"] = row["bf16"] / row["f32"]
+                row["f16_over_f32"] = row["f16"] / row["f32"]
+                rows.append(row)
+    top = max(rows, key=lambda r: r["f16"])
+    return {
+        "metric": METRIC, "value": top["f16"], "unit": "proposals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": top["chains"] * T * N / top["f16"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16 sampling (f32 caches, accept); FP32 and BF16 beside it",
+        "data": "synthetic (seeded random-init RBMs, random initial spins)",
+        "config": {"workload": "tfim2d_10x10_rbm_grid", "lattice": "10x10 periodic", "h": WL.ham.h,
+                   "alphas": alphas, "n_samples": n_samples, "samples_per_chain": T - B, "sweeps": T, "burn_in": B,
+                   "l2": "flushed between timed sweeps (256 MiB write)", "parallelism": "dp1 (chains)"},
+        "note": "value: the largest F16 sweep rate of the grid; the grid is in `rbm_grid`",
+        "rbm_grid": rows, "roofline": None, "clocks": clk.summary(),
+    }
+
+
 def run_rescnn_study(args, rank, world):
     """App. H sampling study of the ResCNN (4 blocks x 16 filters, 3 x 3) on the 4 x 4 TFIM: the
     sweep's proposals/s for the FP32, BF16 and F16 copies against the number of chains N_s,
@@ -1136,7 +1198,7 @@ def main():
                     help="profiling only (tfim2d): RBM sweep chains per warp of the FP32 copy (0: built-in rule)")
     ap.add_argument("--workload", default="tfim2d", choices=["tfim2d", "tfim1d", "heis2d-dense", "batched",
                                                              "j1j2-dense", "noisy-rbm", "crbm-tfim2d", "rescnn-tfim2d",
-                                                             "rescnn-study"],
+                                                             "rescnn-study", "rbm-grid"],
                     help="tfim2d: the 10x10 alpha=4 RBM workload (default); the others measure the other "
                          "workloads' steps with the same line")
     args = ap.parse_args()
@@ -1164,6 +1226,10 @@ def main():
     if args.workload == "rescnn-study":
         if rank == 0:
             print(json.dumps(run_rescnn_study(args, rank, world)), flush=True)
+        return
+    if args.workload == "rbm-grid":
+        if rank == 0:
+            print(json.dumps(run_rbm_grid(args, rank, world)), flush=True)
         return
     if args.workload != "tfim2d":
         line = run_workload(args, rank, world, dist)
