@@ -916,6 +916,57 @@ def run_rbm_grid(args, rank, world):
     }
 
 
+def run_delta_study(args, rank, world):
+    """App. D (the random-state panel of its sigma(delta) figure): the spread of
+    delta(x) = log |psi~(x)|^2 - log |psi(x)|^2 of the BF16 and F16 RBM copies against the chain
+    length N, for a randomly initialised RBM with alpha = 1 (weights N(0, 0.1^2)) on 1D TFIM
+    chains, over uniform random configurations (the flat distribution such a state is close to);
+    log psi through nqs_logpsi of each copy, the FP32 context as the reference (its own error is
+    about 1e-6, far below the 16-bit copies')."""
+    import torch
+    import paper_2601_20782_b300 as nqs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    sizes = [16, 32, 64, 128, 256]
+    n = args.chains or 65536
+    g = torch.Generator(device=dev).manual_seed(WL.seed + 9)
+    rows = []
+    with ClockSampler(dev.index) as clk:
+        for N in sizes:
+            params = torch.from_numpy(workloads.rbm_params(N, N, 0.1, WL.seed + N)).to(dev)
+            lp = {}
+            for dt in ("f32", "bf16", "f16"):
+                ctx = nqs.Context("tfim", N, 1, J1=1.0, h=1.0, model="rbm", n_hidden=N, dtype=dt)
+                ctx.set_params(params)
+                if dt == "f32":  # uniform configurations: random words, bits beyond N cleared
+                    W = ctx.W
+                    cfg = torch.randint(-2 ** 31, 2 ** 31, (n, W), generator=g, device=dev, dtype=torch.int64)
+                    cfg = cfg.to(torch.int32)
+                    last = N - 32 * (W - 1)
+                    if last < 32:
+                        cfg[:, W - 1] &= (1 << last) - 1
+                out = torch.empty(n, dtype=torch.float32, device=dev)
+                ctx.logpsi(cfg, out)
+                lp[dt] = out.double()
+            row = {"N": N, "alpha": 1}
+            for dt in ("bf16", "f16"):
+                d = 2.0 * (lp[dt] - lp["f32"])
+                sd = float(d.std())
+                row["sigma_delta_" + dt] = sd
+                row["pinsker_tv_bound_" + dt] = sd / 2
+            rows.append(row)
+    return {
+        "metric": METRIC, "value": None, "unit": "proposals/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 and f16 RBM copies against the fp32 context",
+        "data": "synthetic (seeded random-init RBMs, uniform random configurations)",
+        "config": {"workload": "tfim1d_rbm_a1_delta_study", "sizes": sizes, "configurations": n,
+                   "weight_sigma": 0.1, "parallelism": "dp1"},
+        "note": "the study is in `delta_study` (sigma of delta per copy against N); no rate is measured",
+        "delta_study": rows, "roofline": None, "clocks": clk.summary(),
+    }
+
+
 def run_rescnn_study(args, rank, world):
     """App. H sampling study of the ResCNN (4 blocks x 16 filters, 3 x 3) on the 4 x 4 TFIM: the
     sweep's proposals/s for the FP32, BF16 and F16 copies against the number of chains N_s,
@@ -1198,7 +1249,7 @@ def main():
                     help="profiling only (tfim2d): RBM sweep chains per warp of the FP32 copy (0: built-in rule)")
     ap.add_argument("--workload", default="tfim2d", choices=["tfim2d", "tfim1d", "heis2d-dense", "batched",
                                                              "j1j2-dense", "noisy-rbm", "crbm-tfim2d", "rescnn-tfim2d",
-                                                             "rescnn-study", "rbm-grid"],
+                                                             "rescnn-study", "rbm-grid", "delta-study"],
                     help="tfim2d: the 10x10 alpha=4 RBM workload (default); the others measure the other "
                          "workloads' steps with the same line")
     args = ap.parse_args()
@@ -1230,6 +1281,10 @@ def main():
     if args.workload == "rbm-grid":
         if rank == 0:
             print(json.dumps(run_rbm_grid(args, rank, world)), flush=True)
+        return
+    if args.workload == "delta-study":
+        if rank == 0:
+            print(json.dumps(run_delta_study(args, rank, world)), flush=True)
         return
     if args.workload != "tfim2d":
         line = run_workload(args, rank, world, dist)
