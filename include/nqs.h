@@ -90,6 +90,10 @@ typedef struct {
  * in its tanh form.  Two-dimensional TFIM (Ly >= 3, N <= 512).  Parameter vector
  *   [K0 (16 x 1 x 3 x 3) | b0 | per block: gamma | beta | K1 (16 x 16 x 3 x 3) | b1 | K2 | b2 |
  *    final gamma | final beta]   (K[co][ci][dy][dx]; P = 192 + 4672 n_layers).
+ * nqs_logpsi_grad / nqs_force_share of a ResCNN context: FP32 reverse pass on the CUDA cores
+ * from the FP32 rounding of the master, one CTA per configuration; needs no workspace;
+ * NQS_EUNSUPPORTED when the residual streams of one configuration ((n_layers + 1) N 16 floats
+ * beside the parameters) exceed shared memory.
  * Sampling copy F32 (CUDA cores), or BF16 / F16 with the convolutions as tcgen05 products:
  * kernels and the activations entering a convolution in the 16-bit type, biases, LN, the
  * residual stream, accumulation and the final sum in FP32; nqs_logpsi and nqs_local_energy

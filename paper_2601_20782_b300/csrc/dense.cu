@@ -1021,7 +1021,7 @@ cudaError_t dense_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swee
   return launch_propose(c, a, s);
 }
 
-static cudaError_t force_rows(const nqs_ctx *c, const float *O, int64_t rows, const float *eloc, const double *stats,
+cudaError_t force_rows(const nqs_ctx *c, const float *O, int64_t rows, const float *eloc, const double *stats,
                               int64_t n_total, bool share, int accumulate, double *force, cudaStream_t s) {
   double *part = reinterpret_cast<double *>(c->d_force_part);
   dense_force_part_kernel<<<dim3((unsigned)((c->P + 255) / 256), FORCE_SLICES), 256, 0, s>>>(O, rows, c->P, eloc, stats,

@@ -182,6 +182,14 @@ void rescnn_free(nqs_ctx *c);
 cudaError_t rescnn_prepare(nqs_ctx *c, const double *params, cudaStream_t s);
 cudaError_t rescnn_logpsi(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *out, cudaStream_t s);
 cudaError_t rescnn_local_energy(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *eloc, cudaStream_t s);
+// O rows (and the force) of the ResCNN from the FP32 copy; n_rows_max: rows of O per launch without O
+bool rescnn_grad_supported(const nqs_ctx *c);
+cudaError_t rescnn_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
+                               const double *stats, double *force, cudaStream_t s, bool share = false);
+// F_k (+)= sum_x O[x][k] (eloc[x] - E) / n over rows of O [rows x P] (fixed-order FP64 sums; the
+// context's d_force_part holds the partials); share: divide by stats[4] (multi-rank step)
+cudaError_t force_rows(const nqs_ctx *c, const float *O, int64_t rows, const float *eloc, const double *stats,
+                       int64_t n_total, bool share, int accumulate, double *force, cudaStream_t s);
 cudaError_t rescnn_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_sweeps, int burn_in, uint64_t seed,
                          uint32_t sweep_offset, uint32_t *samples, float *logpsi, int64_t *n_acc, uint32_t *acc_bits,
                          float *delta, cudaStream_t s);

@@ -353,7 +353,8 @@ nqs_status nqs_logpsi_grad(nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O,
                            const double *stats, double *force, void *ws, size_t ws_bytes, nqs_stream stream) {
   if (!c) return NQS_EINVAL;
   if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_logpsi_grad: parameters not set");
-  if (c->model_kind == NQS_RESCNN) return fail(c, NQS_EUNSUPPORTED, "nqs_logpsi_grad: not built for the ResCNN");
+  if (c->model_kind == NQS_RESCNN && !nqs::rescnn_grad_supported(c))
+    return fail(c, NQS_EUNSUPPORTED, "nqs_logpsi_grad: this ResCNN's residual streams exceed shared memory");
   if (n < 0 || (n > 0 && bad_ptr(cfg))) return fail(c, NQS_EINVAL, "nqs_logpsi_grad: bad arguments");
   if (force && n > 0 && (bad_ptr(eloc) || bad_ptr(stats)))
     return fail(c, NQS_EINVAL, "nqs_logpsi_grad: the force needs eloc and stats");
@@ -366,10 +367,10 @@ nqs_status nqs_logpsi_grad(nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O,
     }
     return NQS_OK;
   }
-  cudaError_t e =
-      c->model_kind == NQS_DENSE
-          ? nqs::dense_logpsi_grad(c, cfg, n, O, eloc, stats, force, reinterpret_cast<cudaStream_t>(stream))
-          : nqs::rbm_logpsi_grad(c, cfg, n, O, eloc, stats, force, ws, reinterpret_cast<cudaStream_t>(stream));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = c->model_kind == NQS_DENSE    ? nqs::dense_logpsi_grad(c, cfg, n, O, eloc, stats, force, st)
+                  : c->model_kind == NQS_RESCNN ? nqs::rescnn_logpsi_grad(c, cfg, n, O, eloc, stats, force, st)
+                                                : nqs::rbm_logpsi_grad(c, cfg, n, O, eloc, stats, force, ws, st);
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_logpsi_grad");
 }
 
@@ -406,7 +407,8 @@ nqs_status nqs_force_share(nqs_ctx *c, const uint32_t *cfg, int64_t n, const flo
                            double *force, void *ws, size_t ws_bytes, nqs_stream stream) {
   if (!c) return NQS_EINVAL;
   if (!c->params_set) return fail(c, NQS_EINVAL, "nqs_force_share: parameters not set");
-  if (c->model_kind == NQS_RESCNN) return fail(c, NQS_EUNSUPPORTED, "nqs_force_share: not built for the ResCNN");
+  if (c->model_kind == NQS_RESCNN && !nqs::rescnn_grad_supported(c))
+    return fail(c, NQS_EUNSUPPORTED, "nqs_force_share: this ResCNN's residual streams exceed shared memory");
   if (n < 0 || bad_ptr(force) || (n > 0 && (bad_ptr(cfg) || bad_ptr(eloc) || bad_ptr(stats))))
     return fail(c, NQS_EINVAL, "nqs_force_share: bad arguments");
   if (n > 0 && c->model_kind == NQS_RBM && (bad_ptr(ws) || ws_bytes < nqs::rbm_grad_workspace(c, n)))
@@ -416,9 +418,9 @@ nqs_status nqs_force_share(nqs_ctx *c, const uint32_t *cfg, int64_t n, const flo
     cudaError_t e = cudaMemsetAsync(force, 0, (size_t)c->P * sizeof(double), s);
     return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_force_share");
   }
-  cudaError_t e = c->model_kind == NQS_DENSE
-                      ? nqs::dense_logpsi_grad(c, cfg, n, nullptr, eloc, stats, force, s, true)
-                      : nqs::rbm_logpsi_grad(c, cfg, n, nullptr, eloc, stats, force, ws, s, true);
+  cudaError_t e = c->model_kind == NQS_DENSE    ? nqs::dense_logpsi_grad(c, cfg, n, nullptr, eloc, stats, force, s, true)
+                  : c->model_kind == NQS_RESCNN ? nqs::rescnn_logpsi_grad(c, cfg, n, nullptr, eloc, stats, force, s, true)
+                                                : nqs::rbm_logpsi_grad(c, cfg, n, nullptr, eloc, stats, force, ws, s, true);
   return e == cudaSuccess ? NQS_OK : cuda_fail(c, e, "nqs_force_share");
 }
 

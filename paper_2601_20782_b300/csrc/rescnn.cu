@@ -378,6 +378,289 @@ size_t smem_bytes_f32(int P, int rows, int G, int N) {
   return f * sizeof(float);
 }
 
+// ---- O_k = d log psi / d theta_k (App. I, Eq. forces), FP32 ----------------------------------
+// One CTA per configuration, thread = site.  The forward pass keeps the residual streams
+// h(0) .. h(B) in shared memory; the backward pass takes the blocks from the last, recomputing
+// each block's LN, GELU and first convolution from its h(l), and writes the row of O in the
+// master order ([co][ci][dy][dx] kernels).  With g = d log psi / d(.):
+//   final LN: d gamma_F = sum_sites zhat, d beta_F = N, g_h = LN'(1);
+//   block l (h' = h + Conv2(c), c = GELU(z1), z1 = Conv1(a), a = GELU(y), y = LN(h)):
+//     dK2 = sum_sites c(nb) g_h', db2 = sum g_h', g_c = Conv2^T(g_h'), g_z1 = g_c GELU'(z1),
+//     dK1 = sum_sites a(nb) g_z1, db1 = sum g_z1, g_a = Conv1^T(g_z1), g_y = g_a GELU'(y),
+//     d gamma = sum g_y zhat, d beta = sum g_y, g_h = g_h' + LN'(g_y);
+//   embedding: dK0 = sum_sites s(nb) g_h(0), db0 = sum g_h(0).
+// Conv^T reads the neighbour at the opposite offset (tap 8 - t) with K[t] transposed.
+
+__device__ __forceinline__ float gelu_grad_f32(float z) {
+  const float u = GELU_C * fmaf(0.044715f * z * z, z, z);
+  const float t = tanhf(u);
+  return fmaf(0.5f, 1.f + t, 0.5f * z * (1.f - t * t) * GELU_C * fmaf(3.f * 0.044715f, z * z, 1.f));
+}
+
+// LN of one site's 16 channels: zhat and 1 / sqrt(var + eps)
+__device__ __forceinline__ void ln_stats16(const float (&v)[CF], float (&zh)[CF], float &rs) {
+  float m = 0.f;
+#pragma unroll
+  for (int c = 0; c < CF; ++c) m += v[c];
+  m *= 1.f / CF;
+  float var = 0.f;
+#pragma unroll
+  for (int c = 0; c < CF; ++c) var = fmaf(v[c] - m, v[c] - m, var);
+  rs = rsqrtf(fmaf(var, 1.f / CF, LN_EPS));
+#pragma unroll
+  for (int c = 0; c < CF; ++c) zh[c] = (v[c] - m) * rs;
+}
+
+// input gradient of y = zhat gamma + beta given g_y: rs (g_z - mean g_z - zhat mean(g_z zhat))
+__device__ __forceinline__ void ln_back16(const float (&gy)[CF], const float (&zh)[CF], float rs, const float *g,
+                                          float (&gv)[CF]) {
+  float mg = 0.f, mgz = 0.f;
+#pragma unroll
+  for (int c = 0; c < CF; ++c) {
+    const float gz = gy[c] * g[c];
+    mg += gz;
+    mgz = fmaf(gz, zh[c], mgz);
+  }
+  mg *= 1.f / CF;
+  mgz *= 1.f / CF;
+#pragma unroll
+  for (int c = 0; c < CF; ++c) gv[c] = rs * (gy[c] * g[c] - mg - zh[c] * mgz);
+}
+
+struct GradSmem {
+  float *w;      // [P] kernel order
+  float *hs;     // [(B + 1)][N][CF] residual streams
+  float *act;    // [N][CF]
+  float *aux;    // [N][CF]
+  float *gb;     // [N][CF]
+  float *spin;   // [N]
+  int *nbt;      // [9][N] neighbour site of (tap, site)
+  float *stage;  // [9 CF CF] one kernel gradient in kernel order, before the ordered store
+  float *red;    // [16][CF] partial channel sums
+};
+
+// sum over the N sites of buf[site][c] (or of buf[site][c] * buf2[site][c]) -> dst[c] (global)
+__device__ void channel_sums(const GradSmem &sm, int N, const float *buf, const float *buf2, float *dst) {
+  const int t = threadIdx.x, c = t & (CF - 1), part = t >> 4;
+  const int parts = blockDim.x >> 4;
+  float v = 0.f;
+  if (part < 16)
+    for (int i = part; i < N; i += min(parts, 16)) v += buf2 ? buf[i * CF + c] * buf2[i * CF + c] : buf[i * CF + c];
+  __syncthreads();
+  if (part < 16) sm.red[part * CF + c] = v;
+  __syncthreads();
+  if (t < CF) {
+    float s = 0.f;
+    for (int q = 0; q < min(parts, 16); ++q) s += sm.red[q * CF + t];
+    dst[t] = s;
+  }
+  __syncthreads();
+}
+
+// dK[tap][ci][co] = sum_sites in[nb(tap, site)][ci] g[site][co], stored in the master order
+// ([co][ci][tap]) at dst
+__device__ void kernel_grad(const GradSmem &sm, int N, const float *in, const float *g, float *dst) {
+  for (int e = threadIdx.x; e < 9 * CF * CF; e += blockDim.x) {
+    const int tap = e / (CF * CF), ci = (e / CF) % CF, co = e % CF;
+    const int *nb = sm.nbt + tap * N;
+    float v = 0.f;
+    for (int i = 0; i < N; ++i) v = fmaf(in[nb[i] * CF + ci], g[i * CF + co], v);
+    sm.stage[e] = v;
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < 9 * CF * CF; m += blockDim.x) {  // master order: m = (co CF + ci) 9 + tap
+    const int tap = m % 9, ci = (m / 9) % CF, co = m / (9 * CF);
+    dst[m] = sm.stage[(tap * CF + ci) * CF + co];
+  }
+  __syncthreads();
+}
+
+// g_in[site][ci] = sum_tap sum_co K[tap][ci][co] g[nb(8 - tap, site)][co]
+__device__ __forceinline__ void conv_transpose_row(const float *K, const float *g, const GradSmem &sm, int N, int site,
+                                                   float (&out)[CF]) {
+#pragma unroll
+  for (int c = 0; c < CF; ++c) out[c] = 0.f;
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    const float *gr = g + sm.nbt[(8 - tap) * N + site] * CF;
+    float gv[CF];
+#pragma unroll
+    for (int c = 0; c < CF; ++c) gv[c] = gr[c];
+    const float *k = K + tap * CF * CF;
+#pragma unroll
+    for (int ci = 0; ci < CF; ++ci) {
+      float s = 0.f;
+#pragma unroll
+      for (int co = 0; co < CF; ++co) s = fmaf(k[ci * CF + co], gv[co], s);
+      out[ci] += s;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(CN_THREADS) rescnn_grad_f32_kernel(const CnnArgs a, float *O) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = a.N, B = a.n_blocks, P = n_params(B), Lx = a.Lx, Ly = a.Ly;
+  GradSmem sm;
+  {
+    float *f = reinterpret_cast<float *>(smem_raw);
+    sm.w = f;
+    f += (P + 3) & ~3;
+    sm.hs = f;
+    f += (B + 1) * N * CF;
+    sm.act = f;
+    f += N * CF;
+    sm.aux = f;
+    f += N * CF;
+    sm.gb = f;
+    f += N * CF;
+    sm.spin = f;
+    f += (N + 3) & ~3;
+    sm.stage = f;
+    f += 9 * CF * CF;
+    sm.red = f;
+    f += 16 * CF;
+    sm.nbt = reinterpret_cast<int *>(f);
+  }
+  load_params(sm.w, a.cw, P);
+  for (int e = threadIdx.x; e < 9 * N; e += blockDim.x) {
+    const int tap = e / N, i = e % N;
+    const RowPos rp{0, i % Lx, i / Lx, Lx, Ly};
+    sm.nbt[e] = rp.nb(tap);
+  }
+  const int r = threadIdx.x;
+  const bool live = r < N;
+  const float *w = sm.w;
+  const float *fw = w + 10 * CF + B * BLOCK_FLOATS;
+  for (int64_t x = blockIdx.x; x < a.n_cfg; x += gridDim.x) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sm.spin[i] = ((a.cfg[x * a.W + (i >> 5)] >> (i & 31)) & 1u) ? 1.f : -1.f;
+    __syncthreads();
+    float *Orow = O + x * P;
+    // ---- forward, keeping h(0) .. h(B)
+    float h[CF], v[CF], z[CF];
+#pragma unroll
+    for (int c = 0; c < CF; ++c) h[c] = w[9 * CF + c];
+    if (live) {
+#pragma unroll 1
+      for (int t = 0; t < 9; ++t) {
+        const float sv = sm.spin[sm.nbt[t * N + r]];
+#pragma unroll
+        for (int c = 0; c < CF; ++c) h[c] = fmaf(w[t * CF + c], sv, h[c]);
+      }
+      store_row(sm.hs, r, h);
+    }
+#pragma unroll 1
+    for (int l = 0; l < B; ++l) {
+      const float *bw = w + 10 * CF + l * BLOCK_FLOATS;
+      layer_norm16(h, bw + OFF_G, bw + OFF_BE, v);
+#pragma unroll
+      for (int c = 0; c < CF; ++c) v[c] = gelu_f32(v[c]);
+      if (live) store_row(sm.act, r, v);
+      __syncthreads();
+      if (live) conv_row_f32(bw + OFF_K1, bw + OFF_B1, sm.act, RowPos{0, r % Lx, r / Lx, Lx, Ly}, z);
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < CF; ++c) v[c] = gelu_f32(z[c]);
+      if (live) store_row(sm.act, r, v);
+      __syncthreads();
+      if (live) {
+        conv_row_f32(bw + OFF_K2, bw + OFF_B2, sm.act, RowPos{0, r % Lx, r / Lx, Lx, Ly}, z);
+#pragma unroll
+        for (int c = 0; c < CF; ++c) h[c] += z[c];
+        store_row(sm.hs + (l + 1) * N * CF, r, h);
+      }
+      __syncthreads();
+    }
+    // ---- final LN: d gamma_F = sum zhat, d beta_F = N, g_h = LN'(1)
+    {
+      float zh[CF], rs, ones[CF], gh[CF];
+      ln_stats16(h, zh, rs);
+#pragma unroll
+      for (int c = 0; c < CF; ++c) ones[c] = 1.f;
+      ln_back16(ones, zh, rs, fw, gh);
+      if (live) {
+        store_row(sm.aux, r, zh);
+        store_row(sm.gb, r, gh);
+      }
+      __syncthreads();
+      channel_sums(sm, N, sm.aux, nullptr, Orow + 10 * CF + B * BLOCK_FLOATS);
+      for (int c = threadIdx.x; c < CF; c += blockDim.x) Orow[10 * CF + B * BLOCK_FLOATS + CF + c] = (float)N;
+    }
+    // ---- residual blocks, the last first
+#pragma unroll 1
+    for (int l = B - 1; l >= 0; --l) {
+      const float *bw = w + 10 * CF + l * BLOCK_FLOATS;
+      float *ob = Orow + 10 * CF + l * BLOCK_FLOATS;
+      float hl[CF], zh[CF], rs, y[CF], gnext[CF];
+#pragma unroll
+      for (int c = 0; c < CF; ++c) hl[c] = live ? sm.hs[(l * N + r) * CF + c] : 0.f;
+      ln_stats16(hl, zh, rs);
+#pragma unroll
+      for (int c = 0; c < CF; ++c) {
+        y[c] = fmaf(zh[c], bw[OFF_G + c], bw[OFF_BE + c]);
+        v[c] = gelu_f32(y[c]);
+      }
+      if (live) {
+        store_row(sm.act, r, v);  // a = GELU(LN(h))
+#pragma unroll
+        for (int c = 0; c < CF; ++c) gnext[c] = sm.gb[r * CF + c];
+      }
+      __syncthreads();
+      if (live) conv_row_f32(bw + OFF_K1, bw + OFF_B1, sm.act, RowPos{0, r % Lx, r / Lx, Lx, Ly}, z);  // z1
+#pragma unroll
+      for (int c = 0; c < CF; ++c) v[c] = gelu_f32(z[c]);
+      if (live) store_row(sm.aux, r, v);  // c = GELU(z1)
+      __syncthreads();
+      kernel_grad(sm, N, sm.aux, sm.gb, ob + OFF_K2);     // dK2
+      channel_sums(sm, N, sm.gb, nullptr, ob + OFF_B2);  // db2
+      float gz[CF];
+      if (live) {
+        conv_transpose_row(bw + OFF_K2, sm.gb, sm, N, r, gz);  // g_c
+#pragma unroll
+        for (int c = 0; c < CF; ++c) gz[c] *= gelu_grad_f32(z[c]);  // g_z1
+      }
+      __syncthreads();  // every read of aux (c) and gb done
+      if (live) store_row(sm.aux, r, gz);
+      __syncthreads();
+      kernel_grad(sm, N, sm.act, sm.aux, ob + OFF_K1);    // dK1
+      channel_sums(sm, N, sm.aux, nullptr, ob + OFF_B1);  // db1
+      float gy[CF], gh[CF];
+      if (live) {
+        conv_transpose_row(bw + OFF_K1, sm.aux, sm, N, r, gy);  // g_a
+#pragma unroll
+        for (int c = 0; c < CF; ++c) gy[c] *= gelu_grad_f32(y[c]);  // g_y
+        ln_back16(gy, zh, rs, bw + OFF_G, gh);
+#pragma unroll
+        for (int c = 0; c < CF; ++c) gh[c] += gnext[c];
+      }
+      __syncthreads();  // every read of aux (g_z1) and act done
+      if (live) {
+        store_row(sm.act, r, gy);
+        store_row(sm.aux, r, zh);
+      }
+      __syncthreads();
+      channel_sums(sm, N, sm.act, sm.aux, ob + OFF_G);    // d gamma = sum g_y zhat
+      channel_sums(sm, N, sm.act, nullptr, ob + OFF_BE);  // d beta = sum g_y
+      if (live) store_row(sm.gb, r, gh);
+      __syncthreads();
+    }
+    // ---- embedding: dK0[co][tap] = sum_sites s(nb(tap)) g_h(0)[co], db0 = sum g_h(0)
+    channel_sums(sm, N, sm.gb, nullptr, Orow + 9 * CF);
+    for (int e = threadIdx.x; e < 9 * CF; e += blockDim.x) {
+      const int co = e / 9, tap = e % 9;
+      const int *nb = sm.nbt + tap * N;
+      float acc = 0.f;
+      for (int i = 0; i < N; ++i) acc = fmaf(sm.spin[nb[i]], sm.gb[i * CF + co], acc);
+      Orow[e] = acc;
+    }
+  }
+}
+
+size_t grad_smem_bytes(int P, int N, int B) {
+  return 4 * ((size_t)((P + 3) & ~3) + (size_t)(B + 1) * N * CF + 3 * (size_t)N * CF + ((N + 3) & ~3) + 9 * CF * CF +
+              16 * CF + 9 * (size_t)N);
+}
+
 template <typename K>
 cudaError_t launch_groups(const nqs_ctx *c, K kern, int64_t groups, size_t shm, cudaStream_t s, const CnnArgs &a) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
@@ -441,12 +724,20 @@ cudaError_t rescnn_alloc(nqs_ctx *c) {
   cudaError_t e = cudaMalloc(&c->d_cw, (size_t)c->P * sizeof(float));
   if (e != cudaSuccess) return e;
   if ((e = cudaMalloc(&c->d_clp, (size_t)c->cnn_rows * sizeof(float))) != cudaSuccess) return e;
+  // the force without caller O rows: chunks of grad_chunk rows in d_grad_scratch, partials in d_force_part
+  c->grad_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(4096, (int64_t)(256u << 20) / (c->P * 4)));
+  if ((e = cudaMalloc(&c->d_grad_scratch, (size_t)c->grad_chunk * c->P * sizeof(float))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->d_force_part, (size_t)64 * c->P * sizeof(double))) != cudaSuccess) return e;
   return c->dtype == NQS_F32 ? cudaSuccess : rescnn_lp_alloc(c);
 }
 
 void rescnn_free(nqs_ctx *c) {
   if (c->d_cw) cudaFree(c->d_cw);
   if (c->d_clp) cudaFree(c->d_clp);
+  if (c->d_grad_scratch) cudaFree(c->d_grad_scratch);
+  if (c->d_force_part) cudaFree(c->d_force_part);
+  c->d_grad_scratch = nullptr;
+  c->d_force_part = nullptr;
   rescnn_lp_free(c);
   c->d_cw = nullptr;
   c->d_clp = nullptr;
@@ -516,6 +807,32 @@ cudaError_t rescnn_sweep(const nqs_ctx *c, uint32_t *state, int64_t C, int n_swe
   a.delta = delta;
   const size_t shm = cnn::smem_bytes_f32((int)c->P, a.rows, a.G, c->N);
   return cnn::launch_groups(c, cnn::rescnn_sweep_f32_kernel, (C + a.G - 1) / a.G, shm, s, a);
+}
+
+bool rescnn_grad_supported(const nqs_ctx *c) {
+  return cnn::grad_smem_bytes((int)c->P, c->N, c->n_blocks) <= (size_t)c->smem_optin;
+}
+
+cudaError_t rescnn_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
+                               const double *stats, double *force, cudaStream_t s, bool share) {
+  cnn::CnnArgs a = cnn::base_args(c);
+  a.rows = ((c->N + 31) / 32) * 32;  // a CTA per configuration, a thread per site
+  const size_t shm = cnn::grad_smem_bytes((int)c->P, c->N, c->n_blocks);
+  cudaError_t e = cudaFuncSetAttribute(cnn::rescnn_grad_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (e != cudaSuccess) return e;
+  const int64_t chunk = O ? n : c->grad_chunk;
+  for (int64_t x0 = 0; x0 < n; x0 += chunk) {
+    const int64_t rows = std::min<int64_t>(chunk, n - x0);
+    a.cfg = cfg + x0 * c->W;
+    a.n_cfg = rows;
+    float *Ob = O ? O + x0 * c->P : c->d_grad_scratch;
+    cnn::rescnn_grad_f32_kernel<<<(unsigned)std::min<int64_t>(rows, (int64_t)c->num_sms * 8), a.rows, shm, s>>>(a, Ob);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (force && !O && (e = force_rows(c, Ob, rows, eloc + x0, stats, n, share, x0 > 0, force, s)) != cudaSuccess)
+      return e;
+  }
+  if (force && O) return force_rows(c, O, n, eloc, stats, n, share, 0, force, s);
+  return cudaSuccess;
 }
 
 }  // namespace nqs

@@ -137,10 +137,54 @@ def test_rescnn_rejections():
         p.Context("tfim", 4, 4, h=1.0, model="rescnn", n_hidden=8, n_blocks=2)      # filters
     with pytest.raises(p.NQSError):
         p.Context("heisenberg", 4, 4, J1=1.0, model="rescnn", n_hidden=16, n_blocks=2)
-    ctx, _, _ = make(4, 4, 1, 3)
-    cfg = to_words_tensor(pack_np(rand_configs(4, 16, 3)))
+    # O rows need one configuration's residual streams in shared memory: 512 sites x 9 streams do not fit
+    big = p.Context("tfim", 16, 32, h=1.0, model="rescnn", n_hidden=16, n_blocks=8)
+    big.set_params(torch.from_numpy(rescnn_params(16, 8, 3)).cuda())
+    cfg = to_words_tensor(pack_np(rand_configs(2, 512, 3)))
     with pytest.raises(p.NQSError):
-        ctx.logpsi_grad(cfg, torch.zeros((4, ctx.P), dtype=torch.float32, device="cuda"))
+        big.logpsi_grad(cfg, torch.zeros((2, big.P), dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("Lx,Ly,B,n", [(4, 4, 2, 19), (10, 10, 4, 7), (5, 3, 0, 11), (6, 5, 1, 9), (16, 16, 4, 3)])
+def test_grad_fp32_matches_oracle(Lx, Ly, B, n):
+    """O_k = d log psi / d theta_k (nqs_logpsi_grad of a ResCNN context, the FP32 reverse pass)
+    against the oracle's layer-by-layer gradient (pinned by central differences), every
+    parameter group (embedding, the blocks' LN, both kernels and biases, the final LN)
+    within 1e-4 of the row's largest entry."""
+    ctx, model, _ = make(Lx, Ly, B, 41 + Lx)
+    s = rand_configs(n, Lx * Ly, 5)
+    O = torch.zeros((n, ctx.P), dtype=torch.float32, device="cuda")
+    ctx.logpsi_grad(to_words_tensor(pack_np(s)), O)
+    ctx.check_status()
+    got = O.cpu().numpy().astype(np.float64)
+    ref = model.grad(s)
+    scale = np.abs(ref).max(axis=1, keepdims=True)
+    err = np.abs(got - ref)
+    assert np.all(err <= 1e-4 * scale + 1e-5 * np.abs(ref)), (err / scale).max()
+
+
+@pytest.mark.parametrize("n", [64, 5000])
+def test_force_fp32_matches_oracle(n):
+    """F_k = mean(O_k (eps - E)) of a ResCNN context, with caller O rows and without (the
+    library's chunked scratch: 5000 rows are two chunks), against the oracle's force of its
+    own O rows."""
+    from oracle.estimators import force as oracle_force
+    ctx, model, _ = make(4, 4, 1, 61)
+    s = rand_configs(n, 16, 6)
+    cfg = to_words_tensor(pack_np(s))
+    eps = np.random.default_rng(7).normal(-3.0, 1.0, n).astype(np.float32)
+    e = torch.from_numpy(eps).cuda()
+    st = torch.empty(5, dtype=torch.float64, device="cuda")
+    ctx.stats(e, n, st)
+    F1 = torch.zeros(ctx.P, dtype=torch.float64, device="cuda")
+    F2 = torch.zeros_like(F1)
+    O = torch.zeros((n, ctx.P), dtype=torch.float32, device="cuda")
+    ctx.logpsi_grad(cfg, O, e, st, F1)
+    ctx.logpsi_grad(cfg, None, e, st, F2)
+    ref = oracle_force(model.grad(s), eps.astype(np.float64))
+    tol = 2e-4 * np.abs(ref).max()
+    assert np.abs(F1.cpu().numpy() - ref).max() <= tol
+    assert np.abs(F2.cpu().numpy() - ref).max() <= tol
 
 
 # ---- 16-bit copies on the tensor cores ---------------------------------------------------------
