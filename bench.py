@@ -563,10 +563,15 @@ class RescnnStep:
         self.nacc, self.eloc = z(self.C, dt=torch.int64), z(self.S, dt=torch.float32)
         self.stats = z(5, dt=torch.float64)
         self.out_h = torch.zeros(5, dtype=torch.float64).pin_memory()
-        self.ph = _Phased(torch, ["set_params+init", "sweep", "local_energy", "stats"])
+        self.force = z(self.ctx.P, dt=torch.float64)
+        self.n_force = self.C          # the force over the last sweep's samples (one per chain)
+        self.ph = _Phased(torch, ["set_params+init", "sweep", "local_energy", "stats", "force"])
         chunks = -(-self.S * (self.N + 1) // (1 << 20))      # local-energy chunks of 2^20 configurations
-        # prepare (+ the 16-bit copy's prepare), init, sweep, per chunk evaluation + combine, stats (2)
-        self.launches = (1 if dtype == "f32" else 2) + 1 + 1 + 2 * chunks + 2
+        # rows of O the library evaluates per launch when the caller gives none (its scratch)
+        fchunks = -(-self.n_force // max(1, min(4096, (256 << 20) // (self.ctx.P * 4))))
+        # prepare (+ the 16-bit copy's prepare), init, sweep, per chunk evaluation + combine, stats (2),
+        # per force chunk the O rows and the two force kernels
+        self.launches = (1 if dtype == "f32" else 2) + 1 + 1 + 2 * chunks + 2 + 3 * fchunks
         self.h2d, self.d2h = self.ctx.P * 8, 5 * 8
 
     def run(self, seed, host_io=False):
@@ -583,6 +588,9 @@ class RescnnStep:
         ph.mark(3)
         c.stats(self.eloc, self.C, self.stats, self.nacc, self.T * self.N)
         ph.mark(4)
+        last = (self.T - self.B - 1) * self.C   # the last sweep's samples and their local energies
+        c.logpsi_grad(self.samples[last:], None, self.eloc[last:], self.stats, self.force)
+        ph.mark(5)
         if host_io:
             self.out_h.copy_(self.stats, non_blocking=True)
 
@@ -607,6 +615,9 @@ class RescnnStep:
             "local_energy": {"value": self.S / (ms["local_energy"] / 1e3), "unit": "samples/s"},
             "sweep": {"value": self.units() / (ms["sweep"] / 1e3), "unit": "proposals/s",
                       "acceptance": accepts / self.units()},
+            "force": {"rows": self.n_force, "rows_per_s": self.n_force / (ms["force"] / 1e3),
+                      "note": "O rows (FP32 reverse pass) and the force of the last sweep's samples; the "
+                              "statistics' E is that of all samples"},
             "energy": float(self.stats[0].item()),
             "roofline": {"bound": "tensor" if tc else "alu",
                          "kernel": "rescnn_tc_sweep_kernel" if tc else "rescnn_sweep_f32_kernel",

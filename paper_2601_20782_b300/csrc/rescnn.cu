@@ -463,9 +463,16 @@ __device__ void kernel_grad(const GradSmem &sm, int N, const float *in, const fl
   for (int e = threadIdx.x; e < 9 * CF * CF; e += blockDim.x) {
     const int tap = e / (CF * CF), ci = (e / CF) % CF, co = e % CF;
     const int *nb = sm.nbt + tap * N;
-    float v = 0.f;
-    for (int i = 0; i < N; ++i) v = fmaf(in[nb[i] * CF + ci], g[i * CF + co], v);
-    sm.stage[e] = v;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;  // four chains of FMAs over the sites
+    int i = 0;
+    for (; i + 3 < N; i += 4) {
+      v0 = fmaf(in[nb[i] * CF + ci], g[i * CF + co], v0);
+      v1 = fmaf(in[nb[i + 1] * CF + ci], g[(i + 1) * CF + co], v1);
+      v2 = fmaf(in[nb[i + 2] * CF + ci], g[(i + 2) * CF + co], v2);
+      v3 = fmaf(in[nb[i + 3] * CF + ci], g[(i + 3) * CF + co], v3);
+    }
+    for (; i < N; ++i) v0 = fmaf(in[nb[i] * CF + ci], g[i * CF + co], v0);
+    sm.stage[e] = (v0 + v1) + (v2 + v3);
   }
   __syncthreads();
   for (int m = threadIdx.x; m < 9 * CF * CF; m += blockDim.x) {  // master order: m = (co CF + ci) 9 + tap
@@ -816,7 +823,9 @@ bool rescnn_grad_supported(const nqs_ctx *c) {
 cudaError_t rescnn_logpsi_grad(const nqs_ctx *c, const uint32_t *cfg, int64_t n, float *O, const float *eloc,
                                const double *stats, double *force, cudaStream_t s, bool share) {
   cnn::CnnArgs a = cnn::base_args(c);
-  a.rows = ((c->N + 31) / 32) * 32;  // a CTA per configuration, a thread per site
+  // a CTA per configuration: a thread per site for the site-wise passes, and every thread of
+  // the CTA for the parameter gradients' sums over sites
+  a.rows = cnn::CN_THREADS;
   const size_t shm = cnn::grad_smem_bytes((int)c->P, c->N, c->n_blocks);
   cudaError_t e = cudaFuncSetAttribute(cnn::rescnn_grad_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e != cudaSuccess) return e;
