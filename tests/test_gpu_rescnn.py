@@ -3,7 +3,8 @@
 FP32 copy (CUDA cores): log psi within 1e-5 relative; local energies within the bound the
 log psi tolerance implies for the ratios psi(x') / psi(x); sweeps replayed in the oracle in
 lockstep (bit-exact proposals, samples and accept counts; decisions may differ only within
-tau of the threshold); the 4 x 3 sampled energy and histogram against exact enumeration.
+tau of the threshold); the 4 x 3 sampled energy and histogram against exact enumeration;
+O rows (the FP32 reverse pass) against the oracle's gradient, and the force.
 """
 import numpy as np
 import pytest
