@@ -1,6 +1,7 @@
 """LogPsi, the torch.autograd.Function over the library's forward (nqs_logpsi) and hand-written
 backward (the force kernel with eloc = upstream gradient, E = 0): the parameter gradient of
-sum_x g_x log psi(x) against the oracle's O rows, for the RBM (FP32 copy) and the dense ansatz."""
+sum_x g_x log psi(x) against the oracle's O rows, for the RBM (FP32 copy), the dense ansatz and
+the ResCNN."""
 import numpy as np
 import pytest
 
@@ -43,3 +44,11 @@ def test_dense_logpsi_autograd_matches_oracle():
     params = dense_params(N, widths, 5, bias_sigma=0.1)
     ctx = nqs().Context("heisenberg", 4, 4, J1=1.0, model="dense", widths=widths, dtype="bf16")
     _check(ctx, Dense(N, widths, params), params, N, n=200)
+
+
+def test_rescnn_logpsi_autograd_matches_oracle():
+    from oracle.rescnn import ResCNN
+    from workloads import rescnn_params
+    params = rescnn_params(16, 2, 9)
+    ctx = nqs().Context("tfim", 4, 4, J1=1.0, h=1.0, model="rescnn", n_hidden=16, n_blocks=2, dtype="f32")
+    _check(ctx, ResCNN(4, 4, 16, 2, params), params, 16, n=150)
