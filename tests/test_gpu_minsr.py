@@ -102,3 +102,27 @@ def test_minsr_rejects_bad_arguments():
     e = torch.zeros(4, dtype=torch.float32, device="cuda")
     with pytest.raises(p.NQSError):
         ctx.minsr(O, e, st, 0.0, d)                                      # lambda must be positive
+
+
+def test_minsr_on_sampled_rescnn_rows():
+    """The minSR step of a ResCNN VMC iteration (the ansatz the paper trains with SR): O rows of
+    the ResCNN's reverse pass on samples of its F16 sampler, local energies, then nqs_minsr,
+    against the oracle's minSR of the same rows."""
+    from workloads import rescnn_params
+    p = nqs()
+    C = 384
+    ctx = p.Context("tfim", 6, 5, J1=1.0, h=3.0, model="rescnn", n_hidden=16, n_blocks=2, dtype="f16")
+    ctx.set_params(torch.from_numpy(rescnn_params(16, 2, 23)).cuda())
+    st = torch.zeros((C, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.init_chains(st, 5)
+    S = torch.zeros((C, ctx.W), dtype=torch.int32, device="cuda")
+    ctx.sweep(st, 6, 5, 6, 0, S)
+    e = torch.empty(C, dtype=torch.float32, device="cuda")
+    ctx.local_energy(S, e)
+    O = torch.empty((C, ctx.P), dtype=torch.float32, device="cuda")
+    ctx.logpsi_grad(S, O)
+    d, T = _run(ctx, O.cpu().numpy(), e.cpu().numpy(), 1e-3)
+    O64, e64 = O.cpu().numpy().astype(np.float64), e.cpu().numpy().astype(np.float64)
+    assert np.abs(T - gram(O64)).max() <= GRAM_TOL * np.abs(gram(O64)).max()
+    dref, _, _ = minsr_update(O64, e64, 1e-3)
+    assert np.abs(d - dref).max() <= 1e-4 * np.abs(dref).max(), (np.abs(d - dref).max(), np.abs(dref).max())
